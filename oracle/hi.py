@@ -1,0 +1,146 @@
+"""Oracle — test infrastructure only.  Hamiltonian interpolation (HI) for
+two-form sites, as plain FP64 numpy on top of the Ewald oracle.
+
+Definitions followed (arxiv 2410.01754):
+
+* Multilinear HI Hamiltonian, Eq. "rek_ham_lambda" generalised to M sites:
+  H = sum over protonation states X of prod_s w_s(X_s) H_X, with
+  w_s(A) = 1 - lambda_s, w_s(B) = lambda_s, and H_X the periodic Coulomb energy
+  of the charges of state X (Eq. "nbody_periodic").
+* Scaled charges, Eq. under "lambda_tilde": q~_i = qA_i + lambda_s (qB_i - qA_i)
+  (for two forms lambda~ = (1 - lambda, lambda)); environment atoms keep q.
+* HI minus QI, Eqs. "DeltaFQIHI" and "Udiff": with
+  k_s = f sum_{i,j in s} D_i D_j A(x_i - x_j), D = qB - qA, the HI energy is
+  E = E(q~) + sum_s 1/2 lambda_s (1 - lambda_s) k_s and
+  dE/dlambda_s = sum_{i in s} D_i phi~_i + (1/2 - lambda_s) k_s.
+  The periodic kernel A replaces 1/r (images included; A_ii = xi), which is the
+  reading this package takes for the paper's periodic correction terms.
+* Forces: F_i = -q~_i grad phi~_i - lambda_s (1 - lambda_s) f
+  sum_{j in s, j != i} D_i D_j grad A(x_i - x_j).
+
+``hi_bruteforce`` evaluates the first definition literally (2^S Ewald energies)
+and is the check on the closed form.
+"""
+from __future__ import annotations
+
+import itertools
+
+import numpy as np
+
+from . import F_COULOMB, ewald, pair_A
+
+
+def scaled_charges(qA, qB, site_of, lam):
+    qA = np.asarray(qA, dtype=np.float64)
+    qB = np.asarray(qB, dtype=np.float64)
+    site_of = np.asarray(site_of)
+    lam_atom = np.where(site_of >= 0, np.asarray(lam)[np.maximum(site_of, 0)], 0.0)
+    return qA + lam_atom * (qB - qA)
+
+
+def site_lists(site_of, n_sites):
+    site_of = np.asarray(site_of)
+    return [np.where(site_of == s)[0] for s in range(n_sites)]
+
+
+def site_kernel(xs, L, rc=None):
+    """A_ij and grad_i A(x_i - x_j) for the atoms of one site (f = 1)."""
+    n = xs.shape[0]
+    A = np.zeros((n, n))
+    G = np.zeros((n, n, 3))
+    for i in range(n):
+        for j in range(n):
+            v, g = pair_A(xs[i] - xs[j], L, rc)
+            A[i, j] = v
+            G[i, j] = g
+    return A, G
+
+
+def hi_eval(sys, rc=None, targets=None, f=F_COULOMB):
+    """HI energy, dE/dlambda and forces for a two-form system.
+
+    ``sys`` holds x, qA, qB, site_of, lam, L.  With ``targets`` None the full
+    energy and all forces are returned; otherwise forces only at ``targets``
+    (site atoms are always evaluated for dE/dlambda) and energy None."""
+    x, qA, qB = sys["x"], sys["qA"], sys["qB"]
+    site_of, lam, L = np.asarray(sys["site_of"]), np.asarray(sys["lam"]), sys["L"]
+    S = lam.shape[0]
+    qt = scaled_charges(qA, qB, site_of, lam)
+    sites = site_lists(site_of, S)
+    site_atoms = np.concatenate(sites) if S else np.zeros(0, dtype=np.int64)
+    if targets is None:
+        phi, grad, e = ewald(x, qt, L, rc)
+        idx_all = np.arange(qt.shape[0])
+        phi_at = {int(i): phi[i] for i in site_atoms}
+        tgt = idx_all
+    else:
+        tgt = np.unique(np.concatenate([np.asarray(targets, dtype=np.int64), site_atoms]))
+        phi, grad, e = ewald(x, qt, L, rc, targets=tgt)
+        phi_at = {int(i): phi[k] for k, i in enumerate(tgt)}
+    phi = phi * f
+    grad = grad * f
+    F = -qt[tgt, None] * grad
+    pos = {int(i): k for k, i in enumerate(tgt)}
+    dq = np.asarray(qB) - np.asarray(qA)
+    k_s = np.zeros(S)
+    g_s = np.zeros(S)
+    for s, at in enumerate(sites):
+        A, G = site_kernel(x[at], L)
+        D = dq[at]
+        k_s[s] = f * D @ A @ D
+        g_s[s] = sum(D[a] * phi_at[int(i)] for a, i in enumerate(at)) * f
+        w = lam[s] * (1.0 - lam[s])
+        for a, i in enumerate(at):
+            corr = np.zeros(3)
+            for b in range(len(at)):
+                if b != a:
+                    corr += D[a] * D[b] * G[a, b]
+            F[pos[int(i)]] -= w * f * corr
+    dEdl = g_s + (0.5 - lam) * k_s
+    out = dict(F=F, targets=tgt, dEdl=dEdl, k=k_s, g=g_s, qt=qt)
+    if targets is None:
+        Et = e * f
+        out["E_qi"] = Et
+        out["E"] = Et + float(np.sum(0.5 * lam * (1.0 - lam) * k_s))
+        out["phi"] = phi
+    else:
+        out["E"] = None
+    return out
+
+
+def energy(x, q, L, rc=None, f=F_COULOMB):
+    """Periodic Coulomb energy of one charge vector."""
+    return ewald(x, q, L, rc)[2] * f
+
+
+def hi_bruteforce(sys, rc=None, f=F_COULOMB):
+    """HI energy and dE/dlambda by enumerating all 2^S protonation states
+    (Eq. "rek_ham_lambda"); dE/dlambda_s = E(lambda_s = 1) - E(lambda_s = 0)
+    at fixed other lambdas (Eq. "ref_two_forms" for one site)."""
+    x, qA, qB = sys["x"], np.asarray(sys["qA"]), np.asarray(sys["qB"])
+    site_of, lam, L = np.asarray(sys["site_of"]), np.asarray(sys["lam"]), sys["L"]
+    S = lam.shape[0]
+    if S > 6:
+        raise ValueError("brute force limited to S <= 6")
+    EX = {}
+    for X in itertools.product((0, 1), repeat=S):
+        sel = np.array([X[s] if s >= 0 else 0 for s in site_of])
+        q = np.where((site_of >= 0) & (sel == 1), qB, qA)
+        EX[X] = energy(x, q, L, rc, f)
+
+    def interp(lv):
+        tot = 0.0
+        for X, e in EX.items():
+            w = 1.0
+            for s in range(S):
+                w *= lv[s] if X[s] else (1.0 - lv[s])
+            tot += w * e
+        return tot
+
+    E = interp(lam)
+    dEdl = np.zeros(S)
+    for s in range(S):
+        l1 = lam.copy(); l1[s] = 1.0
+        l0 = lam.copy(); l0[s] = 0.0
+        dEdl[s] = interp(l1) - interp(l0)
+    return dict(E=E, dEdl=dEdl, states=EX)

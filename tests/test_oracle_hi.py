@@ -1,0 +1,124 @@
+"""Pins for the HI oracle: 2^S brute force vs closed form, multilinearity,
+finite differences in lambda and x, the HI-QI difference (Eqs. DeltaFQIHI, Udiff)."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import hi
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def paper_random_system(seed=1, clustered=True):
+    """1000 environment + 10 site particles, charges U(-1,1) (Sec. 'Random Systems').
+    The site's second form draws fresh U(-1,1) charges."""
+    g = json.load(open(os.path.join(GOLD, "paper_random_system.json")))
+    rng = np.random.default_rng(seed)
+    L = 3.0
+    ne, ns = g["n_environment"], g["n_site"]
+    x = rng.uniform(0, L, (ne + ns, 3))
+    if clustered:
+        c = rng.uniform(0, L, 3)
+        x[ne:] = np.mod(c + rng.uniform(-0.25, 0.25, (ns, 3)), L)
+    lo, hi_ = g["charge_range"]
+    qA = rng.uniform(lo, hi_, ne + ns)
+    qB = qA.copy()
+    qB[ne:] = rng.uniform(lo, hi_, ns)
+    site_of = np.full(ne + ns, -1, dtype=np.int32)
+    site_of[ne:] = 0
+    return dict(x=x, qA=qA, qB=qB, site_of=site_of, lam=np.array([g["lambda_two_forms"]]), L=L)
+
+
+def small_multisite(seed=3, n=80, S=3, L=1.8):
+    rng = np.random.default_rng(seed)
+    x = rng.uniform(0, L, (n, 3))
+    qA = rng.uniform(-1, 1, n)
+    qB = qA.copy()
+    site_of = np.full(n, -1, dtype=np.int32)
+    for s in range(S):
+        at = np.arange(s * 4, s * 4 + 4)
+        site_of[at] = s
+        qB[at] = qA[at] + rng.uniform(-0.5, 0.5, 4)
+    return dict(x=x, qA=qA, qB=qB, site_of=site_of, lam=rng.uniform(0, 1, S), L=L)
+
+
+def test_two_form_reference_lambda_force():
+    """Eq. ref_two_forms: dH/dlambda = H_1 - H_0 for the paper's random system."""
+    s = paper_random_system()
+    out = hi.hi_eval(s)
+    e0 = hi.energy(s["x"], s["qA"], s["L"])
+    e1 = hi.energy(s["x"], s["qB"], s["L"])
+    assert out["dEdl"][0] == pytest.approx(e1 - e0, rel=1e-10)
+    lam = s["lam"][0]
+    assert out["E"] == pytest.approx((1 - lam) * e0 + lam * e1, rel=1e-11)
+
+
+def test_closed_form_equals_bruteforce():
+    s = small_multisite()
+    out = hi.hi_eval(s)
+    bf = hi.hi_bruteforce(s)
+    assert out["E"] == pytest.approx(bf["E"], rel=1e-11)
+    np.testing.assert_allclose(out["dEdl"], bf["dEdl"], rtol=1e-9, atol=1e-9)
+
+
+def test_hi_minus_qi_is_harmonic_in_lambda():
+    """Eq. Udiff: E_QI - E_HI = k/2 (lambda^2 - lambda), with k from the brute force
+    states: k = E(A) + E(B) - 2 E((A+B)/2) ... evaluated through the interpolation."""
+    s = small_multisite(S=2)
+    out = hi.hi_eval(s)
+    bf = hi.hi_bruteforce(s)
+    lam = s["lam"]
+    diff = out["E_qi"] - bf["E"]
+    assert diff == pytest.approx(float(np.sum(0.5 * out["k"] * (lam ** 2 - lam))), rel=1e-9)
+    # Eq. DeltaFQIHI: dE_QI/dlambda = dE_HI/dlambda + (lambda - 1/2) k
+    np.testing.assert_allclose(out["g"], out["dEdl"] + (lam - 0.5) * out["k"], rtol=1e-12)
+
+
+def test_multilinear_in_each_lambda():
+    s = small_multisite()
+    base = hi.hi_eval(s)
+    for sidx in range(3):
+        s2 = dict(s); s2["lam"] = s["lam"].copy(); s2["lam"][sidx] = 0.9 - 0.7 * s["lam"][sidx]
+        o2 = hi.hi_eval(s2)
+        assert o2["dEdl"][sidx] == pytest.approx(base["dEdl"][sidx], rel=1e-10)
+    # HI equals QI when every lambda sits at an end point
+    s4 = dict(s); s4["lam"] = np.array([1.0, 0.0, 1.0])
+    o4 = hi.hi_eval(s4)
+    assert o4["E"] == pytest.approx(o4["E_qi"], rel=1e-14)
+    assert np.all(o4["k"] != 0.0)
+
+
+def test_lambda_central_difference_exact():
+    s = small_multisite()
+    base = hi.hi_eval(s)
+    h = 0.05
+    for sidx in range(3):
+        sp = dict(s); sp["lam"] = s["lam"].copy(); sp["lam"][sidx] += h
+        sm = dict(s); sm["lam"] = s["lam"].copy(); sm["lam"][sidx] -= h
+        d = (hi.hi_eval(sp)["E"] - hi.hi_eval(sm)["E"]) / (2 * h)
+        assert d == pytest.approx(base["dEdl"][sidx], rel=1e-9)
+
+
+def test_forces_central_difference():
+    s = small_multisite(n=40, S=2)
+    base = hi.hi_eval(s)
+    h = 1e-5
+    for k in (0, 1, 5, 30):  # site atoms and environment atoms
+        for ax in range(3):
+            xp = s["x"].copy(); xp[k, ax] += h
+            xm = s["x"].copy(); xm[k, ax] -= h
+            ep = hi.hi_eval(dict(s, x=xp))["E"]
+            em = hi.hi_eval(dict(s, x=xm))["E"]
+            assert -(ep - em) / (2 * h) == pytest.approx(base["F"][k, ax], rel=2e-6, abs=1e-5)
+
+
+def test_subset_targets_match_full():
+    s = small_multisite()
+    full = hi.hi_eval(s)
+    part = hi.hi_eval(s, targets=np.array([20, 50, 70]))
+    np.testing.assert_allclose(part["dEdl"], full["dEdl"], rtol=1e-12)
+    for k, i in enumerate(part["targets"]):
+        np.testing.assert_allclose(part["F"][k], full["F"][i], atol=1e-10)
