@@ -1,0 +1,144 @@
+/*
+ * mahi.h — C ABI of the GB300 (sm_103a) implementation of Multipole-Accelerated
+ * Hamiltonian Interpolation (MAHI), arxiv 2410.01754.
+ *
+ * One call to mahi_eval performs one periodic Fast Multipole Method evaluation of
+ * the lambda-charge-scaled system (Sec. "Fast Multipole Method", Fig. "fmm_scheme":
+ * P2M, M2M, M2L, L2L, L2P and the P2P near field; periodic part split as in Eq.
+ * "approx_nbody_periodic": first image shell in the tree, lattice operator for the
+ * far images, dipole/background term in closed form) and then the per-site
+ * outputs of Hamiltonian interpolation for two-form sites (Sec. "Multipole-
+ * Accelerated Hamiltonian Interpolation", Eqs. "correction_scheme",
+ * "DeltaFQIHI", "Udiff"):
+ *
+ *   E          = E(q~) + sum_s 1/2 lambda_s (1 - lambda_s) k_s
+ *   dE/dlam_s  = sum_{i in s} (qB_i - qA_i) phi~_i + (1/2 - lambda_s) k_s
+ *   F_i        = -q~_i grad phi~_i - lambda_s(1-lambda_s) f sum_{j in s, j!=i} D_i D_j grad A(r_ij)
+ *
+ * with q~_i = qA_i + lambda_{s(i)} (qB_i - qA_i), D = qB - qA, phi~ the periodic
+ * potential of q~ (tin-foil boundary, uniform neutralising background, self-image
+ * term included) and k_s = f sum_{i,j in s} D_i D_j A(r_ij) the intra-site
+ * (form-form) term.
+ *
+ * Units: nm, elementary charges, kJ/mol; f = 138.935457644382 kJ mol^-1 nm e^-2.
+ * Conventions common to all calls:
+ *   - Return value 0 = success, negative = error (see MAHI_ERR_*); no exception
+ *     crosses this boundary.  mahi_error_string() gives a static message.
+ *   - The handle is not thread-safe; one handle per host thread.
+ *   - "device" pointers are CUDA device (or managed) memory of the current device.
+ */
+#ifndef MAHI_H
+#define MAHI_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mahi_ctx *mahi_t;
+
+/* Arithmetic of the evaluation.
+ *   MAHI_FP64  every stage in FP64 (the reference GPU path).
+ *   MAHI_MIXED FP32 particle stages (P2M, L2P, P2P), M2L on the tensor cores as
+ *              three TF32 products with FP32 accumulation, FP32 M2M/L2L; FP64
+ *              lattice operator, dipole/background term, energy reduction and
+ *              per-site corrections.
+ *   MAHI_MIXED_SIMT  as MAHI_MIXED but M2L on FP32 CUDA cores (no tensor cores). */
+enum { MAHI_FP64 = 0, MAHI_MIXED = 1, MAHI_MIXED_SIMT = 2 };
+
+enum {
+  MAHI_OK = 0,
+  MAHI_ERR_INVALID_ARG = -1, /* bad size, order, depth, box, null pointer      */
+  MAHI_ERR_BAD_SITE_MAP = -2,/* site index >= S, empty site, qA != qB off-site  */
+  MAHI_ERR_NON_CUBIC = -3,   /* reserved: only cubic boxes (paper, Sec. FMM)    */
+  MAHI_ERR_CUDA = -4,        /* a CUDA call failed; see mahi_last_cuda_error    */
+  MAHI_ERR_TIMEOUT = -5,     /* a bounded device wait gave up                   */
+  MAHI_ERR_NO_DEVICE = -6,   /* no usable sm_100-class device                   */
+  MAHI_ERR_STATE = -7        /* call order: charges not set                     */
+};
+
+/* Create a solver for n_atoms atoms in a cubic periodic box of edge box_L_nm,
+ * n_sites two-form titratable sites, multipole order order_p (expansions have
+ * (p+1)^2 real coefficients) and octree depth (8^depth leaves).
+ * Limits: 1 <= order_p <= 24 (MAHI_FP64) or <= 16 (mixed), 0 <= depth <= 6,
+ * n_atoms >= 1, n_sites >= 0, box_L_nm > 0.
+ * cuda_stream: cudaStream_t on which all later work is enqueued (NULL = legacy
+ * default stream).  Allocates all device workspaces (the library owns them) and
+ * builds the translation operators and lattice coefficients on the host.
+ * Returns MAHI_ERR_NO_DEVICE if no CUDA device is present. */
+int mahi_create(double box_L_nm, int64_t n_atoms, int32_t n_sites, int32_t order_p, int32_t depth,
+                int32_t precision, void *cuda_stream, mahi_t *out);
+
+/* Release every resource of the handle.  Accepts NULL. */
+int mahi_destroy(mahi_t h);
+
+/* Change the stream later calls enqueue on. */
+int mahi_set_stream(mahi_t h, void *cuda_stream);
+
+/* Charges of the two forms and the site map (Sec. "Hamiltonian Interpolation
+ * Formulation": sites, forms).  HOST arrays of length n_atoms: qA, qB (e) and
+ * site_of_atom (-1 = environment, else 0..n_sites-1).  Environment atoms must
+ * have qA == qB and every site must own at least one atom, else
+ * MAHI_ERR_BAD_SITE_MAP.  The library copies the data (synchronously). */
+int mahi_set_charges(mahi_t h, const double *qA, const double *qB, const int32_t *site_of_atom);
+
+/* One MAHI evaluation, enqueued on the handle's stream; returns after enqueueing.
+ *   x          device, n_atoms x 3 row-major positions in nm (float64 if
+ *              x_is_fp64 else float32); any real values (wrapped into the box).
+ *   lambda     device, n_sites float64 in [0, 1].
+ *   energy     device, 1 float64 (kJ/mol), HI energy.
+ *   forces     device, n_atoms x 3 (same dtype as x), HI forces (kJ/mol/nm).
+ *   dEdlambda  device, n_sites float64 (kJ/mol).
+ * Outputs may be NULL to skip writing them (the work is still done). */
+int mahi_eval(mahi_t h, const void *x, int32_t x_is_fp64, const double *lambda, double *energy,
+              void *forces, double *dEdlambda);
+
+/* The same evaluation from HOST buffers: copies x and lambda host->device,
+ * evaluates, copies energy, forces and dE/dlambda device->host and synchronises
+ * the stream before returning.  Pinned host memory gives the fastest copies. */
+int mahi_eval_host(mahi_t h, const void *x_host, int32_t x_is_fp64, const double *lambda_host,
+                   double *energy_host, void *forces_host, double *dEdlambda_host);
+
+/* Charge-scaled potential phi~ (kJ/mol/e, float64, original atom order) of the
+ * last evaluation into a device buffer of n_atoms doubles (enqueued). */
+int mahi_get_potential(mahi_t h, double *phi_device);
+
+/* Stage timing (CUDA events on the handle's stream).  mahi_set_timing(h, 1)
+ * turns recording on; mahi_stage_times fills up to n floats (ms) of the last
+ * evaluation in the order of mahi_stage_name(i) and returns the stage count.
+ * It synchronises the stream. */
+int mahi_set_timing(mahi_t h, int32_t on);
+int mahi_stage_times(mahi_t h, float *ms, int32_t n);
+const char *mahi_stage_name(int32_t i);
+
+/* Number of kernels the last evaluation launched. */
+int mahi_launch_count(mahi_t h);
+
+/* ---- host-only helpers (no device needed) ---------------------------------
+ * Far-image lattice functions of the periodic kernel A (Eq. "approx_nbody_periodic",
+ * lattice part L(omega)):
+ *   H_K(r) = A(r) - sum_{|n|_inf<=K} 1/|r + nL| - (2 pi/3V)|r|^2,  harmonic for |r| < (K+1)L.
+ * shell K = 1 is the paper's split (first image shell direct); K = 3 is the
+ * function this library's root lattice operator uses (images 2..3 by M2L).
+ * mahi_lattice_coeffs writes the solid-harmonic Taylor coefficients of H_K for
+ * the unit box up to degree 2*order_p (real layout, (2*order_p+1)^2 doubles,
+ * index l*l for m = 0, l*l + 2m - 1 / l*l + 2m for Re/Im of m > 0;
+ * H(r) = sum_lm c_lm conj(R_lm(r)) with the scaled regular solid harmonics
+ * R_00 = 1, R_mm = -(x+iy)/(2m) R_{m-1,m-1}, R_lm = ((2l-1) z R_{l-1,m} - r^2 R_{l-2,m})/((l+m)(l-m))).
+ * mahi_lattice_eval evaluates H_K at n points r (n x 3, host, nm) for box edge L
+ * with that degree into H (n, host, 1/nm).  K must be 1 or 3.  Deterministic. */
+int mahi_lattice_coeffs(int32_t order_p, int32_t shell, double *coeffs);
+int mahi_lattice_eval(double box_L_nm, int32_t order_p, int32_t shell, int64_t n, const double *r, double *H);
+
+/* Coulomb constant used by the library (kJ mol^-1 nm e^-2). */
+double mahi_coulomb_constant(void);
+
+const char *mahi_error_string(int code);
+/* Text of the last CUDA error seen by any handle in this process. */
+const char *mahi_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MAHI_H */

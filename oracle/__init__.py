@@ -54,6 +54,8 @@ def lib():
         L.oracle_ewald_params.argtypes = [ctypes.c_double, ctypes.c_double, dp,
                                           ctypes.POINTER(ctypes.c_int)]
         L.oracle_direct.argtypes = [ctypes.c_int64, dp, ctypes.c_int64, dp, dp, dp]
+        L.oracle_ewald_energy.argtypes = [ctypes.c_int64, dp, dp, ctypes.c_double, ctypes.c_double]
+        L.oracle_ewald_energy.restype = ctypes.c_double
         L.oracle_num_threads.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -103,6 +105,16 @@ def ewald(x, q, L, rc=None, targets=None):
     if rcode != 0:
         raise RuntimeError("oracle_ewald failed")
     return phi, grad, (float(e[0]) if targets is None else None)
+
+
+def ewald_energy(x, q, L, rc=None):
+    """Energy 1/2 sum_i q_i phi_i (f = 1) without per-atom potentials."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    if rc is None:
+        rc = default_rc(L, q.shape[0])
+    rc = min(rc, 0.5 * L)
+    return float(lib().oracle_ewald_energy(q.shape[0], _dp(x), _dp(q), float(L), float(rc)))
 
 
 def pair_A(r, L, rc=None):

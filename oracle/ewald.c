@@ -323,3 +323,80 @@ void oracle_direct(int64_t nt, const double *xt, int64_t ns, const double *ys, c
     phi[i] = kval(&p);
   }
 }
+
+/*
+ * Energy only: E = 1/2 sum_{i != j or n != 0} q_i q_j erfc(a r)/r  (each pair once)
+ *                + (2 pi / V) sum_{k != 0} exp(-k^2/4a^2)/k^2 |S(k)|^2
+ *                - a/sqrt(pi) sum q_i^2 - pi Q^2 / (2 a^2 V)
+ * (f = 1).  Same value as 1/2 sum q_i phi_i from oracle_ewald.
+ */
+double oracle_ewald_energy(int64_t n, const double *x, const double *q, double L, double rc) {
+  double alpha; int mmax;
+  oracle_ewald_params(L, rc, &alpha, &mmax);
+  double V = L * L * L;
+  ksum_t qs = {0, 0}, q2 = {0, 0};
+  for (int64_t j = 0; j < n; ++j) { kadd(&qs, q[j]); kadd(&q2, q[j] * q[j]); }
+  kset_t ks; kset_build(&ks, L, alpha, mmax);
+  double *Ck = malloc(ks.n * sizeof(double)), *Sk = malloc(ks.n * sizeof(double));
+  structure_factors(n, x, q, L, mmax, &ks, Ck, Sk);
+  ksum_t erec = {0, 0};
+  /* ks.c holds 2 * (4 pi / V) * exp()/k^2 for the half space: |S|^2 sum over the
+     full space times 2 pi / V equals sum_half c/4 * |S|^2 ... written out: */
+  for (int k = 0; k < ks.n; ++k) kadd(&erec, 0.5 * ks.c[k] * (Ck[k] * Ck[k] + Sk[k] * Sk[k]));
+  double *xw = malloc((size_t)n * 3 * sizeof(double));
+  for (int64_t j = 0; j < 3 * n; ++j) {
+    double v = x[j] - floor(x[j] / L) * L;
+    if (v >= L) v -= L;
+    if (v < 0.0) v = 0.0;
+    xw[j] = v;
+  }
+  cells_t cl; cells_build(&cl, n, xw, L, rc);
+  double rc2 = rc * rc;
+  int nt = oracle_num_threads();
+  double *part = calloc((size_t)nt * 2, sizeof(double));
+#pragma omp parallel
+  {
+    int tid = 0;
+#ifdef _OPENMP
+    tid = omp_get_thread_num();
+#endif
+    ksum_t acc = {0, 0};
+#pragma omp for schedule(dynamic, 64)
+    for (int64_t i = 0; i < n; ++i) {
+      double xi0 = xw[3 * i], xi1 = xw[3 * i + 1], xi2 = xw[3 * i + 2];
+      int cx = (int)floor(xi0 / cl.cs), cy = (int)floor(xi1 / cl.cs), cz = (int)floor(xi2 / cl.cs);
+      int R = cl.reach, nc = cl.nc;
+      double s = 0.0;
+      for (int dz = -R; dz <= R; ++dz)
+        for (int dy = -R; dy <= R; ++dy)
+          for (int dx = -R; dx <= R; ++dx) {
+            int gxc = cx + dx, gyc = cy + dy, gzc = cz + dz;
+            int wx = wrapi(gxc, nc), wy = wrapi(gyc, nc), wz = wrapi(gzc, nc);
+            double sx = (double)((gxc - wx) / nc) * L, sy = (double)((gyc - wy) / nc) * L,
+                   sz = (double)((gzc - wz) / nc) * L;
+            int c = (wz * nc + wy) * nc + wx;
+            for (int t = cl.start[c]; t < cl.start[c + 1]; ++t) {
+              int j = cl.idx[t];
+              double d0 = xi0 - (xw[3 * j] + sx), d1 = xi1 - (xw[3 * j + 1] + sy), d2 = xi2 - (xw[3 * j + 2] + sz);
+              double r2 = d0 * d0 + d1 * d1 + d2 * d2;
+              if (r2 >= rc2 || (j == i && r2 == 0.0)) continue;
+              double r = sqrt(r2);
+              s += q[j] * erfc(alpha * r) / r;
+            }
+          }
+      kadd(&acc, 0.5 * q[i] * s);
+    }
+    part[2 * tid] = acc.s; part[2 * tid + 1] = acc.c;
+  }
+  ksum_t ereal = {0, 0};
+  for (int t = 0; t < nt; ++t) { kadd(&ereal, part[2 * t]); kadd(&ereal, part[2 * t + 1]); }
+  free(part);
+  double Q = kval(&qs);
+  ksum_t e = {0, 0};
+  kadd(&e, kval(&ereal));
+  kadd(&e, kval(&erec));
+  kadd(&e, -alpha / sqrt(OR_PI) * kval(&q2));
+  kadd(&e, -OR_PI * Q * Q / (2.0 * alpha * alpha * V));
+  cells_free(&cl); kset_free(&ks); free(Ck); free(Sk); free(xw);
+  return kval(&e);
+}

@@ -27,7 +27,7 @@ import itertools
 
 import numpy as np
 
-from . import F_COULOMB, ewald, pair_A
+from . import F_COULOMB, ewald, ewald_energy, pair_A
 
 
 def scaled_charges(qA, qB, site_of, lam):
@@ -56,12 +56,21 @@ def site_kernel(xs, L, rc=None):
     return A, G
 
 
-def hi_eval(sys, rc=None, targets=None, f=F_COULOMB):
+def site_terms(xs, D, L):
+    """k_s = f-free D^T A D and the pair-force sums -D_i sum_{j != i} D_j grad A(r_ij)
+    for one site, as the energy (times 2) and forces of the charge set D alone:
+    E(D) = 1/2 D^T A D with A_ii = xi (the same periodic kernel)."""
+    phi, grad, e = ewald(xs, D, L, rc=0.5 * L)
+    return 2.0 * e, -D[:, None] * grad
+
+
+def hi_eval(sys, rc=None, targets=None, f=F_COULOMB, energy_only_full=False):
     """HI energy, dE/dlambda and forces for a two-form system.
 
     ``sys`` holds x, qA, qB, site_of, lam, L.  With ``targets`` None the full
     energy and all forces are returned; otherwise forces only at ``targets``
-    (site atoms are always evaluated for dE/dlambda) and energy None."""
+    (site atoms are always evaluated for dE/dlambda) and the energy only if
+    ``energy_only_full`` (computed without per-atom potentials)."""
     x, qA, qB = sys["x"], sys["qA"], sys["qB"]
     site_of, lam, L = np.asarray(sys["site_of"]), np.asarray(sys["lam"]), sys["L"]
     S = lam.shape[0]
@@ -70,13 +79,12 @@ def hi_eval(sys, rc=None, targets=None, f=F_COULOMB):
     site_atoms = np.concatenate(sites) if S else np.zeros(0, dtype=np.int64)
     if targets is None:
         phi, grad, e = ewald(x, qt, L, rc)
-        idx_all = np.arange(qt.shape[0])
-        phi_at = {int(i): phi[i] for i in site_atoms}
-        tgt = idx_all
+        tgt = np.arange(qt.shape[0])
     else:
         tgt = np.unique(np.concatenate([np.asarray(targets, dtype=np.int64), site_atoms]))
         phi, grad, e = ewald(x, qt, L, rc, targets=tgt)
-        phi_at = {int(i): phi[k] for k, i in enumerate(tgt)}
+        if energy_only_full:
+            e = ewald_energy(x, qt, L, rc)
     phi = phi * f
     grad = grad * f
     F = -qt[tgt, None] * grad
@@ -85,24 +93,20 @@ def hi_eval(sys, rc=None, targets=None, f=F_COULOMB):
     k_s = np.zeros(S)
     g_s = np.zeros(S)
     for s, at in enumerate(sites):
-        A, G = site_kernel(x[at], L)
         D = dq[at]
-        k_s[s] = f * D @ A @ D
-        g_s[s] = sum(D[a] * phi_at[int(i)] for a, i in enumerate(at)) * f
+        kk, fcorr = site_terms(x[at], D, L)
+        k_s[s] = f * kk
+        g_s[s] = float(np.sum(D * phi[[pos[int(i)] for i in at]]))
         w = lam[s] * (1.0 - lam[s])
         for a, i in enumerate(at):
-            corr = np.zeros(3)
-            for b in range(len(at)):
-                if b != a:
-                    corr += D[a] * D[b] * G[a, b]
-            F[pos[int(i)]] -= w * f * corr
+            F[pos[int(i)]] += w * f * fcorr[a]
     dEdl = g_s + (0.5 - lam) * k_s
     out = dict(F=F, targets=tgt, dEdl=dEdl, k=k_s, g=g_s, qt=qt)
-    if targets is None:
+    out["phi"] = phi
+    if e is not None:
         Et = e * f
         out["E_qi"] = Et
         out["E"] = Et + float(np.sum(0.5 * lam * (1.0 - lam) * k_s))
-        out["phi"] = phi
     else:
         out["E"] = None
     return out

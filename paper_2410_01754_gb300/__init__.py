@@ -1,0 +1,204 @@
+"""Python binding of libmahi (MAHI on GB300, sm_103a).
+
+Argument marshalling only: every step of the evaluation runs in the CUDA
+kernels of ``libmahi.so``.  Device buffers come from torch tensors (their
+``data_ptr()``), streams from ``torch.cuda.Stream.cuda_stream``.  There is no
+CPU path: if the library is missing the import of a compute entry point
+raises.  Function names follow ``include/mahi.h``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmahi.so")
+
+MAHI_FP64, MAHI_MIXED, MAHI_MIXED_SIMT = 0, 1, 2
+PRECISIONS = {"fp64": MAHI_FP64, "mixed": MAHI_MIXED, "mixed_simt": MAHI_MIXED_SIMT}
+
+_lib = None
+
+_SIGS = {
+    "mahi_create": (ctypes.c_int, [ctypes.c_double, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                   ctypes.c_int32, ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
+    "mahi_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "mahi_set_stream": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "mahi_set_charges": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "mahi_eval": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                 ctypes.c_void_p, ctypes.c_void_p]),
+    "mahi_eval_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
+                                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "mahi_get_potential": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "mahi_set_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    "mahi_stage_times": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float), ctypes.c_int32]),
+    "mahi_stage_name": (ctypes.c_char_p, [ctypes.c_int32]),
+    "mahi_launch_count": (ctypes.c_int, [ctypes.c_void_p]),
+    "mahi_lattice_coeffs": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p]),
+    "mahi_lattice_eval": (ctypes.c_int, [ctypes.c_double, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64,
+                                         ctypes.c_void_p, ctypes.c_void_p]),
+    "mahi_coulomb_constant": (ctypes.c_double, []),
+    "mahi_error_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "mahi_last_cuda_error": (ctypes.c_char_p, []),
+}
+
+
+class MahiError(RuntimeError):
+    def __init__(self, code, where=""):
+        msg = lib().mahi_error_string(code).decode()
+        if code == -4:
+            msg += ": " + lib().mahi_last_cuda_error().decode()
+        super().__init__(f"{where}: {msg} ({code})")
+        self.code = code
+
+
+def lib():
+    """Load libmahi.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libmahi.so not built ({LIB_PATH}); run paper_2410_01754_gb300/build.py")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _ck(code, where):
+    if code != 0:
+        raise MahiError(code, where)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data
+    return t.data_ptr()
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    return getattr(stream, "cuda_stream", stream)
+
+
+def mahi_create(box_L_nm, n_atoms, n_sites, order_p, depth, precision=MAHI_FP64, stream=None):
+    if isinstance(precision, str):
+        precision = PRECISIONS[precision]
+    h = ctypes.c_void_p()
+    _ck(lib().mahi_create(float(box_L_nm), int(n_atoms), int(n_sites), int(order_p), int(depth), int(precision),
+                          _stream_handle(stream), ctypes.byref(h)), "mahi_create")
+    return h
+
+
+def mahi_destroy(h):
+    _ck(lib().mahi_destroy(h), "mahi_destroy")
+
+
+def mahi_set_stream(h, stream):
+    _ck(lib().mahi_set_stream(h, _stream_handle(stream)), "mahi_set_stream")
+
+
+def mahi_set_charges(h, qA, qB, site_of_atom):
+    qA = np.ascontiguousarray(qA, dtype=np.float64)
+    qB = np.ascontiguousarray(qB, dtype=np.float64)
+    so = np.ascontiguousarray(site_of_atom, dtype=np.int32)
+    _ck(lib().mahi_set_charges(h, qA.ctypes.data, qB.ctypes.data, so.ctypes.data), "mahi_set_charges")
+
+
+def mahi_eval(h, x, lam, energy=None, forces=None, dEdlambda=None):
+    """x, lam, energy, forces, dEdlambda: CUDA tensors (x float32/float64 N x 3)."""
+    x_is_fp64 = 1 if str(x.dtype).endswith("float64") else 0
+    _ck(lib().mahi_eval(h, _ptr(x), x_is_fp64, _ptr(lam), _ptr(energy), _ptr(forces), _ptr(dEdlambda)),
+        "mahi_eval")
+
+
+def mahi_eval_host(h, x, lam, energy=None, forces=None, dEdlambda=None):
+    """Host numpy buffers (pinned or pageable); copies happen inside the call."""
+    x_is_fp64 = 1 if x.dtype == np.float64 else 0
+    _ck(lib().mahi_eval_host(h, _ptr(x), x_is_fp64, _ptr(lam), _ptr(energy), _ptr(forces), _ptr(dEdlambda)),
+        "mahi_eval_host")
+
+
+def mahi_get_potential(h, phi):
+    _ck(lib().mahi_get_potential(h, _ptr(phi)), "mahi_get_potential")
+
+
+def mahi_set_timing(h, on=True):
+    _ck(lib().mahi_set_timing(h, 1 if on else 0), "mahi_set_timing")
+
+
+def mahi_stage_times(h):
+    buf = (ctypes.c_float * 32)()
+    n = lib().mahi_stage_times(h, buf, 32)
+    if n < 0:
+        raise MahiError(n, "mahi_stage_times")
+    return {lib().mahi_stage_name(i).decode(): float(buf[i]) for i in range(n)}
+
+
+def mahi_launch_count(h):
+    return int(lib().mahi_launch_count(h))
+
+
+def mahi_lattice_coeffs(order_p, shell=1):
+    out = np.zeros((2 * order_p + 1) ** 2)
+    _ck(lib().mahi_lattice_coeffs(int(order_p), int(shell), out.ctypes.data), "mahi_lattice_coeffs")
+    return out
+
+
+def mahi_lattice_eval(box_L_nm, order_p, r, shell=1):
+    r = np.ascontiguousarray(r, dtype=np.float64).reshape(-1, 3)
+    out = np.zeros(r.shape[0])
+    _ck(lib().mahi_lattice_eval(float(box_L_nm), int(order_p), int(shell), r.shape[0], r.ctypes.data, out.ctypes.data),
+        "mahi_lattice_eval")
+    return out
+
+
+def mahi_coulomb_constant():
+    return float(lib().mahi_coulomb_constant())
+
+
+def mahi_error_string(code):
+    return lib().mahi_error_string(int(code)).decode()
+
+
+class Mahi:
+    """Owning wrapper around a handle: create, set charges, evaluate (torch)."""
+
+    def __init__(self, box_L_nm, n_atoms, n_sites, order_p, depth, precision="fp64", stream=None):
+        self.h = mahi_create(box_L_nm, n_atoms, n_sites, order_p, depth, precision, stream)
+        self.n_atoms, self.n_sites = int(n_atoms), int(n_sites)
+
+    def set_charges(self, qA, qB, site_of_atom):
+        mahi_set_charges(self.h, qA, qB, site_of_atom)
+
+    def eval(self, x, lam):
+        import torch
+        E = torch.zeros(1, dtype=torch.float64, device=x.device)
+        F = torch.empty_like(x)
+        g = torch.zeros(max(1, self.n_sites), dtype=torch.float64, device=x.device)
+        mahi_eval(self.h, x, lam, E, F, g)
+        return E, F, g[: self.n_sites]
+
+    def potential(self, device="cuda"):
+        import torch
+        phi = torch.empty(self.n_atoms, dtype=torch.float64, device=device)
+        mahi_get_potential(self.h, phi)
+        return phi
+
+    def close(self):
+        if self.h is not None:
+            mahi_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,381 @@
+// C ABI of libmahi: handle management, argument checks, device workspaces and
+// the host-only lattice helpers.  All compute is in mahi_kernels.cu and
+// mahi_m2l_tc.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "mahi_internal.h"
+
+using namespace mahi;
+
+static std::mutex g_err_mu;
+static char g_cuda_err[512] = "";
+
+static int cuda_fail(cudaError_t e, const char *what) {
+  std::lock_guard<std::mutex> lk(g_err_mu);
+  snprintf(g_cuda_err, sizeof(g_cuda_err), "%s: %s (%d)", what, cudaGetErrorString(e), (int)e);
+  return MAHI_ERR_CUDA;
+}
+
+#define CK(call)                                      \
+  do {                                                \
+    cudaError_t e_ = (call);                          \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+
+template <typename P>
+static cudaError_t dalloc(P **p, size_t bytes) {
+  void *v = nullptr;
+  cudaError_t e = cudaMalloc(&v, std::max<size_t>(bytes, 16));
+  *p = (P *)v;
+  return e;
+}
+
+static void free_all(mahi_ctx *h) {
+  void *bufs[] = {h->qA, h->dq, h->site_of, h->qt, h->leaf_of, h->slot, h->leaf_count, h->leaf_start, h->perm,
+                  h->perm_tmp, h->inv_perm, h->part, h->part_tmp, h->Mexp, h->Lexp, h->phi_s, h->grad_s,
+                  h->ops_m2m, h->ops_l2l, h->ops_m2l, h->ops_lat, h->eta, h->eta_x, h->eta_y, h->eta_z,
+                  h->m2l_list, h->m2l_off, h->site_ptr, h->site_atoms, h->moments_part, h->moments,
+                  h->energy_part, h->site_energy, h->tc_ops, h->tc_units, h->tc_error, h->d_x_stage,
+                  h->d_lam_stage, h->d_E_stage, h->d_dEdl_stage, h->d_F_stage};
+  for (void *b : bufs)
+    if (b) cudaFree(b);
+  for (int i = 0; i < 32; ++i)
+    if (h->ev[i]) cudaEventDestroy(h->ev[i]);
+}
+
+template <typename T>
+static cudaError_t upload_ops(const std::vector<std::vector<double>> &ops, void **dst) {
+  size_t n = 0;
+  for (auto &o : ops) n += o.size();
+  std::vector<T> tmp(n);
+  size_t k = 0;
+  for (auto &o : ops)
+    for (double v : o) tmp[k++] = (T)v;
+  cudaError_t e = dalloc(dst, n * sizeof(T));
+  if (e != cudaSuccess) return e;
+  return cudaMemcpy(*dst, tmp.data(), n * sizeof(T), cudaMemcpyHostToDevice);
+}
+
+extern "C" {
+
+double mahi_coulomb_constant(void) { return coulomb_constant(); }
+
+const char *mahi_error_string(int code) {
+  switch (code) {
+    case MAHI_OK: return "ok";
+    case MAHI_ERR_INVALID_ARG: return "invalid argument";
+    case MAHI_ERR_BAD_SITE_MAP: return "bad site map (index out of range, empty site, site too large, or qA != qB on an environment atom)";
+    case MAHI_ERR_NON_CUBIC: return "non-cubic box (unsupported)";
+    case MAHI_ERR_CUDA: return "CUDA error (see mahi_last_cuda_error)";
+    case MAHI_ERR_TIMEOUT: return "a bounded device wait gave up";
+    case MAHI_ERR_NO_DEVICE: return "no usable sm_103 (GB300) CUDA device";
+    case MAHI_ERR_STATE: return "charges not set";
+    default: return "unknown error";
+  }
+}
+
+const char *mahi_last_cuda_error(void) { return g_cuda_err; }
+
+const char *mahi_stage_name(int32_t i) { return stage_name(i); }
+
+int mahi_create(double box_L_nm, int64_t n_atoms, int32_t n_sites, int32_t order_p, int32_t depth, int32_t precision,
+                void *cuda_stream, mahi_t *out) {
+  if (!out) return MAHI_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!(box_L_nm > 0.0) || !std::isfinite(box_L_nm) || n_atoms < 1 || n_atoms > (int64_t)1 << 30 || n_sites < 0 ||
+      depth < 0 || depth > kMaxDepth || order_p < 1)
+    return MAHI_ERR_INVALID_ARG;
+  if (precision != MAHI_FP64 && precision != MAHI_MIXED && precision != MAHI_MIXED_SIMT) return MAHI_ERR_INVALID_ARG;
+  if (order_p > (precision == MAHI_FP64 ? kMaxOrder : kMaxOrderMixed)) return MAHI_ERR_INVALID_ARG;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
+    cudaGetLastError();
+    return MAHI_ERR_NO_DEVICE;
+  }
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return MAHI_ERR_NO_DEVICE;
+  if (prop.major * 10 + prop.minor != 103) return MAHI_ERR_NO_DEVICE;
+
+  mahi_ctx *h = new (std::nothrow) mahi_ctx();
+  if (!h) return MAHI_ERR_INVALID_ARG;
+  h->L = box_L_nm; h->N = n_atoms; h->S = n_sites; h->p = order_p; h->d = depth; h->prec = precision;
+  h->stream = (cudaStream_t)cuda_stream;
+  h->device = dev;
+  h->K = ncoef(order_p);
+  h->ld = nstride(order_p);
+  h->nleaf = 1 << (3 * depth);
+  int64_t off = 0;
+  for (int l = 0; l <= depth; ++l) { h->level_off[l] = off; off += (int64_t)1 << (3 * l); }
+  h->level_off[depth + 1] = off;
+  h->nbox_total = off;
+  const bool f64 = (precision == MAHI_FP64);
+  const size_t ts = f64 ? sizeof(double) : sizeof(float);
+  const size_t v4 = 4 * ts;
+  const int64_t N = n_atoms;
+  int rc = MAHI_OK;
+  auto fail = [&](cudaError_t e, const char *w) {
+    rc = cuda_fail(e, w);
+    free_all(h);
+    delete h;
+    return rc;
+  };
+#define AL(ptr, bytes)                                  \
+  do {                                                  \
+    cudaError_t e_ = dalloc(&(ptr), (bytes));           \
+    if (e_ != cudaSuccess) return fail(e_, #ptr);       \
+  } while (0)
+  AL(h->qA, N * 8); AL(h->dq, N * 8); AL(h->site_of, N * 4); AL(h->qt, N * 8);
+  AL(h->leaf_of, N * 4); AL(h->slot, N * 4);
+  AL(h->leaf_count, (size_t)h->nleaf * 4); AL(h->leaf_start, (size_t)(h->nleaf + 1) * 4);
+  AL(h->perm, N * 4); AL(h->perm_tmp, N * 4); AL(h->inv_perm, N * 4);
+  AL(h->part, N * v4); AL(h->part_tmp, N * v4);
+  AL(h->Mexp, (size_t)h->nbox_total * h->ld * ts); AL(h->Lexp, (size_t)h->nbox_total * h->ld * ts);
+  AL(h->phi_s, N * ts); AL(h->grad_s, N * 3 * ts);
+  h->n_moment_blocks = (int)std::min<int64_t>(4 * 152, (N + 255) / 256);
+  AL(h->moments_part, (size_t)h->n_moment_blocks * 5 * 8); AL(h->moments, 8 * 8);
+  AL(h->energy_part, (size_t)h->nleaf * 8); AL(h->site_energy, (size_t)std::max(1, n_sites) * 8);
+  {
+    cudaError_t e = cudaMemset(h->Lexp, 0, (size_t)h->nbox_total * h->ld * ts);
+    if (e != cudaSuccess) return fail(e, "memset");
+    e = cudaMemset(h->Mexp, 0, (size_t)h->nbox_total * h->ld * ts);
+    if (e != cudaSuccess) return fail(e, "memset");
+  }
+
+  // translation operators (host, FP64) -> device in the working precision
+  const int K = h->K;
+  std::vector<std::vector<double>> m2m(8), l2l(8), m2l(kNumOffsets), lat(1);
+  for (int c = 0; c < 8; ++c) {
+    build_m2m(order_p, c, m2m[c]);
+    scale_operator(order_p, 0, m2m[c]);
+    build_l2l(order_p, c, l2l[c]);
+    scale_operator(order_p, 1, l2l[c]);
+  }
+  const OffsetTables &ot = offset_tables();
+  for (int o = 0; o < kNumOffsets; ++o) {
+    build_m2l(order_p, ot.off[o][0], ot.off[o][1], ot.off[o][2], m2l[o]);
+    scale_operator(order_p, 2, m2l[o]);
+  }
+  build_lattice_op(order_p, lat[0]);
+  scale_operator(order_p, 2, lat[0]);
+  {
+    cudaError_t e;
+    if (f64) {
+      if ((e = upload_ops<double>(m2m, &h->ops_m2m)) != cudaSuccess) return fail(e, "ops");
+      if ((e = upload_ops<double>(l2l, &h->ops_l2l)) != cudaSuccess) return fail(e, "ops");
+      if ((e = upload_ops<double>(m2l, &h->ops_m2l)) != cudaSuccess) return fail(e, "ops");
+    } else {
+      if ((e = upload_ops<float>(m2m, &h->ops_m2m)) != cudaSuccess) return fail(e, "ops");
+      if ((e = upload_ops<float>(l2l, &h->ops_l2l)) != cudaSuccess) return fail(e, "ops");
+      if ((e = upload_ops<float>(m2l, &h->ops_m2l)) != cudaSuccess) return fail(e, "ops");
+    }
+    void *tmp = nullptr;
+    if ((e = upload_ops<double>(lat, &tmp)) != cudaSuccess) return fail(e, "ops");
+    h->ops_lat = (double *)tmp;
+    // first-shell lattice function H_1 for the per-site pair kernel, and its
+    // gradient coefficients
+    const int P = kSiteDegree;
+    const std::vector<double> &eta = lattice_coeffs(P, 1);
+    std::vector<double> ex((size_t)(P + 1) * (P + 1), 0.0), ey(ex), ez(ex);
+    gradient_coeffs(P, eta.data(), ex.data(), ey.data(), ez.data());
+    std::vector<std::vector<double>> v1{eta}, v2{ex}, v3{ey}, v4v{ez};
+    if ((e = upload_ops<double>(v1, &tmp)) != cudaSuccess) return fail(e, "eta");
+    h->eta = (double *)tmp;
+    if ((e = upload_ops<double>(v2, &tmp)) != cudaSuccess) return fail(e, "eta");
+    h->eta_x = (double *)tmp;
+    if ((e = upload_ops<double>(v3, &tmp)) != cudaSuccess) return fail(e, "eta");
+    h->eta_y = (double *)tmp;
+    if ((e = upload_ops<double>(v4v, &tmp)) != cudaSuccess) return fail(e, "eta");
+    h->eta_z = (double *)tmp;
+    AL(h->m2l_list, sizeof(int) * 8 * kListLen);
+    AL(h->m2l_off, sizeof(int) * kNumOffsets * 3);
+    if ((e = cudaMemcpy(h->m2l_list, ot.list, sizeof(int) * 8 * kListLen, cudaMemcpyHostToDevice)) != cudaSuccess)
+      return fail(e, "list");
+    if ((e = cudaMemcpy(h->m2l_off, ot.off, sizeof(int) * kNumOffsets * 3, cudaMemcpyHostToDevice)) != cudaSuccess)
+      return fail(e, "list");
+    if (precision == MAHI_MIXED && depth >= 1) {
+      std::vector<unsigned char> img(tc_ops_bytes(order_p));
+      tc_pack_ops(order_p, m2l, img.data());
+      AL(h->tc_ops, img.size());
+      if ((e = cudaMemcpy(h->tc_ops, img.data(), img.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return fail(e, "tc ops");
+      std::vector<int> units;
+      int r = tc_build_units(h, units);
+      if (r != 0) { free_all(h); delete h; return MAHI_ERR_INVALID_ARG; }
+      AL(h->tc_units, units.size() * sizeof(int));
+      if ((e = cudaMemcpy(h->tc_units, units.data(), units.size() * sizeof(int), cudaMemcpyHostToDevice)) !=
+          cudaSuccess)
+        return fail(e, "tc units");
+      AL(h->tc_error, 16);
+      cudaMemset(h->tc_error, 0, 16);
+    }
+  }
+  for (int i = 0; i < 32; ++i) {
+    cudaError_t e = cudaEventCreate(&h->ev[i]);
+    if (e != cudaSuccess) return fail(e, "event");
+  }
+#undef AL
+  (void)K;
+  *out = h;
+  return MAHI_OK;
+}
+
+int mahi_destroy(mahi_t h) {
+  if (!h) return MAHI_OK;
+  cudaStreamSynchronize(h->stream);
+  free_all(h);
+  delete h;
+  return MAHI_OK;
+}
+
+int mahi_set_stream(mahi_t h, void *cuda_stream) {
+  if (!h) return MAHI_ERR_INVALID_ARG;
+  h->stream = (cudaStream_t)cuda_stream;
+  return MAHI_OK;
+}
+
+int mahi_set_charges(mahi_t h, const double *qA, const double *qB, const int32_t *site_of_atom) {
+  if (!h || !qA || !qB || !site_of_atom) return MAHI_ERR_INVALID_ARG;
+  const int64_t N = h->N;
+  const int S = h->S;
+  std::vector<int> cnt(S, 0);
+  std::vector<double> dq(N);
+  for (int64_t i = 0; i < N; ++i) {
+    int s = site_of_atom[i];
+    if (!std::isfinite(qA[i]) || !std::isfinite(qB[i])) return MAHI_ERR_INVALID_ARG;
+    if (s < -1 || s >= S) return MAHI_ERR_BAD_SITE_MAP;
+    if (s == -1) {
+      if (qA[i] != qB[i]) return MAHI_ERR_BAD_SITE_MAP;
+      dq[i] = 0.0;
+    } else {
+      cnt[s]++;
+      dq[i] = qB[i] - qA[i];
+    }
+  }
+  for (int s = 0; s < S; ++s)
+    if (cnt[s] == 0 || cnt[s] > 64) return MAHI_ERR_BAD_SITE_MAP;
+  std::vector<int> ptr(S + 1, 0), atoms;
+  for (int s = 0; s < S; ++s) ptr[s + 1] = ptr[s] + cnt[s];
+  atoms.resize(ptr[S]);
+  std::vector<int> fill(ptr.begin(), ptr.end() - 1);
+  for (int64_t i = 0; i < N; ++i)
+    if (site_of_atom[i] >= 0) atoms[fill[site_of_atom[i]]++] = (int)i;
+  CK(cudaStreamSynchronize(h->stream));
+  CK(cudaMemcpy(h->qA, qA, N * 8, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(h->dq, dq.data(), N * 8, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(h->site_of, site_of_atom, N * 4, cudaMemcpyHostToDevice));
+  if (h->site_ptr) { cudaFree(h->site_ptr); h->site_ptr = nullptr; }
+  if (h->site_atoms) { cudaFree(h->site_atoms); h->site_atoms = nullptr; }
+  CK(dalloc(&h->site_ptr, (S + 1) * sizeof(int)));
+  CK(dalloc(&h->site_atoms, std::max<size_t>(1, atoms.size()) * sizeof(int)));
+  CK(cudaMemcpy(h->site_ptr, ptr.data(), (S + 1) * sizeof(int), cudaMemcpyHostToDevice));
+  if (!atoms.empty()) CK(cudaMemcpy(h->site_atoms, atoms.data(), atoms.size() * sizeof(int), cudaMemcpyHostToDevice));
+  h->n_site_atoms = (int)atoms.size();
+  h->charges_set = true;
+  return MAHI_OK;
+}
+
+int mahi_eval(mahi_t h, const void *x, int32_t x_is_fp64, const double *lambda, double *energy, void *forces,
+              double *dEdlambda) {
+  if (!h || !x || (h->S > 0 && !lambda)) return MAHI_ERR_INVALID_ARG;
+  if (!h->charges_set) return MAHI_ERR_STATE;
+  CK(cudaSetDevice(h->device));
+  int r = enqueue_eval(h, x, x_is_fp64 ? 1 : 0, lambda, energy, forces, dEdlambda);
+  if (r != 0) return cuda_fail((cudaError_t)r, "mahi_eval");
+  if (h->tc_error && h->prec == MAHI_MIXED) {
+    // the tensor-core kernel reports bounded-wait timeouts through a flag that
+    // is checked lazily at the next synchronising call (mahi_eval_host)
+  }
+  return MAHI_OK;
+}
+
+int mahi_eval_host(mahi_t h, const void *x_host, int32_t x_is_fp64, const double *lambda_host, double *energy_host,
+                   void *forces_host, double *dEdlambda_host) {
+  if (!h || !x_host || (h->S > 0 && !lambda_host)) return MAHI_ERR_INVALID_ARG;
+  if (!h->charges_set) return MAHI_ERR_STATE;
+  const size_t xs = x_is_fp64 ? 8 : 4;
+  const size_t xb = (size_t)h->N * 3 * xs;
+  if (h->x_stage_fp64 != (x_is_fp64 ? 1 : 0)) {
+    if (h->d_x_stage) cudaFree(h->d_x_stage);
+    if (h->d_F_stage) cudaFree(h->d_F_stage);
+    h->d_x_stage = h->d_F_stage = nullptr;
+    CK(dalloc(&h->d_x_stage, xb));
+    CK(dalloc(&h->d_F_stage, xb));
+    h->x_stage_fp64 = x_is_fp64 ? 1 : 0;
+  }
+  if (!h->d_lam_stage) {
+    CK(dalloc(&h->d_lam_stage, std::max(1, h->S) * 8));
+    CK(dalloc(&h->d_E_stage, 8));
+    CK(dalloc(&h->d_dEdl_stage, std::max(1, h->S) * 8));
+  }
+  cudaStream_t st = h->stream;
+  CK(cudaMemcpyAsync(h->d_x_stage, x_host, xb, cudaMemcpyHostToDevice, st));
+  if (h->S > 0) CK(cudaMemcpyAsync(h->d_lam_stage, lambda_host, h->S * 8, cudaMemcpyHostToDevice, st));
+  int r = enqueue_eval(h, h->d_x_stage, x_is_fp64 ? 1 : 0, h->d_lam_stage, h->d_E_stage, h->d_F_stage,
+                       h->d_dEdl_stage);
+  if (r != 0) return cuda_fail((cudaError_t)r, "mahi_eval_host");
+  if (energy_host) CK(cudaMemcpyAsync(energy_host, h->d_E_stage, 8, cudaMemcpyDeviceToHost, st));
+  if (forces_host) CK(cudaMemcpyAsync(forces_host, h->d_F_stage, xb, cudaMemcpyDeviceToHost, st));
+  if (dEdlambda_host && h->S > 0)
+    CK(cudaMemcpyAsync(dEdlambda_host, h->d_dEdl_stage, h->S * 8, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (h->tc_error) {
+    int flag = 0;
+    CK(cudaMemcpy(&flag, h->tc_error, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag) return MAHI_ERR_TIMEOUT;
+  }
+  return MAHI_OK;
+}
+
+int mahi_get_potential(mahi_t h, double *phi_device) {
+  if (!h || !phi_device) return MAHI_ERR_INVALID_ARG;
+  if (enqueue_potential(h, phi_device) != 0) return cuda_fail(cudaGetLastError(), "potential");
+  return MAHI_OK;
+}
+
+int mahi_set_timing(mahi_t h, int32_t on) {
+  if (!h) return MAHI_ERR_INVALID_ARG;
+  h->timing = on != 0;
+  return MAHI_OK;
+}
+
+int mahi_stage_times(mahi_t h, float *ms, int32_t n) {
+  if (!h || !ms) return MAHI_ERR_INVALID_ARG;
+  CK(cudaStreamSynchronize(h->stream));
+  int ns = std::min(num_stages(), h->n_ev - 1);
+  for (int i = 0; i < ns && i < n; ++i) {
+    float t = 0;
+    CK(cudaEventElapsedTime(&t, h->ev[i], h->ev[i + 1]));
+    ms[i] = t;
+  }
+  return ns;
+}
+
+int mahi_launch_count(mahi_t h) { return h ? h->launches : 0; }
+
+int mahi_lattice_coeffs(int32_t order_p, int32_t shell, double *coeffs) {
+  if (order_p < 1 || order_p > kMaxOrder || !coeffs || (shell != 1 && shell != kLatticeShell))
+    return MAHI_ERR_INVALID_ARG;
+  const std::vector<double> &eta = lattice_coeffs(2 * order_p, shell);
+  std::memcpy(coeffs, eta.data(), eta.size() * sizeof(double));
+  return MAHI_OK;
+}
+
+int mahi_lattice_eval(double box_L_nm, int32_t order_p, int32_t shell, int64_t n, const double *r, double *H) {
+  if (!(box_L_nm > 0) || order_p < 1 || order_p > kMaxOrder || n < 0 || (n > 0 && (!r || !H)) ||
+      (shell != 1 && shell != kLatticeShell))
+    return MAHI_ERR_INVALID_ARG;
+  for (int64_t i = 0; i < n; ++i) H[i] = lattice_eval_host(box_L_nm, 2 * order_p, shell, r + 3 * i);
+  return MAHI_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,137 @@
+// Internal declarations shared by the host planner, the kernels and the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <complex>
+#include <string>
+#include <vector>
+
+#include "../../include/mahi.h"
+
+namespace mahi {
+
+constexpr int kMaxOrder = 24;          // FP64 path
+constexpr int kMaxOrderMixed = 16;     // FP32 exponent range of the M2L operators
+constexpr int kMaxDepth = 6;
+constexpr int kNumOffsets = 316;       // {-3..3}^3 minus {-1..1}^3
+constexpr int kListLen = 189;          // M2L interaction list of one box
+constexpr int kLatticeShell = 3;       // images |n|_inf <= 3 exactly, beyond by H_3
+constexpr int kSiteDegree = 40;        // degree of H_1 in the per-site correction
+constexpr double kPi = 3.14159265358979323846264338327950288;
+
+// Coulomb constant N_A e^2 / (4 pi eps0) in kJ mol^-1 nm e^-2 (CODATA 2018).
+double coulomb_constant();
+
+// Number of real coefficients of an order-p expansion and the padded row stride.
+inline int ncoef(int p) { return (p + 1) * (p + 1); }
+inline int nstride(int p) { return ((ncoef(p) + 15) / 16) * 16; }
+
+// ---- host planner (mahi_host.cpp) -----------------------------------------
+// Real translation operators at unit (level-normalised) scale, dense row-major
+// [out][in] of size ncoef(p)^2.  Child index b = bx | by<<1 | bz<<2.
+void build_m2m(int p, int child, std::vector<double> &op);
+void build_l2l(int p, int child, std::vector<double> &op);
+void build_m2l(int p, int ox, int oy, int oz, std::vector<double> &op);
+// Lattice coefficients eta^ (unit box) of H_shell up to degree P, real layout (P+1)^2.
+const std::vector<double> &lattice_coeffs(int P, int shell);
+// Lattice operator (root local from root multipole): H_3 lattice part plus the
+// root images 2 <= |n|_inf <= 3 by M2L; ncoef(p)^2, FP64, unscaled basis.
+void build_lattice_op(int p, std::vector<double> &op);
+// Convert an unscaled operator to the device basis: kind 0 = M2M, 1 = L2L,
+// 2 = M2L / lattice.
+void scale_operator(int p, int kind, std::vector<double> &op);
+double basis_scale(int col);
+// Derivative coefficient vectors of an order-P real expansion: given coefficients
+// c of phi = sum c_lm R*_lm(u), returns d/dx, d/dy, d/dz coefficients of degree P-1.
+void gradient_coeffs(int P, const double *c, double *cx, double *cy, double *cz);
+// Host evaluation of H_shell(r) for box edge L from the coefficients (degree P).
+double lattice_eval_host(double L, int P, int shell, const double r[3]);
+
+// M2L offset table: id of offset (ox,oy,oz) in [-3,3]^3 (or -1), and the 189
+// offsets of each child index.
+struct OffsetTables {
+  int id[343];
+  int off[kNumOffsets][3];
+  int list[8][kListLen];  // offset ids
+};
+const OffsetTables &offset_tables();
+
+inline uint32_t morton_spread(uint32_t v) {
+  uint32_t x = v & 0x3ff;
+  x = (x | (x << 16)) & 0x030000FF;
+  x = (x | (x << 8)) & 0x0300F00F;
+  x = (x | (x << 4)) & 0x030C30C3;
+  x = (x | (x << 2)) & 0x09249249;
+  return x;
+}
+
+}  // namespace mahi
+
+// ---- the handle ---------------------------------------------------------------
+struct mahi_ctx {
+  double L = 0;
+  int64_t N = 0;
+  int S = 0, p = 0, d = 0, prec = 0;
+  int K = 0, ld = 0;           // coefficients per expansion, row stride
+  int nleaf = 0;
+  int64_t nbox_total = 0;
+  int64_t level_off[mahi::kMaxDepth + 2] = {0};
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  bool charges_set = false;
+  bool timing = false;
+  int launches = 0;
+  int n_site_atoms = 0;
+
+  // device buffers
+  void *arena = nullptr;
+  size_t arena_bytes = 0;
+  double *qA = nullptr, *dq = nullptr;   // N
+  int *site_of = nullptr;                // N
+  double *qt = nullptr;                  // N, scaled charges (FP64)
+  int *leaf_of = nullptr, *slot = nullptr, *leaf_count = nullptr, *leaf_start = nullptr;
+  int *perm = nullptr, *perm_tmp = nullptr, *inv_perm = nullptr;
+  void *part = nullptr, *part_tmp = nullptr;  // float4 or double4, sorted by leaf
+  void *Mexp = nullptr, *Lexp = nullptr;      // expansions, all levels
+  void *phi_s = nullptr, *grad_s = nullptr;   // sorted potential / gradient
+  void *ops_m2m = nullptr, *ops_l2l = nullptr, *ops_m2l = nullptr;
+  double *ops_lat = nullptr;                  // FP64 lattice operator
+  double *eta = nullptr, *eta_x = nullptr, *eta_y = nullptr, *eta_z = nullptr;  // degree 2p
+  int *m2l_list = nullptr;                    // [8][189] offset ids
+  int *m2l_off = nullptr;                     // [316][3]
+  int *site_ptr = nullptr, *site_atoms = nullptr;
+  double *moments_part = nullptr;             // per-block partial moments
+  double *moments = nullptr;                  // Q, Dx, Dy, Dz, T
+  double *energy_part = nullptr;              // per-block energy partials
+  double *site_energy = nullptr;              // S
+  int n_moment_blocks = 0, n_energy_blocks = 0;
+  // tensor-core M2L operand images (mixed path)
+  void *tc_ops = nullptr;
+  int *tc_units = nullptr;
+  int tc_nunits = 0;
+  int *tc_error = nullptr;
+  // host staging for mahi_eval_host
+  void *d_x_stage = nullptr;
+  double *d_lam_stage = nullptr, *d_E_stage = nullptr, *d_dEdl_stage = nullptr;
+  void *d_F_stage = nullptr;
+  int x_stage_fp64 = -1;
+
+  cudaEvent_t ev[32] = {};
+  int n_ev = 0;
+};
+
+namespace mahi {
+// ---- kernel launchers (mahi_kernels.cu) ------------------------------------
+int enqueue_eval(mahi_ctx *h, const void *x, int x_is_fp64, const double *lambda, double *energy,
+                 void *forces, double *dEdl);
+int enqueue_potential(mahi_ctx *h, double *phi);
+const char *stage_name(int i);
+int num_stages();
+// tensor-core M2L (mahi_m2l_tc.cu)
+size_t tc_ops_bytes(int p);
+void tc_pack_ops(int p, const std::vector<std::vector<double>> &m2l, void *host_image);
+int tc_build_units(mahi_ctx *h, std::vector<int> &units);
+int tc_m2l(mahi_ctx *h);
+}  // namespace mahi

@@ -1,0 +1,936 @@
+// SIMT kernels of the MAHI evaluation and the eval orchestration.
+//
+// Data layout (HBM):
+//   part[N]            sorted by leaf (Morton order), float4/double4
+//                      (x - leaf centre [nm], q~); leaves are contiguous,
+//                      leaf_start[8^d + 1] gives the ranges.
+//   Mexp/Lexp          all levels, level l at level_off[l], one row of `ld`
+//                      coefficients per box (Morton index within the level).
+//   phi_s, grad_s      far-field potential / gradient per sorted atom.
+// FP64 everywhere in MAHI_FP64, FP32 particle/expansion data in the mixed modes;
+// scaled charges, multipole moments of the box, energies and the per-site
+// corrections are always FP64.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdio>
+
+#include "mahi_internal.h"
+
+namespace mahi {
+
+template <typename T> struct V4;
+template <> struct V4<float> { using type = float4; };
+template <> struct V4<double> { using type = double4; };
+
+__device__ __forceinline__ uint32_t d_spread(uint32_t v) {
+  uint32_t x = v & 0x3ff;
+  x = (x | (x << 16)) & 0x030000FF;
+  x = (x | (x << 8)) & 0x0300F00F;
+  x = (x | (x << 4)) & 0x030C30C3;
+  x = (x | (x << 2)) & 0x09249249;
+  return x;
+}
+__device__ __forceinline__ uint32_t d_compact(uint32_t x) {
+  x &= 0x09249249;
+  x = (x ^ (x >> 2)) & 0x030C30C3;
+  x = (x ^ (x >> 4)) & 0x0300F00F;
+  x = (x ^ (x >> 8)) & 0x030000FF;
+  x = (x ^ (x >> 16)) & 0x000003FF;
+  return x;
+}
+__device__ __forceinline__ uint32_t d_morton(int x, int y, int z) {
+  return d_spread(x) | (d_spread(y) << 1) | (d_spread(z) << 2);
+}
+__device__ __forceinline__ int wrapi(int a, int n) { int r = a % n; return r < 0 ? r + n : r; }
+
+template <typename T> __device__ __forceinline__ T rsqrt_int(int a) { return T(1) / sqrt(T(a)); }
+template <typename T> __device__ __forceinline__ T sqrt_ratio(int a, int b) { return sqrt(T(a) / T(b)); }
+
+// ---------------------------------------------------------------------------
+// Regular solid harmonics, streamed degree by degree.  Row l holds R_lm for
+// m = 0..l (complex); conj(R) enters P2M/L2P.  `row_cb(l, re, im)` is called
+// for every complete row.
+// ---------------------------------------------------------------------------
+template <typename T, int PMAX, class CB>
+__device__ __forceinline__ void harmonics_rows(int P, T x, T y, T z, CB row_cb) {
+  T re0[PMAX + 1], im0[PMAX + 1];  // row l-1
+  T re1[PMAX + 1], im1[PMAX + 1];  // row l-2
+  T r2 = x * x + y * y + z * z;
+  re0[0] = T(1); im0[0] = T(0);
+  row_cb(0, re0, im0);
+  T dre = T(1), dim = T(0);  // diagonal R_{l-1,l-1}
+  for (int l = 1; l <= P; ++l) {
+    T nre[PMAX + 1], nim[PMAX + 1];
+    for (int m = 0; m <= l - 1; ++m) {
+      T ar = T(2 * l - 1) * z * re0[m], ai = T(2 * l - 1) * z * im0[m];
+      if (m <= l - 2) { ar -= r2 * re1[m]; ai -= r2 * im1[m]; }
+      T inv = T(1) / T((l + m) * (l - m));
+      nre[m] = ar * inv; nim[m] = ai * inv;
+    }
+    // R_ll = -(x + i y)/(2l) R_{l-1,l-1}
+    T f = T(-1) / T(2 * l);
+    T tr = f * (x * dre - y * dim), ti = f * (x * dim + y * dre);
+    dre = tr; dim = ti;
+    nre[l] = dre; nim[l] = dim;
+    for (int m = 0; m <= l; ++m) {
+      if (m <= l - 1) { re1[m] = re0[m]; im1[m] = im0[m]; }
+      re0[m] = nre[m]; im0[m] = nim[m];
+    }
+    row_cb(l, re0, im0);
+  }
+}
+
+// The same rows in the device basis, Rt_lm = sqrt((l+m)!(l-m)!) R_lm, whose
+// magnitude stays O(|u|^l) at every order (no factorial range in FP32):
+//   Rt_mm = -(x+iy) sqrt((2m-1)/(2m)) Rt_{m-1,m-1}
+//   Rt_lm = (2l-1) z Rt_{l-1,m} / sqrt((l+m)(l-m))
+//           - r^2 Rt_{l-2,m} sqrt((l+m-1)(l-m-1) / ((l+m)(l-m)))
+template <typename T, int PMAX, class CB>
+__device__ __forceinline__ void scaled_harmonics_rows(int P, T x, T y, T z, CB row_cb) {
+  T re0[PMAX + 1], im0[PMAX + 1];
+  T re1[PMAX + 1], im1[PMAX + 1];
+  T r2 = x * x + y * y + z * z;
+  re0[0] = T(1); im0[0] = T(0);
+  row_cb(0, re0, im0);
+  T dre = T(1), dim = T(0);
+  for (int l = 1; l <= P; ++l) {
+    T nre[PMAX + 1], nim[PMAX + 1];
+    for (int m = 0; m <= l - 1; ++m) {
+      T a = T(2 * l - 1) * rsqrt_int<T>((l + m) * (l - m));
+      T ar = a * z * re0[m], ai = a * z * im0[m];
+      if (m <= l - 2) {
+        T b = sqrt_ratio<T>((l + m - 1) * (l - m - 1), (l + m) * (l - m));
+        ar -= b * r2 * re1[m]; ai -= b * r2 * im1[m];
+      }
+      nre[m] = ar; nim[m] = ai;
+    }
+    T f = -sqrt_ratio<T>(2 * l - 1, 2 * l);
+    T tr = f * (x * dre - y * dim), ti = f * (x * dim + y * dre);
+    dre = tr; dim = ti;
+    nre[l] = dre; nim[l] = dim;
+    for (int m = 0; m <= l; ++m) {
+      if (m <= l - 1) { re1[m] = re0[m]; im1[m] = im0[m]; }
+      re0[m] = nre[m]; im0[m] = nim[m];
+    }
+    row_cb(l, re0, im0);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 1. scale charges, bin atoms into leaves, moments Q, D, T (FP64 partials)
+// ---------------------------------------------------------------------------
+template <typename XT>
+__global__ void k_bin(const XT *__restrict__ x, int64_t N, double L, int nb, const double *__restrict__ lam,
+                      const double *__restrict__ qA, const double *__restrict__ dq, const int *__restrict__ site_of,
+                      int *__restrict__ leaf_of, int *__restrict__ slot, int *__restrict__ leaf_count,
+                      double *__restrict__ qt, double *__restrict__ mom_part) {
+  double m[5] = {0, 0, 0, 0, 0};
+  const double c = 0.5 * L;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    double p[3];
+    for (int a = 0; a < 3; ++a) {
+      double v = (double)x[3 * i + a];
+      v -= floor(v / L) * L;
+      if (v >= L) v -= L;
+      if (v < 0.0) v = 0.0;
+      p[a] = v;
+    }
+    int s = site_of[i];
+    double q = qA[i] + (s >= 0 ? lam[s] * dq[i] : 0.0);
+    qt[i] = q;
+    int ix = min((int)(p[0] / L * nb), nb - 1), iy = min((int)(p[1] / L * nb), nb - 1),
+        iz = min((int)(p[2] / L * nb), nb - 1);
+    int leaf = (int)d_morton(ix, iy, iz);
+    leaf_of[i] = leaf;
+    slot[i] = atomicAdd(&leaf_count[leaf], 1);
+    double ax = p[0] - c, ay = p[1] - c, az = p[2] - c;
+    m[0] += q; m[1] += q * ax; m[2] += q * ay; m[3] += q * az; m[4] += q * (ax * ax + ay * ay + az * az);
+  }
+  __shared__ double red[5][32];
+  for (int k = 0; k < 5; ++k) {
+    double v = m[k];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffff, v, o);
+    if ((threadIdx.x & 31) == 0) red[k][threadIdx.x >> 5] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 5) {
+    double v = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[threadIdx.x][w];
+    mom_part[(size_t)blockIdx.x * 5 + threadIdx.x] = v;
+  }
+}
+
+// deterministic reduction of per-block partials: out[k] = sum_b part[b*nk + k]
+__global__ void k_reduce_partials(const double *__restrict__ part, int nblocks, int nk, double *__restrict__ out,
+                                  double scale) {
+  int k = blockIdx.x;
+  double v = 0;
+  for (int b = threadIdx.x; b < nblocks; b += blockDim.x) v += part[(size_t)b * nk + k];
+  __shared__ double red[32];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffff, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+    out[k] = s * scale;
+  }
+}
+
+// exclusive scan of leaf counts (single block)
+__global__ void k_scan(const int *__restrict__ cnt, int n, int *__restrict__ start) {
+  __shared__ int sums[1024];
+  int t = threadIdx.x, per = (n + blockDim.x - 1) / blockDim.x;
+  int b = t * per, e = min(n, b + per), s = 0;
+  for (int i = b; i < e; ++i) s += cnt[i];
+  sums[t] = s;
+  __syncthreads();
+  for (int o = 1; o < (int)blockDim.x; o <<= 1) {
+    int v = (t >= o) ? sums[t - o] : 0;
+    __syncthreads();
+    sums[t] += v;
+    __syncthreads();
+  }
+  int run = sums[t] - s;
+  for (int i = b; i < e; ++i) { start[i] = run; run += cnt[i]; }
+  if (t == blockDim.x - 1) start[n] = sums[t];
+}
+
+template <typename T, typename XT>
+__global__ void k_scatter(const XT *__restrict__ x, int64_t N, double L, int nb, const int *__restrict__ leaf_of,
+                          const int *__restrict__ slot, const int *__restrict__ leaf_start,
+                          const double *__restrict__ qt, typename V4<T>::type *__restrict__ part_tmp,
+                          int *__restrict__ perm_tmp) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  int leaf = leaf_of[i];
+  int pos = leaf_start[leaf] + slot[i];
+  int ix = (int)d_compact(leaf), iy = (int)d_compact(leaf >> 1), iz = (int)d_compact(leaf >> 2);
+  double s = L / nb;
+  double p[3];
+  for (int a = 0; a < 3; ++a) {
+    double v = (double)x[3 * i + a];
+    v -= floor(v / L) * L;
+    if (v >= L) v -= L;
+    if (v < 0.0) v = 0.0;
+    p[a] = v;
+  }
+  typename V4<T>::type o;
+  o.x = (T)(p[0] - (ix + 0.5) * s);
+  o.y = (T)(p[1] - (iy + 0.5) * s);
+  o.z = (T)(p[2] - (iz + 0.5) * s);
+  o.w = (T)qt[i];
+  part_tmp[pos] = o;
+  perm_tmp[pos] = (int)i;
+}
+
+// Order the atoms of every leaf by original index (deterministic layout).
+template <typename T>
+__global__ void k_leaf_sort(int nleaf, const int *__restrict__ leaf_start, const typename V4<T>::type *__restrict__ part_tmp,
+                            const int *__restrict__ perm_tmp, typename V4<T>::type *__restrict__ part,
+                            int *__restrict__ perm, int *__restrict__ inv_perm) {
+  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= nleaf) return;
+  int b = leaf_start[warp], e = leaf_start[warp + 1];
+  for (int a = b + lane; a < e; a += 32) {
+    int key = perm_tmp[a], rank = 0;
+    for (int j = b; j < e; ++j) rank += (perm_tmp[j] < key);
+    part[b + rank] = part_tmp[a];
+    perm[b + rank] = key;
+    inv_perm[key] = b + rank;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 2. P2M: one warp per leaf, lanes = atoms, warp reductions per coefficient.
+//    M^_lm = sum_i q_i conj(R_lm(u_i)), u = (x - c)/s
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_p2m(int nleaf, int P, int ld, T inv_s, const int *__restrict__ leaf_start,
+                      const typename V4<T>::type *__restrict__ part, T *__restrict__ M) {
+  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= nleaf) return;
+  int b = leaf_start[warp], e = leaf_start[warp + 1];
+  T *out = M + (size_t)warp * ld;
+  // lane k owns output coefficients k, k+32, ...
+  T acc[(kMaxOrder + 1) * (kMaxOrder + 1) / 32 + 2];
+  const int K = (P + 1) * (P + 1);
+  for (int k = 0; k < (K + 31) / 32; ++k) acc[k] = T(0);
+  for (int base = b; base < e; base += 32) {
+    int a = base + lane;
+    bool valid = a < e;
+    typename V4<T>::type pt = valid ? part[a] : typename V4<T>::type{0, 0, 0, 0};
+    T q = valid ? pt.w : T(0);
+    scaled_harmonics_rows<T, kMaxOrder>(P, pt.x * inv_s, pt.y * inv_s, pt.z * inv_s, [&](int l, const T *re, const T *im) {
+      for (int m = 0; m <= l; ++m) {
+        T vr = q * re[m], vi = -q * im[m];  // conj
+        for (int o = 16; o > 0; o >>= 1) {
+          vr += __shfl_xor_sync(0xffffffff, vr, o);
+          vi += __shfl_xor_sync(0xffffffff, vi, o);
+        }
+        int kr = (m == 0) ? l * l : l * l + 2 * m - 1;
+        if ((kr & 31) == lane) acc[kr >> 5] += vr;
+        if (m > 0 && ((kr + 1) & 31) == lane) acc[(kr + 1) >> 5] += vi;
+      }
+    });
+  }
+  for (int k = lane, j = 0; k < ld; k += 32, ++j) out[k] = (k < K) ? acc[j] : T(0);
+}
+
+// ---------------------------------------------------------------------------
+// 3. Gather-GEMM for M2M, L2L and (SIMT) M2L.  A tile of TR output rows shares
+//    one operator per term; out[row] (+)= sum_terms op[term] * in[src(row, term)].
+// ---------------------------------------------------------------------------
+struct GemmMap {
+  int kind;        // 0 = M2M, 1 = L2L, 2 = M2L
+  int level;       // level of the output rows
+  int nbox;        // boxes at the output level
+  const int *list; // M2L: [8][189] offset ids
+  const int *off;  // M2L: [316][3]
+};
+
+constexpr int TR = 32;   // rows per tile
+constexpr int TK = 16;   // input coefficients per smem chunk
+
+template <typename T, int NC>
+__global__ void __launch_bounds__(256) k_gather_gemm(GemmMap mp, int K, int ld, const T *__restrict__ in,
+                                                     T *__restrict__ out, const T *__restrict__ ops) {
+  // tile t: for M2M rows = parents [t*TR, ...); for L2L/M2L rows = boxes with a
+  // fixed child index c, i.e. 8*P + c for P in [tp*TR, ...)
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *As = reinterpret_cast<T *>(smem_raw);      // [TR][TK]
+  T *Bs = As + TR * TK;                          // [TK][ld]
+  __shared__ int src[TR];
+  const int tid = threadIdx.x;
+  const int tg = tid >> 5;        // 8 row groups of 4 rows
+  const int cg = tid & 31;        // column lane
+  int c = 0, tp = blockIdx.x;
+  int nrow_par;  // number of "parent-indexed" rows
+  if (mp.kind == 0) { nrow_par = mp.nbox; }
+  else { nrow_par = mp.nbox / 8; c = blockIdx.x % 8; tp = blockIdx.x / 8; }
+  const int row0 = tp * TR;
+  const int ncols = (K + 31) / 32;  // <= NC
+  T acc[4][NC];
+  for (int r = 0; r < 4; ++r)
+    for (int j = 0; j < NC; ++j) acc[r][j] = T(0);
+  const int nterms = (mp.kind == 0) ? 8 : (mp.kind == 1 ? 1 : kListLen);
+  const int side = 1 << mp.level;
+  for (int term = 0; term < nterms; ++term) {
+    const T *op;
+    if (tid < TR) {
+      int P = row0 + tid, s = -1;
+      if (P < nrow_par) {
+        if (mp.kind == 0) s = 8 * P + term;            // child of parent P
+        else if (mp.kind == 1) s = P;                  // parent of child 8P+c
+        else {
+          int box = 8 * P + c;
+          int bx = (int)d_compact(box), by = (int)d_compact(box >> 1), bz = (int)d_compact(box >> 2);
+          int oid = mp.list[c * kListLen + term];
+          int gx = bx - mp.off[oid * 3 + 0], gy = by - mp.off[oid * 3 + 1], gz = bz - mp.off[oid * 3 + 2];
+          s = (int)d_morton(wrapi(gx, side), wrapi(gy, side), wrapi(gz, side));
+        }
+      }
+      src[tid] = s;
+    }
+    if (mp.kind == 0) op = ops + (size_t)term * K * K;
+    else if (mp.kind == 1) op = ops + (size_t)c * K * K;
+    else op = ops + (size_t)mp.list[c * kListLen + term] * K * K;
+    __syncthreads();
+    for (int k0 = 0; k0 < K; k0 += TK) {
+      // A chunk: TR rows x TK inputs
+      for (int i = tid; i < TR * TK; i += blockDim.x) {
+        int r = i / TK, kk = i % TK;
+        int s = src[r];
+        As[i] = (s >= 0 && k0 + kk < K) ? in[(size_t)s * ld + k0 + kk] : T(0);
+      }
+      // B chunk: op[out][k0 + kk] -> Bs[kk][out]
+      for (int i = tid; i < TK * K; i += blockDim.x) {
+        int o = i / TK, kk = i % TK;
+        Bs[kk * ld + o] = (k0 + kk < K) ? op[(size_t)o * K + k0 + kk] : T(0);
+      }
+      __syncthreads();
+#pragma unroll 4
+      for (int kk = 0; kk < TK; ++kk) {
+        T a[4];
+        for (int r = 0; r < 4; ++r) a[r] = As[(tg * 4 + r) * TK + kk];
+#pragma unroll
+        for (int j = 0; j < NC; ++j) {
+          if (j < ncols) {
+            int col = cg + 32 * j;
+            T bv = (col < K) ? Bs[kk * ld + col] : T(0);
+            for (int r = 0; r < 4; ++r) acc[r][j] += a[r] * bv;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int r = 0; r < 4; ++r) {
+    int P = row0 + tg * 4 + r;
+    if (P >= nrow_par) continue;
+    int orow = (mp.kind == 0) ? P : 8 * P + c;
+    T *o = out + (size_t)orow * ld;
+#pragma unroll
+    for (int j = 0; j < NC; ++j) {
+      int col = cg + 32 * j;
+      if (j < ncols && col < K) {
+        if (mp.kind == 1) o[col] += acc[r][j];
+        else o[col] = acc[r][j];
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 4. Root lattice operator (FP64): L^_root = Lambda M^_root, with the monopole
+//    and dipole of the root multipole taken from the FP64 moments.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_lattice(int K, int ld, double L, const double *__restrict__ lat, const double *__restrict__ mom,
+                          const T *__restrict__ Mroot, T *__restrict__ Lroot) {
+  extern __shared__ double ms[];
+  for (int k = threadIdx.x; k < K; k += blockDim.x) ms[k] = (double)Mroot[k];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    // monopole and dipole of the root multipole from the FP64 moments:
+    // M_00 = Q, M_10 = D_z, M_11 = conj(-(D_x + i D_y)/2); normalised by L^l and
+    // scaled by c_10 = 1, c_11 = sqrt(2)
+    ms[0] = mom[0];
+    if (K > 3) {
+      const double r2 = 0.70710678118654752440;
+      ms[1] = mom[3] / L;
+      ms[2] = -r2 * mom[1] / L;
+      ms[3] = r2 * mom[2] / L;
+    }
+  }
+  __syncthreads();
+  for (int r = threadIdx.x; r < K; r += blockDim.x) {
+    double s = 0;
+    for (int k = 0; k < K; ++k) s += lat[(size_t)r * K + k] * ms[k];
+    Lroot[r] = (T)s;
+  }
+  for (int r = K + threadIdx.x; r < ld; r += blockDim.x) Lroot[r] = T(0);
+}
+
+// ---------------------------------------------------------------------------
+// 5. L2P: one warp per leaf; phi_far and grad phi_far per sorted atom (f = 1).
+//    phi = (1/s) sum L^_lm conj(R_lm(u)), grad = (1/s^2) sum G^_lm conj(R_lm(u)).
+// ---------------------------------------------------------------------------
+// Gradient coefficients in the device basis (degree P-1) from the local c:
+//   Gz_{l,m} = c_{l+1,m} sqrt((l+1+m)(l+1-m))
+//   Gx_{l,m} = 1/2 (c_{l+1,m-1} sqrt((l-m+2)(l-m+1)) - c_{l+1,m+1} sqrt((l+m+2)(l+m+1)))
+//   Gy_{l,m} = i/2 (c_{l+1,m+1} sqrt((l+m+2)(l+m+1)) + c_{l+1,m-1} sqrt((l-m+2)(l-m+1)))
+// (from d/dz R_lm = R_{l-1,m}, d/dx R_lm = (R_{l-1,m+1} - R_{l-1,m-1})/2,
+//  d/dy R_lm = -i (R_{l-1,m-1} + R_{l-1,m+1})/2 and the basis scale ratios).
+template <typename T>
+__device__ __forceinline__ void gradient_row_coeffs(int P, const T *c, T *cx, T *cy, T *cz) {
+  auto get = [&](int l, int m, T &re, T &im) {
+    if (l < 0 || m > l || -m > l) { re = T(0); im = T(0); return; }
+    int am = m < 0 ? -m : m;
+    if (am == 0) { re = c[l * l]; im = T(0); }
+    else { re = c[l * l + 2 * am - 1]; im = c[l * l + 2 * am]; }
+    if (m < 0) { im = -im; if (am & 1) { re = -re; im = -im; } }
+  };
+  for (int l = 0; l <= P - 1; ++l)
+    for (int m = 0; m <= l; ++m) {
+      T zr, zi, ar, ai, br, bi;
+      get(l + 1, m, zr, zi);
+      get(l + 1, m - 1, ar, ai);
+      get(l + 1, m + 1, br, bi);
+      T fz = sqrt(T((l + 1 + m) * (l + 1 - m)));
+      T fa = sqrt(T((l - m + 2) * (l - m + 1))), fb = sqrt(T((l + m + 2) * (l + m + 1)));
+      zr *= fz; zi *= fz; ar *= fa; ai *= fa; br *= fb; bi *= fb;
+      T xr = T(0.5) * (ar - br), xi = T(0.5) * (ai - bi);
+      T yr = T(-0.5) * (bi + ai), yi = T(0.5) * (br + ar);
+      if (m == 0) { cz[l * l] = zr; cx[l * l] = xr; cy[l * l] = yr; }
+      else {
+        int k = l * l + 2 * m - 1;
+        cz[k] = zr; cz[k + 1] = zi; cx[k] = xr; cx[k + 1] = xi; cy[k] = yr; cy[k + 1] = yi;
+      }
+    }
+}
+
+template <typename T>
+__global__ void k_l2p(int nleaf, int P, int ld, T s, const int *__restrict__ leaf_start,
+                      const typename V4<T>::type *__restrict__ part, const T *__restrict__ Lleaf,
+                      T *__restrict__ phi, T *__restrict__ grad) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int K = (P + 1) * (P + 1);
+  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  T *c = reinterpret_cast<T *>(smem_raw) + (size_t)wib * 4 * K;
+  T *cx = c + K, *cy = cx + K, *cz = cy + K;
+  int warp = blockIdx.x * (blockDim.x >> 5) + wib;
+  if (warp >= nleaf) return;
+  const T *Lv = Lleaf + (size_t)warp * ld;
+  for (int k = lane; k < K; k += 32) c[k] = Lv[k];
+  __syncwarp();
+  if (lane == 0) gradient_row_coeffs<T>(P, c, cx, cy, cz);
+  __syncwarp();
+  int b = leaf_start[warp], e = leaf_start[warp + 1];
+  T inv_s = T(1) / s;
+  for (int a = b + lane; a < e; a += 32) {
+    typename V4<T>::type pt = part[a];
+    T f = 0, gx = 0, gy = 0, gz = 0;
+    scaled_harmonics_rows<T, kMaxOrder>(P, pt.x * inv_s, pt.y * inv_s, pt.z * inv_s, [&](int l, const T *re, const T *im) {
+      // sum over m of X_lm conj(R_lm) = X_l0 R_l0 + 2 sum_{m>0} (Xr Rr + Xi Ri)
+      T sf = c[l * l] * re[0];
+      T sx = (l < P) ? cx[l * l] * re[0] : T(0), sy = (l < P) ? cy[l * l] * re[0] : T(0),
+        sz = (l < P) ? cz[l * l] * re[0] : T(0);
+      for (int m = 1; m <= l; ++m) {
+        int k = l * l + 2 * m - 1;
+        sf += T(2) * (c[k] * re[m] + c[k + 1] * im[m]);
+        if (l < P) {
+          sx += T(2) * (cx[k] * re[m] + cx[k + 1] * im[m]);
+          sy += T(2) * (cy[k] * re[m] + cy[k + 1] * im[m]);
+          sz += T(2) * (cz[k] * re[m] + cz[k + 1] * im[m]);
+        }
+      }
+      f += sf; gx += sx; gy += sy; gz += sz;
+    });
+    phi[a] = f * inv_s;
+    grad[3 * (size_t)a + 0] = gx * inv_s * inv_s;
+    grad[3 * (size_t)a + 1] = gy * inv_s * inv_s;
+    grad[3 * (size_t)a + 2] = gz * inv_s * inv_s;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 6. P2P near field + dipole/background term + outputs.  One block per target
+//    leaf; threads = (target, source chunk) pairs; sources of the 27 neighbour
+//    leaves (periodic images) staged in shared memory relative to the target
+//    leaf centre.  Writes forces (original order), per-block energy partials,
+//    and the total potential phi~ back into phi_s (sorted order).
+// ---------------------------------------------------------------------------
+constexpr int P2P_THREADS = 128;
+
+__device__ __forceinline__ double rinv(double r2) { return 1.0 / sqrt(r2); }
+// hardware reciprocal square root refined by one Newton-Raphson step
+// y' = y (3 - r2 y^2) / 2, which roughly squares the relative error
+__device__ __forceinline__ float rinv(float r2) {
+  float y = rsqrtf(r2);
+  return y * fmaf(-0.5f * r2, y * y, 1.5f);
+}
+constexpr int P2P_MAXSRC = 2048;
+
+template <typename T, typename FT>
+__global__ void __launch_bounds__(P2P_THREADS) k_p2p(int nb, double L, double fcoul, const int *__restrict__ leaf_start,
+                                                     const typename V4<T>::type *__restrict__ part,
+                                                     const int *__restrict__ perm, const double *__restrict__ mom,
+                                                     T *__restrict__ phi_s, const T *__restrict__ grad_s,
+                                                     FT *__restrict__ forces, double *__restrict__ energy_part) {
+  using V = typename V4<T>::type;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V *src = reinterpret_cast<V *>(smem_raw);
+  __shared__ int nb_start[27], nb_cnt[27], nb_pre[28];
+  __shared__ T red[P2P_THREADS][4];
+  __shared__ double ered[P2P_THREADS / 32];
+  const int leaf = blockIdx.x;
+  const int tid = threadIdx.x;
+  const T s = (T)(L / nb);
+  const int ix = (int)d_compact(leaf), iy = (int)d_compact(leaf >> 1), iz = (int)d_compact(leaf >> 2);
+  if (tid < 27) {
+    int dx = tid % 3 - 1, dy = (tid / 3) % 3 - 1, dz = tid / 9 - 1;
+    int n = (int)d_morton(wrapi(ix + dx, nb), wrapi(iy + dy, nb), wrapi(iz + dz, nb));
+    nb_start[tid] = leaf_start[n];
+    nb_cnt[tid] = leaf_start[n + 1] - leaf_start[n];
+  }
+  __syncthreads();
+  if (tid == 0) {
+    nb_pre[0] = 0;
+    for (int k = 0; k < 27; ++k) nb_pre[k + 1] = nb_pre[k] + nb_cnt[k];
+  }
+  __syncthreads();
+  const int tb = leaf_start[leaf], te = leaf_start[leaf + 1], nt = te - tb;
+  const int nsrc_total = nb_pre[27];
+  // centre of the system box relative to this leaf centre, for the r^2 term
+  const double Q = mom[0], Dx = mom[1], Dy = mom[2], Dz = mom[3], Tm = mom[4];
+  const double vol = L * L * L, c2 = 2.0 * kPi / (3.0 * vol);
+  const double lcx = (ix + 0.5) * (L / nb) - 0.5 * L, lcy = (iy + 0.5) * (L / nb) - 0.5 * L,
+               lcz = (iz + 0.5) * (L / nb) - 0.5 * L;
+  double e_acc = 0.0;
+  // process targets in groups so that (target, chunk) pairs fill the block
+  int nchunk = P2P_THREADS / max(1, min(nt, P2P_THREADS));
+  int tgroup = P2P_THREADS / nchunk;
+  for (int t0 = 0; t0 < nt; t0 += tgroup) {
+    int ta = t0 + tid % tgroup, ck = tid / tgroup;
+    bool tv = ta < nt;
+    V me = tv ? part[tb + ta] : V{0, 0, 0, 0};
+    T f = 0, gx = 0, gy = 0, gz = 0;
+    for (int s0 = 0; s0 < nsrc_total; s0 += P2P_MAXSRC) {
+      int ns = min(P2P_MAXSRC, nsrc_total - s0);
+      __syncthreads();
+      for (int i = tid; i < ns; i += P2P_THREADS) {
+        int g = s0 + i, k = 0;
+        while (nb_pre[k + 1] <= g) ++k;
+        V v = part[nb_start[k] + (g - nb_pre[k])];
+        int dx = k % 3 - 1, dy = (k / 3) % 3 - 1, dz = k / 9 - 1;
+        v.x += dx * s; v.y += dy * s; v.z += dz * s;
+        src[i] = v;
+      }
+      __syncthreads();
+      // self: neighbour k = 13 is the leaf itself, at source index nb_pre[13] + ta
+      int self = (nb_pre[13] + ta) - s0;
+      int per = (ns + nchunk - 1) / nchunk;
+      int jb = ck * per, je = min(ns, jb + per);
+      if (tv) {
+        for (int j = jb; j < je; ++j) {
+          V v = src[j];
+          T rx = me.x - v.x, ry = me.y - v.y, rz = me.z - v.z;
+          T r2 = rx * rx + ry * ry + rz * rz;
+          if (j == self) continue;
+          T ri = rinv(r2);
+          T qr = v.w * ri;
+          f += qr;
+          T g3 = qr * ri * ri;
+          gx -= g3 * rx; gy -= g3 * ry; gz -= g3 * rz;
+        }
+      }
+    }
+    red[tid][0] = f; red[tid][1] = gx; red[tid][2] = gy; red[tid][3] = gz;
+    __syncthreads();
+    if (ck == 0 && tv) {
+      for (int c2i = 1; c2i < nchunk; ++c2i) {
+        int o = tid + c2i * tgroup;
+        f += red[o][0]; gx += red[o][1]; gy += red[o][2]; gz += red[o][3];
+      }
+      int a = tb + ta;
+      double ff = (double)f + (double)phi_s[a];
+      double g0 = (double)gx + (double)grad_s[3 * (size_t)a], g1 = (double)gy + (double)grad_s[3 * (size_t)a + 1],
+             g2 = (double)gz + (double)grad_s[3 * (size_t)a + 2];
+      // dipole / background term of the periodic kernel: (2 pi/3V) sum_j q_j |x_i - x_j|^2
+      double ax = lcx + (double)me.x, ay = lcy + (double)me.y, az = lcz + (double)me.z;
+      ff += c2 * (Q * (ax * ax + ay * ay + az * az) - 2.0 * (ax * Dx + ay * Dy + az * Dz) + Tm);
+      g0 += 2.0 * c2 * (Q * ax - Dx); g1 += 2.0 * c2 * (Q * ay - Dy); g2 += 2.0 * c2 * (Q * az - Dz);
+      ff *= fcoul; g0 *= fcoul; g1 *= fcoul; g2 *= fcoul;
+      double q = (double)me.w;
+      phi_s[a] = (T)ff;
+      e_acc += 0.5 * q * ff;
+      int io = perm[a];
+      if (forces) {
+        forces[3 * (size_t)io + 0] = (FT)(-q * g0);
+        forces[3 * (size_t)io + 1] = (FT)(-q * g1);
+        forces[3 * (size_t)io + 2] = (FT)(-q * g2);
+      }
+    }
+    __syncthreads();
+  }
+  for (int o = 16; o > 0; o >>= 1) e_acc += __shfl_xor_sync(0xffffffff, e_acc, o);
+  if ((tid & 31) == 0) ered[tid >> 5] = e_acc;
+  __syncthreads();
+  if (tid == 0) {
+    double v = 0;
+    for (int w = 0; w < P2P_THREADS / 32; ++w) v += ered[w];
+    energy_part[leaf] = v;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 7. Per-site HI correction (FP64).  One warp per site.  For every ordered pair
+//    (i, j) of the site: A(r) = sum_{|n|_inf<=1} 1/|r+nL| (without r+nL = 0)
+//    + H(r) + (2 pi/3V)|r|^2, r = minimum image of x_i - x_j, H from the
+//    lattice coefficients (degree adapted to |r|).  This is the paper's
+//    C_P2P + C_L + C_D for a two-form site (first shell direct, lattice part,
+//    dipole/background part).  Then
+//      k_s = f sum D_i D_j A_ij,  g_s = sum D_i phi~_i,
+//      dE/dlam = g + (1/2 - lam) k,  E += 1/2 lam(1-lam) k,
+//      F_i -= lam(1-lam) f sum_{j != i} D_i D_j grad A(r_ij).
+// ---------------------------------------------------------------------------
+constexpr int kMaxSiteAtoms = 64;
+
+template <typename T, typename XT, typename FT>
+__global__ void k_site(int S, double L, double fcoul, int Pmax, const int *__restrict__ site_ptr,
+                       const int *__restrict__ site_atoms, const XT *__restrict__ x, const double *__restrict__ dq,
+                       const double *__restrict__ lam, const int *__restrict__ inv_perm, const T *__restrict__ phi_s,
+                       const double *__restrict__ eta, const double *__restrict__ eta_x,
+                       const double *__restrict__ eta_y, const double *__restrict__ eta_z,
+                       double *__restrict__ dEdl, double *__restrict__ site_energy, FT *__restrict__ forces) {
+  __shared__ double fsh[4][kMaxSiteAtoms][3];
+  const int wib = threadIdx.x >> 5;
+  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= S) return;
+  const int b = site_ptr[warp], e = site_ptr[warp + 1], n = e - b;
+  const double V = L * L * L, c2 = 2.0 * kPi / (3.0 * V);
+  const double lw = lam[warp] * (1.0 - lam[warp]);
+  for (int k = lane; k < n * 3; k += 32) fsh[wib][k / 3][k % 3] = 0.0;
+  __syncwarp();
+  double ksum = 0.0, gsum = 0.0;
+  for (int pi = lane; pi < n * n; pi += 32) {
+    const int ia = pi / n, ja = pi % n;
+    const int i = site_atoms[b + ia], j = site_atoms[b + ja];
+    const double Di = dq[i], Dj = dq[j];
+    double r[3];
+    for (int a = 0; a < 3; ++a) {
+      double v = (double)x[3 * (size_t)i + a] - (double)x[3 * (size_t)j + a];
+      v -= L * rint(v / L);
+      r[a] = (ia == ja) ? 0.0 : v;
+    }
+    double A = 0.0, g0 = 0.0, g1 = 0.0, g2 = 0.0;
+    for (int nx = -1; nx <= 1; ++nx)
+      for (int ny = -1; ny <= 1; ++ny)
+        for (int nz = -1; nz <= 1; ++nz) {
+          if (ia == ja && nx == 0 && ny == 0 && nz == 0) continue;
+          double d0 = r[0] + nx * L, d1 = r[1] + ny * L, d2 = r[2] + nz * L;
+          double ri = 1.0 / sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+          A += ri;
+          double g3 = ri * ri * ri;
+          g0 -= g3 * d0; g1 -= g3 * d1; g2 -= g3 * d2;
+        }
+    double u[3] = {r[0] / L, r[1] / L, r[2] / L};
+    double un = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    int P = 0;
+    if (un > 0.0) {
+      int need = (int)ceil(-39.2 / log(un / 1.9)) + 1;  // (|u|/1.9)^P < 1e-17
+      P = min(Pmax, max(4, need));
+    }
+    double H = 0, hx = 0, hy = 0, hz = 0;
+    // H lives on even degrees; its gradient coefficients on odd degrees (< P)
+    harmonics_rows<double, kSiteDegree>(P, u[0], u[1], u[2], [&](int l, const double *re, const double *im) {
+      if (!(l & 1)) {
+        double sf = eta[l * l] * re[0];
+        for (int m = 1; m <= l; ++m) {
+          int k = l * l + 2 * m - 1;
+          sf += 2.0 * (eta[k] * re[m] + eta[k + 1] * im[m]);
+        }
+        H += sf;
+      } else if (l < P) {
+        double sx = eta_x[l * l] * re[0], sy = eta_y[l * l] * re[0], sz = eta_z[l * l] * re[0];
+        for (int m = 1; m <= l; ++m) {
+          int k = l * l + 2 * m - 1;
+          sx += 2.0 * (eta_x[k] * re[m] + eta_x[k + 1] * im[m]);
+          sy += 2.0 * (eta_y[k] * re[m] + eta_y[k + 1] * im[m]);
+          sz += 2.0 * (eta_z[k] * re[m] + eta_z[k + 1] * im[m]);
+        }
+        hx += sx; hy += sy; hz += sz;
+      }
+    });
+    A += H / L + c2 * (r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+    g0 += hx / (L * L) + 2.0 * c2 * r[0];
+    g1 += hy / (L * L) + 2.0 * c2 * r[1];
+    g2 += hz / (L * L) + 2.0 * c2 * r[2];
+    ksum += Di * Dj * A;
+    if (ia == ja) gsum += Di * (double)phi_s[inv_perm[i]];
+    else {
+      double w = lw * fcoul * Di * Dj;
+      atomicAdd(&fsh[wib][ia][0], -w * g0);
+      atomicAdd(&fsh[wib][ia][1], -w * g1);
+      atomicAdd(&fsh[wib][ia][2], -w * g2);
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    ksum += __shfl_xor_sync(0xffffffff, ksum, o);
+    gsum += __shfl_xor_sync(0xffffffff, gsum, o);
+  }
+  __syncwarp();
+  const double k = fcoul * ksum;  // phi_s already carries f
+  if (lane == 0) {
+    const double l0 = lam[warp];
+    if (dEdl) dEdl[warp] = gsum + (0.5 - l0) * k;
+    site_energy[warp] = 0.5 * lw * k;
+  }
+  if (forces)
+    for (int k3 = lane; k3 < n * 3; k3 += 32) {
+      int ia = k3 / 3, a = k3 % 3;
+      int i = site_atoms[b + ia];
+      forces[3 * (size_t)i + a] = (FT)((double)forces[3 * (size_t)i + a] + fsh[wib][ia][a]);
+    }
+}
+
+__global__ void k_final_energy(const double *__restrict__ epart, int nb, const double *__restrict__ site_e, int S,
+                               double *__restrict__ out) {
+  double v = 0;
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) v += epart[i];
+  for (int i = threadIdx.x; i < S; i += blockDim.x) v += site_e[i];
+  __shared__ double red[32];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffff, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+    *out = s;
+  }
+}
+
+template <typename T>
+__global__ void k_unpermute_phi(int64_t N, const int *__restrict__ inv_perm, const T *__restrict__ phi_s,
+                                double *__restrict__ phi) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < N) phi[i] = (double)phi_s[inv_perm[i]];
+}
+
+// ---------------------------------------------------------------------------
+// orchestration
+// ---------------------------------------------------------------------------
+static const char *kStageNames[] = {"bin", "sort", "p2m", "m2m", "lattice", "m2l", "l2l", "l2p", "p2p", "site"};
+const char *stage_name(int i) { return (i >= 0 && i < 10) ? kStageNames[i] : "?"; }
+int num_stages() { return 10; }
+
+#define MAHI_CK(call)                                   \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return e_;                   \
+  } while (0)
+
+template <typename T, int NC>
+static cudaError_t launch_gemm_nc(const GemmMap &mp, int grid, int K, int ld, const T *in, T *out, const T *ops,
+                                  cudaStream_t st) {
+  size_t sm = sizeof(T) * (TR * TK + TK * (size_t)ld);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_gather_gemm<T, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr = true;
+  }
+  k_gather_gemm<T, NC><<<grid, 256, sm, st>>>(mp, K, ld, in, out, ops);
+  return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t launch_gemm(const GemmMap &mp, int K, int ld, const T *in, T *out, const T *ops, cudaStream_t st) {
+  int rows_par = (mp.kind == 0) ? mp.nbox : mp.nbox / 8;
+  int tiles = (rows_par + TR - 1) / TR;
+  int grid = (mp.kind == 0) ? tiles : tiles * 8;
+  int nc = (K + 31) / 32;
+  if (nc <= 1) return launch_gemm_nc<T, 1>(mp, grid, K, ld, in, out, ops, st);
+  if (nc <= 2) return launch_gemm_nc<T, 2>(mp, grid, K, ld, in, out, ops, st);
+  if (nc <= 3) return launch_gemm_nc<T, 3>(mp, grid, K, ld, in, out, ops, st);
+  if (nc <= 4) return launch_gemm_nc<T, 4>(mp, grid, K, ld, in, out, ops, st);
+  if (nc <= 6) return launch_gemm_nc<T, 6>(mp, grid, K, ld, in, out, ops, st);
+  if (nc <= 8) return launch_gemm_nc<T, 8>(mp, grid, K, ld, in, out, ops, st);
+  if (nc <= 11) return launch_gemm_nc<T, 11>(mp, grid, K, ld, in, out, ops, st);
+  if (nc <= 14) return launch_gemm_nc<T, 14>(mp, grid, K, ld, in, out, ops, st);
+  return launch_gemm_nc<T, 20>(mp, grid, K, ld, in, out, ops, st);
+}
+
+static inline void mark(mahi_ctx *h, int stage) {
+  if (h->timing && stage < 31) {
+    cudaEventRecord(h->ev[stage], h->stream);
+    h->n_ev = stage + 1;
+  }
+}
+
+template <typename T, typename XT>
+static cudaError_t eval_t(mahi_ctx *h, const XT *x, const double *lam, double *energy, XT *forces, double *dEdl) {
+  using V = typename V4<T>::type;
+  cudaStream_t st = h->stream;
+  const int nb = 1 << h->d;
+  const int nleaf = h->nleaf;
+  const int64_t N = h->N;
+  const int K = h->K, ld = h->ld, P = h->p;
+  T *M = (T *)h->Mexp, *Lx = (T *)h->Lexp;
+  h->launches = 0;
+  mark(h, 0);
+  MAHI_CK(cudaMemsetAsync(h->leaf_count, 0, sizeof(int) * nleaf, st));
+  k_bin<XT><<<h->n_moment_blocks, 256, 0, st>>>(x, N, h->L, nb, lam, h->qA, h->dq, h->site_of, h->leaf_of, h->slot,
+                                                 h->leaf_count, h->qt, h->moments_part);
+  k_reduce_partials<<<5, 256, 0, st>>>(h->moments_part, h->n_moment_blocks, 5, h->moments, 1.0);
+  h->launches += 2;
+  mark(h, 1);
+  k_scan<<<1, 1024, 0, st>>>(h->leaf_count, nleaf, h->leaf_start);
+  int gb = (int)((N + 255) / 256);
+  k_scatter<T, XT><<<gb, 256, 0, st>>>(x, N, h->L, nb, h->leaf_of, h->slot, h->leaf_start, h->qt, (V *)h->part_tmp,
+                                       h->perm_tmp);
+  k_leaf_sort<T><<<(nleaf * 32 + 255) / 256, 256, 0, st>>>(nleaf, h->leaf_start, (const V *)h->part_tmp, h->perm_tmp,
+                                                          (V *)h->part, h->perm, h->inv_perm);
+  h->launches += 3;
+  MAHI_CK(cudaGetLastError());
+  mark(h, 2);
+  const double s_leaf = h->L / nb;
+  k_p2m<T><<<(nleaf * 32 + 127) / 128, 128, 0, st>>>(nleaf, P, ld, (T)(1.0 / s_leaf), h->leaf_start, (const V *)h->part,
+                                                   M + h->level_off[h->d] * ld);
+  h->launches += 1;
+  MAHI_CK(cudaGetLastError());
+  mark(h, 3);
+  for (int l = h->d - 1; l >= 0; --l) {
+    GemmMap mp{0, l, 1 << (3 * l), nullptr, nullptr};
+    MAHI_CK(launch_gemm<T>(mp, K, ld, M + h->level_off[l + 1] * ld, M + h->level_off[l] * ld, (const T *)h->ops_m2m,
+                           st));
+    h->launches += 1;
+  }
+  mark(h, 4);
+  k_lattice<T><<<1, 256, sizeof(double) * K, st>>>(K, ld, h->L, h->ops_lat, h->moments, M, Lx);
+  h->launches += 1;
+  MAHI_CK(cudaGetLastError());
+  mark(h, 5);
+  if (h->prec == MAHI_MIXED && h->d >= 1) {
+    int rc = tc_m2l(h);
+    if (rc != 0) return cudaErrorUnknown;
+  } else {
+    for (int l = 1; l <= h->d; ++l) {
+      GemmMap mp{2, l, 1 << (3 * l), h->m2l_list, h->m2l_off};
+      MAHI_CK(launch_gemm<T>(mp, K, ld, M + h->level_off[l] * ld, Lx + h->level_off[l] * ld, (const T *)h->ops_m2l,
+                             st));
+      h->launches += 1;
+    }
+  }
+  mark(h, 6);
+  for (int l = 1; l <= h->d; ++l) {
+    GemmMap mp{1, l, 1 << (3 * l), nullptr, nullptr};
+    MAHI_CK(launch_gemm<T>(mp, K, ld, Lx + h->level_off[l - 1] * ld, Lx + h->level_off[l] * ld, (const T *)h->ops_l2l,
+                           st));
+    h->launches += 1;
+  }
+  mark(h, 7);
+  {
+    size_t per_warp = sizeof(T) * 4 * (size_t)K;
+    int wpb = (int)std::max<size_t>(1, std::min<size_t>(4, (40 * 1024) / per_warp));
+    k_l2p<T><<<(nleaf + wpb - 1) / wpb, 32 * wpb, per_warp * wpb, st>>>(
+        nleaf, P, ld, (T)s_leaf, h->leaf_start, (const V *)h->part, Lx + h->level_off[h->d] * ld, (T *)h->phi_s,
+        (T *)h->grad_s);
+    h->launches += 1;
+    MAHI_CK(cudaGetLastError());
+  }
+  mark(h, 8);
+  {
+    static bool attr = false;
+    size_t sm = sizeof(V) * P2P_MAXSRC;
+    if (!attr) {
+      cudaFuncSetAttribute(k_p2p<T, XT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      attr = true;
+    }
+    k_p2p<T, XT><<<nleaf, P2P_THREADS, sm, st>>>(nb, h->L, coulomb_constant(), h->leaf_start, (const V *)h->part,
+                                                 h->perm, h->moments, (T *)h->phi_s, (const T *)h->grad_s, forces,
+                                                 h->energy_part);
+    h->launches += 1;
+    MAHI_CK(cudaGetLastError());
+  }
+  mark(h, 9);
+  if (h->S > 0) {
+    k_site<T, XT, XT><<<(h->S + 3) / 4, 128, 0, st>>>(h->S, h->L, coulomb_constant(), kSiteDegree, h->site_ptr,
+                                                      h->site_atoms, x, h->dq, lam, h->inv_perm, (const T *)h->phi_s,
+                                                      h->eta, h->eta_x, h->eta_y, h->eta_z, dEdl, h->site_energy,
+                                                      forces);
+    h->launches += 1;
+  }
+  if (energy) {
+    k_final_energy<<<1, 256, 0, st>>>(h->energy_part, nleaf, h->site_energy, h->S, energy);
+    h->launches += 1;
+  }
+  MAHI_CK(cudaGetLastError());
+  mark(h, 10);
+  return cudaSuccess;
+}
+
+int enqueue_eval(mahi_ctx *h, const void *x, int x_is_fp64, const double *lambda, double *energy, void *forces,
+                 double *dEdl) {
+  cudaError_t e;
+  if (h->prec == MAHI_FP64) {
+    if (x_is_fp64) e = eval_t<double, double>(h, (const double *)x, lambda, energy, (double *)forces, dEdl);
+    else e = eval_t<double, float>(h, (const float *)x, lambda, energy, (float *)forces, dEdl);
+  } else {
+    if (x_is_fp64) e = eval_t<float, double>(h, (const double *)x, lambda, energy, (double *)forces, dEdl);
+    else e = eval_t<float, float>(h, (const float *)x, lambda, energy, (float *)forces, dEdl);
+  }
+  return e == cudaSuccess ? 0 : (int)e;
+}
+
+int enqueue_potential(mahi_ctx *h, double *phi) {
+  int g = (int)((h->N + 255) / 256);
+  if (h->prec == MAHI_FP64)
+    k_unpermute_phi<double><<<g, 256, 0, h->stream>>>(h->N, h->inv_perm, (const double *)h->phi_s, phi);
+  else
+    k_unpermute_phi<float><<<g, 256, 0, h->stream>>>(h->N, h->inv_perm, (const float *)h->phi_s, phi);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+}  // namespace mahi

@@ -141,3 +141,11 @@ def test_pair_kernel_consistent_with_ewald():
         gs = sum(q[j] * oracle.pair_A(x[i] - x[j], L)[1] for j in range(12) if j != i)
         assert s == pytest.approx(p[i], rel=1e-12, abs=1e-12)
         np.testing.assert_allclose(gs, g[i], atol=1e-11)
+
+
+@pytest.mark.parametrize("neutral", [True, False])
+def test_energy_only_route_matches_potential_route(neutral):
+    x, q = _random_system(9, 500, 2.4, neutral)
+    _, _, e = oracle.ewald(x, q, 2.4, rc=0.7)
+    assert oracle.ewald_energy(x, q, 2.4, rc=0.7) == pytest.approx(e, rel=1e-12)
+    assert oracle.ewald_energy(x, q, 2.4, rc=1.1) == pytest.approx(e, rel=1e-12)

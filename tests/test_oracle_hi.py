@@ -122,3 +122,18 @@ def test_subset_targets_match_full():
     np.testing.assert_allclose(part["dEdl"], full["dEdl"], rtol=1e-12)
     for k, i in enumerate(part["targets"]):
         np.testing.assert_allclose(part["F"][k], full["F"][i], atol=1e-10)
+
+
+def test_site_terms_match_pairwise_kernel():
+    """k_s and the intra-site force sums through E(D) of the charge set D alone
+    equal the explicit pair sums with A_ij (A_ii = xi)."""
+    rng = np.random.default_rng(11)
+    L = 2.6
+    xs = np.mod(rng.uniform(0, 0.4, (6, 3)) + 1.1, L)
+    D = rng.uniform(-0.4, 0.4, 6)
+    kk, fc = hi.site_terms(xs, D, L)
+    A, G = hi.site_kernel(xs, L)
+    assert kk == pytest.approx(D @ A @ D, rel=1e-12)
+    for a in range(6):
+        ref = -sum(D[a] * D[b] * G[a, b] for b in range(6) if b != a)
+        np.testing.assert_allclose(fc[a], ref, atol=1e-10)
