@@ -49,6 +49,8 @@ def lib():
         L.oracle_ewald.argtypes = [ctypes.c_int64, dp, dp, ctypes.c_double, ctypes.c_double,
                                    ctypes.c_int64, ctypes.POINTER(ctypes.c_int64), dp, dp, dp]
         L.oracle_ewald.restype = ctypes.c_int
+        L.oracle_ewald_parts.argtypes = L.oracle_ewald.argtypes + [ctypes.c_int]
+        L.oracle_ewald_parts.restype = ctypes.c_int
         L.oracle_pair_A.argtypes = [dp, ctypes.c_double, ctypes.c_double, dp]
         L.oracle_pair_A.restype = ctypes.c_double
         L.oracle_ewald_params.argtypes = [ctypes.c_double, ctypes.c_double, dp,
@@ -78,12 +80,13 @@ def default_rc(L: float, n: int) -> float:
     return float(rcs[int(np.argmin(cost))])
 
 
-def ewald(x, q, L, rc=None, targets=None):
+def ewald(x, q, L, rc=None, targets=None, parts=3):
     """Periodic potential phi (e/nm), its gradient and the energy (e^2/nm), f = 1.
 
     phi_i = sum_j q_j A(x_i - x_j) with A(0) = xi; grad excludes the j = i term.
     With ``targets`` None all atoms are targets and the energy 1/2 sum q phi is
-    returned, otherwise energy is None."""
+    returned, otherwise energy is None.  ``parts`` = 1 (real space only), 2
+    (reciprocal space with self and background terms only) or 3 (both)."""
     x = np.ascontiguousarray(x, dtype=np.float64)
     q = np.ascontiguousarray(q, dtype=np.float64)
     n = q.shape[0]
@@ -100,8 +103,8 @@ def ewald(x, q, L, rc=None, targets=None):
     phi = np.zeros(nt)
     grad = np.zeros((nt, 3))
     e = np.zeros(1)
-    rcode = lib().oracle_ewald(n, _dp(x), _dp(q), float(L), float(rc), nt, tptr, _dp(phi), _dp(grad),
-                               _dp(e))
+    rcode = lib().oracle_ewald_parts(n, _dp(x), _dp(q), float(L), float(rc), nt, tptr, _dp(phi), _dp(grad),
+                                     _dp(e), int(parts))
     if rcode != 0:
         raise RuntimeError("oracle_ewald failed")
     return phi, grad, (float(e[0]) if targets is None else None)

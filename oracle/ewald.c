@@ -168,16 +168,27 @@ static void cells_free(cells_t *cl) { free(cl->start); free(cl->idx); }
  * x: n x 3 positions (any real values; the kernel is periodic), q: n charges.
  * Returns 0 on success.
  */
+int oracle_ewald_parts(int64_t n, const double *x, const double *q, double L, double rc, int64_t ntarget,
+                       const int64_t *targets, double *phi, double *grad, double *energy, int parts);
+
 int oracle_ewald(int64_t n, const double *x, const double *q, double L, double rc, int64_t ntarget,
                  const int64_t *targets, double *phi, double *grad, double *energy) {
+  return oracle_ewald_parts(n, x, q, L, rc, ntarget, targets, phi, grad, energy, 3);
+}
+
+/* parts: bit 0 = real-space sum, bit 1 = reciprocal-space sum and self/background
+ * terms (both = the full potential).  Used to time the two halves separately. */
+int oracle_ewald_parts(int64_t n, const double *x, const double *q, double L, double rc, int64_t ntarget,
+                       const int64_t *targets, double *phi, double *grad, double *energy, int parts) {
   double alpha; int mmax;
   oracle_ewald_params(L, rc, &alpha, &mmax);
   double V = L * L * L;
   double Qtot = 0;
   { ksum_t k = {0, 0}; for (int64_t j = 0; j < n; ++j) kadd(&k, q[j]); Qtot = kval(&k); }
   kset_t ks; kset_build(&ks, L, alpha, mmax);
-  double *Ck = malloc(ks.n * sizeof(double)), *Sk = malloc(ks.n * sizeof(double));
-  structure_factors(n, x, q, L, mmax, &ks, Ck, Sk);
+  if (!(parts & 2)) ks.n = 0;
+  double *Ck = malloc((ks.n + 1) * sizeof(double)), *Sk = malloc((ks.n + 1) * sizeof(double));
+  if (ks.n) structure_factors(n, x, q, L, mmax, &ks, Ck, Sk);
   /* wrap a private copy of the positions into [0, L) for the cell search */
   double *xw = malloc((size_t)n * 3 * sizeof(double));
   for (int64_t j = 0; j < 3 * n; ++j) {
@@ -204,7 +215,7 @@ int oracle_ewald(int64_t n, const double *x, const double *q, double L, double r
       ksum_t p = {0, 0};
       double gx = 0, gy = 0, gz = 0;
       int cx = (int)floor(xi0 / cl.cs), cy = (int)floor(xi1 / cl.cs), cz = (int)floor(xi2 / cl.cs);
-      int R = cl.reach, nc = cl.nc;
+      int R = (parts & 1) ? cl.reach : -1, nc = cl.nc;
       for (int dz = -R; dz <= R; ++dz)
         for (int dy = -R; dy <= R; ++dy)
           for (int dx = -R; dx <= R; ++dx) {
@@ -244,8 +255,10 @@ int oracle_ewald(int64_t n, const double *x, const double *q, double L, double r
         rgx += gg * ks.kx[k]; rgy += gg * ks.ky[k]; rgz += gg * ks.kz[k];
       }
       kadd(&p, pr);
-      kadd(&p, -OR_2_SQRTPI * alpha * q[i]);          /* remove erf(a r)/r self limit */
-      kadd(&p, -OR_PI * Qtot / (alpha * alpha * V));  /* neutralising background */
+      if (parts & 2) {
+        kadd(&p, -OR_2_SQRTPI * alpha * q[i]);          /* remove erf(a r)/r self limit */
+        kadd(&p, -OR_PI * Qtot / (alpha * alpha * V));  /* neutralising background */
+      }
       phi[t] = kval(&p);
       grad[3 * t] = gx + rgx; grad[3 * t + 1] = gy + rgy; grad[3 * t + 2] = gz + rgz;
     }

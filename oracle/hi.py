@@ -34,7 +34,10 @@ def scaled_charges(qA, qB, site_of, lam):
     qA = np.asarray(qA, dtype=np.float64)
     qB = np.asarray(qB, dtype=np.float64)
     site_of = np.asarray(site_of)
-    lam_atom = np.where(site_of >= 0, np.asarray(lam)[np.maximum(site_of, 0)], 0.0)
+    lam = np.asarray(lam, dtype=np.float64)
+    if lam.size == 0:
+        return qA.copy()
+    lam_atom = np.where(site_of >= 0, lam[np.maximum(site_of, 0)], 0.0)
     return qA + lam_atom * (qB - qA)
 
 

@@ -43,12 +43,25 @@ static void free_all(mahi_ctx *h) {
                   h->perm_tmp, h->inv_perm, h->part, h->part_tmp, h->Mexp, h->Lexp, h->phi_s, h->grad_s,
                   h->ops_m2m, h->ops_l2l, h->ops_m2l, h->ops_lat, h->eta, h->eta_x, h->eta_y, h->eta_z,
                   h->m2l_list, h->m2l_off, h->site_ptr, h->site_atoms, h->moments_part, h->moments,
-                  h->energy_part, h->site_energy, h->tc_ops, h->tc_units, h->tc_error, h->d_x_stage,
-                  h->d_lam_stage, h->d_E_stage, h->d_dEdl_stage, h->d_F_stage};
+                  h->energy_part, h->site_energy, h->tc_ops, h->tc_msplit, h->tc_level_off, h->tc_units, h->tc_error, h->d_x_stage,
+                  h->d_lam_stage, h->d_E_stage, h->d_dEdl_stage, h->d_F_stage, h->ops_lat_h3, h->L_h3,
+                  h->box_qd, h->phi_site, h->phi_part, h->d_level_off};
   for (void *b : bufs)
     if (b) cudaFree(b);
   for (int i = 0; i < 32; ++i)
     if (h->ev[i]) cudaEventDestroy(h->ev[i]);
+}
+
+// SIMT operator layout: transposed and zero padded, opT[term][k][n], k, n < ld.
+template <typename T>
+static cudaError_t upload_ops_t(const std::vector<std::vector<double>> &ops, int K, int ld, void **dst) {
+  std::vector<T> tmp(ops.size() * (size_t)ld * ld, T(0));
+  for (size_t t = 0; t < ops.size(); ++t)
+    for (int n = 0; n < K; ++n)
+      for (int k = 0; k < K; ++k) tmp[t * (size_t)ld * ld + (size_t)k * ld + n] = (T)ops[t][(size_t)n * K + k];
+  cudaError_t e = dalloc(dst, tmp.size() * sizeof(T));
+  if (e != cudaSuccess) return e;
+  return cudaMemcpy(*dst, tmp.data(), tmp.size() * sizeof(T), cudaMemcpyHostToDevice);
 }
 
 template <typename T>
@@ -95,6 +108,7 @@ int mahi_create(double box_L_nm, int64_t n_atoms, int32_t n_sites, int32_t order
     return MAHI_ERR_INVALID_ARG;
   if (precision != MAHI_FP64 && precision != MAHI_MIXED && precision != MAHI_MIXED_SIMT) return MAHI_ERR_INVALID_ARG;
   if (order_p > (precision == MAHI_FP64 ? kMaxOrder : kMaxOrderMixed)) return MAHI_ERR_INVALID_ARG;
+  if (precision == MAHI_MIXED && nstride(order_p) > 256) return MAHI_ERR_INVALID_ARG;  // MMA N <= 256
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
     cudaGetLastError();
@@ -106,6 +120,7 @@ int mahi_create(double box_L_nm, int64_t n_atoms, int32_t n_sites, int32_t order
   if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return MAHI_ERR_NO_DEVICE;
   if (prop.major * 10 + prop.minor != 103) return MAHI_ERR_NO_DEVICE;
 
+  if (upload_tables() != 0) return cuda_fail(cudaGetLastError(), "constant tables");
   mahi_ctx *h = new (std::nothrow) mahi_ctx();
   if (!h) return MAHI_ERR_INVALID_ARG;
   h->L = box_L_nm; h->N = n_atoms; h->S = n_sites; h->p = order_p; h->d = depth; h->prec = precision;
@@ -153,7 +168,7 @@ int mahi_create(double box_L_nm, int64_t n_atoms, int32_t n_sites, int32_t order
 
   // translation operators (host, FP64) -> device in the working precision
   const int K = h->K;
-  std::vector<std::vector<double>> m2m(8), l2l(8), m2l(kNumOffsets), lat(1);
+  std::vector<std::vector<double>> m2m(8), l2l(8), m2l(kNumOffsets), lat(1), lat3(1);
   for (int c = 0; c < 8; ++c) {
     build_m2m(order_p, c, m2m[c]);
     scale_operator(order_p, 0, m2m[c]);
@@ -167,20 +182,32 @@ int mahi_create(double box_L_nm, int64_t n_atoms, int32_t n_sites, int32_t order
   }
   build_lattice_op(order_p, lat[0]);
   scale_operator(order_p, 2, lat[0]);
+  build_lattice_op(order_p, lat3[0], false);
+  scale_operator(order_p, 2, lat3[0]);
   {
     cudaError_t e;
+    const int ldp = h->ld;
     if (f64) {
-      if ((e = upload_ops<double>(m2m, &h->ops_m2m)) != cudaSuccess) return fail(e, "ops");
-      if ((e = upload_ops<double>(l2l, &h->ops_l2l)) != cudaSuccess) return fail(e, "ops");
-      if ((e = upload_ops<double>(m2l, &h->ops_m2l)) != cudaSuccess) return fail(e, "ops");
+      if ((e = upload_ops_t<double>(m2m, K, ldp, &h->ops_m2m)) != cudaSuccess) return fail(e, "ops");
+      if ((e = upload_ops_t<double>(l2l, K, ldp, &h->ops_l2l)) != cudaSuccess) return fail(e, "ops");
+      if ((e = upload_ops_t<double>(m2l, K, ldp, &h->ops_m2l)) != cudaSuccess) return fail(e, "ops");
     } else {
-      if ((e = upload_ops<float>(m2m, &h->ops_m2m)) != cudaSuccess) return fail(e, "ops");
-      if ((e = upload_ops<float>(l2l, &h->ops_l2l)) != cudaSuccess) return fail(e, "ops");
-      if ((e = upload_ops<float>(m2l, &h->ops_m2l)) != cudaSuccess) return fail(e, "ops");
+      if ((e = upload_ops_t<float>(m2m, K, ldp, &h->ops_m2m)) != cudaSuccess) return fail(e, "ops");
+      if ((e = upload_ops_t<float>(l2l, K, ldp, &h->ops_l2l)) != cudaSuccess) return fail(e, "ops");
+      if (precision != MAHI_MIXED)
+        if ((e = upload_ops_t<float>(m2l, K, ldp, &h->ops_m2l)) != cudaSuccess) return fail(e, "ops");
     }
     void *tmp = nullptr;
     if ((e = upload_ops<double>(lat, &tmp)) != cudaSuccess) return fail(e, "ops");
     h->ops_lat = (double *)tmp;
+    if ((e = upload_ops<double>(lat3, &tmp)) != cudaSuccess) return fail(e, "ops");
+    h->ops_lat_h3 = (double *)tmp;
+    AL(h->L_h3, sizeof(double) * K);
+    AL(h->box_qd, sizeof(double) * 4 * h->nbox_total);
+    AL(h->d_level_off, sizeof(int64_t) * (kMaxDepth + 2));
+    if ((e = cudaMemcpy(h->d_level_off, h->level_off, sizeof(int64_t) * (kMaxDepth + 2), cudaMemcpyHostToDevice)) !=
+        cudaSuccess)
+      return fail(e, "level offsets");
     // first-shell lattice function H_1 for the per-site pair kernel, and its
     // gradient coefficients
     const int P = kSiteDegree;
@@ -217,6 +244,11 @@ int mahi_create(double box_L_nm, int64_t n_atoms, int32_t n_sites, int32_t order
         return fail(e, "tc units");
       AL(h->tc_error, 16);
       cudaMemset(h->tc_error, 0, 16);
+      AL(h->tc_msplit, (size_t)h->nbox_total * h->ld * 2 * sizeof(float));
+      AL(h->tc_level_off, sizeof(int64_t) * (kMaxDepth + 2));
+      if ((e = cudaMemcpy(h->tc_level_off, h->level_off, sizeof(int64_t) * (kMaxDepth + 2), cudaMemcpyHostToDevice)) !=
+          cudaSuccess)
+        return fail(e, "tc level offsets");
     }
   }
   for (int i = 0; i < 32; ++i) {
@@ -275,6 +307,10 @@ int mahi_set_charges(mahi_t h, const double *qA, const double *qB, const int32_t
   CK(cudaMemcpy(h->site_of, site_of_atom, N * 4, cudaMemcpyHostToDevice));
   if (h->site_ptr) { cudaFree(h->site_ptr); h->site_ptr = nullptr; }
   if (h->site_atoms) { cudaFree(h->site_atoms); h->site_atoms = nullptr; }
+  if (h->phi_site) { cudaFree(h->phi_site); h->phi_site = nullptr; }
+  if (h->phi_part) { cudaFree(h->phi_part); h->phi_part = nullptr; }
+  CK(dalloc(&h->phi_site, std::max<size_t>(1, atoms.size()) * sizeof(double)));
+  CK(dalloc(&h->phi_part, std::max<size_t>(1, atoms.size()) * (h->d + 2) * sizeof(double)));
   CK(dalloc(&h->site_ptr, (S + 1) * sizeof(int)));
   CK(dalloc(&h->site_atoms, std::max<size_t>(1, atoms.size()) * sizeof(int)));
   CK(cudaMemcpy(h->site_ptr, ptr.data(), (S + 1) * sizeof(int), cudaMemcpyHostToDevice));

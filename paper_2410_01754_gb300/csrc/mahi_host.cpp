@@ -290,7 +290,7 @@ const std::vector<double> &lattice_coeffs(int P, int shell) {
   return res.first->second;
 }
 
-void build_lattice_op(int p, std::vector<double> &op) {
+void build_lattice_op(int p, std::vector<double> &op, bool with_images) {
   const int K = ncoef(p), P = 2 * p;
   // far images |n|_inf >= 4 through the lattice function H_3 ...
   const std::vector<double> &eta = lattice_coeffs(P, kLatticeShell);
@@ -310,6 +310,7 @@ void build_lattice_op(int p, std::vector<double> &op) {
     });
   }
   // ... and the images 2 <= |n|_inf <= 3 of the root by plain M2L (offset o = n)
+  if (!with_images) return;
   const OffsetTables &ot = offset_tables();
   std::vector<double> t;
   for (int o = 0; o < kNumOffsets; ++o) {

@@ -38,7 +38,7 @@ void build_m2l(int p, int ox, int oy, int oz, std::vector<double> &op);
 const std::vector<double> &lattice_coeffs(int P, int shell);
 // Lattice operator (root local from root multipole): H_3 lattice part plus the
 // root images 2 <= |n|_inf <= 3 by M2L; ncoef(p)^2, FP64, unscaled basis.
-void build_lattice_op(int p, std::vector<double> &op);
+void build_lattice_op(int p, std::vector<double> &op, bool with_images = true);
 // Convert an unscaled operator to the device basis: kind 0 = M2M, 1 = L2L,
 // 2 = M2L / lattice.
 void scale_operator(int p, int kind, std::vector<double> &op);
@@ -97,7 +97,13 @@ struct mahi_ctx {
   void *Mexp = nullptr, *Lexp = nullptr;      // expansions, all levels
   void *phi_s = nullptr, *grad_s = nullptr;   // sorted potential / gradient
   void *ops_m2m = nullptr, *ops_l2l = nullptr, *ops_m2l = nullptr;
-  double *ops_lat = nullptr;                  // FP64 lattice operator
+  double *ops_lat = nullptr;                  // FP64 root operator (images 2..3 + H_3)
+  double *ops_lat_h3 = nullptr;               // FP64 H_3 part alone (site-atom path)
+  double *L_h3 = nullptr;                     // root local of H_3 (K doubles)
+  double *box_qd = nullptr;                   // FP64 charge + dipole per box, all levels
+  double *phi_site = nullptr;                 // refined potential at site atoms
+  double *phi_part = nullptr;                 // its per-part partial sums
+  int64_t *d_level_off = nullptr;             // device copy of level_off
   double *eta = nullptr, *eta_x = nullptr, *eta_y = nullptr, *eta_z = nullptr;  // degree 2p
   int *m2l_list = nullptr;                    // [8][189] offset ids
   int *m2l_off = nullptr;                     // [316][3]
@@ -109,6 +115,8 @@ struct mahi_ctx {
   int n_moment_blocks = 0, n_energy_blocks = 0;
   // tensor-core M2L operand images (mixed path)
   void *tc_ops = nullptr;
+  void *tc_msplit = nullptr;                  // TF32 hi | lo copies of Mexp
+  int64_t *tc_level_off = nullptr;            // device copy of level_off
   int *tc_units = nullptr;
   int tc_nunits = 0;
   int *tc_error = nullptr;
@@ -127,6 +135,7 @@ namespace mahi {
 int enqueue_eval(mahi_ctx *h, const void *x, int x_is_fp64, const double *lambda, double *energy,
                  void *forces, double *dEdl);
 int enqueue_potential(mahi_ctx *h, double *phi);
+int upload_tables();
 const char *stage_name(int i);
 int num_stages();
 // tensor-core M2L (mahi_m2l_tc.cu)

@@ -13,6 +13,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cmath>
 #include <cstdio>
 
 #include "mahi_internal.h"
@@ -48,74 +49,102 @@ template <typename T> __device__ __forceinline__ T rsqrt_int(int a) { return T(1
 template <typename T> __device__ __forceinline__ T sqrt_ratio(int a, int b) { return sqrt(T(a) / T(b)); }
 
 // ---------------------------------------------------------------------------
-// Regular solid harmonics, streamed degree by degree.  Row l holds R_lm for
-// m = 0..l (complex); conj(R) enters P2M/L2P.  `row_cb(l, re, im)` is called
-// for every complete row.
+// Recursion coefficients (filled once by the host, mahi_upload_tables):
+//   device basis  Rt: a_lm = (2l-1)/sqrt((l+m)(l-m)), b_lm = sqrt((l+m-1)(l-m-1)/((l+m)(l-m))),
+//                     diag_m = sqrt((2m-1)/(2m))
+//   plain basis   R : ua_lm = (2l-1)/((l+m)(l-m)),  ub_lm = 1/((l+m)(l-m)),  udiag_m = 1/(2m)
+// indexed by tri(l, m) = l(l+1)/2 + m.
 // ---------------------------------------------------------------------------
-template <typename T, int PMAX, class CB>
-__device__ __forceinline__ void harmonics_rows(int P, T x, T y, T z, CB row_cb) {
-  T re0[PMAX + 1], im0[PMAX + 1];  // row l-1
-  T re1[PMAX + 1], im1[PMAX + 1];  // row l-2
-  T r2 = x * x + y * y + z * z;
-  re0[0] = T(1); im0[0] = T(0);
-  row_cb(0, re0, im0);
-  T dre = T(1), dim = T(0);  // diagonal R_{l-1,l-1}
-  for (int l = 1; l <= P; ++l) {
-    T nre[PMAX + 1], nim[PMAX + 1];
-    for (int m = 0; m <= l - 1; ++m) {
-      T ar = T(2 * l - 1) * z * re0[m], ai = T(2 * l - 1) * z * im0[m];
-      if (m <= l - 2) { ar -= r2 * re1[m]; ai -= r2 * im1[m]; }
-      T inv = T(1) / T((l + m) * (l - m));
-      nre[m] = ar * inv; nim[m] = ai * inv;
+constexpr int kTriMax = (kMaxOrder + 1) * (kMaxOrder + 2) / 2;
+constexpr int kTriSite = (kSiteDegree + 1) * (kSiteDegree + 2) / 2;
+__constant__ double c_a[kTriMax], c_b[kTriMax], c_diag[kMaxOrder + 1];
+__constant__ float c_af[kTriMax], c_bf[kTriMax], c_diagf[kMaxOrder + 1];
+__constant__ double c_ua[kTriSite], c_ub[kTriSite], c_udiag[kSiteDegree + 1];
+
+template <typename T> __device__ __forceinline__ T tab_a(int k);
+template <> __device__ __forceinline__ float tab_a<float>(int k) { return c_af[k]; }
+template <> __device__ __forceinline__ double tab_a<double>(int k) { return c_a[k]; }
+template <typename T> __device__ __forceinline__ T tab_b(int k);
+template <> __device__ __forceinline__ float tab_b<float>(int k) { return c_bf[k]; }
+template <> __device__ __forceinline__ double tab_b<double>(int k) { return c_b[k]; }
+template <typename T> __device__ __forceinline__ T tab_diag(int m);
+template <> __device__ __forceinline__ float tab_diag<float>(int m) { return c_diagf[m]; }
+template <> __device__ __forceinline__ double tab_diag<double>(int m) { return c_diag[m]; }
+
+// Regular harmonics of the device basis, column by column (m outer, l inner),
+// O(1) state: cb(l, m, re, im) gets Rt_lm for all 0 <= m <= l <= P.
+template <typename T, class CB>
+__device__ __forceinline__ void rt_columns(int P, T x, T y, T z, CB cb) {
+  const T r2 = x * x + y * y + z * z;
+  T dre = T(1), dim = T(0);
+  for (int m = 0; m <= P; ++m) {
+    if (m > 0) {
+      const T f = -tab_diag<T>(m);
+      const T tr = f * (x * dre - y * dim), ti = f * (x * dim + y * dre);
+      dre = tr; dim = ti;
     }
-    // R_ll = -(x + i y)/(2l) R_{l-1,l-1}
-    T f = T(-1) / T(2 * l);
-    T tr = f * (x * dre - y * dim), ti = f * (x * dim + y * dre);
-    dre = tr; dim = ti;
-    nre[l] = dre; nim[l] = dim;
-    for (int m = 0; m <= l; ++m) {
-      if (m <= l - 1) { re1[m] = re0[m]; im1[m] = im0[m]; }
-      re0[m] = nre[m]; im0[m] = nim[m];
+    T pr = T(0), pi = T(0), cr = dre, ci = dim;
+    cb(m, m, cr, ci);
+    for (int l = m + 1; l <= P; ++l) {
+      const int k = l * (l + 1) / 2 + m;
+      const T a = tab_a<T>(k) * z, b = tab_b<T>(k) * r2;
+      const T nr = a * cr - b * pr, ni = a * ci - b * pi;
+      pr = cr; pi = ci; cr = nr; ci = ni;
+      cb(l, m, cr, ci);
     }
-    row_cb(l, re0, im0);
   }
 }
 
-// The same rows in the device basis, Rt_lm = sqrt((l+m)!(l-m)!) R_lm, whose
-// magnitude stays O(|u|^l) at every order (no factorial range in FP32):
-//   Rt_mm = -(x+iy) sqrt((2m-1)/(2m)) Rt_{m-1,m-1}
-//   Rt_lm = (2l-1) z Rt_{l-1,m} / sqrt((l+m)(l-m))
-//           - r^2 Rt_{l-2,m} sqrt((l+m-1)(l-m-1) / ((l+m)(l-m)))
-template <typename T, int PMAX, class CB>
-__device__ __forceinline__ void scaled_harmonics_rows(int P, T x, T y, T z, CB row_cb) {
-  T re0[PMAX + 1], im0[PMAX + 1];
-  T re1[PMAX + 1], im1[PMAX + 1];
-  T r2 = x * x + y * y + z * z;
-  re0[0] = T(1); im0[0] = T(0);
-  row_cb(0, re0, im0);
-  T dre = T(1), dim = T(0);
-  for (int l = 1; l <= P; ++l) {
-    T nre[PMAX + 1], nim[PMAX + 1];
-    for (int m = 0; m <= l - 1; ++m) {
-      T a = T(2 * l - 1) * rsqrt_int<T>((l + m) * (l - m));
-      T ar = a * z * re0[m], ai = a * z * im0[m];
-      if (m <= l - 2) {
-        T b = sqrt_ratio<T>((l + m - 1) * (l - m - 1), (l + m) * (l - m));
-        ar -= b * r2 * re1[m]; ai -= b * r2 * im1[m];
-      }
-      nre[m] = ar; nim[m] = ai;
+// Irregular harmonics of the device basis It_lm = I_lm / sqrt((l+m)!(l-m)!):
+// It_00 = 1/r, It_mm = -diag_m (x+iy)/r^2 It_{m-1,m-1},
+// It_lm = (a_lm z It_{l-1,m} - b_lm It_{l-2,m}) / r^2.
+template <typename T, class CB>
+__device__ __forceinline__ void it_columns(int P, T x, T y, T z, CB cb) {
+  const T r2 = x * x + y * y + z * z, ir2 = T(1) / r2;
+  T dre = sqrt(ir2), dim = T(0);
+  for (int m = 0; m <= P; ++m) {
+    if (m > 0) {
+      const T f = -tab_diag<T>(m) * ir2;
+      const T tr = f * (x * dre - y * dim), ti = f * (x * dim + y * dre);
+      dre = tr; dim = ti;
     }
-    T f = -sqrt_ratio<T>(2 * l - 1, 2 * l);
-    T tr = f * (x * dre - y * dim), ti = f * (x * dim + y * dre);
-    dre = tr; dim = ti;
-    nre[l] = dre; nim[l] = dim;
-    for (int m = 0; m <= l; ++m) {
-      if (m <= l - 1) { re1[m] = re0[m]; im1[m] = im0[m]; }
-      re0[m] = nre[m]; im0[m] = nim[m];
+    T pr = T(0), pi = T(0), cr = dre, ci = dim;
+    cb(m, m, cr, ci);
+    for (int l = m + 1; l <= P; ++l) {
+      const int k = l * (l + 1) / 2 + m;
+      const T a = tab_a<T>(k) * z * ir2, b = tab_b<T>(k) * ir2;
+      const T nr = a * cr - b * pr, ni = a * ci - b * pi;
+      pr = cr; pi = ci; cr = nr; ci = ni;
+      cb(l, m, cr, ci);
     }
-    row_cb(l, re0, im0);
   }
 }
+
+// Plain regular harmonics R_lm (site kernel, FP64, degree <= kSiteDegree).
+template <class CB>
+__device__ __forceinline__ void r_columns(int P, double x, double y, double z, CB cb) {
+  const double r2 = x * x + y * y + z * z;
+  double dre = 1.0, dim = 0.0;
+  for (int m = 0; m <= P; ++m) {
+    if (m > 0) {
+      const double f = -c_udiag[m];
+      const double tr = f * (x * dre - y * dim), ti = f * (x * dim + y * dre);
+      dre = tr; dim = ti;
+    }
+    double pr = 0.0, pi = 0.0, cr = dre, ci = dim;
+    cb(m, m, cr, ci);
+    for (int l = m + 1; l <= P; ++l) {
+      const int k = l * (l + 1) / 2 + m;
+      const double a = c_ua[k] * z, b = c_ub[k] * r2;
+      const double nr = a * cr - b * pr, ni = a * ci - b * pi;
+      pr = cr; pi = ci; cr = nr; ci = ni;
+      cb(l, m, cr, ci);
+    }
+  }
+}
+
+// real-layout index of (l, m >= 0): Re part (Im = +1 for m > 0)
+__device__ __forceinline__ int ridx(int l, int m) { return m == 0 ? l * l : l * l + 2 * m - 1; }
 
 // ---------------------------------------------------------------------------
 // 1. scale charges, bin atoms into leaves, moments Q, D, T (FP64 partials)
@@ -249,33 +278,35 @@ __global__ void k_leaf_sort(int nleaf, const int *__restrict__ leaf_start, const
 template <typename T>
 __global__ void k_p2m(int nleaf, int P, int ld, T inv_s, const int *__restrict__ leaf_start,
                       const typename V4<T>::type *__restrict__ part, T *__restrict__ M) {
-  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int warp = blockIdx.x * (blockDim.x >> 5) + wib;
   if (warp >= nleaf) return;
-  int b = leaf_start[warp], e = leaf_start[warp + 1];
-  T *out = M + (size_t)warp * ld;
-  // lane k owns output coefficients k, k+32, ...
-  T acc[(kMaxOrder + 1) * (kMaxOrder + 1) / 32 + 2];
-  const int K = (P + 1) * (P + 1);
-  for (int k = 0; k < (K + 31) / 32; ++k) acc[k] = T(0);
+  T *acc = reinterpret_cast<T *>(smem_raw) + (size_t)wib * ld;
+  for (int k = lane; k < ld; k += 32) acc[k] = T(0);
+  __syncwarp();
+  const int b = leaf_start[warp], e = leaf_start[warp + 1];
   for (int base = b; base < e; base += 32) {
-    int a = base + lane;
-    bool valid = a < e;
-    typename V4<T>::type pt = valid ? part[a] : typename V4<T>::type{0, 0, 0, 0};
-    T q = valid ? pt.w : T(0);
-    scaled_harmonics_rows<T, kMaxOrder>(P, pt.x * inv_s, pt.y * inv_s, pt.z * inv_s, [&](int l, const T *re, const T *im) {
-      for (int m = 0; m <= l; ++m) {
-        T vr = q * re[m], vi = -q * im[m];  // conj
-        for (int o = 16; o > 0; o >>= 1) {
-          vr += __shfl_xor_sync(0xffffffff, vr, o);
-          vi += __shfl_xor_sync(0xffffffff, vi, o);
-        }
-        int kr = (m == 0) ? l * l : l * l + 2 * m - 1;
-        if ((kr & 31) == lane) acc[kr >> 5] += vr;
-        if (m > 0 && ((kr + 1) & 31) == lane) acc[(kr + 1) >> 5] += vi;
+    const int a = base + lane;
+    const bool valid = a < e;
+    const typename V4<T>::type pt = valid ? part[a] : typename V4<T>::type{0, 0, 0, 0};
+    const T q = valid ? pt.w : T(0);
+    rt_columns<T>(P, pt.x * inv_s, pt.y * inv_s, pt.z * inv_s, [&](int l, int m, T re, T im) {
+      T vr = q * re, vi = -q * im;  // conj
+      for (int o = 16; o > 0; o >>= 1) {
+        vr += __shfl_xor_sync(0xffffffff, vr, o);
+        vi += __shfl_xor_sync(0xffffffff, vi, o);
+      }
+      if (lane == 0) {
+        const int k = ridx(l, m);
+        acc[k] += vr;
+        if (m > 0) acc[k + 1] += vi;
       }
     });
   }
-  for (int k = lane, j = 0; k < ld; k += 32, ++j) out[k] = (k < K) ? acc[j] : T(0);
+  __syncwarp();
+  T *out = M + (size_t)warp * ld;
+  for (int k = lane; k < ld; k += 32) out[k] = acc[k];
 }
 
 // ---------------------------------------------------------------------------
@@ -291,89 +322,109 @@ struct GemmMap {
 };
 
 constexpr int TR = 32;   // rows per tile
-constexpr int TK = 16;   // input coefficients per smem chunk
+constexpr int TK = 16;   // input coefficients per pipeline stage
 
+__device__ __forceinline__ void cpa16(void *smem, const void *gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(smem)), "l"(gmem)
+               : "memory");
+}
+
+// Operators are stored transposed and zero padded: opT[term][k][n] with k, n < ld.
+// Two-stage cp.async pipeline over (term, k-chunk); all source rows of the tile
+// are resolved up front.
 template <typename T, int NC>
 __global__ void __launch_bounds__(256) k_gather_gemm(GemmMap mp, int K, int ld, const T *__restrict__ in,
-                                                     T *__restrict__ out, const T *__restrict__ ops) {
-  // tile t: for M2M rows = parents [t*TR, ...); for L2L/M2L rows = boxes with a
-  // fixed child index c, i.e. 8*P + c for P in [tp*TR, ...)
+                                                     T *__restrict__ out, const T *__restrict__ opsT) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T *As = reinterpret_cast<T *>(smem_raw);      // [TR][TK]
-  T *Bs = As + TR * TK;                          // [TK][ld]
-  __shared__ int src[TR];
+  const int nterms = (mp.kind == 0) ? 8 : (mp.kind == 1 ? 1 : kListLen);
+  constexpr int LDB = 32 * NC;                         // B row stride >= ld: columns ld..LDB-1 stay zero
+  T *As = reinterpret_cast<T *>(smem_raw);            // [2][TR][TK]
+  T *Bs = As + 2 * TR * TK;                            // [2][TK][LDB]
+  int *src = reinterpret_cast<int *>(Bs + 2 * TK * LDB);  // [nterms][TR]
+  for (int i = threadIdx.x; i < 2 * TK * LDB; i += blockDim.x) Bs[i] = T(0);
   const int tid = threadIdx.x;
-  const int tg = tid >> 5;        // 8 row groups of 4 rows
-  const int cg = tid & 31;        // column lane
-  int c = 0, tp = blockIdx.x;
-  int nrow_par;  // number of "parent-indexed" rows
-  if (mp.kind == 0) { nrow_par = mp.nbox; }
+  const int tg = tid >> 5, cg = tid & 31;
+  int c = 0, tp = blockIdx.x, nrow_par;
+  if (mp.kind == 0) nrow_par = mp.nbox;
   else { nrow_par = mp.nbox / 8; c = blockIdx.x % 8; tp = blockIdx.x / 8; }
   const int row0 = tp * TR;
-  const int ncols = (K + 31) / 32;  // <= NC
+  const int side = 1 << mp.level;
+  for (int i = tid; i < nterms * TR; i += blockDim.x) {
+    const int term = i / TR, r = i % TR, P = row0 + r;
+    int sidx = -1;
+    if (P < nrow_par) {
+      if (mp.kind == 0) sidx = 8 * P + term;
+      else if (mp.kind == 1) sidx = P;
+      else {
+        const int box = 8 * P + c;
+        const int bx = (int)d_compact(box), by = (int)d_compact(box >> 1), bz = (int)d_compact(box >> 2);
+        const int oid = mp.list[c * kListLen + term];
+        sidx = (int)d_morton(wrapi(bx - mp.off[oid * 3 + 0], side), wrapi(by - mp.off[oid * 3 + 1], side),
+                             wrapi(bz - mp.off[oid * 3 + 2], side));
+      }
+    }
+    src[i] = sidx;
+  }
+  __syncthreads();
+  const int nch = ld / TK;            // ld is a multiple of 16
+  const int total = nterms * nch;
+  constexpr int EPV = 16 / sizeof(T);  // elements per 16-byte copy
+  auto issue = [&](int it, int stg) {
+    const int term = it / nch, k0 = (it % nch) * TK;
+    const int oid = (mp.kind == 0) ? term : (mp.kind == 1 ? c : mp.list[c * kListLen + term]);
+    const T *op = opsT + (size_t)oid * ld * ld;
+    T *a = As + stg * TR * TK;
+    T *b = Bs + stg * TK * LDB;
+    for (int i = tid; i < TR * (TK / EPV); i += blockDim.x) {
+      const int r = i / (TK / EPV), q = i % (TK / EPV);
+      const int sidx = src[term * TR + r];
+      T *dst = a + r * TK + q * EPV;
+      if (sidx >= 0) cpa16(dst, in + (size_t)sidx * ld + k0 + q * EPV);
+      else
+        for (int e = 0; e < EPV; ++e) dst[e] = T(0);
+    }
+    const int per_row = ld / EPV;
+    for (int i = tid; i < TK * per_row; i += blockDim.x) {
+      const int kk = i / per_row, q = i % per_row;
+      cpa16(b + kk * LDB + q * EPV, op + (size_t)(k0 + kk) * ld + q * EPV);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
   T acc[4][NC];
   for (int r = 0; r < 4; ++r)
     for (int j = 0; j < NC; ++j) acc[r][j] = T(0);
-  const int nterms = (mp.kind == 0) ? 8 : (mp.kind == 1 ? 1 : kListLen);
-  const int side = 1 << mp.level;
-  for (int term = 0; term < nterms; ++term) {
-    const T *op;
-    if (tid < TR) {
-      int P = row0 + tid, s = -1;
-      if (P < nrow_par) {
-        if (mp.kind == 0) s = 8 * P + term;            // child of parent P
-        else if (mp.kind == 1) s = P;                  // parent of child 8P+c
-        else {
-          int box = 8 * P + c;
-          int bx = (int)d_compact(box), by = (int)d_compact(box >> 1), bz = (int)d_compact(box >> 2);
-          int oid = mp.list[c * kListLen + term];
-          int gx = bx - mp.off[oid * 3 + 0], gy = by - mp.off[oid * 3 + 1], gz = bz - mp.off[oid * 3 + 2];
-          s = (int)d_morton(wrapi(gx, side), wrapi(gy, side), wrapi(gz, side));
-        }
-      }
-      src[tid] = s;
+  const int ncols = (K + 31) / 32;
+  issue(0, 0);
+  for (int it = 0; it < total; ++it) {
+    if (it + 1 < total) {
+      issue(it + 1, (it + 1) & 1);
+      asm volatile("cp.async.wait_group 1;" ::: "memory");
+    } else {
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
     }
-    if (mp.kind == 0) op = ops + (size_t)term * K * K;
-    else if (mp.kind == 1) op = ops + (size_t)c * K * K;
-    else op = ops + (size_t)mp.list[c * kListLen + term] * K * K;
     __syncthreads();
-    for (int k0 = 0; k0 < K; k0 += TK) {
-      // A chunk: TR rows x TK inputs
-      for (int i = tid; i < TR * TK; i += blockDim.x) {
-        int r = i / TK, kk = i % TK;
-        int s = src[r];
-        As[i] = (s >= 0 && k0 + kk < K) ? in[(size_t)s * ld + k0 + kk] : T(0);
-      }
-      // B chunk: op[out][k0 + kk] -> Bs[kk][out]
-      for (int i = tid; i < TK * K; i += blockDim.x) {
-        int o = i / TK, kk = i % TK;
-        Bs[kk * ld + o] = (k0 + kk < K) ? op[(size_t)o * K + k0 + kk] : T(0);
-      }
-      __syncthreads();
+    const T *a = As + (it & 1) * TR * TK;
+    const T *b = Bs + (it & 1) * TK * LDB;
 #pragma unroll 4
-      for (int kk = 0; kk < TK; ++kk) {
-        T a[4];
-        for (int r = 0; r < 4; ++r) a[r] = As[(tg * 4 + r) * TK + kk];
+    for (int kk = 0; kk < TK; ++kk) {
+      T av[4];
+      for (int r = 0; r < 4; ++r) av[r] = a[(tg * 4 + r) * TK + kk];
 #pragma unroll
-        for (int j = 0; j < NC; ++j) {
-          if (j < ncols) {
-            int col = cg + 32 * j;
-            T bv = (col < K) ? Bs[kk * ld + col] : T(0);
-            for (int r = 0; r < 4; ++r) acc[r][j] += a[r] * bv;
-          }
-        }
+      for (int j = 0; j < NC; ++j) {
+        const T bv = b[kk * LDB + cg + 32 * j];
+        for (int r = 0; r < 4; ++r) acc[r][j] += av[r] * bv;
       }
-      __syncthreads();
     }
+    __syncthreads();
   }
   for (int r = 0; r < 4; ++r) {
-    int P = row0 + tg * 4 + r;
+    const int P = row0 + tg * 4 + r;
     if (P >= nrow_par) continue;
-    int orow = (mp.kind == 0) ? P : 8 * P + c;
+    const int orow = (mp.kind == 0) ? P : 8 * P + c;
     T *o = out + (size_t)orow * ld;
 #pragma unroll
     for (int j = 0; j < NC; ++j) {
-      int col = cg + 32 * j;
+      const int col = cg + 32 * j;
       if (j < ncols && col < K) {
         if (mp.kind == 1) o[col] += acc[r][j];
         else o[col] = acc[r][j];
@@ -387,8 +438,9 @@ __global__ void __launch_bounds__(256) k_gather_gemm(GemmMap mp, int K, int ld, 
 //    and dipole of the root multipole taken from the FP64 moments.
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void k_lattice(int K, int ld, double L, const double *__restrict__ lat, const double *__restrict__ mom,
-                          const T *__restrict__ Mroot, T *__restrict__ Lroot) {
+__global__ void k_lattice(int K, int ld, double L, const double *__restrict__ lat, const double *__restrict__ lat_h3,
+                          const double *__restrict__ mom, const T *__restrict__ Mroot, T *__restrict__ Lroot,
+                          double *__restrict__ Lh3) {
   extern __shared__ double ms[];
   for (int k = threadIdx.x; k < K; k += blockDim.x) ms[k] = (double)Mroot[k];
   __syncthreads();
@@ -406,9 +458,13 @@ __global__ void k_lattice(int K, int ld, double L, const double *__restrict__ la
   }
   __syncthreads();
   for (int r = threadIdx.x; r < K; r += blockDim.x) {
-    double s = 0;
-    for (int k = 0; k < K; ++k) s += lat[(size_t)r * K + k] * ms[k];
+    double s = 0, s3 = 0;
+    for (int k = 0; k < K; ++k) {
+      s += lat[(size_t)r * K + k] * ms[k];
+      s3 += lat_h3[(size_t)r * K + k] * ms[k];
+    }
     Lroot[r] = (T)s;
+    Lh3[r] = s3;
   }
   for (int r = K + threadIdx.x; r < ld; r += blockDim.x) Lroot[r] = T(0);
 }
@@ -472,21 +528,20 @@ __global__ void k_l2p(int nleaf, int P, int ld, T s, const int *__restrict__ lea
   for (int a = b + lane; a < e; a += 32) {
     typename V4<T>::type pt = part[a];
     T f = 0, gx = 0, gy = 0, gz = 0;
-    scaled_harmonics_rows<T, kMaxOrder>(P, pt.x * inv_s, pt.y * inv_s, pt.z * inv_s, [&](int l, const T *re, const T *im) {
-      // sum over m of X_lm conj(R_lm) = X_l0 R_l0 + 2 sum_{m>0} (Xr Rr + Xi Ri)
-      T sf = c[l * l] * re[0];
-      T sx = (l < P) ? cx[l * l] * re[0] : T(0), sy = (l < P) ? cy[l * l] * re[0] : T(0),
-        sz = (l < P) ? cz[l * l] * re[0] : T(0);
-      for (int m = 1; m <= l; ++m) {
-        int k = l * l + 2 * m - 1;
-        sf += T(2) * (c[k] * re[m] + c[k + 1] * im[m]);
+    // sum over m of X_lm conj(R_lm) = X_l0 R_l0 + 2 sum_{m>0} (Xr Rr + Xi Ri)
+    rt_columns<T>(P, pt.x * inv_s, pt.y * inv_s, pt.z * inv_s, [&](int l, int m, T re, T im) {
+      const int k = ridx(l, m);
+      if (m == 0) {
+        f += c[k] * re;
+        if (l < P) { gx += cx[k] * re; gy += cy[k] * re; gz += cz[k] * re; }
+      } else {
+        f += T(2) * (c[k] * re + c[k + 1] * im);
         if (l < P) {
-          sx += T(2) * (cx[k] * re[m] + cx[k + 1] * im[m]);
-          sy += T(2) * (cy[k] * re[m] + cy[k + 1] * im[m]);
-          sz += T(2) * (cz[k] * re[m] + cz[k + 1] * im[m]);
+          gx += T(2) * (cx[k] * re + cx[k + 1] * im);
+          gy += T(2) * (cy[k] * re + cy[k + 1] * im);
+          gz += T(2) * (cz[k] * re + cz[k + 1] * im);
         }
       }
-      f += sf; gx += sx; gy += sy; gz += sz;
     });
     phi[a] = f * inv_s;
     grad[3 * (size_t)a + 0] = gx * inv_s * inv_s;
@@ -641,7 +696,7 @@ constexpr int kMaxSiteAtoms = 64;
 template <typename T, typename XT, typename FT>
 __global__ void k_site(int S, double L, double fcoul, int Pmax, const int *__restrict__ site_ptr,
                        const int *__restrict__ site_atoms, const XT *__restrict__ x, const double *__restrict__ dq,
-                       const double *__restrict__ lam, const int *__restrict__ inv_perm, const T *__restrict__ phi_s,
+                       const double *__restrict__ lam, const double *__restrict__ phi_site,
                        const double *__restrict__ eta, const double *__restrict__ eta_x,
                        const double *__restrict__ eta_y, const double *__restrict__ eta_z,
                        double *__restrict__ dEdl, double *__restrict__ site_energy, FT *__restrict__ forces) {
@@ -685,23 +740,15 @@ __global__ void k_site(int S, double L, double fcoul, int Pmax, const int *__res
     }
     double H = 0, hx = 0, hy = 0, hz = 0;
     // H lives on even degrees; its gradient coefficients on odd degrees (< P)
-    harmonics_rows<double, kSiteDegree>(P, u[0], u[1], u[2], [&](int l, const double *re, const double *im) {
+    r_columns(P, u[0], u[1], u[2], [&](int l, int m, double re, double im) {
+      const int k = ridx(l, m);
+      const double w = (m == 0) ? 1.0 : 2.0;
       if (!(l & 1)) {
-        double sf = eta[l * l] * re[0];
-        for (int m = 1; m <= l; ++m) {
-          int k = l * l + 2 * m - 1;
-          sf += 2.0 * (eta[k] * re[m] + eta[k + 1] * im[m]);
-        }
-        H += sf;
+        H += (m == 0) ? eta[k] * re : w * (eta[k] * re + eta[k + 1] * im);
       } else if (l < P) {
-        double sx = eta_x[l * l] * re[0], sy = eta_y[l * l] * re[0], sz = eta_z[l * l] * re[0];
-        for (int m = 1; m <= l; ++m) {
-          int k = l * l + 2 * m - 1;
-          sx += 2.0 * (eta_x[k] * re[m] + eta_x[k + 1] * im[m]);
-          sy += 2.0 * (eta_y[k] * re[m] + eta_y[k + 1] * im[m]);
-          sz += 2.0 * (eta_z[k] * re[m] + eta_z[k + 1] * im[m]);
-        }
-        hx += sx; hy += sy; hz += sz;
+        hx += (m == 0) ? eta_x[k] * re : w * (eta_x[k] * re + eta_x[k + 1] * im);
+        hy += (m == 0) ? eta_y[k] * re : w * (eta_y[k] * re + eta_y[k + 1] * im);
+        hz += (m == 0) ? eta_z[k] * re : w * (eta_z[k] * re + eta_z[k + 1] * im);
       }
     });
     A += H / L + c2 * (r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
@@ -709,7 +756,7 @@ __global__ void k_site(int S, double L, double fcoul, int Pmax, const int *__res
     g1 += hy / (L * L) + 2.0 * c2 * r[1];
     g2 += hz / (L * L) + 2.0 * c2 * r[2];
     ksum += Di * Dj * A;
-    if (ia == ja) gsum += Di * (double)phi_s[inv_perm[i]];
+    if (ia == ja) gsum += Di * phi_site[b + ia];
     else {
       double w = lw * fcoul * Di * Dj;
       atomicAdd(&fsh[wib][ia][0], -w * g0);
@@ -722,7 +769,7 @@ __global__ void k_site(int S, double L, double fcoul, int Pmax, const int *__res
     gsum += __shfl_xor_sync(0xffffffff, gsum, o);
   }
   __syncwarp();
-  const double k = fcoul * ksum;  // phi_s already carries f
+  const double k = fcoul * ksum;  // phi_site already carries f
   if (lane == 0) {
     const double l0 = lam[warp];
     if (dEdl) dEdl[warp] = gsum + (0.5 - l0) * k;
@@ -734,6 +781,273 @@ __global__ void k_site(int S, double L, double fcoul, int Pmax, const int *__res
       int i = site_atoms[b + ia];
       forces[3 * (size_t)i + a] = (FT)((double)forces[3 * (size_t)i + a] + fsh[wib][ia][a]);
     }
+}
+
+// ---------------------------------------------------------------------------
+// 8. FP64 charge and dipole (about the box centre) of every box: leaves from the
+//    atoms (original FP64 positions), parents by exact translation.  They feed
+//    the l <= 1 terms of the per-site-atom potential below.
+// ---------------------------------------------------------------------------
+template <typename XT>
+__global__ void k_qd_leaf(int nleaf, int nb, double L, const int *__restrict__ leaf_start, const int *__restrict__ perm,
+                          const XT *__restrict__ x, const double *__restrict__ qt, double *__restrict__ qd) {
+  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= nleaf) return;
+  const double s = L / nb;
+  const int ix = (int)d_compact(warp), iy = (int)d_compact(warp >> 1), iz = (int)d_compact(warp >> 2);
+  const double c[3] = {(ix + 0.5) * s, (iy + 0.5) * s, (iz + 0.5) * s};
+  double v[4] = {0, 0, 0, 0};
+  for (int a = leaf_start[warp] + lane; a < leaf_start[warp + 1]; a += 32) {
+    int i = perm[a];
+    double q = qt[i];
+    v[0] += q;
+    for (int k = 0; k < 3; ++k) {
+      double w = (double)x[3 * (size_t)i + k];
+      w -= floor(w / L) * L;
+      if (w >= L) w -= L;
+      if (w < 0.0) w = 0.0;
+      v[1 + k] += q * (w - c[k]);
+    }
+  }
+  for (int k = 0; k < 4; ++k) {
+    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffff, v[k], o);
+    if (lane == 0) qd[(size_t)warp * 4 + k] = v[k];
+  }
+}
+
+__global__ void k_qd_up(int nparent, double s_child, const double *__restrict__ child, double *__restrict__ parent) {
+  int P = blockIdx.x * blockDim.x + threadIdx.x;
+  if (P >= nparent) return;
+  double v[4] = {0, 0, 0, 0};
+  for (int c = 0; c < 8; ++c) {
+    const double *ch = child + (size_t)(8 * P + c) * 4;
+    double off[3] = {((c & 1) ? 0.5 : -0.5) * s_child, ((c & 2) ? 0.5 : -0.5) * s_child,
+                     ((c & 4) ? 0.5 : -0.5) * s_child};
+    v[0] += ch[0];
+    for (int k = 0; k < 3; ++k) v[1 + k] += ch[1 + k] + ch[0] * off[k];
+  }
+  for (int k = 0; k < 4; ++k) parent[(size_t)P * 4 + k] = v[k];
+}
+
+// ---------------------------------------------------------------------------
+// 9. Potential at the site atoms for dE/dlambda, evaluated more accurately than
+//    the bulk path: FP64 near field from the original positions, then M2P from
+//    every interaction-list box of every ancestor level and from the root images
+//    2 <= |n|_inf <= 3 (multipole truncation only, no local expansion), the
+//    far-image lattice part H_3 through its own root local expansion, and the
+//    dipole/background term.  The l <= 1 multipole terms use the FP64 box charge
+//    and dipole; l >= 2 use the working-precision multipoles.  One warp per site
+//    atom; all sums are FP64.
+//    M2P in the device basis: phi = (1/s) sum_lm M~_lm It_lm(u), u = (x - z)/s,
+//    It_lm = I_lm / sqrt((l+m)!(l-m)!), recursion
+//      It_00 = 1/r, It_mm = -sqrt((2m-1)/(2m)) (x+iy)/r^2 It_{m-1,m-1},
+//      It_lm = (a_lm z It_{l-1,m} - b_lm It_{l-2,m}) / r^2  (a, b as for Rt).
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T m2p_high(int P, const T *__restrict__ M, T ux, T uy, T uz) {
+  // sum over l >= 2 of M~_lm It_lm(u): M_l0 I_l0 + 2 sum_{m>0} (Mr Ir - Mi Ii)
+  T acc = T(0);
+  it_columns<T>(P, ux, uy, uz, [&](int l, int m, T re, T im) {
+    if (l < 2) return;
+    const int k = ridx(l, m);
+    acc += (m == 0) ? M[k] * re : T(2) * (M[k] * re - M[k + 1] * im);
+  });
+  return acc;
+}
+
+// phi of a box (charge Q, dipole D about its centre z, physical units) at x:
+// low orders in FP64 plus the l >= 2 tail from the multipole row.
+template <typename T>
+__device__ __forceinline__ double box_potential(int P, const T *__restrict__ Mrow, const double *__restrict__ qd,
+                                                double rx, double ry, double rz, double s) {
+  const double r2 = rx * rx + ry * ry + rz * rz, ri = 1.0 / sqrt(r2);
+  double v = qd[0] * ri + (qd[1] * rx + qd[2] * ry + qd[3] * rz) * ri * ri * ri;
+  if (P >= 2) v += (double)m2p_high<T>(P, Mrow, (T)(rx / s), (T)(ry / s), (T)(rz / s)) / s;
+  return v;
+}
+
+constexpr int kSitePhiThreads = 128;
+constexpr int kSiteBatch = 32;  // source boxes staged per round
+
+template <typename T>
+__device__ __forceinline__ T m2p_high_smem(int P, const T *M, T ux, T uy, T uz) {
+  T acc = T(0);
+  it_columns<T>(P, ux, uy, uz, [&](int l, int m, T re, T im) {
+    if (l < 2) return;
+    const int k = ridx(l, m);
+    acc += (m == 0) ? M[k] * re : T(2) * (M[k] * re - M[k + 1] * im);
+  });
+  return acc;
+}
+
+// Grid (site, part): part l-1 < d does the M2P of interaction level l, part d the
+// root images 2 <= |n|_inf <= 3, part d+1 the near field, the far-image lattice
+// part and the dipole/background term.  Atoms of the site that share an
+// ancestor box at level l share its 189 interaction-list boxes, whose multipole
+// rows are staged in shared memory 32 at a time (coalesced).  Every sum is
+// reduced in a fixed order, so results are bitwise reproducible.  Output:
+// phi_part[atom][part] (f = 1).
+template <typename T, typename XT>
+__global__ void __launch_bounds__(kSitePhiThreads) k_site_phi(
+    int S, const int *__restrict__ site_ptr, const int *__restrict__ site_atoms, int d, int P, int ld, double L,
+    const int64_t *__restrict__ level_off, const int *__restrict__ leaf_start, const int *__restrict__ perm,
+    const XT *__restrict__ x, const double *__restrict__ qt, const T *__restrict__ M, const double *__restrict__ qd,
+    const double *__restrict__ mom, const double *__restrict__ Lh3, const int *__restrict__ list,
+    const int *__restrict__ off, double *__restrict__ phi_part) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *Ms = reinterpret_cast<T *>(smem_raw);                                // [kSiteBatch][ld]
+  __shared__ double ps[kMaxSiteAtoms][3], acc[kMaxSiteAtoms];
+  __shared__ double vals[kSiteBatch * kMaxSiteAtoms];
+  __shared__ int Is[kMaxSiteAtoms][3], grp[kMaxSiteAtoms];
+  __shared__ double bq[kSiteBatch][4], bc[kSiteBatch][3];
+  __shared__ int64_t brow[kSiteBatch];
+  const int site = blockIdx.x, part = blockIdx.y, nparts = d + 2;
+  if (site >= S) return;
+  const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
+  const int b0 = site_ptr[site], n = site_ptr[site + 1] - b0;
+  const int nb = 1 << d;
+  for (int a = tid; a < n; a += blockDim.x) {
+    const int i = site_atoms[b0 + a];
+    for (int k = 0; k < 3; ++k) {
+      double w = (double)x[3 * (size_t)i + k];
+      w -= floor(w / L) * L;
+      if (w >= L) w -= L;
+      if (w < 0.0) w = 0.0;
+      ps[a][k] = w;
+      Is[a][k] = min((int)(w / L * nb), nb - 1);
+    }
+    acc[a] = 0.0;
+  }
+  __syncthreads();
+  // evaluate a batch of nbx sources for the atoms selected by `sel`, then reduce
+  // per atom in source order
+  auto reduce_batch = [&](int nbx) {
+    __syncthreads();
+    for (int a = tid; a < n; a += blockDim.x) {
+      double v = acc[a];
+      for (int r = 0; r < nbx; ++r) v += vals[r * kMaxSiteAtoms + a];
+      acc[a] = v;
+    }
+    __syncthreads();
+  };
+  if (part < d) {
+    const int l = part + 1, shift = d - l, side = 1 << l;
+    const double s = L / side;
+    for (int a = tid; a < n; a += blockDim.x) {
+      int g = a;
+      for (int b = 0; b < a; ++b)
+        if ((Is[b][0] >> shift) == (Is[a][0] >> shift) && (Is[b][1] >> shift) == (Is[a][1] >> shift) &&
+            (Is[b][2] >> shift) == (Is[a][2] >> shift)) { g = b; break; }
+      grp[a] = g;
+    }
+    __syncthreads();
+    for (int lead = 0; lead < n; ++lead) {
+      if (grp[lead] != lead) continue;  // uniform across the block
+      const int A[3] = {Is[lead][0] >> shift, Is[lead][1] >> shift, Is[lead][2] >> shift};
+      const int c = (A[0] & 1) | ((A[1] & 1) << 1) | ((A[2] & 1) << 2);
+      for (int o0 = 0; o0 < kListLen; o0 += kSiteBatch) {
+        const int nbx = min(kSiteBatch, kListLen - o0);
+        if (tid < nbx) {
+          const int oid = list[c * kListLen + o0 + tid];
+          const int g[3] = {A[0] - off[oid * 3], A[1] - off[oid * 3 + 1], A[2] - off[oid * 3 + 2]};
+          const int64_t box = level_off[l] + d_morton(wrapi(g[0], side), wrapi(g[1], side), wrapi(g[2], side));
+          brow[tid] = box;
+          for (int k = 0; k < 4; ++k) bq[tid][k] = qd[box * 4 + k];
+          for (int k = 0; k < 3; ++k) bc[tid][k] = (g[k] + 0.5) * s;
+        }
+        __syncthreads();
+        constexpr int EPV = 16 / sizeof(T);
+        const int per_row = ld / EPV;
+        for (int q = tid; q < nbx * per_row; q += blockDim.x) {
+          const int r = q / per_row, e = q % per_row;
+          reinterpret_cast<float4 *>(Ms + (size_t)r * ld)[e] = reinterpret_cast<const float4 *>(M + brow[r] * ld)[e];
+        }
+        __syncthreads();
+        for (int q = tid; q < nbx * n; q += blockDim.x) {
+          const int r = q % nbx, a = q / nbx;
+          double v = 0.0;
+          if (grp[a] == lead) {
+            const double rx = ps[a][0] - bc[r][0], ry = ps[a][1] - bc[r][1], rz = ps[a][2] - bc[r][2];
+            const double r2 = rx * rx + ry * ry + rz * rz, ri = 1.0 / sqrt(r2);
+            v = bq[r][0] * ri + (bq[r][1] * rx + bq[r][2] * ry + bq[r][3] * rz) * ri * ri * ri;
+            if (P >= 2) v += (double)m2p_high_smem<T>(P, Ms + (size_t)r * ld, (T)(rx / s), (T)(ry / s), (T)(rz / s)) / s;
+          }
+          vals[r * kMaxSiteAtoms + a] = v;
+        }
+        reduce_batch(nbx);
+      }
+    }
+  } else if (part == d) {
+    // root images 2 <= |n|_inf <= 3: source centre c - nL
+    for (int o0 = 0; o0 < kNumOffsets; o0 += kSiteBatch) {
+      const int nbx = min(kSiteBatch, kNumOffsets - o0);
+      for (int q = tid; q < nbx * n; q += blockDim.x) {
+        const int r = q % nbx, a = q / nbx, oid = o0 + r;
+        const double rx = ps[a][0] - (0.5 * L - off[oid * 3] * L), ry = ps[a][1] - (0.5 * L - off[oid * 3 + 1] * L),
+                     rz = ps[a][2] - (0.5 * L - off[oid * 3 + 2] * L);
+        const double r2 = rx * rx + ry * ry + rz * rz, ri = 1.0 / sqrt(r2);
+        double v = mom[0] * ri + (mom[1] * rx + mom[2] * ry + mom[3] * rz) * ri * ri * ri;
+        if (P >= 2) v += (double)m2p_high<T>(P, M, (T)(rx / L), (T)(ry / L), (T)(rz / L)) / L;
+        vals[r * kMaxSiteAtoms + a] = v;
+      }
+      reduce_batch(nbx);
+    }
+  } else {
+    // near field: warp w takes atoms w, w+4, ...; lanes over sources (FP64)
+    for (int a = wib; a < n; a += blockDim.x / 32) {
+      const int i = site_atoms[b0 + a];
+      double v = 0.0;
+      for (int k = 0; k < 27; ++k) {
+        const int dx = k % 3 - 1, dy = (k / 3) % 3 - 1, dz = k / 9 - 1;
+        const int g[3] = {Is[a][0] + dx, Is[a][1] + dy, Is[a][2] + dz};
+        double sh[3];
+        int w[3];
+        for (int c = 0; c < 3; ++c) { w[c] = wrapi(g[c], nb); sh[c] = (double)((g[c] - w[c]) / nb) * L; }
+        const int leaf = (int)d_morton(w[0], w[1], w[2]);
+        for (int t = leaf_start[leaf] + lane; t < leaf_start[leaf + 1]; t += 32) {
+          const int j = perm[t];
+          if (j == i && k == 13) continue;
+          double r[3];
+          for (int c = 0; c < 3; ++c) {
+            double q = (double)x[3 * (size_t)j + c];
+            q -= floor(q / L) * L;
+            if (q >= L) q -= L;
+            if (q < 0.0) q = 0.0;
+            r[c] = ps[a][c] - (q + sh[c]);
+          }
+          v += qt[j] / sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+        }
+      }
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffff, v, o);
+      if (lane == 0) acc[a] = v;
+    }
+    __syncthreads();
+    for (int a = tid; a < n; a += blockDim.x) {
+      // far-image lattice part: (1/L) sum L~_H3 conj(Rt(u)), u = (x - c)/L
+      double h = 0.0;
+      rt_columns<double>(P, (ps[a][0] - 0.5 * L) / L, (ps[a][1] - 0.5 * L) / L, (ps[a][2] - 0.5 * L) / L,
+                         [&](int l, int m, double re, double im) {
+                           const int k = ridx(l, m);
+                           h += (m == 0) ? Lh3[k] * re : 2.0 * (Lh3[k] * re + Lh3[k + 1] * im);
+                         });
+      const double V = L * L * L, c2 = 2.0 * kPi / (3.0 * V);
+      const double ax = ps[a][0] - 0.5 * L, ay = ps[a][1] - 0.5 * L, az = ps[a][2] - 0.5 * L;
+      acc[a] += h / L + c2 * (mom[0] * (ax * ax + ay * ay + az * az) -
+                              2.0 * (ax * mom[1] + ay * mom[2] + az * mom[3]) + mom[4]);
+    }
+    __syncthreads();
+  }
+  for (int a = tid; a < n; a += blockDim.x) phi_part[(size_t)(b0 + a) * nparts + part] = acc[a];
+}
+
+// phi_site = f * (sum of the parts, in part order)
+__global__ void k_site_phi_sum(int nsa, int nparts, double fcoul, const double *__restrict__ phi_part,
+                               double *__restrict__ phi_site) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nsa) return;
+  double v = 0.0;
+  for (int q = 0; q < nparts; ++q) v += phi_part[(size_t)k * nparts + q];
+  phi_site[k] = fcoul * v;
 }
 
 __global__ void k_final_energy(const double *__restrict__ epart, int nb, const double *__restrict__ site_e, int S,
@@ -775,11 +1089,12 @@ int num_stages() { return 10; }
 template <typename T, int NC>
 static cudaError_t launch_gemm_nc(const GemmMap &mp, int grid, int K, int ld, const T *in, T *out, const T *ops,
                                   cudaStream_t st) {
-  size_t sm = sizeof(T) * (TR * TK + TK * (size_t)ld);
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_gather_gemm<T, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr = true;
+  const int nterms = (mp.kind == 0) ? 8 : (mp.kind == 1 ? 1 : kListLen);
+  size_t sm = sizeof(T) * 2 * (TR * TK + TK * (size_t)(32 * NC)) + sizeof(int) * nterms * TR;
+  if (32 * NC < ld) return cudaErrorInvalidValue;
+  if (sm > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_gather_gemm<T, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
   }
   k_gather_gemm<T, NC><<<grid, 256, sm, st>>>(mp, K, ld, in, out, ops);
   return cudaGetLastError();
@@ -832,12 +1147,14 @@ static cudaError_t eval_t(mahi_ctx *h, const XT *x, const double *lam, double *e
                                        h->perm_tmp);
   k_leaf_sort<T><<<(nleaf * 32 + 255) / 256, 256, 0, st>>>(nleaf, h->leaf_start, (const V *)h->part_tmp, h->perm_tmp,
                                                           (V *)h->part, h->perm, h->inv_perm);
-  h->launches += 3;
+  k_qd_leaf<XT><<<(nleaf * 32 + 255) / 256, 256, 0, st>>>(nleaf, nb, h->L, h->leaf_start, h->perm, x, h->qt,
+                                                          h->box_qd + h->level_off[h->d] * 4);
+  h->launches += 4;
   MAHI_CK(cudaGetLastError());
   mark(h, 2);
   const double s_leaf = h->L / nb;
-  k_p2m<T><<<(nleaf * 32 + 127) / 128, 128, 0, st>>>(nleaf, P, ld, (T)(1.0 / s_leaf), h->leaf_start, (const V *)h->part,
-                                                   M + h->level_off[h->d] * ld);
+  k_p2m<T><<<(nleaf * 32 + 127) / 128, 128, 4 * sizeof(T) * ld, st>>>(
+      nleaf, P, ld, (T)(1.0 / s_leaf), h->leaf_start, (const V *)h->part, M + h->level_off[h->d] * ld);
   h->launches += 1;
   MAHI_CK(cudaGetLastError());
   mark(h, 3);
@@ -845,10 +1162,14 @@ static cudaError_t eval_t(mahi_ctx *h, const XT *x, const double *lam, double *e
     GemmMap mp{0, l, 1 << (3 * l), nullptr, nullptr};
     MAHI_CK(launch_gemm<T>(mp, K, ld, M + h->level_off[l + 1] * ld, M + h->level_off[l] * ld, (const T *)h->ops_m2m,
                            st));
-    h->launches += 1;
+    const int np = 1 << (3 * l);
+    k_qd_up<<<(np + 127) / 128, 128, 0, st>>>(np, h->L / (1 << (l + 1)), h->box_qd + h->level_off[l + 1] * 4,
+                                              h->box_qd + h->level_off[l] * 4);
+    h->launches += 2;
   }
   mark(h, 4);
-  k_lattice<T><<<1, 256, sizeof(double) * K, st>>>(K, ld, h->L, h->ops_lat, h->moments, M, Lx);
+  k_lattice<T><<<1, 256, sizeof(double) * K, st>>>(K, ld, h->L, h->ops_lat, h->ops_lat_h3, h->moments, M, Lx,
+                                                    h->L_h3);
   h->launches += 1;
   MAHI_CK(cudaGetLastError());
   mark(h, 5);
@@ -882,12 +1203,8 @@ static cudaError_t eval_t(mahi_ctx *h, const XT *x, const double *lam, double *e
   }
   mark(h, 8);
   {
-    static bool attr = false;
     size_t sm = sizeof(V) * P2P_MAXSRC;
-    if (!attr) {
-      cudaFuncSetAttribute(k_p2p<T, XT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      attr = true;
-    }
+    if (sm > 48 * 1024) MAHI_CK(cudaFuncSetAttribute(k_p2p<T, XT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     k_p2p<T, XT><<<nleaf, P2P_THREADS, sm, st>>>(nb, h->L, coulomb_constant(), h->leaf_start, (const V *)h->part,
                                                  h->perm, h->moments, (T *)h->phi_s, (const T *)h->grad_s, forces,
                                                  h->energy_part);
@@ -896,11 +1213,18 @@ static cudaError_t eval_t(mahi_ctx *h, const XT *x, const double *lam, double *e
   }
   mark(h, 9);
   if (h->S > 0) {
+    const size_t smp = sizeof(T) * kSiteBatch * ld;
+    if (smp > 40 * 1024)
+      MAHI_CK(cudaFuncSetAttribute(k_site_phi<T, XT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smp));
+    k_site_phi<T, XT><<<dim3(h->S, h->d + 2), kSitePhiThreads, smp, st>>>(
+        h->S, h->site_ptr, h->site_atoms, h->d, P, ld, h->L, h->d_level_off, h->leaf_start, h->perm, x, h->qt, M,
+        h->box_qd, h->moments, h->L_h3, h->m2l_list, h->m2l_off, h->phi_part);
+    k_site_phi_sum<<<(h->n_site_atoms + 127) / 128, 128, 0, st>>>(h->n_site_atoms, h->d + 2, coulomb_constant(),
+                                                                   h->phi_part, h->phi_site);
     k_site<T, XT, XT><<<(h->S + 3) / 4, 128, 0, st>>>(h->S, h->L, coulomb_constant(), kSiteDegree, h->site_ptr,
-                                                      h->site_atoms, x, h->dq, lam, h->inv_perm, (const T *)h->phi_s,
-                                                      h->eta, h->eta_x, h->eta_y, h->eta_z, dEdl, h->site_energy,
-                                                      forces);
-    h->launches += 1;
+                                                      h->site_atoms, x, h->dq, lam, h->phi_site, h->eta, h->eta_x,
+                                                      h->eta_y, h->eta_z, dEdl, h->site_energy, forces);
+    h->launches += 3;
   }
   if (energy) {
     k_final_energy<<<1, 256, 0, st>>>(h->energy_part, nleaf, h->site_energy, h->S, energy);
@@ -909,6 +1233,44 @@ static cudaError_t eval_t(mahi_ctx *h, const XT *x, const double *lam, double *e
   MAHI_CK(cudaGetLastError());
   mark(h, 10);
   return cudaSuccess;
+}
+
+int upload_tables() {
+  static bool done = false;
+  if (done) return 0;
+  double a[kTriMax] = {0}, b[kTriMax] = {0}, dg[kMaxOrder + 1] = {0};
+  float af[kTriMax] = {0}, bf[kTriMax] = {0}, dgf[kMaxOrder + 1] = {0};
+  for (int l = 0; l <= kMaxOrder; ++l)
+    for (int m = 0; m <= l; ++m) {
+      const int k = l * (l + 1) / 2 + m;
+      if (l > m) {
+        a[k] = (2.0 * l - 1.0) / std::sqrt((double)(l + m) * (l - m));
+        b[k] = (l - m >= 2) ? std::sqrt((double)(l + m - 1) * (l - m - 1) / ((double)(l + m) * (l - m))) : 0.0;
+      }
+      af[k] = (float)a[k];
+      bf[k] = (float)b[k];
+    }
+  for (int m = 1; m <= kMaxOrder; ++m) { dg[m] = std::sqrt((2.0 * m - 1.0) / (2.0 * m)); dgf[m] = (float)dg[m]; }
+  static double ua[kTriSite], ub[kTriSite], ud[kSiteDegree + 1];
+  for (int l = 0; l <= kSiteDegree; ++l)
+    for (int m = 0; m <= l; ++m) {
+      const int k = l * (l + 1) / 2 + m;
+      ua[k] = (l > m) ? (2.0 * l - 1.0) / ((double)(l + m) * (l - m)) : 0.0;
+      ub[k] = (l > m) ? 1.0 / ((double)(l + m) * (l - m)) : 0.0;
+    }
+  ud[0] = 0.0;
+  for (int m = 1; m <= kSiteDegree; ++m) ud[m] = 1.0 / (2.0 * m);
+  if (cudaMemcpyToSymbol(c_a, a, sizeof(a)) != cudaSuccess) return -1;
+  if (cudaMemcpyToSymbol(c_b, b, sizeof(b)) != cudaSuccess) return -1;
+  if (cudaMemcpyToSymbol(c_diag, dg, sizeof(dg)) != cudaSuccess) return -1;
+  if (cudaMemcpyToSymbol(c_af, af, sizeof(af)) != cudaSuccess) return -1;
+  if (cudaMemcpyToSymbol(c_bf, bf, sizeof(bf)) != cudaSuccess) return -1;
+  if (cudaMemcpyToSymbol(c_diagf, dgf, sizeof(dgf)) != cudaSuccess) return -1;
+  if (cudaMemcpyToSymbol(c_ua, ua, sizeof(ua)) != cudaSuccess) return -1;
+  if (cudaMemcpyToSymbol(c_ub, ub, sizeof(ub)) != cudaSuccess) return -1;
+  if (cudaMemcpyToSymbol(c_udiag, ud, sizeof(ud)) != cudaSuccess) return -1;
+  done = true;
+  return 0;
 }
 
 int enqueue_eval(mahi_ctx *h, const void *x, int x_is_fp64, const double *lambda, double *energy, void *forces,
@@ -924,12 +1286,21 @@ int enqueue_eval(mahi_ctx *h, const void *x, int x_is_fp64, const double *lambda
   return e == cudaSuccess ? 0 : (int)e;
 }
 
+__global__ void k_patch_site_phi(int nsa, const int *__restrict__ site_atoms, const double *__restrict__ phi_site,
+                                 double *__restrict__ phi) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < nsa) phi[site_atoms[k]] = phi_site[k];
+}
+
 int enqueue_potential(mahi_ctx *h, double *phi) {
   int g = (int)((h->N + 255) / 256);
   if (h->prec == MAHI_FP64)
     k_unpermute_phi<double><<<g, 256, 0, h->stream>>>(h->N, h->inv_perm, (const double *)h->phi_s, phi);
   else
     k_unpermute_phi<float><<<g, 256, 0, h->stream>>>(h->N, h->inv_perm, (const float *)h->phi_s, phi);
+  if (h->n_site_atoms > 0)
+    k_patch_site_phi<<<(h->n_site_atoms + 255) / 256, 256, 0, h->stream>>>(h->n_site_atoms, h->site_atoms,
+                                                                          h->phi_site, phi);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

@@ -149,3 +149,12 @@ def test_energy_only_route_matches_potential_route(neutral):
     _, _, e = oracle.ewald(x, q, 2.4, rc=0.7)
     assert oracle.ewald_energy(x, q, 2.4, rc=0.7) == pytest.approx(e, rel=1e-12)
     assert oracle.ewald_energy(x, q, 2.4, rc=1.1) == pytest.approx(e, rel=1e-12)
+
+
+def test_real_and_reciprocal_parts_add_up():
+    x, q = _random_system(10, 300, 2.2, neutral=False)
+    p, g, _ = oracle.ewald(x, q, 2.2)
+    p1, g1, _ = oracle.ewald(x, q, 2.2, parts=1)
+    p2, g2, _ = oracle.ewald(x, q, 2.2, parts=2)
+    np.testing.assert_allclose(p1 + p2, p, atol=1e-12)
+    np.testing.assert_allclose(g1 + g2, g, atol=1e-11)
