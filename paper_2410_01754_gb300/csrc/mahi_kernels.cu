@@ -143,6 +143,15 @@ __device__ __forceinline__ void r_columns(int P, double x, double y, double z, C
   }
 }
 
+// 1/sqrt(r2) to FP64 accuracy from the FP32 hardware estimate and two FP64
+// Newton-Raphson steps y <- y (3 - r2 y^2)/2 (each squares the relative error)
+__device__ __forceinline__ double rsqrt_dp(double r2) {
+  double y = (double)rsqrtf((float)r2);
+  y = y * fma(-0.5 * r2, y * y, 1.5);
+  y = y * fma(-0.5 * r2, y * y, 1.5);
+  return y;
+}
+
 // real-layout index of (l, m >= 0): Re part (Im = +1 for m > 0)
 __device__ __forceinline__ int ridx(int l, int m) { return m == 0 ? l * l : l * l + 2 * m - 1; }
 
@@ -891,7 +900,8 @@ template <typename T, typename XT>
 __global__ void __launch_bounds__(kSitePhiThreads) k_site_phi(
     int S, const int *__restrict__ site_ptr, const int *__restrict__ site_atoms, int d, int P, int ld, double L,
     const int64_t *__restrict__ level_off, const int *__restrict__ leaf_start, const int *__restrict__ perm,
-    const XT *__restrict__ x, const double *__restrict__ qt, const T *__restrict__ M, const double *__restrict__ qd,
+    const int *__restrict__ inv_perm, const typename V4<T>::type *__restrict__ part, const XT *__restrict__ x,
+    const double *__restrict__ qt, const T *__restrict__ M, const double *__restrict__ qd,
     const double *__restrict__ mom, const double *__restrict__ Lh3, const int *__restrict__ list,
     const int *__restrict__ off, double *__restrict__ phi_part) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -901,11 +911,12 @@ __global__ void __launch_bounds__(kSitePhiThreads) k_site_phi(
   __shared__ int Is[kMaxSiteAtoms][3], grp[kMaxSiteAtoms];
   __shared__ double bq[kSiteBatch][4], bc[kSiteBatch][3];
   __shared__ int64_t brow[kSiteBatch];
-  const int site = blockIdx.x, part = blockIdx.y, nparts = d + 2;
+  const int site = blockIdx.x, pidx = blockIdx.y, nparts = d + 2;
   if (site >= S) return;
   const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
   const int b0 = site_ptr[site], n = site_ptr[site + 1] - b0;
   const int nb = 1 << d;
+  const double sl = L / nb;
   for (int a = tid; a < n; a += blockDim.x) {
     const int i = site_atoms[b0 + a];
     for (int k = 0; k < 3; ++k) {
@@ -930,9 +941,9 @@ __global__ void __launch_bounds__(kSitePhiThreads) k_site_phi(
     }
     __syncthreads();
   };
-  if (part < d) {
-    const int l = part + 1, shift = d - l, side = 1 << l;
-    const double s = L / side;
+  if (pidx < d) {
+    const int l = pidx + 1, shift = d - l, side = 1 << l;
+    const double s = L / side, inv_s = 1.0 / s;
     for (int a = tid; a < n; a += blockDim.x) {
       int g = a;
       for (int b = 0; b < a; ++b)
@@ -968,16 +979,18 @@ __global__ void __launch_bounds__(kSitePhiThreads) k_site_phi(
           double v = 0.0;
           if (grp[a] == lead) {
             const double rx = ps[a][0] - bc[r][0], ry = ps[a][1] - bc[r][1], rz = ps[a][2] - bc[r][2];
-            const double r2 = rx * rx + ry * ry + rz * rz, ri = 1.0 / sqrt(r2);
+            const double ri = rsqrt_dp(rx * rx + ry * ry + rz * rz);
             v = bq[r][0] * ri + (bq[r][1] * rx + bq[r][2] * ry + bq[r][3] * rz) * ri * ri * ri;
-            if (P >= 2) v += (double)m2p_high_smem<T>(P, Ms + (size_t)r * ld, (T)(rx / s), (T)(ry / s), (T)(rz / s)) / s;
+            if (P >= 2)
+              v += (double)m2p_high_smem<T>(P, Ms + (size_t)r * ld, (T)(rx * inv_s), (T)(ry * inv_s), (T)(rz * inv_s)) *
+                   inv_s;
           }
           vals[r * kMaxSiteAtoms + a] = v;
         }
         reduce_batch(nbx);
       }
     }
-  } else if (part == d) {
+  } else if (pidx == d) {
     // root images 2 <= |n|_inf <= 3: source centre c - nL
     for (int o0 = 0; o0 < kNumOffsets; o0 += kSiteBatch) {
       const int nbx = min(kSiteBatch, kNumOffsets - o0);
@@ -985,37 +998,33 @@ __global__ void __launch_bounds__(kSitePhiThreads) k_site_phi(
         const int r = q % nbx, a = q / nbx, oid = o0 + r;
         const double rx = ps[a][0] - (0.5 * L - off[oid * 3] * L), ry = ps[a][1] - (0.5 * L - off[oid * 3 + 1] * L),
                      rz = ps[a][2] - (0.5 * L - off[oid * 3 + 2] * L);
-        const double r2 = rx * rx + ry * ry + rz * rz, ri = 1.0 / sqrt(r2);
+        const double ri = rsqrt_dp(rx * rx + ry * ry + rz * rz), iL = 1.0 / L;
         double v = mom[0] * ri + (mom[1] * rx + mom[2] * ry + mom[3] * rz) * ri * ri * ri;
-        if (P >= 2) v += (double)m2p_high<T>(P, M, (T)(rx / L), (T)(ry / L), (T)(rz / L)) / L;
+        if (P >= 2) v += (double)m2p_high<T>(P, M, (T)(rx * iL), (T)(ry * iL), (T)(rz * iL)) * iL;
         vals[r * kMaxSiteAtoms + a] = v;
       }
       reduce_batch(nbx);
     }
   } else {
-    // near field: warp w takes atoms w, w+4, ...; lanes over sources (FP64)
+    // near field: warp w takes atoms w, w+4, ...; lanes over sources.  Positions
+    // come from the sorted leaf-relative coordinates (exact differences in
+    // FP64: r = (u_i - u_j) - o s), charges from the FP64 scaled charges.
+    using V = typename V4<T>::type;
     for (int a = wib; a < n; a += blockDim.x / 32) {
       const int i = site_atoms[b0 + a];
+      const V me = part[inv_perm[i]];
       double v = 0.0;
       for (int k = 0; k < 27; ++k) {
         const int dx = k % 3 - 1, dy = (k / 3) % 3 - 1, dz = k / 9 - 1;
-        const int g[3] = {Is[a][0] + dx, Is[a][1] + dy, Is[a][2] + dz};
-        double sh[3];
-        int w[3];
-        for (int c = 0; c < 3; ++c) { w[c] = wrapi(g[c], nb); sh[c] = (double)((g[c] - w[c]) / nb) * L; }
-        const int leaf = (int)d_morton(w[0], w[1], w[2]);
+        const int leaf = (int)d_morton(wrapi(Is[a][0] + dx, nb), wrapi(Is[a][1] + dy, nb), wrapi(Is[a][2] + dz, nb));
+        const double ox = dx * sl, oy = dy * sl, oz = dz * sl;
         for (int t = leaf_start[leaf] + lane; t < leaf_start[leaf + 1]; t += 32) {
           const int j = perm[t];
           if (j == i && k == 13) continue;
-          double r[3];
-          for (int c = 0; c < 3; ++c) {
-            double q = (double)x[3 * (size_t)j + c];
-            q -= floor(q / L) * L;
-            if (q >= L) q -= L;
-            if (q < 0.0) q = 0.0;
-            r[c] = ps[a][c] - (q + sh[c]);
-          }
-          v += qt[j] / sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+          const V src = part[t];
+          const double rx = ((double)me.x - (double)src.x) - ox, ry = ((double)me.y - (double)src.y) - oy,
+                       rz = ((double)me.z - (double)src.z) - oz;
+          v += qt[j] * rsqrt_dp(rx * rx + ry * ry + rz * rz);
         }
       }
       for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffff, v, o);
@@ -1037,7 +1046,7 @@ __global__ void __launch_bounds__(kSitePhiThreads) k_site_phi(
     }
     __syncthreads();
   }
-  for (int a = tid; a < n; a += blockDim.x) phi_part[(size_t)(b0 + a) * nparts + part] = acc[a];
+  for (int a = tid; a < n; a += blockDim.x) phi_part[(size_t)(b0 + a) * nparts + pidx] = acc[a];
 }
 
 // phi_site = f * (sum of the parts, in part order)
@@ -1217,8 +1226,8 @@ static cudaError_t eval_t(mahi_ctx *h, const XT *x, const double *lam, double *e
     if (smp > 40 * 1024)
       MAHI_CK(cudaFuncSetAttribute(k_site_phi<T, XT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smp));
     k_site_phi<T, XT><<<dim3(h->S, h->d + 2), kSitePhiThreads, smp, st>>>(
-        h->S, h->site_ptr, h->site_atoms, h->d, P, ld, h->L, h->d_level_off, h->leaf_start, h->perm, x, h->qt, M,
-        h->box_qd, h->moments, h->L_h3, h->m2l_list, h->m2l_off, h->phi_part);
+        h->S, h->site_ptr, h->site_atoms, h->d, P, ld, h->L, h->d_level_off, h->leaf_start, h->perm, h->inv_perm,
+        (const V *)h->part, x, h->qt, M, h->box_qd, h->moments, h->L_h3, h->m2l_list, h->m2l_off, h->phi_part);
     k_site_phi_sum<<<(h->n_site_atoms + 127) / 128, 128, 0, st>>>(h->n_site_atoms, h->d + 2, coulomb_constant(),
                                                                    h->phi_part, h->phi_site);
     k_site<T, XT, XT><<<(h->S + 3) / 4, 128, 0, st>>>(h->S, h->L, coulomb_constant(), kSiteDegree, h->site_ptr,
