@@ -131,6 +131,37 @@ int mahi_launch_count(mahi_t h);
 int mahi_lattice_coeffs(int32_t order_p, int32_t shell, double *coeffs);
 int mahi_lattice_eval(double box_L_nm, int32_t order_p, int32_t shell, int64_t n, const double *r, double *H);
 
+/* Per-site HI terms without any device allocation.  The paper has no
+ * counterpart to this entry point: it is for callers that cannot allocate
+ * device memory at the point where they need the terms (code running while a
+ * stream is captured, programs whose device memory belongs to another
+ * runtime or a fixed pool, or MD engines that compute the charge-scaled
+ * potential phi~ with their own solver).  It runs the per-site stage of
+ * mahi_eval (k_s, dE/dlambda, energy and force corrections) on
+ * caller-provided inputs; its only scratch is a file-scope device array.
+ *   site_ptr    device, n_sites + 1 int32 (CSR offsets into site_atoms)
+ *   site_atoms  device, site_ptr[n_sites] int32 atom indices; every site has
+ *               1..64 atoms (a malformed site yields NaN in its outputs)
+ *   x           device, positions (float64 if x_is_fp64 else float32), n x 3
+ *   qA, qB      device float64 charges of the two forms (indexed by atom)
+ *   lambda      device, n_sites float64
+ *   phi         device float64 charge-scaled potential phi~ (kJ/mol/e) per atom,
+ *               e.g. from mahi_get_potential after mahi_eval
+ *   dEdlambda   device, n_sites float64 (out; may be NULL)
+ *   energy_correction  device, 1 float64 (out; sum_s 1/2 lam(1-lam) k_s; may be NULL)
+ *   forces      device, n x 3 in the x dtype: the intra-site force corrections are
+ *               ADDED to the values already there for site atoms (may be NULL)
+ * Limits: n_sites <= 4096 (the scratch holds one energy slot per site, 32 KiB),
+ * else MAHI_ERR_INVALID_ARG.  The first call on a device (with that device
+ * current) resolves the scratch address and fills its lattice tables
+ * synchronously; make it before any stream capture.  Later calls only enqueue
+ * kernels on cuda_stream.  Calls share the scratch: calls that overlap on the
+ * GPU race. */
+int mahi_site_terms_static(double box_L_nm, int32_t n_sites, const int32_t *site_ptr, const int32_t *site_atoms,
+                           const void *x, int32_t x_is_fp64, const double *qA, const double *qB,
+                           const double *lambda, const double *phi, double *dEdlambda, double *energy_correction,
+                           void *forces, void *cuda_stream);
+
 /* Coulomb constant used by the library (kJ mol^-1 nm e^-2). */
 double mahi_coulomb_constant(void);
 

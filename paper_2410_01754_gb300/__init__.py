@@ -39,6 +39,10 @@ _SIGS = {
     "mahi_lattice_coeffs": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p]),
     "mahi_lattice_eval": (ctypes.c_int, [ctypes.c_double, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64,
                                          ctypes.c_void_p, ctypes.c_void_p]),
+    "mahi_site_terms_static": (ctypes.c_int, [ctypes.c_double, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                              ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                              ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                              ctypes.c_void_p, ctypes.c_void_p]),
     "mahi_coulomb_constant": (ctypes.c_double, []),
     "mahi_error_string": (ctypes.c_char_p, [ctypes.c_int]),
     "mahi_last_cuda_error": (ctypes.c_char_p, []),
@@ -158,6 +162,17 @@ def mahi_lattice_eval(box_L_nm, order_p, r, shell=1):
     _ck(lib().mahi_lattice_eval(float(box_L_nm), int(order_p), int(shell), r.shape[0], r.ctypes.data, out.ctypes.data),
         "mahi_lattice_eval")
     return out
+
+
+def mahi_site_terms_static(box_L_nm, site_ptr, site_atoms, x, qA, qB, lam, phi, dEdlambda=None,
+                           energy_correction=None, forces=None, stream=None):
+    """Allocation-free per-site HI terms (device tensors in, device tensors out)."""
+    n_sites = int(site_ptr.numel()) - 1
+    x_is_fp64 = 1 if str(x.dtype).endswith("float64") else 0
+    _ck(lib().mahi_site_terms_static(float(box_L_nm), n_sites, _ptr(site_ptr), _ptr(site_atoms), _ptr(x), x_is_fp64,
+                                     _ptr(qA), _ptr(qB), _ptr(lam), _ptr(phi), _ptr(dEdlambda),
+                                     _ptr(energy_correction), _ptr(forces), _stream_handle(stream)),
+        "mahi_site_terms_static")
 
 
 def mahi_coulomb_constant():
