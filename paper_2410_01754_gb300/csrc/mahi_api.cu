@@ -45,7 +45,7 @@ static void free_all(mahi_ctx *h) {
                   h->m2l_list, h->m2l_off, h->site_ptr, h->site_atoms, h->moments_part, h->moments,
                   h->energy_part, h->site_energy, h->tc_ops, h->tc_msplit, h->tc_level_off, h->tc_units, h->tc_error, h->d_x_stage,
                   h->d_lam_stage, h->d_E_stage, h->d_dEdl_stage, h->d_F_stage, h->ops_lat_h3, h->L_h3,
-                  h->box_qd, h->phi_site, h->phi_part, h->d_level_off};
+                  h->box_qd, h->phi_site, h->phi_part, h->d_level_off, h->tc_error_site};
   for (void *b : bufs)
     if (b) cudaFree(b);
   for (int i = 0; i < 32; ++i)
@@ -126,6 +126,7 @@ int mahi_create(double box_L_nm, int64_t n_atoms, int32_t n_sites, int32_t order
   h->L = box_L_nm; h->N = n_atoms; h->S = n_sites; h->p = order_p; h->d = depth; h->prec = precision;
   h->stream = (cudaStream_t)cuda_stream;
   h->device = dev;
+  h->num_sms = prop.multiProcessorCount;
   h->K = ncoef(order_p);
   h->ld = nstride(order_p);
   h->nleaf = 1 << (3 * depth);
@@ -203,6 +204,8 @@ int mahi_create(double box_L_nm, int64_t n_atoms, int32_t n_sites, int32_t order
     if ((e = upload_ops<double>(lat3, &tmp)) != cudaSuccess) return fail(e, "ops");
     h->ops_lat_h3 = (double *)tmp;
     AL(h->L_h3, sizeof(double) * K);
+    AL(h->tc_error_site, 16);
+    cudaMemset(h->tc_error_site, 0, 16);
     AL(h->box_qd, sizeof(double) * 4 * h->nbox_total);
     AL(h->d_level_off, sizeof(int64_t) * (kMaxDepth + 2));
     if ((e = cudaMemcpy(h->d_level_off, h->level_off, sizeof(int64_t) * (kMaxDepth + 2), cudaMemcpyHostToDevice)) !=
@@ -310,7 +313,7 @@ int mahi_set_charges(mahi_t h, const double *qA, const double *qB, const int32_t
   if (h->phi_site) { cudaFree(h->phi_site); h->phi_site = nullptr; }
   if (h->phi_part) { cudaFree(h->phi_part); h->phi_part = nullptr; }
   CK(dalloc(&h->phi_site, std::max<size_t>(1, atoms.size()) * sizeof(double)));
-  CK(dalloc(&h->phi_part, std::max<size_t>(1, atoms.size()) * (h->d + 2) * sizeof(double)));
+  CK(dalloc(&h->phi_part, std::max<size_t>(1, atoms.size()) * kSiteChunksMax * sizeof(double)));
   CK(dalloc(&h->site_ptr, (S + 1) * sizeof(int)));
   CK(dalloc(&h->site_atoms, std::max<size_t>(1, atoms.size()) * sizeof(int)));
   CK(cudaMemcpy(h->site_ptr, ptr.data(), (S + 1) * sizeof(int), cudaMemcpyHostToDevice));
@@ -368,6 +371,11 @@ int mahi_eval_host(mahi_t h, const void *x_host, int32_t x_is_fp64, const double
     int flag = 0;
     CK(cudaMemcpy(&flag, h->tc_error, sizeof(int), cudaMemcpyDeviceToHost));
     if (flag) return MAHI_ERR_TIMEOUT;
+  }
+  {
+    int flag = 0;
+    CK(cudaMemcpy(&flag, h->tc_error_site, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag) return MAHI_ERR_INVALID_ARG;  // site traversal frontier overflowed
   }
   return MAHI_OK;
 }

@@ -19,6 +19,7 @@ constexpr int kNumOffsets = 316;       // {-3..3}^3 minus {-1..1}^3
 constexpr int kListLen = 189;          // M2L interaction list of one box
 constexpr int kLatticeShell = 3;       // images |n|_inf <= 3 exactly, beyond by H_3
 constexpr int kSiteDegree = 40;        // degree of H_1 in the per-site correction
+constexpr int kSiteChunksMax = 16;   // blocks sharing one site in the site-potential traversal
 constexpr double kPi = 3.14159265358979323846264338327950288;
 
 // Coulomb constant N_A e^2 / (4 pi eps0) in kJ mol^-1 nm e^-2 (CODATA 2018).
@@ -74,6 +75,7 @@ struct mahi_ctx {
   double L = 0;
   int64_t N = 0;
   int S = 0, p = 0, d = 0, prec = 0;
+  int num_sms = 152;                          // streaming multiprocessors of the device
   int K = 0, ld = 0;           // coefficients per expansion, row stride
   int nleaf = 0;
   int64_t nbox_total = 0;
@@ -120,6 +122,7 @@ struct mahi_ctx {
   int *tc_units = nullptr;
   int tc_nunits = 0;
   int *tc_error = nullptr;
+  int *tc_error_site = nullptr;               // frontier overflow flag of the site traversal
   // host staging for mahi_eval_host
   void *d_x_stage = nullptr;
   double *d_lam_stage = nullptr, *d_E_stage = nullptr, *d_dEdl_stage = nullptr;

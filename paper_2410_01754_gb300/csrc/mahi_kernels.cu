@@ -576,6 +576,12 @@ __device__ __forceinline__ float rinv(float r2) {
   return y * fmaf(-0.5f * r2, y * y, 1.5f);
 }
 constexpr int P2P_MAXSRC = 2048;
+// FP64 1/sqrt(r2): single-precision seed and one FP64 Newton-Raphson step; the
+// seed's relative error e (about 2^-23) becomes 1.5 e^2 after the step
+__device__ __forceinline__ double rinv_dd(double r2) {
+  const double y = (double)rsqrtf((float)r2);
+  return y * fma(-0.5 * r2, y * y, 1.5);
+}
 
 template <typename T, typename FT>
 __global__ void __launch_bounds__(P2P_THREADS) k_p2p(int nb, double L, double fcoul, const int *__restrict__ leaf_start,
@@ -864,189 +870,465 @@ __device__ __forceinline__ T m2p_high(int P, const T *__restrict__ M, T ux, T uy
   return acc;
 }
 
-// phi of a box (charge Q, dipole D about its centre z, physical units) at x:
-// low orders in FP64 plus the l >= 2 tail from the multipole row.
-template <typename T>
-__device__ __forceinline__ double box_potential(int P, const T *__restrict__ Mrow, const double *__restrict__ qd,
-                                                double rx, double ry, double rz, double s) {
-  const double r2 = rx * rx + ry * ry + rz * rz, ri = 1.0 / sqrt(r2);
-  double v = qd[0] * ri + (qd[1] * rx + qd[2] * ry + qd[3] * rz) * ri * ri * ri;
-  if (P >= 2) v += (double)m2p_high<T>(P, Mrow, (T)(rx / s), (T)(ry / s), (T)(rz / s)) / s;
-  return v;
+// Site-atom potential by a separation-controlled traversal of the periodic
+// octree, shared by all atoms of a site.  The sources are the 343 root images
+// |n|_inf <= 3 (beyond them the H_3 lattice expansion takes over).  With R the
+// radius of the site's atoms about their centroid c, a box of edge s at
+// distance D from c is used through its multipole (M2P at every atom) only if
+// its circumradius (sqrt(3)/2) s < theta (D - R), so every multipole term
+// converges at least like theta^(p+1) at every atom; otherwise it is opened,
+// and unseparated leaves are summed directly.
+//
+// Precision.  The sites change charge, so the HI derivative needs the absolute
+// potential at the site to about 1e-8 relative, which single precision per term
+// does not reach over thousands of terms.  FP64 is slow on this part, so it is
+// kept to dense per-site work:
+//  * charge + dipole of a separated box: the FP64 value at c (one per box and
+//    site, packed across the lanes that stage the batch) plus, per atom, the
+//    change from c to the atom in working precision by a cancellation-free
+//    difference formula, whose error is smaller by |x - c| / D;
+//  * orders l >= 2: working precision (their rounding is far below the bar);
+//  * direct leaves: double-float pair sums from error-free transforms (relative
+//    error near 2^-44 per pair);
+//  * per-thread sums in double-float, reduced in FP64 in a fixed order.
+// The batches of separated boxes and leaves are dealt round-robin to G blocks
+// per site; each block repeats the (cheap) classification and writes its own
+// partial sum, so results are bitwise reproducible.
+constexpr float kSiteTheta = 0.35f;
+constexpr int kFrontier = 1536;            // frontier / list entries per buffer
+constexpr int kSiteThreads = 128;
+constexpr int kSiteBatchMax = 64;
+
+__device__ __forceinline__ int pack_entry(int box, int img) { return (box << 9) | img; }
+
+// block-wide exclusive prefix of `cnt` (per thread) in thread order; returns the
+// offset of this thread and writes the total to *total
+__device__ __forceinline__ int block_scan(int cnt, int *wsum, int *total) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  int x = cnt;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffff, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wsum[w] = x;
+  __syncthreads();
+  int off = 0, tot = 0;
+  for (int k = 0; k < nw; ++k) {
+    if (k < w) off += wsum[k];
+    tot += wsum[k];
+  }
+  __syncthreads();
+  *total = tot;
+  return off + x - cnt;
 }
 
-constexpr int kSitePhiThreads = 128;
-constexpr int kSiteBatch = 32;  // source boxes staged per round
-
-template <typename T>
-__device__ __forceinline__ T m2p_high_smem(int P, const T *M, T ux, T uy, T uz) {
-  T acc = T(0);
-  it_columns<T>(P, ux, uy, uz, [&](int l, int m, T re, T im) {
-    if (l < 2) return;
-    const int k = ridx(l, m);
-    acc += (m == 0) ? M[k] * re : T(2) * (M[k] * re - M[k + 1] * im);
-  });
-  return acc;
+// Knuth's two-sum: a + b = s + e exactly
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+  s = a + b;
+  const float bv = s - a;
+  e = (a - (s - bv)) + (b - bv);
 }
 
-// Grid (site, part): part l-1 < d does the M2P of interaction level l, part d the
-// root images 2 <= |n|_inf <= 3, part d+1 the near field, the far-image lattice
-// part and the dipole/background term.  Atoms of the site that share an
-// ancestor box at level l share its 189 interaction-list boxes, whose multipole
-// rows are staged in shared memory 32 at a time (coalesced).  Every sum is
-// reduced in a fixed order, so results are bitwise reproducible.  Output:
-// phi_part[atom][part] (f = 1).
-template <typename T, typename XT>
-__global__ void __launch_bounds__(kSitePhiThreads) k_site_phi(
-    int S, const int *__restrict__ site_ptr, const int *__restrict__ site_atoms, int d, int P, int ld, double L,
-    const int64_t *__restrict__ level_off, const int *__restrict__ leaf_start, const int *__restrict__ perm,
-    const int *__restrict__ inv_perm, const typename V4<T>::type *__restrict__ part, const XT *__restrict__ x,
-    const double *__restrict__ qt, const T *__restrict__ M, const double *__restrict__ qd,
-    const double *__restrict__ mom, const double *__restrict__ Lh3, const int *__restrict__ list,
-    const int *__restrict__ off, double *__restrict__ phi_part) {
+// running sum in double-float (single precision) or plain FP64
+template <typename T> struct SiteAcc;
+template <> struct SiteAcc<float> {
+  float h = 0.f, l = 0.f;
+  __device__ __forceinline__ void add(float v) {
+    float s, e;
+    two_sum(h, v, s, e);
+    h = s;
+    l += e;
+  }
+  __device__ __forceinline__ void add2(float vh, float vl) {
+    float s, e;
+    two_sum(h, vh, s, e);
+    h = s;
+    l += e + vl;
+  }
+  __device__ __forceinline__ double value() const { return (double)h + (double)l; }
+};
+template <> struct SiteAcc<double> {
+  double h = 0.0;
+  __device__ __forceinline__ void add(double v) { h += v; }
+  __device__ __forceinline__ void add2(double vh, double vl) { h += vh + vl; }
+  __device__ __forceinline__ double value() const { return h; }
+};
+
+// target m = h + l relative to a leaf centre (double-float; plain FP64 in h)
+template <typename T> struct SiteTarget { T hx, hy, hz, lx, ly, lz; };
+
+// m = x - g sl for a stored coordinate x and an integer leaf offset g, with
+// sl = slh + sll; g slh is split exactly by an FMA
+__device__ __forceinline__ void split_offset(float x, int g, float slh, float sll, float &mh, float &ml) {
+  const float gf = (float)g, oh = gf * slh, oe = fmaf(gf, slh, -oh);
+  two_sum(x, -oh, mh, ml);
+  ml = (ml - oe) - gf * sll;
+}
+
+__device__ __forceinline__ SiteTarget<float> site_target(float x, float y, float z, int gx, int gy, int gz, double sl) {
+  const float slh = (float)sl, sll = (float)(sl - (double)slh);
+  SiteTarget<float> t;
+  split_offset(x, gx, slh, sll, t.hx, t.lx);
+  split_offset(y, gy, slh, sll, t.hy, t.ly);
+  split_offset(z, gz, slh, sll, t.hz, t.lz);
+  return t;
+}
+__device__ __forceinline__ SiteTarget<double> site_target(double x, double y, double z, int gx, int gy, int gz,
+                                                          double sl) {
+  return SiteTarget<double>{x - gx * sl, y - gy * sl, z - gz * sl, 0.0, 0.0, 0.0};
+}
+
+// q / |m - y| for a source y (stored coordinates relative to the leaf centre).
+// Single precision: the difference and its square are kept exactly as hi + lo
+// pairs; 1/sqrt comes from the hardware seed y0 and one Newton correction
+// y0 (1 + res/2), whose residual res = 1 - r^2 y0^2 is formed from exact
+// products; the result is vh + vl.
+__device__ __forceinline__ void pair_pot(const SiteTarget<float> &m, float sx, float sy, float sz, float q,
+                                         float &vh, float &vl) {
+  float hx, ex, hy, ey, hz, ez;
+  two_sum(m.hx, -sx, hx, ex);
+  two_sum(m.hy, -sy, hy, ey);
+  two_sum(m.hz, -sz, hz, ez);
+  ex += m.lx; ey += m.ly; ez += m.lz;
+  const float px = hx * hx, py = hy * hy, pz = hz * hz;
+  const float qx = fmaf(hx, hx, -px), qy = fmaf(hy, hy, -py), qz = fmaf(hz, hz, -pz);
+  float s1, t1, s2, t2;
+  two_sum(px, py, s1, t1);
+  two_sum(s1, pz, s2, t2);
+  const float r2l = (t1 + t2) + (qx + qy + qz) + 2.0f * (hx * ex + hy * ey + hz * ez);
+  const float y0 = rsqrtf(s2);
+  const float t = y0 * y0, te = fmaf(y0, y0, -t);
+  const float u = s2 * t, ue = fmaf(s2, t, -u);
+  const float res = ((1.0f - u) - ue) - fmaf(s2, te, r2l * t);
+  vh = q * y0;
+  vl = fmaf(q, y0, -vh) + q * (0.5f * y0 * res);
+}
+__device__ __forceinline__ void pair_pot(const SiteTarget<double> &m, double sx, double sy, double sz, double q,
+                                         double &vh, double &vl) {
+  const double dx = m.hx - sx, dy = m.hy - sy, dz = m.hz - sz;
+  vh = q / sqrt(dx * dx + dy * dy + dz * dz);
+  vl = 0.0;
+}
+
+__device__ __forceinline__ float site_div(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double site_div(double a, double b) { return a / b; }
+
+// l >= 2 part of the M2P, sum_lm M~_lm It_lm(u) over 2 <= l <= PP, at two points
+// sharing one multipole row; with the order a compile-time constant the
+// recursion coefficients become immediate operands and each row load serves
+// both points.
+template <typename T, int PP>
+__device__ __forceinline__ void m2p_high2(const T *__restrict__ M, T x0, T y0, T z0, T x1, T y1, T z1, T &v0,
+                                          T &v1) {
+  const T i0 = rinv(x0 * x0 + y0 * y0 + z0 * z0), i1 = rinv(x1 * x1 + y1 * y1 + z1 * z1);
+  const T q0 = i0 * i0, q1 = i1 * i1, zq0 = z0 * q0, zq1 = z1 * q1;
+  T dr0 = i0, di0 = T(0), dr1 = i1, di1 = T(0);
+  T acc0 = T(0), acc1 = T(0);
+#pragma unroll
+  for (int m = 0; m <= PP; ++m) {
+    if (m > 0) {
+      const T f = -tab_diag<T>(m);
+      const T f0 = f * q0, f1 = f * q1;
+      const T tr0 = f0 * (x0 * dr0 - y0 * di0), ti0 = f0 * (x0 * di0 + y0 * dr0);
+      const T tr1 = f1 * (x1 * dr1 - y1 * di1), ti1 = f1 * (x1 * di1 + y1 * dr1);
+      dr0 = tr0; di0 = ti0; dr1 = tr1; di1 = ti1;
+    }
+    T pr0 = T(0), pi0 = T(0), cr0 = dr0, ci0 = di0;
+    T pr1 = T(0), pi1 = T(0), cr1 = dr1, ci1 = di1;
+    if (m >= 2) {
+      const int k = ridx(m, m);
+      const T mr = T(2) * M[k], mi = T(-2) * M[k + 1];
+      acc0 += mr * cr0 + mi * ci0;
+      acc1 += mr * cr1 + mi * ci1;
+    }
+#pragma unroll
+    for (int l = m + 1; l <= PP; ++l) {
+      const int k = l * (l + 1) / 2 + m;
+      const T a = tab_a<T>(k), b = tab_b<T>(k);
+      const T a0 = a * zq0, b0 = b * q0, a1 = a * zq1, b1 = b * q1;
+      const T nr0 = a0 * cr0 - b0 * pr0, ni0 = a0 * ci0 - b0 * pi0;
+      const T nr1 = a1 * cr1 - b1 * pr1, ni1 = a1 * ci1 - b1 * pi1;
+      pr0 = cr0; pi0 = ci0; cr0 = nr0; ci0 = ni0;
+      pr1 = cr1; pi1 = ci1; cr1 = nr1; ci1 = ni1;
+      if (l >= 2) {
+        const int kk = ridx(l, m);
+        if (m == 0) {
+          const T mr = M[kk];
+          acc0 += mr * cr0;
+          acc1 += mr * cr1;
+        } else {
+          const T mr = T(2) * M[kk], mi = T(-2) * M[kk + 1];
+          acc0 += mr * cr0 + mi * ci0;
+          acc1 += mr * cr1 + mi * ci1;
+        }
+      }
+    }
+  }
+  v0 = acc0;
+  v1 = acc1;
+}
+
+template <typename T, int PP>
+__global__ void __launch_bounds__(kSiteThreads, 3) k_site_phi(
+    int S, int G, const int *__restrict__ site_ptr, const int *__restrict__ site_atoms, int d, int P, int ld,
+    int lds, int nbmax, double L, const int64_t *__restrict__ level_off, const int *__restrict__ leaf_start,
+    const int *__restrict__ inv_perm, const typename V4<T>::type *__restrict__ part, const T *__restrict__ M,
+    const double *__restrict__ qd, const double *__restrict__ mom, const double *__restrict__ Lh3,
+    double *__restrict__ phi_part, int *__restrict__ err) {
+  using V = typename V4<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T *Ms = reinterpret_cast<T *>(smem_raw);                                // [kSiteBatch][ld]
-  __shared__ double ps[kMaxSiteAtoms][3], acc[kMaxSiteAtoms];
-  __shared__ double vals[kSiteBatch * kMaxSiteAtoms];
-  __shared__ int Is[kMaxSiteAtoms][3], grp[kMaxSiteAtoms];
-  __shared__ double bq[kSiteBatch][4], bc[kSiteBatch][3];
-  __shared__ int64_t brow[kSiteBatch];
-  const int site = blockIdx.x, pidx = blockIdx.y, nparts = d + 2;
+  int *fa = reinterpret_cast<int *>(smem_raw);          // frontier (current)
+  int *fb = fa + kFrontier;                             // frontier (next)
+  int *sep = fb + kFrontier;                            // separated boxes / direct leaves of this level
+  T *Ms = reinterpret_cast<T *>(sep + kFrontier);       // [nbmax][lds] staged multipole rows
+  __shared__ double pa[kMaxSiteAtoms][3], cen[4], base_s[kSiteBatchMax], res_s[kSiteThreads][2];
+  __shared__ T pu[kMaxSiteAtoms][3], puu[kMaxSiteAtoms];
+  __shared__ T rw[kSiteBatchMax][3], rp[kSiteBatchMax][3], rQ[kSiteBatchMax], rB[kSiteBatchMax],
+      rBi[kSiteBatchMax], rpw[kSiteBatchMax];
+  __shared__ V me[kMaxSiteAtoms];
+  __shared__ int sa_s[kMaxSiteAtoms], aI[kMaxSiteAtoms][3], brow_s[kSiteBatchMax], bimg[kSiteBatchMax], wsum[32];
+  const int site = blockIdx.x / G, g = blockIdx.x % G, tid = threadIdx.x;
   if (site >= S) return;
-  const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
   const int b0 = site_ptr[site], n = site_ptr[site + 1] - b0;
+  if (n <= 0 || n > kMaxSiteAtoms) return;  // rejected when the site map is set
   const int nb = 1 << d;
   const double sl = L / nb;
   for (int a = tid; a < n; a += blockDim.x) {
-    const int i = site_atoms[b0 + a];
-    for (int k = 0; k < 3; ++k) {
-      double w = (double)x[3 * (size_t)i + k];
-      w -= floor(w / L) * L;
-      if (w >= L) w -= L;
-      if (w < 0.0) w = 0.0;
-      ps[a][k] = w;
-      Is[a][k] = min((int)(w / L * nb), nb - 1);
+    const int i = site_atoms[b0 + a], sa = inv_perm[i];
+    int lo = 0, hi = (1 << (3 * d)) - 1;  // leaf of sorted position sa
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (leaf_start[mid] <= sa) lo = mid; else hi = mid - 1;
     }
-    acc[a] = 0.0;
+    const V v = part[sa];
+    me[a] = v;
+    sa_s[a] = sa;
+    aI[a][0] = (int)d_compact(lo); aI[a][1] = (int)d_compact(lo >> 1); aI[a][2] = (int)d_compact(lo >> 2);
+    pa[a][0] = (aI[a][0] + 0.5) * sl + (double)v.x;
+    pa[a][1] = (aI[a][1] + 0.5) * sl + (double)v.y;
+    pa[a][2] = (aI[a][2] + 0.5) * sl + (double)v.z;
   }
   __syncthreads();
-  // evaluate a batch of nbx sources for the atoms selected by `sel`, then reduce
-  // per atom in source order
-  auto reduce_batch = [&](int nbx) {
-    __syncthreads();
-    for (int a = tid; a < n; a += blockDim.x) {
-      double v = acc[a];
-      for (int r = 0; r < nbx; ++r) v += vals[r * kMaxSiteAtoms + a];
-      acc[a] = v;
+  // represent the site by its minimum images around its first atom (a site may
+  // straddle the box faces); the periodic decomposition holds at any position,
+  // and the leaf index used by the direct sums moves with the image
+  for (int a = tid; a < n; a += blockDim.x) {
+    if (a == 0) continue;
+    for (int k = 0; k < 3; ++k) {
+      const double dk = rint((pa[a][k] - pa[0][k]) / L);
+      pa[a][k] -= dk * L;
+      aI[a][k] -= (int)dk * nb;
+    }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double c[3] = {0, 0, 0};
+    for (int a = 0; a < n; ++a)
+      for (int k = 0; k < 3; ++k) c[k] += pa[a][k];
+    for (int k = 0; k < 3; ++k) c[k] /= n;
+    double R = 0.0;
+    for (int a = 0; a < n; ++a) {
+      const double dx = pa[a][0] - c[0], dy = pa[a][1] - c[1], dz = pa[a][2] - c[2];
+      R = fmax(R, sqrt(dx * dx + dy * dy + dz * dz));
+    }
+    cen[0] = c[0]; cen[1] = c[1]; cen[2] = c[2]; cen[3] = R;
+  }
+  __syncthreads();
+  for (int a = tid; a < n; a += blockDim.x) {
+    const double ux = pa[a][0] - cen[0], uy = pa[a][1] - cen[1], uz = pa[a][2] - cen[2];
+    pu[a][0] = (T)ux; pu[a][1] = (T)uy; pu[a][2] = (T)uz;
+    puu[a] = (T)(ux * ux + uy * uy + uz * uz);
+  }
+  for (int t = tid; t < 343; t += blockDim.x) fa[t] = pack_entry(0, t);  // root images
+  __syncthreads();
+  // thread -> (atom pair, slot), fixed for the whole traversal; a slot takes
+  // the rows slot, slot + nslot, ... of every batch
+  const int npair = (n + 1) >> 1, nslot = blockDim.x / npair;
+  const int my_p = (tid < nslot * npair) ? tid % npair : -1, my_s = tid / npair;
+  const int a0 = my_p < 0 ? 0 : my_p, a1 = (my_p >= 0 && my_p + npair < n) ? my_p + npair : a0;
+  const int nbatch = (nslot <= nbmax) ? nslot * (nbmax / nslot) : nbmax;
+  SiteAcc<T> acc0, acc1;
+  double base = 0.0;  // FP64 charge + dipole values at c of the rows this thread stages
+  int n0 = 343, bc = 0;
+  const T Rf = (T)cen[3];
+  for (int l = 0; l <= d && n0 > 0; ++l) {
+    const double s = L / (double)(1 << l);
+    const T a_l = (T)(0.86602540378443865 * s), th = (T)kSiteTheta, is = (T)(1.0 / s);
+    int nsep = 0, n1 = 0;
+    for (int t0 = 0; t0 < n0; t0 += blockDim.x) {
+      const int t = t0 + tid;
+      int kind = -1;  // 0 separated, 1 direct leaf, 2 open
+      int e = 0;
+      if (t < n0) {
+        e = fa[t];
+        const int box = e >> 9, img = e & 511;
+        const int nx = img / 49 - 3, ny = (img / 7) % 7 - 3, nz = img % 7 - 3;
+        const T dx = (T)(cen[0] - (((int)d_compact(box) + 0.5) * s + nx * L)),
+                dy = (T)(cen[1] - (((int)d_compact(box >> 1) + 0.5) * s + ny * L)),
+                dz = (T)(cen[2] - (((int)d_compact(box >> 2) + 0.5) * s + nz * L));
+        const T D = sqrt(dx * dx + dy * dy + dz * dz);
+        if (a_l < th * (D - Rf) * (T)0.9999) kind = 0;
+        else if (l == d) kind = 1;
+        else kind = 2;
+      }
+      int tot;
+      const int osep = block_scan(kind == 0 || kind == 1 ? 1 : 0, wsum, &tot);
+      if ((kind == 0 || kind == 1) && nsep + osep < kFrontier) sep[nsep + osep] = (kind == 1) ? (e | (1 << 31)) : e;
+      nsep += tot;
+      const int oopen = block_scan(kind == 2 ? 8 : 0, wsum, &tot);
+      if (kind == 2) {
+        const int box = e >> 9, img = e & 511;
+        for (int c = 0; c < 8; ++c)
+          if (n1 + oopen + c < kFrontier) fb[n1 + oopen + c] = pack_entry(8 * box + c, img);
+      }
+      n1 += tot;
+    }
+    if (nsep > kFrontier || n1 > kFrontier) {
+      if (tid == 0) atomicExch(err, 1);
+      nsep = min(nsep, kFrontier);
+      n1 = min(n1, kFrontier);
     }
     __syncthreads();
-  };
-  if (pidx < d) {
-    const int l = pidx + 1, shift = d - l, side = 1 << l;
-    const double s = L / side, inv_s = 1.0 / s;
-    for (int a = tid; a < n; a += blockDim.x) {
-      int g = a;
-      for (int b = 0; b < a; ++b)
-        if ((Is[b][0] >> shift) == (Is[a][0] >> shift) && (Is[b][1] >> shift) == (Is[a][1] >> shift) &&
-            (Is[b][2] >> shift) == (Is[a][2] >> shift)) { g = b; break; }
-      grp[a] = g;
-    }
-    __syncthreads();
-    for (int lead = 0; lead < n; ++lead) {
-      if (grp[lead] != lead) continue;  // uniform across the block
-      const int A[3] = {Is[lead][0] >> shift, Is[lead][1] >> shift, Is[lead][2] >> shift};
-      const int c = (A[0] & 1) | ((A[1] & 1) << 1) | ((A[2] & 1) << 2);
-      for (int o0 = 0; o0 < kListLen; o0 += kSiteBatch) {
-        const int nbx = min(kSiteBatch, kListLen - o0);
-        if (tid < nbx) {
-          const int oid = list[c * kListLen + o0 + tid];
-          const int g[3] = {A[0] - off[oid * 3], A[1] - off[oid * 3 + 1], A[2] - off[oid * 3 + 2]};
-          const int64_t box = level_off[l] + d_morton(wrapi(g[0], side), wrapi(g[1], side), wrapi(g[2], side));
-          brow[tid] = box;
-          for (int k = 0; k < 4; ++k) bq[tid][k] = qd[box * 4 + k];
-          for (int k = 0; k < 3; ++k) bc[tid][k] = (g[k] + 0.5) * s;
+    for (int b = 0; b < nsep; b += nbatch, ++bc) {
+      if (bc % G != g) continue;  // batch dealt to another block of this site
+      const int nbx = min(nbatch, nsep - b);
+      if (tid < nbx) {
+        const int e = sep[b + tid] & 0x7fffffff, box = e >> 9, img = e & 511;
+        const int nx = img / 49 - 3, ny = (img / 7) % 7 - 3, nz = img % 7 - 3;
+        if (sep[b + tid] < 0) {
+          brow_s[tid] = -1 - box;
+        } else {
+          const int64_t row = level_off[l] + box;
+          brow_s[tid] = (int)row;
+          const double wx = (((int)d_compact(box) + 0.5) * s + nx * L) - cen[0];
+          const double wy = (((int)d_compact(box >> 1) + 0.5) * s + ny * L) - cen[1];
+          const double wz = (((int)d_compact(box >> 2) + 0.5) * s + nz * L) - cen[2];
+          const double B2 = wx * wx + wy * wy + wz * wz, Bi = rinv_dd(B2);
+          const double Q = qd[row * 4], px = qd[row * 4 + 1], py = qd[row * 4 + 2], pz = qd[row * 4 + 3];
+          const double pw = px * wx + py * wy + pz * wz;
+          base += Q * Bi - pw * (Bi * Bi * Bi);  // at c the box centre is at -w
+          rw[tid][0] = (T)wx; rw[tid][1] = (T)wy; rw[tid][2] = (T)wz;
+          rp[tid][0] = (T)px; rp[tid][1] = (T)py; rp[tid][2] = (T)pz;
+          rQ[tid] = (T)Q;
+          rB[tid] = (T)(B2 * Bi);
+          rBi[tid] = (T)Bi;
+          rpw[tid] = (T)pw;
         }
-        __syncthreads();
+        bimg[tid] = img;
+      }
+      __syncthreads();
+      if (P >= 2) {
         constexpr int EPV = 16 / sizeof(T);
         const int per_row = ld / EPV;
         for (int q = tid; q < nbx * per_row; q += blockDim.x) {
-          const int r = q / per_row, e = q % per_row;
-          reinterpret_cast<float4 *>(Ms + (size_t)r * ld)[e] = reinterpret_cast<const float4 *>(M + brow[r] * ld)[e];
+          const int r = q / per_row, e2 = q % per_row;
+          if (brow_s[r] >= 0)
+            reinterpret_cast<float4 *>(Ms + (size_t)r * lds)[e2] =
+                reinterpret_cast<const float4 *>(M + (size_t)brow_s[r] * ld)[e2];
         }
-        __syncthreads();
-        for (int q = tid; q < nbx * n; q += blockDim.x) {
-          const int r = q % nbx, a = q / nbx;
-          double v = 0.0;
-          if (grp[a] == lead) {
-            const double rx = ps[a][0] - bc[r][0], ry = ps[a][1] - bc[r][1], rz = ps[a][2] - bc[r][2];
-            const double ri = rsqrt_dp(rx * rx + ry * ry + rz * rz);
-            v = bq[r][0] * ri + (bq[r][1] * rx + bq[r][2] * ry + bq[r][3] * rz) * ri * ri * ri;
-            if (P >= 2)
-              v += (double)m2p_high_smem<T>(P, Ms + (size_t)r * ld, (T)(rx * inv_s), (T)(ry * inv_s), (T)(rz * inv_s)) *
-                   inv_s;
+      }
+      __syncthreads();
+      if (my_p >= 0) {
+        for (int r = my_s; r < nbx; r += nslot) {
+          if (brow_s[r] >= 0) {
+            // charge + dipole: change from the value at c,
+            //   Q (1/A - 1/B) + p.u / A^3 - (p.w) (1/A^3 - 1/B^3),
+            // A = |u - w|, B = |w|, A^2 - B^2 = u.u - 2 u.w, A - B = (A^2 - B^2) / (A + B)
+            const T wx = rw[r][0], wy = rw[r][1], wz = rw[r][2];
+            const T Q = rQ[r], px = rp[r][0], py = rp[r][1], pz = rp[r][2];
+            const T B = rB[r], Bi = rBi[r], pw = rpw[r], Bi3 = Bi * Bi * Bi;
+            T ux[2], uy[2], uz[2], dev[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const int a = h ? a1 : a0;
+              ux[h] = pu[a][0] - wx; uy[h] = pu[a][1] - wy; uz[h] = pu[a][2] - wz;
+              const T A2 = ux[h] * ux[h] + uy[h] * uy[h] + uz[h] * uz[h];
+              const T Ai = rinv(A2), A = A2 * Ai, Ai3 = Ai * Ai * Ai;
+              const T d2 = puu[a] - T(2) * (pu[a][0] * wx + pu[a][1] * wy + pu[a][2] * wz);
+              const T f1 = site_div(d2, A + B);
+              const T pu_ = px * pu[a][0] + py * pu[a][1] + pz * pu[a][2];
+              dev[h] = -Q * f1 * Ai * Bi + pu_ * Ai3 + pw * f1 * (A2 + A * B + B * B) * Ai3 * Bi3;
+            }
+            if (P >= 2) {
+              const T *Mr = Ms + (size_t)r * lds;
+              T v0, v1;
+              if constexpr (PP > 0) {
+                m2p_high2<T, PP>(Mr, ux[0] * is, uy[0] * is, uz[0] * is, ux[1] * is, uy[1] * is, uz[1] * is, v0, v1);
+              } else {
+                v0 = m2p_high<T>(P, Mr, ux[0] * is, uy[0] * is, uz[0] * is);
+                v1 = m2p_high<T>(P, Mr, ux[1] * is, uy[1] * is, uz[1] * is);
+              }
+              dev[0] += v0 * is;
+              dev[1] += v1 * is;
+            }
+            acc0.add(dev[0]);
+            acc1.add(dev[1]);
+          } else {
+            // unseparated leaf: direct sum over its atoms
+            const int box = -1 - brow_s[r], img = bimg[r];
+            const int nx = img / 49 - 3, ny = (img / 7) % 7 - 3, nz = img % 7 - 3;
+            const int bx = (int)d_compact(box) + nx * nb, by = (int)d_compact(box >> 1) + ny * nb,
+                      bz = (int)d_compact(box >> 2) + nz * nb;
+            const int gx0 = bx - aI[a0][0], gy0 = by - aI[a0][1], gz0 = bz - aI[a0][2];
+            const int gx1 = bx - aI[a1][0], gy1 = by - aI[a1][1], gz1 = bz - aI[a1][2];
+            const int self0 = (gx0 == 0 && gy0 == 0 && gz0 == 0) ? sa_s[a0] : -1;
+            const int self1 = (gx1 == 0 && gy1 == 0 && gz1 == 0) ? sa_s[a1] : -1;
+            const V m0 = me[a0], m1 = me[a1];
+            const SiteTarget<T> t0 = site_target(m0.x, m0.y, m0.z, gx0, gy0, gz0, sl);
+            const SiteTarget<T> t1 = site_target(m1.x, m1.y, m1.z, gx1, gy1, gz1, sl);
+            for (int q2 = leaf_start[box]; q2 < leaf_start[box + 1]; ++q2) {
+              const V src = part[q2];
+              T vh, vl;
+              if (q2 != self0) {
+                pair_pot(t0, src.x, src.y, src.z, src.w, vh, vl);
+                acc0.add2(vh, vl);
+              }
+              if (q2 != self1) {
+                pair_pot(t1, src.x, src.y, src.z, src.w, vh, vl);
+                acc1.add2(vh, vl);
+              }
+            }
           }
-          vals[r * kMaxSiteAtoms + a] = v;
-        }
-        reduce_batch(nbx);
-      }
-    }
-  } else if (pidx == d) {
-    // root images 2 <= |n|_inf <= 3: source centre c - nL
-    for (int o0 = 0; o0 < kNumOffsets; o0 += kSiteBatch) {
-      const int nbx = min(kSiteBatch, kNumOffsets - o0);
-      for (int q = tid; q < nbx * n; q += blockDim.x) {
-        const int r = q % nbx, a = q / nbx, oid = o0 + r;
-        const double rx = ps[a][0] - (0.5 * L - off[oid * 3] * L), ry = ps[a][1] - (0.5 * L - off[oid * 3 + 1] * L),
-                     rz = ps[a][2] - (0.5 * L - off[oid * 3 + 2] * L);
-        const double ri = rsqrt_dp(rx * rx + ry * ry + rz * rz), iL = 1.0 / L;
-        double v = mom[0] * ri + (mom[1] * rx + mom[2] * ry + mom[3] * rz) * ri * ri * ri;
-        if (P >= 2) v += (double)m2p_high<T>(P, M, (T)(rx * iL), (T)(ry * iL), (T)(rz * iL)) * iL;
-        vals[r * kMaxSiteAtoms + a] = v;
-      }
-      reduce_batch(nbx);
-    }
-  } else {
-    // near field: warp w takes atoms w, w+4, ...; lanes over sources.  Positions
-    // come from the sorted leaf-relative coordinates (exact differences in
-    // FP64: r = (u_i - u_j) - o s), charges from the FP64 scaled charges.
-    using V = typename V4<T>::type;
-    for (int a = wib; a < n; a += blockDim.x / 32) {
-      const int i = site_atoms[b0 + a];
-      const V me = part[inv_perm[i]];
-      double v = 0.0;
-      for (int k = 0; k < 27; ++k) {
-        const int dx = k % 3 - 1, dy = (k / 3) % 3 - 1, dz = k / 9 - 1;
-        const int leaf = (int)d_morton(wrapi(Is[a][0] + dx, nb), wrapi(Is[a][1] + dy, nb), wrapi(Is[a][2] + dz, nb));
-        const double ox = dx * sl, oy = dy * sl, oz = dz * sl;
-        for (int t = leaf_start[leaf] + lane; t < leaf_start[leaf + 1]; t += 32) {
-          const int j = perm[t];
-          if (j == i && k == 13) continue;
-          const V src = part[t];
-          const double rx = ((double)me.x - (double)src.x) - ox, ry = ((double)me.y - (double)src.y) - oy,
-                       rz = ((double)me.z - (double)src.z) - oz;
-          v += qt[j] * rsqrt_dp(rx * rx + ry * ry + rz * rz);
         }
       }
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffff, v, o);
-      if (lane == 0) acc[a] = v;
+      __syncthreads();
     }
-    __syncthreads();
-    for (int a = tid; a < n; a += blockDim.x) {
-      // far-image lattice part: (1/L) sum L~_H3 conj(Rt(u)), u = (x - c)/L
-      double h = 0.0;
-      rt_columns<double>(P, (ps[a][0] - 0.5 * L) / L, (ps[a][1] - 0.5 * L) / L, (ps[a][2] - 0.5 * L) / L,
-                         [&](int l, int m, double re, double im) {
-                           const int k = ridx(l, m);
-                           h += (m == 0) ? Lh3[k] * re : 2.0 * (Lh3[k] * re + Lh3[k + 1] * im);
-                         });
-      const double V = L * L * L, c2 = 2.0 * kPi / (3.0 * V);
-      const double ax = ps[a][0] - 0.5 * L, ay = ps[a][1] - 0.5 * L, az = ps[a][2] - 0.5 * L;
-      acc[a] += h / L + c2 * (mom[0] * (ax * ax + ay * ay + az * az) -
-                              2.0 * (ax * mom[1] + ay * mom[2] + az * mom[3]) + mom[4]);
-    }
+    for (int t = tid; t < n1; t += blockDim.x) fa[t] = fb[t];
+    n0 = (l < d) ? n1 : 0;
     __syncthreads();
   }
-  for (int a = tid; a < n; a += blockDim.x) phi_part[(size_t)(b0 + a) * nparts + pidx] = acc[a];
+  // fixed-order reductions: the staged FP64 values, then per atom over its slots
+  if (tid < kSiteBatchMax) base_s[tid] = base;
+  res_s[tid][0] = acc0.value();
+  res_s[tid][1] = acc1.value();
+  __syncthreads();
+  if (tid < 32) {
+    double v = base_s[tid] + base_s[tid + 32];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffff, v, o);
+    if (tid == 0) cen[3] = v;  // R is no longer needed
+  }
+  __syncthreads();
+  const double common = cen[3];
+  for (int a = tid; a < n; a += blockDim.x) {
+    const int pp = (a < npair) ? a : a - npair, hh = (a < npair) ? 0 : 1;
+    double acc = common;
+    for (int k = 0; k < nslot; ++k) acc += res_s[pp + k * npair][hh];
+    if (g == 0) {
+      // far-image lattice part and dipole / background term
+      const double px = pa[a][0], py = pa[a][1], pz = pa[a][2];
+      double hsum = 0.0;
+      rt_columns<double>(P, (px - 0.5 * L) / L, (py - 0.5 * L) / L, (pz - 0.5 * L) / L,
+                         [&](int l, int m, double re, double im) {
+                           const int k = ridx(l, m);
+                           hsum += (m == 0) ? Lh3[k] * re : 2.0 * (Lh3[k] * re + Lh3[k + 1] * im);
+                         });
+      const double V3 = L * L * L, c2 = 2.0 * kPi / (3.0 * V3);
+      const double ax = px - 0.5 * L, ay = py - 0.5 * L, az = pz - 0.5 * L;
+      acc += hsum / L + c2 * (mom[0] * (ax * ax + ay * ay + az * az) -
+                              2.0 * (ax * mom[1] + ay * mom[2] + az * mom[3]) + mom[4]);
+    }
+    phi_part[(size_t)(b0 + a) * G + g] = acc;
+  }
 }
 
 // phi_site = f * (sum of the parts, in part order)
@@ -1094,6 +1376,26 @@ int num_stages() { return 10; }
     cudaError_t e_ = (call);                            \
     if (e_ != cudaSuccess) return e_;                   \
   } while (0)
+
+// k_site_phi with the M2P order a compile-time constant where one is built
+template <typename T, int PP, typename... A>
+static cudaError_t launch_site_phi_pp(int G, size_t smp, cudaStream_t st, int S, A... args) {
+  cudaError_t e = cudaFuncSetAttribute(k_site_phi<T, PP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smp);
+  if (e != cudaSuccess) return e;
+  k_site_phi<T, PP><<<S * G, kSiteThreads, smp, st>>>(S, args...);
+  return cudaGetLastError();
+}
+template <typename T, typename... A>
+static cudaError_t launch_site_phi(int P, int G, size_t smp, cudaStream_t st, int S, A... args) {
+  switch (P) {
+    case 8: return launch_site_phi_pp<T, 8>(G, smp, st, S, args...);
+    case 10: return launch_site_phi_pp<T, 10>(G, smp, st, S, args...);
+    case 12: return launch_site_phi_pp<T, 12>(G, smp, st, S, args...);
+    case 14: return launch_site_phi_pp<T, 14>(G, smp, st, S, args...);
+    case 16: return launch_site_phi_pp<T, 16>(G, smp, st, S, args...);
+    default: return launch_site_phi_pp<T, 0>(G, smp, st, S, args...);
+  }
+}
 
 template <typename T, int NC>
 static cudaError_t launch_gemm_nc(const GemmMap &mp, int grid, int K, int ld, const T *in, T *out, const T *ops,
@@ -1222,13 +1524,17 @@ static cudaError_t eval_t(mahi_ctx *h, const XT *x, const double *lam, double *e
   }
   mark(h, 9);
   if (h->S > 0) {
-    const size_t smp = sizeof(T) * kSiteBatch * ld;
-    if (smp > 40 * 1024)
-      MAHI_CK(cudaFuncSetAttribute(k_site_phi<T, XT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smp));
-    k_site_phi<T, XT><<<dim3(h->S, h->d + 2), kSitePhiThreads, smp, st>>>(
-        h->S, h->site_ptr, h->site_atoms, h->d, P, ld, h->L, h->d_level_off, h->leaf_start, h->perm, h->inv_perm,
-        (const V *)h->part, x, h->qt, M, h->box_qd, h->moments, h->L_h3, h->m2l_list, h->m2l_off, h->phi_part);
-    k_site_phi_sum<<<(h->n_site_atoms + 127) / 128, 128, 0, st>>>(h->n_site_atoms, h->d + 2, coulomb_constant(),
+    // rows of staged multipoles: as many as keep three blocks per SM
+    const int lds = ld + 16 / (int)sizeof(T);
+    const size_t fixed = sizeof(int) * 3 * kFrontier;
+    const size_t budget = 72 * 1024;
+    const int nbmax = (int)std::max<size_t>(8, std::min<size_t>(kSiteBatchMax, (budget - fixed) / (sizeof(T) * lds)));
+    const size_t smp = fixed + sizeof(T) * nbmax * lds;
+    const int G = std::max(1, std::min(kSiteChunksMax, (4 * 3 * h->num_sms + h->S - 1) / std::max(1, h->S)));
+    MAHI_CK(launch_site_phi<T>(P, G, smp, st, h->S, G, h->site_ptr, h->site_atoms, h->d, P, ld, lds, nbmax, h->L,
+                               h->d_level_off, h->leaf_start, h->inv_perm, (const V *)h->part, M, h->box_qd,
+                               h->moments, h->L_h3, h->phi_part, h->tc_error_site));
+    k_site_phi_sum<<<(h->n_site_atoms + 127) / 128, 128, 0, st>>>(h->n_site_atoms, G, coulomb_constant(),
                                                                    h->phi_part, h->phi_site);
     k_site<T, XT, XT><<<(h->S + 3) / 4, 128, 0, st>>>(h->S, h->L, coulomb_constant(), kSiteDegree, h->site_ptr,
                                                       h->site_atoms, x, h->dq, lam, h->phi_site, h->eta, h->eta_x,

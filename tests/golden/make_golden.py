@@ -7,6 +7,7 @@ tests/golden/water_1m_seed1.json.  Takes tens of minutes on a few cores.
 
     python tests/golden/make_golden.py [config] [seed]
 """
+import hashlib
 import json
 import os
 import sys
@@ -30,6 +31,14 @@ def sample_atoms(n, seed):
     return idx
 
 
+def input_digest(s):
+    """sha256 of the generated inputs, to check that a machine regenerates them bit for bit."""
+    h = hashlib.sha256()
+    for k in ("x", "qA", "qB", "site_of", "lam"):
+        h.update(np.ascontiguousarray(s[k]).tobytes())
+    return h.hexdigest()
+
+
 def main(config="C", seed=1):
     t0 = time.time()
     s = synth.make(config, seed)
@@ -42,7 +51,7 @@ def main(config="C", seed=1):
         config=config, seed=seed, n_atoms=n, L=s["L"], n_sites=len(s["lam"]),
         E=out["E"], E_qi=out["E_qi"], dEdl=out["dEdl"].tolist(), k=out["k"].tolist(),
         sample=tgt.tolist(), F=F.tolist(),
-        oracle_threads=oracle.num_threads(), seconds=time.time() - t0,
+        oracle_threads=oracle.num_threads(), seconds=time.time() - t0, input_sha256=input_digest(s),
         made_by="tests/golden/make_golden.py (oracle only)",
     )
     path = os.path.join(HERE, f"water_1m_seed{seed}.json" if config == "C" else f"config{config}_seed{seed}.json")
