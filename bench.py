@@ -40,21 +40,24 @@ def _peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clock / throttle samples while the timed region runs."""
+    """nvidia-smi clock / throttle samples, time-stamped on arrival, so that the
+    summary can keep those taken while the timed region ran.  Start it before
+    the warm-up: nvidia-smi takes a while to come up."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index=0):
+    def __init__(self, index=0, period_ms=20):
         self.index = index
+        self.period_ms = period_ms
         self.proc = None
         self.lines = []
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", str(self.period_ms)],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -64,7 +67,12 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
+
+    def wait_ready(self, timeout=5.0):
+        t0 = time.perf_counter()
+        while self.proc and not self.lines and time.perf_counter() - t0 < timeout:
+            time.sleep(0.01)
 
     def __exit__(self, *a):
         if self.proc:
@@ -74,10 +82,13 @@ class ClockSampler:
             except subprocess.TimeoutExpired:
                 self.proc.kill()
 
-    def summary(self):
+    def summary(self, t0=None, t1=None):
         sm, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ts, ln in self.lines:
+            # a sample stamped up to one period after the window still reports it
+            if t0 is not None and not (t0 <= ts <= t1 + self.period_ms * 1e-3):
+                continue
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 9:
                 continue
@@ -90,7 +101,7 @@ class ClockSampler:
                 if f[5 + k].lower().startswith("active"):
                     reasons.add(nm)
         return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "period_ms": self.period_ms}
 
 
 def _dist():
@@ -140,29 +151,43 @@ def run_ours(args):
         return h
 
     h = make("mixed")
+    clk = ClockSampler(local).__enter__()
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
             pkg.mahi_eval(h, x, lam, E, F, g)
         stream.synchronize()
+        clk.wait_ready()
         launches = pkg.mahi_launch_count(h)
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
-        with ClockSampler(local) as clk:
-            t_wall = time.perf_counter()
-            for k in range(args.steps):
-                flush.fill_(float(k))
-                ev[k][0].record(stream)
-                pkg.mahi_eval(h, x, lam, E, F, g)
-                ev[k][1].record(stream)
-            stream.synchronize()
-            t_wall = time.perf_counter() - t_wall
+        t_wall = time.perf_counter()
+        t_clk0 = t_wall
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            ev[k][0].record(stream)
+            pkg.mahi_eval(h, x, lam, E, F, g)
+            ev[k][1].record(stream)
+        stream.synchronize()
+        t_clk1 = time.perf_counter()
+        t_wall = t_clk1 - t_wall
         torch.cuda.synchronize()
         step_ms = [a.elapsed_time(b) for a, b in ev]
         if dist:
             dist.barrier()
+    clk.__exit__()
     ms = _max_over_ranks(dist, float(np.mean(step_ms)), dev)
+    if args.kernels_only:
+        # the timed steps alone (profiling runs): no stages, e2e, comparator
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": round(ms, 4), "unit": "ms", "n_gpus": ws,
+                              "steps": args.steps, "warmup": args.warmup, "kernels_only": True,
+                              "gpu_launches": int(launches * args.steps)}), flush=True)
+        pkg.mahi_destroy(h)
+        if dist:
+            dist.destroy_process_group()
+        return
 
     # stage breakdown and the dominant kernel (tensor-core M2L) timed with the
     # library's CUDA events on the same stream
@@ -237,7 +262,7 @@ def run_ours(args):
             traffic = json.load(open(tpath)).get("bytes_per_launch")
         except (OSError, ValueError):
             traffic = None
-    clocks = clk.summary()
+    clocks = clk.summary(t_clk0, t_clk1)
     out = {
         "metric": METRIC, "value": round(ms, 4), "unit": "ms", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": False, "scaling": "weak",
@@ -269,11 +294,11 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def cpu_baseline(s, n_targets=1024, atom_frac=1 / 64):
+def cpu_baseline(s, n_targets=8192, atom_frac=1 / 8):
     """The oracle (FP64 Ewald + HI closed form) timed on the host cores on a
     bounded sample, extrapolated to one full evaluation of the workload:
-    structure factors over a random 1/64 of the atoms (linear in atoms) and the
-    real- and reciprocal-space sums at 1024 random target atoms of the full
+    structure factors over a random fraction of the atoms (linear in atoms) and
+    the real- and reciprocal-space sums at random target atoms of the full
     system (linear in targets)."""
     import oracle
     from oracle import hi
@@ -310,7 +335,7 @@ def run_reference(args):
     s = synth.make(WORKLOAD["config"], WORKLOAD["seed"])
     vals = []
     for k in range(args.warmup + args.steps):
-        cb = cpu_baseline(s)
+        cb = cpu_baseline(s, n_targets=1024, atom_frac=1 / 64)
         if k >= args.warmup:
             vals.append(cb["value"])
     v = float(np.mean(vals))
@@ -333,12 +358,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--kernels-only", action="store_true",
+                    help="time the mixed steps only (for profiler runs); skips stages, e2e, FP64 comparator")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
-        args.steps = min(args.steps, 1)
-        args.warmup = 0
         run_reference(args)
     else:
         run_ours(args)

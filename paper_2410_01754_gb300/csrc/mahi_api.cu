@@ -43,7 +43,7 @@ static void free_all(mahi_ctx *h) {
                   h->perm_tmp, h->inv_perm, h->part, h->part_tmp, h->Mexp, h->Lexp, h->phi_s, h->grad_s,
                   h->ops_m2m, h->ops_l2l, h->ops_m2l, h->ops_lat, h->eta, h->eta_x, h->eta_y, h->eta_z,
                   h->m2l_list, h->m2l_off, h->site_ptr, h->site_atoms, h->moments_part, h->moments,
-                  h->energy_part, h->site_energy, h->tc_ops, h->tc_msplit, h->tc_level_off, h->tc_units, h->tc_error, h->d_x_stage,
+                  h->energy_part, h->site_energy, h->tc_ops, h->tc_partial, h->tc_msrc, h->tc_level_off, h->tc_units, h->tc_error, h->d_x_stage,
                   h->d_lam_stage, h->d_E_stage, h->d_dEdl_stage, h->d_F_stage, h->ops_lat_h3, h->L_h3,
                   h->box_qd, h->phi_site, h->phi_part, h->d_level_off, h->tc_error_site};
   for (void *b : bufs)
@@ -247,7 +247,8 @@ int mahi_create(double box_L_nm, int64_t n_atoms, int32_t n_sites, int32_t order
         return fail(e, "tc units");
       AL(h->tc_error, 16);
       cudaMemset(h->tc_error, 0, 16);
-      AL(h->tc_msplit, (size_t)h->nbox_total * h->ld * 2 * sizeof(float));
+      AL(h->tc_partial, (size_t)h->num_sms * 2 * 128 * h->ld * sizeof(float));  // remainder-unit partial tiles
+      AL(h->tc_msrc, (size_t)h->nbox_total * h->ld * sizeof(float));            // M2L source layout
       AL(h->tc_level_off, sizeof(int64_t) * (kMaxDepth + 2));
       if ((e = cudaMemcpy(h->tc_level_off, h->level_off, sizeof(int64_t) * (kMaxDepth + 2), cudaMemcpyHostToDevice)) !=
           cudaSuccess)

@@ -117,7 +117,8 @@ struct mahi_ctx {
   int n_moment_blocks = 0, n_energy_blocks = 0;
   // tensor-core M2L operand images (mixed path)
   void *tc_ops = nullptr;
-  void *tc_msplit = nullptr;                  // TF32 hi | lo copies of Mexp
+  void *tc_partial = nullptr;                 // M2L partial tiles of units split across CTAs
+  void *tc_msrc = nullptr;                    // multipoles in the M2L gather layout
   int64_t *tc_level_off = nullptr;            // device copy of level_off
   int *tc_units = nullptr;
   int tc_nunits = 0;

@@ -36,9 +36,11 @@ namespace mahi {
 
 namespace tc {
 constexpr int kRows = 128;       // targets per tile (MMA M)
-constexpr int kKC = 16;          // input coefficients per pipeline stage
-constexpr int kStages = 5;
-constexpr int kThreads = 192;
+constexpr int kKC = 8;           // input coefficients per pipeline stage (one MMA K)
+constexpr int kStagesA = 4;      // A stages in tensor memory
+constexpr int kStagesS = 8;      // A staging slots in shared memory (cp.async, own rows per thread)
+constexpr int kStagesB = 12;     // B stages in shared memory
+constexpr int kThreads = 320;
 constexpr uint32_t kSpinLimit = 1u << 26;
 constexpr int kMaxN = 256;       // MMA N limit: Kp <= 256, order <= 15
 
@@ -47,7 +49,7 @@ struct Unit {
 };
 
 struct Params {
-  const float *Mhi, *Mlo;       // split multipoles, all levels (row stride ld)
+  const float *M;               // multipoles in the M2L source layout (see k_m2l_src_layout)
   float *L;                     // locals, all levels (row stride ld)
   const unsigned char *ops;     // B images [316][nch][hi|lo]
   const int4 *units;
@@ -57,6 +59,8 @@ struct Params {
   int *error;
   int ld, nch, ngroups;         // row stride, K chunks, N row groups (Kp/8)
   int nunits;
+  int nfull, nrem, q;           // units done whole (round-robin), remainder units, slices per remainder unit
+  float *partial;               // [nrem * q][2][kRows][ld] partial tiles of the remainder units
 };
 }  // namespace tc
 
@@ -95,14 +99,20 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity, volatile
   *abort_flag = 1;
   return false;
 }
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem)), "l"(gmem) : "memory");
+// 16-byte copy; with src_bytes = 0 the destination is zero-filled and nothing is read
+__device__ __forceinline__ void cp_async16_zfill(void *smem, const void *gmem, uint32_t src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(smem)), "l"(gmem), "r"(src_bytes)
+               : "memory");
 }
 // arrive on the barrier once all prior cp.async copies of this thread have landed
 __device__ __forceinline__ void cp_async_arrive(uint64_t *b) {
   asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(b)) : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait_group() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
 __device__ __forceinline__ void fence_proxy_async() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
@@ -135,6 +145,34 @@ __device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t adesc, uint64_
       "setp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+      : "memory");
+}
+// D (tmem) += A (tmem, M lanes x 8 tf32 columns) * B (shared memory descriptor)
+__device__ __forceinline__ void mma_tf32_ts(uint32_t dtmem, uint32_t atmem, uint64_t bdesc, uint32_t idesc,
+                                            uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}" ::"r"(dtmem),
+      "r"(atmem), "l"(bdesc), "r"(idesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t *r) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+          taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
+      "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+      : "memory");
+}
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t *r) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+      "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
+      "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]), "r"(r[16]), "r"(r[17]), "r"(r[18]),
+      "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]),
+      "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
       : "memory");
 }
 __device__ __forceinline__ void mma_commit(uint64_t *bar) {
@@ -170,42 +208,229 @@ __device__ __forceinline__ uint32_t tc_compact(uint32_t x) {
 }
 
 // ---------------------------------------------------------------------------
-// the kernel
+// the kernel: persistent, one CTA per SM (grid G).  A unit is a pair of
+// 128-target tiles of one level and child class (same offset list, so both
+// tiles use every staged operator chunk: half the operator traffic per flop).
+// CTA k computes the whole units k, k + G, ... below nfull = G * floor(nunits
+// / G), so all CTAs walk the same (offset, K chunk) sequence at the same time
+// and share the operator chunks in L2.  The nrem remainder units are cut along
+// that sequence into q equal slices each, one slice per CTA; slices write
+// partial tiles that k_m2l_tc_reduce adds up in a fixed order.
+//
+// The A operand (gathered multipoles) lives in tensor memory: the producer
+// warps load each target's source rows from global memory, split them into
+// TF32 hi and lo in registers and store them with tcgen05.st, so shared memory
+// carries only the operator chunks (B).
+// Warp roles: 0 = TMEM owner + MMA issuer (one lane), 1-4 = A producers (row
+// t of both tiles = TMEM lane t), 5 = B producer (bulk copies), 6-9 = epilogue
+// (TMEM -> L).  TMEM columns: [0, 176) tile-0 accumulator, [192, 368) tile-1
+// accumulator, [384 + 32 s, 416 + 32 s) A stage s as tile-0 hi | lo, tile-1 hi | lo.
 // ---------------------------------------------------------------------------
+namespace tc {
+constexpr uint32_t kAcc1 = 192, kAcol = 384;
+
+// Walks the items of CTA k in order without divisions: segment (whole unit
+// or remainder slice), unit, offset j and K chunk kc.
+struct ItemIter {
+  int seg, unit, i, i1, j, kc;
+};
+__device__ __forceinline__ void iter_seg(const Params &p, int k, int nA, int nit, ItemIter &it) {
+  if (it.seg < nA) {
+    it.unit = k + it.seg * (int)gridDim.x;
+    it.i = 0;
+    it.i1 = nit;
+    it.j = 0;
+    it.kc = 0;
+  } else {
+    const int sl = k % p.q;
+    it.unit = p.nfull + k / p.q;
+    it.i = (int)(((int64_t)sl * nit) / p.q);
+    it.i1 = (int)(((int64_t)(sl + 1) * nit) / p.q);
+    it.j = it.i / p.nch;
+    it.kc = it.i - it.j * p.nch;
+  }
+}
+__device__ __forceinline__ void iter_begin(const Params &p, int k, int nA, int nit, ItemIter &it) {
+  it.seg = 0;
+  iter_seg(p, k, nA, nit, it);
+}
+// advance by one item; returns true when a new segment starts
+__device__ __forceinline__ bool iter_next(const Params &p, int k, int nA, int nit, ItemIter &it) {
+  ++it.i;
+  if (++it.kc == p.nch) {
+    it.kc = 0;
+    ++it.j;
+  }
+  if (it.i < it.i1) return false;
+  ++it.seg;
+  iter_seg(p, k, nA, nit, it);
+  return true;
+}
+
+// targets in tile h (0 or 1) of a unit
+__device__ __forceinline__ int tile_count(const int4 &u, int h) {
+  if (h == 0) return u.w;
+  const int per_child = 1 << (3 * (u.x - 1));
+  const int c = per_child - u.z - kRows;
+  return c < 0 ? 0 : (c > kRows ? kRows : c);
+}
+
+// TF32 round-to-nearest (ties away) on the bit pattern; the remainder is exact
+__device__ __forceinline__ void tf32_split(float x, uint32_t &hi, uint32_t &lo) {
+  uint32_t u = __float_as_uint(x);
+  if ((u & 0x7f800000u) != 0x7f800000u) u = (u + 0x1000u) & 0xffffe000u;
+  hi = u;
+  lo = __float_as_uint(x - __uint_as_float(u));
+}
+
+// the source rows of one producer thread (row t of both tiles), advanced item by item
+struct ARow {
+  int unit = -1, j = -1, lev = 1, child = 0;
+  int bx[2] = {0, 0}, by[2] = {0, 0}, bz[2] = {0, 0};
+  bool valid[2] = {false, false};
+  const float *base = nullptr;
+  int64_t sidx[2] = {0, 0};      // source chunk index within a K plane
+};
+
+// target tau of a child class c at level l (parity class c, grid order
+// z/2, y/2, x/2 within the class) -> box coordinates
+__device__ __forceinline__ void class_target(int l, int c, int tau, int &x, int &y, int &z) {
+  const int hb = l - 1, hm = (1 << hb) - 1;
+  x = 2 * (tau & hm) + (c & 1);
+  y = 2 * ((tau >> hb) & hm) + ((c >> 1) & 1);
+  z = 2 * (tau >> (2 * hb)) + ((c >> 2) & 1);
+}
+
+// issue the cp.async copies of item q for row t of both tiles into staging
+// slot `dst` (4 granules of 16 bytes at dst + (g * kRows + t) * 16; rows past
+// a tile's count are zero-filled)
+__device__ __forceinline__ void arow_issue(const Params &p, const int *s_list, const int *s_off, int t,
+                                           const ItemIter &it, ARow &a, unsigned char *dst) {
+  const int unit = it.unit, j = it.j, kc = it.kc;
+  if (unit != a.unit) {
+    const int4 u = p.units[unit];
+    a.lev = u.x;
+    a.child = u.y;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      a.valid[h] = t < tile_count(u, h);
+      class_target(u.x, u.y, u.z + h * kRows + t, a.bx[h], a.by[h], a.bz[h]);
+    }
+    a.base = p.M + p.level_off[u.x] * p.ld;
+    a.sidx[0] = a.sidx[1] = 0;
+    a.unit = unit;
+    a.j = -1;
+  }
+  const int hb = a.lev - 1;                         // log2 of the half side
+  if (j != a.j) {
+    const int oid = s_list[a.child * kListLen + j];
+    const int ox = s_off[oid * 3 + 0], oy = s_off[oid * 3 + 1], oz = s_off[oid * 3 + 2];
+    const int sm = (1 << a.lev) - 1;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      if (!a.valid[h]) continue;
+      // source box, periodic wrap (the side is a power of two)
+      const int sx = (a.bx[h] - ox) & sm, sy = (a.by[h] - oy) & sm, sz = (a.bz[h] - oz) & sm;
+      const int cls = (sx & 1) | ((sy & 1) << 1) | ((sz & 1) << 2);
+      a.sidx[h] = ((((int64_t)cls << hb | (sz >> 1)) << hb | (sy >> 1)) << hb) | (sx >> 1);
+    }
+    a.j = j;
+  }
+  const int64_t plane = (int64_t)kc << (3 * hb + 3);  // chunks of one K plane: 8 classes x half^3
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const uint32_t n = a.valid[h] ? 16u : 0u;
+    const float *g = a.base + (plane + a.sidx[h]) * kKC;
+    cp_async16_zfill(dst + ((2 * h + 0) * kRows + t) * 16, g, n);
+    cp_async16_zfill(dst + ((2 * h + 1) * kRows + t) * 16, g + 4, n);
+  }
+}
+
+}  // namespace tc
+
+// Multipoles of levels 1..d rewritten for the M2L gathers: per level, K planes
+// of 8 coefficients, each plane ordered by parity class (x&1, y&1, z&1) and then
+// z/2, y/2, x/2, so that the sources of consecutive targets of one class under
+// one offset are consecutive 32-byte chunks.
+__global__ void k_m2l_src_layout(const float *__restrict__ M, float *__restrict__ S, const int64_t *__restrict__ level_off,
+                                 int ld, int d) {
+  const int64_t n4 = (level_off[d + 1] - level_off[1]) * ld / 4;  // float4 granules of levels 1..d
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n4; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t f = e * 4 + level_off[1] * ld;  // destination float index
+    int l = 1;
+    while (l < d && f >= level_off[l + 1] * ld) ++l;
+    const int hb = l - 1;
+    const int64_t r = f - level_off[l] * ld;       // float index within the level
+    const int g = (int)(r & 7);                    // 0 or 4: half of a chunk
+    const int64_t ch = r >> 3;                     // chunk index
+    const int64_t per_plane = (int64_t)8 << (3 * hb);
+    const int kc = (int)(ch / per_plane);
+    const int64_t w = ch - kc * per_plane;
+    const int hm = (1 << hb) - 1;
+    const int hx = (int)(w & hm), hy = (int)((w >> hb) & hm), hz = (int)((w >> (2 * hb)) & hm);
+    const int cls = (int)(w >> (3 * hb));
+    const int x = 2 * hx + (cls & 1), y = 2 * hy + ((cls >> 1) & 1), z = 2 * hz + ((cls >> 2) & 1);
+    const int64_t box = (int64_t)(tc_spread(x) | (tc_spread(y) << 1) | (tc_spread(z) << 2));
+    const float4 v = *reinterpret_cast<const float4 *>(M + (level_off[l] + box) * ld + kc * tc::kKC + g);
+    *reinterpret_cast<float4 *>(S + f) = v;
+  }
+}
+
+namespace tc {
+__device__ __forceinline__ int64_t class_box_row(const Params &p, int l, int c, int tau) {
+  int x, y, z;
+  class_target(l, c, tau, x, y, z);
+  return p.level_off[l] + (int64_t)(tc_spread(x) | (tc_spread(y) << 1) | (tc_spread(z) << 2));
+}
+}  // namespace tc
+
 __global__ void __launch_bounds__(tc::kThreads, 1) k_m2l_tc(tc::Params prm) {
   using namespace tc;
   extern __shared__ __align__(1024) unsigned char smem[];
   const int ng = prm.ngroups;                       // N row groups (Kp / 8)
-  const uint32_t a_bytes = (kKC / 4) * (kRows / 8) * 128;   // one A operand chunk (8 KB)
-  const uint32_t b_bytes = (kKC / 4) * ng * 128;            // one B operand chunk
-  unsigned char *sA = smem;                                  // [stage][hi|lo][a_bytes]
-  unsigned char *sB = sA + kStages * 2 * a_bytes;            // [stage][hi|lo][b_bytes]
-  uint64_t *bars = reinterpret_cast<uint64_t *>(sB + kStages * 2 * b_bytes);
-  uint64_t *full = bars, *bfull = bars + kStages, *empty = bars + 2 * kStages, *accb = bars + 3 * kStages;
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 3 * kStages + 1);
+  const uint32_t b_bytes = (kKC / 4) * ng * 128;    // hi (or lo) of one B chunk
+  unsigned char *sB = smem;                         // [B stage][hi|lo][b_bytes]
+  unsigned char *sS = sB + kStagesB * 2 * b_bytes;  // [slot][4 granules][kRows][16 B] A staging
+  int *s_list = reinterpret_cast<int *>(sS + kStagesS * 4 * kRows * 16);  // [8][189] offset ids
+  int *s_off = s_list + 8 * kListLen;                                   // [316][3] offsets
+  uint64_t *bars = reinterpret_cast<uint64_t *>(s_off + ((3 * kNumOffsets + 1) & ~1));
+  uint64_t *fullA = bars, *emptyA = bars + kStagesA, *fullB = bars + 2 * kStagesA,
+           *emptyB = bars + 2 * kStagesA + kStagesB;
+  uint64_t *accb = bars + 2 * kStagesA + 2 * kStagesB, *tfree = accb + 1;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(tfree + 1);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int4 u = prm.units[blockIdx.x];
-  const int level = u.x, child = u.y, p0 = u.z, count = u.w;
-  const int nit = kListLen * prm.nch;
+  const int nit = kListLen * prm.nch;               // stages of one unit
+  const int k = blockIdx.x;
+  const int nA = prm.nfull / (int)gridDim.x;        // whole units of this CTA
+  int slice_len = 0;
+  if (k < prm.nrem * prm.q) {
+    const int j = k % prm.q;
+    slice_len = (int)(((int64_t)(j + 1) * nit) / prm.q - ((int64_t)j * nit) / prm.q);
+  }
+  const int nloc = nA * nit + slice_len;
+  const int nseg = nA + (slice_len > 0 ? 1 : 0);
+  if (nloc == 0) return;                            // uniform over the block
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kStages; ++s) {
-      mbar_init(&full[s], kRows);
-      mbar_init(&bfull[s], 1);
-      mbar_init(&empty[s], 1);
+    for (int s = 0; s < kStagesA; ++s) {
+      mbar_init(&fullA[s], kRows);
+      mbar_init(&emptyA[s], 1);
+    }
+    for (int s = 0; s < kStagesB; ++s) {
+      mbar_init(&fullB[s], 1);
+      mbar_init(&emptyB[s], 1);
     }
     mbar_init(accb, 1);
+    mbar_init(tfree, kRows);
     *abort_flag = 0;
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  // zero the A stages once: rows beyond `count` stay zero for the whole tile
-  for (uint32_t i = threadIdx.x * 16; i < kStages * 2 * a_bytes; i += kThreads * 16)
-    *reinterpret_cast<float4 *>(sA + i) = make_float4(0.f, 0.f, 0.f, 0.f);
-  fence_proxy_async();
+  for (int e = threadIdx.x; e < 8 * kListLen; e += blockDim.x) s_list[e] = prm.list[e];
+  for (int e = threadIdx.x; e < 3 * kNumOffsets; e += blockDim.x) s_off[e] = prm.off[e];
+  if (threadIdx.x == 0) asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(smem_u32(tmem_slot))
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(tmem_slot))
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -215,64 +440,91 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_m2l_tc(tc::Params prm) {
   const uint32_t tmem = *tmem_slot;
 
   if (warp >= 1 && warp <= 4) {
-    // ---------------- A producers: one target row per thread ----------------
-    const int t = threadIdx.x - 32;
-    const bool valid = t < count;
-    const int side = 1 << level;
-    int bx = 0, by = 0, bz = 0;
-    if (valid) {
-      const int box = 8 * (p0 + t) + child;
-      bx = (int)tc_compact(box); by = (int)tc_compact(box >> 1); bz = (int)tc_compact(box >> 2);
+    // ---------------- A producers: row t of both tiles (TMEM lane t) per thread ----------------
+    // each thread copies its own rows into a staging slot kStagesS - 1 items
+    // ahead (cp.async groups, one per item), then splits them into TMEM
+    const int quarter = warp & 3;
+    const int t = quarter * 32 + lane;
+    const uint32_t lane_addr = tmem + ((uint32_t)(quarter * 32) << 16);
+    constexpr int D = kStagesS - 1;
+    ARow a;
+    ItemIter it;                                    // issue position, D items ahead
+    iter_begin(prm, k, nA, nit, it);
+    int slot_i = 0;                                 // staging slot of the next issue
+    for (int qq = 0; qq < D; ++qq) {
+      if (qq < nloc) {
+        arow_issue(prm, s_list, s_off, t, it, a, sS + (size_t)slot_i * 4 * kRows * 16);
+        iter_next(prm, k, nA, nit, it);
+      }
+      slot_i = slot_i + 1 == kStagesS ? 0 : slot_i + 1;
+      cp_async_commit();
     }
-    const float *Mh = prm.Mhi + prm.level_off[level] * prm.ld;
-    const float *Ml = prm.Mlo + prm.level_off[level] * prm.ld;
-    const uint32_t row_off = (uint32_t)((t >> 3) * 128 + (t & 7) * 16);
-    const float *src_h = Mh, *src_l = Ml;
-    for (int i = 0; i < nit; ++i) {
-      const int s = i % kStages, use = i / kStages;
-      if (use > 0 && !mbar_wait(&empty[s], (use - 1) & 1, abort_flag)) break;
-      const int j = i / prm.nch, kc = i - j * prm.nch;
-      if (valid && kc == 0) {
-        const int oid = prm.list[child * kListLen + j];
-        int gx = bx - prm.off[oid * 3 + 0], gy = by - prm.off[oid * 3 + 1], gz = bz - prm.off[oid * 3 + 2];
-        gx &= side - 1; gy &= side - 1; gz &= side - 1;   // periodic wrap (side is a power of two)
-        const int64_t row = (int64_t)(tc_spread(gx) | (tc_spread(gy) << 1) | (tc_spread(gz) << 2));
-        src_h = Mh + row * prm.ld;
-        src_l = Ml + row * prm.ld;
+    int slot_c = 0, s = 0;                          // staging slot and TMEM stage of item q
+    uint32_t ph = 0;                                // phase parity of emptyA[s] to wait for
+    for (int q = 0; q < nloc; ++q) {
+      if (q + D < nloc) {
+        arow_issue(prm, s_list, s_off, t, it, a, sS + (size_t)slot_i * 4 * kRows * 16);
+        iter_next(prm, k, nA, nit, it);
       }
-      if (valid) {
-        unsigned char *dh = sA + (s * 2 + 0) * a_bytes + row_off;
-        unsigned char *dl = sA + (s * 2 + 1) * a_bytes + row_off;
+      slot_i = slot_i + 1 == kStagesS ? 0 : slot_i + 1;
+      cp_async_commit();
+      cp_async_wait_group<D>();                     // this thread's copies of item q have landed
+      if (q >= kStagesA && !mbar_wait(&emptyA[s], ph, abort_flag)) break;
+      tc_fence_after();
+      const unsigned char *src = sS + (size_t)slot_c * 4 * kRows * 16 + t * 16;
+      uint32_t w[32];  // tile-0 hi | tile-0 lo | tile-1 hi | tile-1 lo, 8 columns each
 #pragma unroll
-        for (int g = 0; g < kKC / 4; ++g) {
-          cp_async16(dh + g * (kRows / 8) * 128, src_h + kc * kKC + g * 4);
-          cp_async16(dl + g * (kRows / 8) * 128, src_l + kc * kKC + g * 4);
+      for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          const float4 x = *reinterpret_cast<const float4 *>(src + (2 * h + e) * kRows * 16);
+          uint32_t *hi = w + 16 * h + 4 * e, *lo = hi + 8;
+          tf32_split(x.x, hi[0], lo[0]);
+          tf32_split(x.y, hi[1], lo[1]);
+          tf32_split(x.z, hi[2], lo[2]);
+          tf32_split(x.w, hi[3], lo[3]);
         }
+      tmem_st32(lane_addr + kAcol + 32u * (uint32_t)s, w);
+      asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+      tc_fence_before();
+      mbar_arrive(&fullA[s]);
+      slot_c = slot_c + 1 == kStagesS ? 0 : slot_c + 1;
+      if (++s == kStagesA) {
+        s = 0;
+        if (q + 1 > kStagesA) ph ^= 1u;             // from the third use on
       }
-      // the stage's barrier receives this thread's arrival when its copies land
-      cp_async_arrive(&full[s]);
     }
     cp_async_wait_all();
   } else if (warp == 5) {
     // ---------------- B producer ----------------
     if (lane == 0) {
       const uint32_t img = 2 * b_bytes;  // hi | lo of one (offset, chunk)
-      int issued = 0;
-      for (int i = 0; i < nit; ++i) {
-        const int s = i % kStages, use = i / kStages;
-        if (use > 0 && !mbar_wait(&empty[s], (use - 1) & 1, abort_flag)) break;
-        const int j = i / prm.nch, kc = i - j * prm.nch;
-        const int oid = prm.list[child * kListLen + j];
-        const unsigned char *g = prm.ops + ((size_t)oid * prm.nch + kc) * img;
-        mbar_arrive_expect_tx(&bfull[s], img);
-        bulk_g2s(sB + (size_t)s * img, g, img, &bfull[s]);
+      int issued = 0, ucur = -1, child = 0, s = 0;
+      uint32_t ph = 0;
+      ItemIter it;
+      iter_begin(prm, k, nA, nit, it);
+      for (int q = 0; q < nloc; ++q) {
+        if (q >= kStagesB && !mbar_wait(&emptyB[s], ph, abort_flag)) break;
+        if (it.unit != ucur) {
+          child = prm.units[it.unit].y;
+          ucur = it.unit;
+        }
+        const int oid = s_list[child * kListLen + it.j];
+        const unsigned char *g = prm.ops + ((size_t)oid * prm.nch + it.kc) * img;
+        mbar_arrive_expect_tx(&fullB[s], img);
+        bulk_g2s(sB + (size_t)s * img, g, img, &fullB[s]);
         ++issued;
+        iter_next(prm, k, nA, nit, it);
+        if (++s == kStagesB) {
+          s = 0;
+          if (q + 1 > kStagesB) ph ^= 1u;           // from the third use on
+        }
       }
       // the last copy into each stage is the latest phase of its barrier: wait
       // (bounded) until it has landed before the CTA can retire
-      for (int i = (issued > kStages ? issued - kStages : 0); i < issued; ++i) {
-        uint64_t *b = &bfull[i % kStages];
-        const uint32_t par = (i / kStages) & 1;
+      for (int i = (issued > kStagesB ? issued - kStagesB : 0); i < issued; ++i) {
+        uint64_t *b = &fullB[i % kStagesB];
+        const uint32_t par = (i / kStagesB) & 1;
         for (uint32_t it = 0; it < kSpinLimit && !mbar_try_wait(b, par); ++it) {
         }
       }
@@ -280,71 +532,100 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_m2l_tc(tc::Params prm) {
   } else if (warp == 0 && lane == 0) {
     // ---------------- MMA issuer ----------------
     const uint32_t idesc = idesc_tf32(kRows, ng * 8);
-    const uint32_t a_lbo = (kRows / 8) * 128, b_lbo = ng * 128;
-    int done = 0;
-    for (int i = 0; i < nit; ++i) {
-      const int s = i % kStages, use = i / kStages;
-      if (!mbar_wait(&full[s], use & 1, abort_flag)) break;
-      if (!mbar_wait(&bfull[s], use & 1, abort_flag)) break;
-      // A was written by cp.async (generic proxy): order it before the MMA reads
-      fence_proxy_async();
-      tc_fence_after();
-      const uint32_t ah = smem_u32(sA + (s * 2 + 0) * a_bytes), al = smem_u32(sA + (s * 2 + 1) * a_bytes);
-      const uint32_t bh = smem_u32(sB + (size_t)s * 2 * b_bytes), bl = bh + b_bytes;
-#pragma unroll
-      for (int ks = 0; ks < kKC / 8; ++ks) {
-        const uint32_t ao = ks * 2 * a_lbo, bo = ks * 2 * b_lbo;
-        const uint32_t acc0 = (i > 0 || ks > 0) ? 1u : 0u;
-        mma_tf32(tmem, smem_desc(ah + ao, a_lbo, 128), smem_desc(bh + bo, b_lbo, 128), idesc, acc0);
-        mma_tf32(tmem, smem_desc(ah + ao, a_lbo, 128), smem_desc(bl + bo, b_lbo, 128), idesc, 1u);
-        mma_tf32(tmem, smem_desc(al + ao, a_lbo, 128), smem_desc(bh + bo, b_lbo, 128), idesc, 1u);
+    const uint32_t b_lbo = ng * 128;
+    int ntile = 1, sa = 0, sb = 0;
+    uint32_t pa = 0, pb = 0;                        // phase parities of fullA[sa], fullB[sb]
+    bool first = true, seg_start = true;
+    ItemIter it;
+    iter_begin(prm, k, nA, nit, it);
+    const uint32_t sB0 = smem_u32(sB);
+    for (int q = 0; q < nloc; ++q) {
+      if (seg_start) {
+        // new segment: the accumulators must have been drained by the epilogue
+        if (it.seg >= 1 && !mbar_wait(tfree, (it.seg - 1) & 1, abort_flag)) break;
+        tc_fence_after();
+        first = true;
+        ntile = tile_count(prm.units[it.unit], 1) > 0 ? 2 : 1;
       }
-      mma_commit(&empty[s]);
-      ++done;
+      if (!mbar_wait(&fullA[sa], pa, abort_flag)) break;
+      if (!mbar_wait(&fullB[sb], pb, abort_flag)) break;
+      tc_fence_after();
+      const uint32_t bh = sB0 + (uint32_t)sb * 2u * b_bytes, bl = bh + b_bytes;
+      const uint64_t dbh = smem_desc(bh, b_lbo, 128), dbl = smem_desc(bl, b_lbo, 128);
+      const uint32_t acc0 = first ? 0u : 1u;
+      const uint32_t ah0 = tmem + kAcol + 32u * (uint32_t)sa;
+      mma_tf32_ts(tmem, ah0, dbh, idesc, acc0);
+      mma_tf32_ts(tmem, ah0, dbl, idesc, 1u);
+      mma_tf32_ts(tmem, ah0 + 8u, dbh, idesc, 1u);
+      if (ntile == 2) {
+        mma_tf32_ts(tmem + kAcc1, ah0 + 16u, dbh, idesc, acc0);
+        mma_tf32_ts(tmem + kAcc1, ah0 + 16u, dbl, idesc, 1u);
+        mma_tf32_ts(tmem + kAcc1, ah0 + 24u, dbh, idesc, 1u);
+      }
+      first = false;
+      mma_commit(&emptyA[sa]);
+      mma_commit(&emptyB[sb]);
+      seg_start = iter_next(prm, k, nA, nit, it);
+      if (seg_start || q == nloc - 1) mma_commit(accb);  // segment complete
+      if (++sa == kStagesA) { sa = 0; pa ^= 1u; }
+      if (++sb == kStagesB) { sb = 0; pb ^= 1u; }
     }
-    mma_commit(accb);
+  } else if (warp >= 6) {
+    // ---------------- epilogue: TMEM -> L rows, one segment at a time ----------------
+    const int quarter = warp & 3;                   // TMEM lanes this warp may read
+    const int r = quarter * 32 + lane;
+    for (int seg = 0; seg < nseg; ++seg) {
+      if (!mbar_wait(accb, seg & 1, abort_flag)) break;
+      tc_fence_after();
+      const int unit = seg < nA ? k + seg * (int)gridDim.x : prm.nfull + k / prm.q;
+      const int4 u = prm.units[unit];
+#pragma unroll 1
+      for (int h = 0; h < 2; ++h) {
+        const int cnt = tile_count(u, h);
+        if (cnt == 0) continue;                     // uniform over the warp
+        const uint32_t taddr = tmem + (h ? kAcc1 : 0u) + ((uint32_t)(quarter * 32) << 16);
+        float *Lrow = nullptr;
+        if (r < cnt)
+          Lrow = seg < nA ? prm.L + class_box_row(prm, u.x, u.y, u.z + h * kRows + r) * prm.ld
+                          : prm.partial + (((size_t)k * 2 + h) * kRows + r) * prm.ld;
+        for (int c0 = 0; c0 < ng * 8; c0 += 16) {
+          float v[16];
+          tmem_ld16(taddr + c0, v);
+          if (Lrow) {
+#pragma unroll
+            for (int e = 0; e < 16; e += 4)
+              *reinterpret_cast<float4 *>(Lrow + c0 + e) = make_float4(v[e], v[e + 1], v[e + 2], v[e + 3]);
+          }
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(tfree);
+    }
   }
   __syncwarp();
-
-  // ---------------- epilogue: TMEM -> L rows ----------------
-  bool ok = true;
-  if (warp <= 3) {
-    ok = mbar_wait(accb, 0, abort_flag);
-    tc_fence_after();
-    const int r = warp * 32 + lane;
-    const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
-    float *Lrow = nullptr;
-    if (ok && !*abort_flag && r < count) Lrow = prm.L + (prm.level_off[level] + 8 * (p0 + r) + child) * prm.ld;
-    for (int c0 = 0; c0 < ng * 8; c0 += 16) {
-      float v[16];
-      tmem_ld16(taddr + c0, v);
-      if (Lrow) {
-#pragma unroll
-        for (int q = 0; q < 16; q += 4)
-          *reinterpret_cast<float4 *>(Lrow + c0 + q) = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
-      }
-    }
-  }
   tc_fence_before();
   __syncthreads();
   if (*abort_flag && threadIdx.x == 0) atomicExch(prm.error, 1);
   if (warp == 0) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
   }
 }
 
-// Split fp32 multipoles into TF32 hi and the fp32 remainder lo = x - hi.
-__global__ void k_split_tf32(const float *__restrict__ M, float *__restrict__ hi, float *__restrict__ lo, int64_t n) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    // round to the nearest value with 10 explicit mantissa bits (ties away from
-    // zero) by integer arithmetic on the bit pattern; the remainder is exact
-    const float x = M[i];
-    uint32_t u = __float_as_uint(x);
-    if ((u & 0x7f800000u) != 0x7f800000u) u = (u + 0x1000u) & 0xffffe000u;
-    const float fh = __uint_as_float(u);
-    hi[i] = fh;
-    lo[i] = x - fh;
+// L rows of the remainder units: the q partial tiles of each, added in slice order
+__global__ void k_m2l_tc_reduce(tc::Params prm) {
+  const int64_t n = (int64_t)prm.nrem * 2 * tc::kRows * prm.ld;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(e % prm.ld);
+    const int r = (int)((e / prm.ld) % tc::kRows);
+    const int h = (int)((e / ((int64_t)prm.ld * tc::kRows)) % 2);
+    const int ru = (int)(e / ((int64_t)prm.ld * tc::kRows * 2));
+    const int4 u = prm.units[prm.nfull + ru];
+    if (r >= tc::tile_count(u, h)) continue;
+    float v = 0.f;
+    for (int sl = 0; sl < prm.q; ++sl)
+      v += prm.partial[(((size_t)(ru * prm.q + sl) * 2 + h) * tc::kRows + r) * prm.ld + c];
+    prm.L[tc::class_box_row(prm, u.x, u.y, u.z + h * tc::kRows + r) * prm.ld + c] = v;
   }
 }
 
@@ -393,10 +674,10 @@ void tc_pack_ops(int p, const std::vector<std::vector<double>> &m2l, void *host_
 int tc_build_units(mahi_ctx *h, std::vector<int> &units) {
   if (h->ld > tc::kMaxN || h->ld % tc::kKC) return -1;
   units.clear();
-  for (int l = 1; l <= h->d; ++l) {
+  for (int l = h->d; l >= 1; --l) {
     const int per_child = 1 << (3 * (l - 1));
     for (int c = 0; c < 8; ++c)
-      for (int p0 = 0; p0 < per_child; p0 += tc::kRows) {
+      for (int p0 = 0; p0 < per_child; p0 += 2 * tc::kRows) {
         units.push_back(l);
         units.push_back(c);
         units.push_back(p0);
@@ -408,18 +689,19 @@ int tc_build_units(mahi_ctx *h, std::vector<int> &units) {
 }
 
 static size_t tc_smem_bytes(int ng) {
-  const size_t a = (tc::kKC / 4) * (tc::kRows / 8) * 128, b = (size_t)(tc::kKC / 4) * ng * 128;
-  return tc::kStages * 2 * (a + b) + (3 * tc::kStages + 1) * 8 + 16;
+  const size_t b = (size_t)(tc::kKC / 4) * ng * 128;
+  const size_t stage = (size_t)tc::kStagesS * 4 * tc::kRows * 16;
+  const size_t tables = sizeof(int) * (8 * kListLen + ((3 * kNumOffsets + 1) & ~1));
+  return tc::kStagesB * 2 * b + stage + tables + (2 * tc::kStagesA + 2 * tc::kStagesB + 2) * 8 + 16;
 }
 
 int tc_m2l(mahi_ctx *h) {
-  // split the multipoles (all levels) into TF32 hi / lo
-  const int64_t n = h->nbox_total * h->ld;
-  float *Mhi = (float *)h->tc_msplit, *Mlo = Mhi + n;
-  k_split_tf32<<<4 * 152, 256, 0, h->stream>>>((const float *)h->Mexp, Mhi, Mlo, n);
+  // rewrite the multipoles of levels 1..d for coalesced gathers
+  k_m2l_src_layout<<<4 * h->num_sms, 256, 0, h->stream>>>((const float *)h->Mexp, (float *)h->tc_msrc, h->tc_level_off,
+                                                         h->ld, h->d);
+  h->launches += 1;
   tc::Params prm;
-  prm.Mhi = Mhi;
-  prm.Mlo = Mlo;
+  prm.M = (const float *)h->tc_msrc;
   prm.L = (float *)h->Lexp;
   prm.ops = (const unsigned char *)h->tc_ops;
   prm.units = (const int4 *)h->tc_units;
@@ -435,8 +717,17 @@ int tc_m2l(mahi_ctx *h) {
   if (sm > 227 * 1024) return -1;
   if (cudaFuncSetAttribute(k_m2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess) return -1;
   if (h->tc_nunits == 0) return 0;
-  k_m2l_tc<<<h->tc_nunits, tc::kThreads, sm, h->stream>>>(prm);
-  h->launches += 2;
+  const int G = h->num_sms;
+  prm.nfull = (h->tc_nunits / G) * G;
+  prm.nrem = h->tc_nunits - prm.nfull;
+  prm.q = prm.nrem > 0 ? G / prm.nrem : 1;
+  prm.partial = (float *)h->tc_partial;
+  k_m2l_tc<<<G, tc::kThreads, sm, h->stream>>>(prm);
+  if (prm.nrem > 0) {
+    k_m2l_tc_reduce<<<2 * G, 256, 0, h->stream>>>(prm);
+    h->launches += 1;
+  }
+  h->launches += 1;
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
