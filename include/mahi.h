@@ -61,7 +61,8 @@ enum {
 /* Create a solver for n_atoms atoms in a cubic periodic box of edge box_L_nm,
  * n_sites two-form titratable sites, multipole order order_p (expansions have
  * (p+1)^2 real coefficients) and octree depth (8^depth leaves).
- * Limits: 1 <= order_p <= 24 (MAHI_FP64) or <= 16 (mixed), 0 <= depth <= 6,
+ * Limits: 1 <= order_p <= 24 (MAHI_FP64), <= 16 (MAHI_MIXED_SIMT) or <= 15
+ * (MAHI_MIXED: the tensor-core tile holds at most 256 coefficients), 0 <= depth <= 6,
  * n_atoms >= 1, n_sites >= 0, box_L_nm > 0.
  * cuda_stream: cudaStream_t on which all later work is enqueued (NULL = legacy
  * default stream).  Allocates all device workspaces (the library owns them) and

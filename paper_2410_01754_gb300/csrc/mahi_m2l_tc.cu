@@ -39,7 +39,7 @@ constexpr int kRows = 128;       // targets per tile (MMA M)
 constexpr int kKC = 8;           // input coefficients per pipeline stage (one MMA K)
 constexpr int kStagesA = 4;      // A stages in tensor memory
 constexpr int kStagesS = 8;      // A staging slots in shared memory (cp.async, own rows per thread)
-constexpr int kStagesB = 12;     // B stages in shared memory
+constexpr int kStagesB = 12;     // B stages in shared memory (at most; Params::nsb is the count used)
 constexpr int kThreads = 320;
 constexpr uint32_t kSpinLimit = 1u << 26;
 constexpr int kMaxN = 256;       // MMA N limit: Kp <= 256, order <= 15
@@ -60,6 +60,8 @@ struct Params {
   int ld, nch, ngroups;         // row stride, K chunks, N row groups (Kp/8)
   int nunits;
   int nfull, nrem, q;           // units done whole (round-robin), remainder units, slices per remainder unit
+  int paired;                   // 1: a unit is two 128-target tiles (Kp <= 192); 0: one tile
+  int nsb;                      // B stages that fit in shared memory (4..kStagesB)
   float *partial;               // [nrem * q][2][kRows][ld] partial tiles of the remainder units
 };
 }  // namespace tc
@@ -268,8 +270,9 @@ __device__ __forceinline__ bool iter_next(const Params &p, int k, int nA, int ni
 }
 
 // targets in tile h (0 or 1) of a unit
-__device__ __forceinline__ int tile_count(const int4 &u, int h) {
+__device__ __forceinline__ int tile_count(const Params &p, const int4 &u, int h) {
   if (h == 0) return u.w;
+  if (!p.paired) return 0;
   const int per_child = 1 << (3 * (u.x - 1));
   const int c = per_child - u.z - kRows;
   return c < 0 ? 0 : (c > kRows ? kRows : c);
@@ -313,7 +316,7 @@ __device__ __forceinline__ void arow_issue(const Params &p, const int *s_list, c
     a.child = u.y;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-      a.valid[h] = t < tile_count(u, h);
+      a.valid[h] = t < tile_count(p, u, h);
       class_target(u.x, u.y, u.z + h * kRows + t, a.bx[h], a.by[h], a.bz[h]);
     }
     a.base = p.M + p.level_off[u.x] * p.ld;
@@ -390,7 +393,8 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_m2l_tc(tc::Params prm) {
   const int ng = prm.ngroups;                       // N row groups (Kp / 8)
   const uint32_t b_bytes = (kKC / 4) * ng * 128;    // hi (or lo) of one B chunk
   unsigned char *sB = smem;                         // [B stage][hi|lo][b_bytes]
-  unsigned char *sS = sB + kStagesB * 2 * b_bytes;  // [slot][4 granules][kRows][16 B] A staging
+  const int nsb = prm.nsb;
+  unsigned char *sS = sB + nsb * 2 * b_bytes;       // [slot][4 granules][kRows][16 B] A staging
   int *s_list = reinterpret_cast<int *>(sS + kStagesS * 4 * kRows * 16);  // [8][189] offset ids
   int *s_off = s_list + 8 * kListLen;                                   // [316][3] offsets
   uint64_t *bars = reinterpret_cast<uint64_t *>(s_off + ((3 * kNumOffsets + 1) & ~1));
@@ -504,7 +508,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_m2l_tc(tc::Params prm) {
       ItemIter it;
       iter_begin(prm, k, nA, nit, it);
       for (int q = 0; q < nloc; ++q) {
-        if (q >= kStagesB && !mbar_wait(&emptyB[s], ph, abort_flag)) break;
+        if (q >= nsb && !mbar_wait(&emptyB[s], ph, abort_flag)) break;
         if (it.unit != ucur) {
           child = prm.units[it.unit].y;
           ucur = it.unit;
@@ -515,16 +519,16 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_m2l_tc(tc::Params prm) {
         bulk_g2s(sB + (size_t)s * img, g, img, &fullB[s]);
         ++issued;
         iter_next(prm, k, nA, nit, it);
-        if (++s == kStagesB) {
+        if (++s == nsb) {
           s = 0;
-          if (q + 1 > kStagesB) ph ^= 1u;           // from the third use on
+          if (q + 1 > nsb) ph ^= 1u;                // from the third use on
         }
       }
       // the last copy into each stage is the latest phase of its barrier: wait
       // (bounded) until it has landed before the CTA can retire
-      for (int i = (issued > kStagesB ? issued - kStagesB : 0); i < issued; ++i) {
-        uint64_t *b = &fullB[i % kStagesB];
-        const uint32_t par = (i / kStagesB) & 1;
+      for (int i = (issued > nsb ? issued - nsb : 0); i < issued; ++i) {
+        uint64_t *b = &fullB[i % nsb];
+        const uint32_t par = (i / nsb) & 1;
         for (uint32_t it = 0; it < kSpinLimit && !mbar_try_wait(b, par); ++it) {
         }
       }
@@ -545,7 +549,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_m2l_tc(tc::Params prm) {
         if (it.seg >= 1 && !mbar_wait(tfree, (it.seg - 1) & 1, abort_flag)) break;
         tc_fence_after();
         first = true;
-        ntile = tile_count(prm.units[it.unit], 1) > 0 ? 2 : 1;
+        ntile = tile_count(prm, prm.units[it.unit], 1) > 0 ? 2 : 1;
       }
       if (!mbar_wait(&fullA[sa], pa, abort_flag)) break;
       if (!mbar_wait(&fullB[sb], pb, abort_flag)) break;
@@ -568,7 +572,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_m2l_tc(tc::Params prm) {
       seg_start = iter_next(prm, k, nA, nit, it);
       if (seg_start || q == nloc - 1) mma_commit(accb);  // segment complete
       if (++sa == kStagesA) { sa = 0; pa ^= 1u; }
-      if (++sb == kStagesB) { sb = 0; pb ^= 1u; }
+      if (++sb == nsb) { sb = 0; pb ^= 1u; }
     }
   } else if (warp >= 6) {
     // ---------------- epilogue: TMEM -> L rows, one segment at a time ----------------
@@ -581,7 +585,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_m2l_tc(tc::Params prm) {
       const int4 u = prm.units[unit];
 #pragma unroll 1
       for (int h = 0; h < 2; ++h) {
-        const int cnt = tile_count(u, h);
+        const int cnt = tile_count(prm, u, h);
         if (cnt == 0) continue;                     // uniform over the warp
         const uint32_t taddr = tmem + (h ? kAcc1 : 0u) + ((uint32_t)(quarter * 32) << 16);
         float *Lrow = nullptr;
@@ -621,7 +625,7 @@ __global__ void k_m2l_tc_reduce(tc::Params prm) {
     const int h = (int)((e / ((int64_t)prm.ld * tc::kRows)) % 2);
     const int ru = (int)(e / ((int64_t)prm.ld * tc::kRows * 2));
     const int4 u = prm.units[prm.nfull + ru];
-    if (r >= tc::tile_count(u, h)) continue;
+    if (r >= tc::tile_count(prm, u, h)) continue;
     float v = 0.f;
     for (int sl = 0; sl < prm.q; ++sl)
       v += prm.partial[(((size_t)(ru * prm.q + sl) * 2 + h) * tc::kRows + r) * prm.ld + c];
@@ -671,13 +675,17 @@ void tc_pack_ops(int p, const std::vector<std::vector<double>> &m2l, void *host_
     }
 }
 
+// two accumulators of Kp columns fit below the A stages only for Kp <= 192
+static inline bool tc_paired(int ld) { return ld <= (int)tc::kAcc1; }
+
 int tc_build_units(mahi_ctx *h, std::vector<int> &units) {
   if (h->ld > tc::kMaxN || h->ld % tc::kKC) return -1;
+  const int step = (tc_paired(h->ld) ? 2 : 1) * tc::kRows;
   units.clear();
   for (int l = h->d; l >= 1; --l) {
     const int per_child = 1 << (3 * (l - 1));
     for (int c = 0; c < 8; ++c)
-      for (int p0 = 0; p0 < per_child; p0 += 2 * tc::kRows) {
+      for (int p0 = 0; p0 < per_child; p0 += step) {
         units.push_back(l);
         units.push_back(c);
         units.push_back(p0);
@@ -688,11 +696,12 @@ int tc_build_units(mahi_ctx *h, std::vector<int> &units) {
   return 0;
 }
 
-static size_t tc_smem_bytes(int ng) {
+// dynamic shared memory of k_m2l_tc with nsb operator stages
+static size_t tc_smem_bytes(int ng, int nsb) {
   const size_t b = (size_t)(tc::kKC / 4) * ng * 128;
   const size_t stage = (size_t)tc::kStagesS * 4 * tc::kRows * 16;
   const size_t tables = sizeof(int) * (8 * kListLen + ((3 * kNumOffsets + 1) & ~1));
-  return tc::kStagesB * 2 * b + stage + tables + (2 * tc::kStagesA + 2 * tc::kStagesB + 2) * 8 + 16;
+  return nsb * 2 * b + stage + tables + (2 * tc::kStagesA + 2 * tc::kStagesB + 2) * 8 + 16;
 }
 
 int tc_m2l(mahi_ctx *h) {
@@ -713,7 +722,11 @@ int tc_m2l(mahi_ctx *h) {
   prm.nch = h->ld / tc::kKC;
   prm.ngroups = h->ld / 8;
   prm.nunits = h->tc_nunits;
-  const size_t sm = tc_smem_bytes(prm.ngroups);
+  prm.paired = tc_paired(h->ld) ? 1 : 0;
+  // as many operator stages as fit (12 at p <= 12, 9 at p = 15)
+  prm.nsb = tc::kStagesB;
+  while (prm.nsb > 4 && tc_smem_bytes(prm.ngroups, prm.nsb) > 227 * 1024) --prm.nsb;
+  const size_t sm = tc_smem_bytes(prm.ngroups, prm.nsb);
   if (sm > 227 * 1024) return -1;
   if (cudaFuncSetAttribute(k_m2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess) return -1;
   if (h->tc_nunits == 0) return 0;

@@ -49,8 +49,9 @@ def test_full_size_against_oracle(full, prec):
     dd = np.abs(dEdl.cpu().numpy() - np.array(g["dEdl"]))
     print(f"{prec}: force rel rms {frel:.3e}, energy rel {erel:.3e}, dE/dlambda max {dd.max():.3e} "
           f"median {np.median(dd):.3e} kJ/mol")
-    assert frel < 1e-4          # spec force bar
-    # energy: FP64 reaches 2e-8; the mixed path carries the tensor-core
-    # accumulation bias of the M2L (round toward zero)
+    assert frel < 1e-4          # required force accuracy (relative RMS)
+    # energy: FP64 reaches 2e-8; the mixed path carries the accumulation bias
+    # of the tensor-core M2L (its fp32 accumulator rounds toward zero, about
+    # -1 ulp per accumulate)
     assert erel < (1e-7 if prec == "fp64" else 3e-6)
-    assert dd.max() < 1e-3      # spec dE/dlambda bar (kJ/mol)
+    assert dd.max() < 1e-3      # required dE/dlambda accuracy (kJ/mol)

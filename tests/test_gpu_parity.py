@@ -1,6 +1,6 @@
 """GPU parity: the CUDA path against the FP64 Ewald/HI oracle on seeded inputs.
 
-Tolerances: the spec bars are a relative RMS force error <= 1e-4 and
+Tolerances: the required accuracy is a relative RMS force error <= 1e-4 and
 |d dE/dlambda| <= 1e-3 kJ/mol.  FMM truncation at order p sets the floor for
 both precisions, so each test states the bound it checks and why."""
 import numpy as np
@@ -48,13 +48,13 @@ def test_fp64_error_falls_with_order(sysA):
         assert b["Frel"] < 0.5 * a["Frel"] and b["phi"] < 0.5 * a["phi"], errs
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed_simt"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed_simt", "mixed"])
 def test_water_production_order(sysB, prec):
     """32,000 waters, d = 4, p = 10 (the workload's production order)."""
     s, ref = sysB
     e = errors(run_gpu(s, prec), ref)
-    assert e["Frel"] < 1e-5, e          # north-star bar is 1e-4
-    assert e["Erel"] < (1e-8 if prec == "fp64" else 1e-6), e
+    assert e["Frel"] < 1e-5, e          # required accuracy is 1e-4
+    assert e["Erel"] < {"fp64": 1e-8, "mixed_simt": 1e-6, "mixed": 3e-6}[prec], e
     assert e["dEdl"] < 2e-2, e          # truncation-limited at p = 10
 
 
@@ -68,13 +68,38 @@ def test_mixed_matches_fp64_path(sysB):
     assert np.abs(a["dEdl"] - b["dEdl"]).max() < 1e-2
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed_simt"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed_simt", "mixed"])
 def test_bitwise_deterministic(prec):
     s = synth.make_water(n_water=4000, grid=16, L=4.93, n_sites=8, seed=3, depth=3, order=8)
     a = run_gpu(s, prec, evals=2)
     b = run_gpu(s, prec)
     assert a["E"] == b["E"]
     assert np.array_equal(a["F"], b["F"]) and np.array_equal(a["dEdl"], b["dEdl"])
+
+
+@pytest.mark.parametrize("p", [8, 12, 13, 15])
+def test_tensor_core_m2l_matches_fp64_path(sysB, p):
+    """Tensor-core M2L (3xTF32) against the FP64 path at the same order: paired
+    128-target tiles up to p = 12, single tiles with fewer operator stages at
+    p = 13 and 15.  Water B at depth 4 has 40 M2L units (fewer than the SMs), so
+    every unit is cut into slices whose partial tiles are reduced."""
+    s, _ = sysB
+    a = run_gpu(s, "fp64", p=p)
+    b = run_gpu(s, "mixed", p=p)
+    rel = np.sqrt(((a["F"] - b["F"]) ** 2).sum() / (a["F"] ** 2).sum())
+    assert rel < 2e-5, rel
+    assert abs(a["E"] - b["E"]) / abs(a["E"]) < 3e-6
+    assert np.abs(a["dEdl"] - b["dEdl"]).max() < 1e-3
+
+
+def test_tensor_core_m2l_full_units():
+    """Depth 5: 160 M2L units, 152 of them whole (one per SM) and 8 sliced."""
+    s = synth.make_water(n_water=20000, grid=64, L=12.0, n_sites=4, seed=11, depth=5, order=8)
+    a = run_gpu(s, "mixed_simt")
+    b = run_gpu(s, "mixed")
+    rel = np.sqrt(((a["F"] - b["F"]) ** 2).sum() / (a["F"] ** 2).sum())
+    assert rel < 2e-5, rel
+    assert abs(a["E"] - b["E"]) / abs(a["E"]) < 3e-6
 
 
 def test_positions_outside_box_are_wrapped():
