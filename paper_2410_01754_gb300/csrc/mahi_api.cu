@@ -42,10 +42,10 @@ static void free_all(mahi_ctx *h) {
   void *bufs[] = {h->qA, h->dq, h->site_of, h->qt, h->leaf_of, h->slot, h->leaf_count, h->leaf_start, h->perm,
                   h->perm_tmp, h->inv_perm, h->part, h->part_tmp, h->Mexp, h->Lexp, h->phi_s, h->grad_s,
                   h->ops_m2m, h->ops_l2l, h->ops_m2l, h->ops_lat, h->eta, h->eta_x, h->eta_y, h->eta_z,
-                  h->m2l_list, h->m2l_off, h->site_ptr, h->site_atoms, h->moments_part, h->moments,
+                  h->m2l_list, h->m2l_off, h->site_ptr, h->site_atoms,
                   h->energy_part, h->site_energy, h->tc_ops, h->tc_partial, h->tc_msrc, h->tc_level_off, h->tc_units, h->tc_error, h->d_x_stage,
                   h->d_lam_stage, h->d_E_stage, h->d_dEdl_stage, h->d_F_stage, h->ops_lat_h3, h->L_h3,
-                  h->box_qd, h->phi_site, h->phi_part, h->d_level_off, h->tc_error_site};
+                  h->box_qd, h->vtmp, h->relD, h->phi_site, h->phi_part, h->d_level_off, h->tc_error_site};
   for (void *b : bufs)
     if (b) cudaFree(b);
   for (int i = 0; i < 32; ++i)
@@ -154,11 +154,10 @@ int mahi_create(double box_L_nm, int64_t n_atoms, int32_t n_sites, int32_t order
   AL(h->leaf_of, N * 4); AL(h->slot, N * 4);
   AL(h->leaf_count, (size_t)h->nleaf * 4); AL(h->leaf_start, (size_t)(h->nleaf + 1) * 4);
   AL(h->perm, N * 4); AL(h->perm_tmp, N * 4); AL(h->inv_perm, N * 4);
-  AL(h->part, N * v4); AL(h->part_tmp, N * v4);
+  AL(h->part, N * v4); AL(h->part_tmp, N * v4); AL(h->vtmp, N * v4); AL(h->relD, N * 3 * 8);
   AL(h->Mexp, (size_t)h->nbox_total * h->ld * ts); AL(h->Lexp, (size_t)h->nbox_total * h->ld * ts);
   AL(h->phi_s, N * ts); AL(h->grad_s, N * 3 * ts);
   h->n_moment_blocks = (int)std::min<int64_t>(4 * 152, (N + 255) / 256);
-  AL(h->moments_part, (size_t)h->n_moment_blocks * 5 * 8); AL(h->moments, 8 * 8);
   AL(h->energy_part, (size_t)h->nleaf * 8); AL(h->site_energy, (size_t)std::max(1, n_sites) * 8);
   {
     cudaError_t e = cudaMemset(h->Lexp, 0, (size_t)h->nbox_total * h->ld * ts);
@@ -206,7 +205,7 @@ int mahi_create(double box_L_nm, int64_t n_atoms, int32_t n_sites, int32_t order
     AL(h->L_h3, sizeof(double) * K);
     AL(h->tc_error_site, 16);
     cudaMemset(h->tc_error_site, 0, 16);
-    AL(h->box_qd, sizeof(double) * 4 * h->nbox_total);
+    AL(h->box_qd, sizeof(double) * 8 * h->nbox_total);
     AL(h->d_level_off, sizeof(int64_t) * (kMaxDepth + 2));
     if ((e = cudaMemcpy(h->d_level_off, h->level_off, sizeof(int64_t) * (kMaxDepth + 2), cudaMemcpyHostToDevice)) !=
         cudaSuccess)

@@ -96,13 +96,15 @@ struct mahi_ctx {
   int *leaf_of = nullptr, *slot = nullptr, *leaf_count = nullptr, *leaf_start = nullptr;
   int *perm = nullptr, *perm_tmp = nullptr, *inv_perm = nullptr;
   void *part = nullptr, *part_tmp = nullptr;  // float4 or double4, sorted by leaf
+  void *vtmp = nullptr;                       // float4 or double4, original order
+  double *relD = nullptr;                     // N x 3 offsets from the leaf centre (FP64)
   void *Mexp = nullptr, *Lexp = nullptr;      // expansions, all levels
   void *phi_s = nullptr, *grad_s = nullptr;   // sorted potential / gradient
   void *ops_m2m = nullptr, *ops_l2l = nullptr, *ops_m2l = nullptr;
   double *ops_lat = nullptr;                  // FP64 root operator (images 2..3 + H_3)
   double *ops_lat_h3 = nullptr;               // FP64 H_3 part alone (site-atom path)
   double *L_h3 = nullptr;                     // root local of H_3 (K doubles)
-  double *box_qd = nullptr;                   // FP64 charge + dipole per box, all levels
+  double *box_qd = nullptr;                   // FP64 Q, D, T per box (8 doubles), all levels
   double *phi_site = nullptr;                 // refined potential at site atoms
   double *phi_part = nullptr;                 // its per-part partial sums
   int64_t *d_level_off = nullptr;             // device copy of level_off
@@ -110,11 +112,9 @@ struct mahi_ctx {
   int *m2l_list = nullptr;                    // [8][189] offset ids
   int *m2l_off = nullptr;                     // [316][3]
   int *site_ptr = nullptr, *site_atoms = nullptr;
-  double *moments_part = nullptr;             // per-block partial moments
-  double *moments = nullptr;                  // Q, Dx, Dy, Dz, T
   double *energy_part = nullptr;              // per-block energy partials
   double *site_energy = nullptr;              // S
-  int n_moment_blocks = 0, n_energy_blocks = 0;
+  int n_moment_blocks = 0;                    // grid of k_bin
   // tensor-core M2L operand images (mixed path)
   void *tc_ops = nullptr;
   void *tc_partial = nullptr;                 // M2L partial tiles of units split across CTAs

@@ -156,46 +156,60 @@ __device__ __forceinline__ double rsqrt_dp(double r2) {
 __device__ __forceinline__ int ridx(int l, int m) { return m == 0 ? l * l : l * l + 2 * m - 1; }
 
 // ---------------------------------------------------------------------------
-// 1. scale charges, bin atoms into leaves, moments Q, D, T (FP64 partials)
+// 1. scale charges, bin atoms into leaves.  GB300 runs FP64 at a small fraction
+//    of its FP32 rate, so every per-atom FP64 operation counts: positions
+//    already inside the box skip the wrap, the leaf index comes from one
+//    multiplication, the leaf centres from a shared table.  Per atom this
+//    writes the leaf, its slot in the leaf, q~ (FP64), the offset from the leaf
+//    centre (FP64) and the working-precision particle (offset, q~), all in
+//    the original atom order.
 // ---------------------------------------------------------------------------
-template <typename XT>
-__global__ void k_bin(const XT *__restrict__ x, int64_t N, double L, int nb, const double *__restrict__ lam,
-                      const double *__restrict__ qA, const double *__restrict__ dq, const int *__restrict__ site_of,
-                      int *__restrict__ leaf_of, int *__restrict__ slot, int *__restrict__ leaf_count,
-                      double *__restrict__ qt, double *__restrict__ mom_part) {
-  double m[5] = {0, 0, 0, 0, 0};
-  const double c = 0.5 * L;
+constexpr int kMaxSide = 1 << kMaxDepth;  // leaves along one edge
+constexpr int kQD = 8;                    // doubles per box in box_qd: Q, Dx, Dy, Dz, T, pad
+
+// wrapped coordinate in [0, L); the in-box test is exact: Lf_up is the
+// smallest float >= L, so x < Lf_up <=> x < L for a float x
+__device__ __forceinline__ double wrap_slow(double v, double L) {
+  v -= floor(v / L) * L;
+  if (v >= L) v -= L;
+  if (v < 0.0) v = 0.0;
+  return v;
+}
+__device__ __forceinline__ double wrap_coord(float x, double L, float Lf_up) {
+  return (x >= 0.f && x < Lf_up) ? (double)x : wrap_slow((double)x, L);
+}
+__device__ __forceinline__ double wrap_coord(double x, double L, float) {
+  return (x >= 0.0 && x < L) ? x : wrap_slow(x, L);
+}
+
+template <typename T, typename XT>
+__global__ void k_bin(const XT *__restrict__ x, int64_t N, double L, double s, double inv_s, float Lf_up, int nb,
+                      const double *__restrict__ lam, const double *__restrict__ qA, const double *__restrict__ dq,
+                      const int *__restrict__ site_of, int *__restrict__ leaf_of, int *__restrict__ slot,
+                      int *__restrict__ leaf_count, double *__restrict__ qt, typename V4<T>::type *__restrict__ vtmp,
+                      double *__restrict__ relD) {
+  __shared__ double ctab[kMaxSide];
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) ctab[i] = (i + 0.5) * s;
+  __syncthreads();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
     double p[3];
+    int c[3];
+#pragma unroll
     for (int a = 0; a < 3; ++a) {
-      double v = (double)x[3 * i + a];
-      v -= floor(v / L) * L;
-      if (v >= L) v -= L;
-      if (v < 0.0) v = 0.0;
-      p[a] = v;
+      p[a] = wrap_coord(x[3 * i + a], L, Lf_up);
+      c[a] = min((int)(p[a] * inv_s), nb - 1);
+      p[a] -= ctab[c[a]];
     }
-    int s = site_of[i];
-    double q = qA[i] + (s >= 0 ? lam[s] * dq[i] : 0.0);
+    const int st = site_of[i];
+    const double q = st >= 0 ? fma(lam[st], dq[i], qA[i]) : qA[i];
     qt[i] = q;
-    int ix = min((int)(p[0] / L * nb), nb - 1), iy = min((int)(p[1] / L * nb), nb - 1),
-        iz = min((int)(p[2] / L * nb), nb - 1);
-    int leaf = (int)d_morton(ix, iy, iz);
+    const int leaf = (int)d_morton(c[0], c[1], c[2]);
     leaf_of[i] = leaf;
     slot[i] = atomicAdd(&leaf_count[leaf], 1);
-    double ax = p[0] - c, ay = p[1] - c, az = p[2] - c;
-    m[0] += q; m[1] += q * ax; m[2] += q * ay; m[3] += q * az; m[4] += q * (ax * ax + ay * ay + az * az);
-  }
-  __shared__ double red[5][32];
-  for (int k = 0; k < 5; ++k) {
-    double v = m[k];
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffff, v, o);
-    if ((threadIdx.x & 31) == 0) red[k][threadIdx.x >> 5] = v;
-  }
-  __syncthreads();
-  if (threadIdx.x < 5) {
-    double v = 0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[threadIdx.x][w];
-    mom_part[(size_t)blockIdx.x * 5 + threadIdx.x] = v;
+    relD[3 * i + 0] = p[0];
+    relD[3 * i + 1] = p[1];
+    relD[3 * i + 2] = p[2];
+    vtmp[i] = typename V4<T>::type{(T)p[0], (T)p[1], (T)p[2], (T)q};
   }
 }
 
@@ -216,58 +230,78 @@ __global__ void k_reduce_partials(const double *__restrict__ part, int nblocks, 
   }
 }
 
-// exclusive scan of leaf counts (single block)
-__global__ void k_scan(const int *__restrict__ cnt, int n, int *__restrict__ start) {
-  __shared__ int sums[1024];
-  int t = threadIdx.x, per = (n + blockDim.x - 1) / blockDim.x;
-  int b = t * per, e = min(n, b + per), s = 0;
-  for (int i = b; i < e; ++i) s += cnt[i];
-  sums[t] = s;
-  __syncthreads();
-  for (int o = 1; o < (int)blockDim.x; o <<= 1) {
-    int v = (t >= o) ? sums[t - o] : 0;
-    __syncthreads();
-    sums[t] += v;
-    __syncthreads();
+// exclusive scan of the leaf counts (one block of 1024 threads): every thread
+// owns a contiguous run of n / 1024 counts (n is a power of 8), read and
+// written as int4 where the run allows it
+__global__ void __launch_bounds__(1024) k_scan(const int *__restrict__ cnt, int n, int *__restrict__ start) {
+  __shared__ int wsum[32];
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  const int per = (n + blockDim.x - 1) / blockDim.x;
+  const int b = min(n, t * per), e = min(n, b + per);
+  int loc = 0;
+  const bool vec = (per % 4) == 0 && (e - b) == per;
+  if (vec) {
+    for (int i = b; i < e; i += 4) {
+      const int4 v = *reinterpret_cast<const int4 *>(cnt + i);
+      loc += v.x + v.y + v.z + v.w;
+    }
+  } else {
+    for (int i = b; i < e; ++i) loc += cnt[i];
   }
-  int run = sums[t] - s;
-  for (int i = b; i < e; ++i) { start[i] = run; run += cnt[i]; }
-  if (t == blockDim.x - 1) start[n] = sums[t];
+  int inc = loc;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffff, inc, o);
+    if (lane >= o) inc += y;
+  }
+  if (lane == 31) wsum[w] = inc;
+  __syncthreads();
+  if (w == 0) {
+    int v = lane < (int)(blockDim.x >> 5) ? wsum[lane] : 0;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffff, v, o);
+      if (lane >= o) v += y;
+    }
+    wsum[lane] = v;  // inclusive
+  }
+  __syncthreads();
+  int run = inc - loc + (w > 0 ? wsum[w - 1] : 0);
+  if (vec) {
+    for (int i = b; i < e; i += 4) {
+      const int4 v = *reinterpret_cast<const int4 *>(cnt + i);
+      int4 o;
+      o.x = run; run += v.x;
+      o.y = run; run += v.y;
+      o.z = run; run += v.z;
+      o.w = run; run += v.w;
+      *reinterpret_cast<int4 *>(start + i) = o;
+    }
+  } else {
+    for (int i = b; i < e; ++i) { start[i] = run; run += cnt[i]; }
+  }
+  if (t == blockDim.x - 1) start[n] = run;
 }
 
-template <typename T, typename XT>
-__global__ void k_scatter(const XT *__restrict__ x, int64_t N, double L, int nb, const int *__restrict__ leaf_of,
-                          const int *__restrict__ slot, const int *__restrict__ leaf_start,
-                          const double *__restrict__ qt, typename V4<T>::type *__restrict__ part_tmp,
-                          int *__restrict__ perm_tmp) {
+template <typename T>
+__global__ void k_scatter(int64_t N, const int *__restrict__ leaf_of, const int *__restrict__ slot,
+                          const int *__restrict__ leaf_start, const typename V4<T>::type *__restrict__ vtmp,
+                          typename V4<T>::type *__restrict__ part_tmp, int *__restrict__ perm_tmp) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= N) return;
-  int leaf = leaf_of[i];
-  int pos = leaf_start[leaf] + slot[i];
-  int ix = (int)d_compact(leaf), iy = (int)d_compact(leaf >> 1), iz = (int)d_compact(leaf >> 2);
-  double s = L / nb;
-  double p[3];
-  for (int a = 0; a < 3; ++a) {
-    double v = (double)x[3 * i + a];
-    v -= floor(v / L) * L;
-    if (v >= L) v -= L;
-    if (v < 0.0) v = 0.0;
-    p[a] = v;
-  }
-  typename V4<T>::type o;
-  o.x = (T)(p[0] - (ix + 0.5) * s);
-  o.y = (T)(p[1] - (iy + 0.5) * s);
-  o.z = (T)(p[2] - (iz + 0.5) * s);
-  o.w = (T)qt[i];
-  part_tmp[pos] = o;
+  const int pos = leaf_start[leaf_of[i]] + slot[i];
+  part_tmp[pos] = vtmp[i];
   perm_tmp[pos] = (int)i;
 }
 
-// Order the atoms of every leaf by original index (deterministic layout).
+// Order the atoms of every leaf by original index (deterministic layout), then
+// the FP64 charge Q, dipole D and second moment T = sum q |x - c|^2 of the leaf
+// about its centre c, summed in that order.  These feed the l <= 1 terms of the
+// site-atom potential and, through exact translation up the tree, the
+// dipole / background term of the periodic kernel.
 template <typename T>
 __global__ void k_leaf_sort(int nleaf, const int *__restrict__ leaf_start, const typename V4<T>::type *__restrict__ part_tmp,
-                            const int *__restrict__ perm_tmp, typename V4<T>::type *__restrict__ part,
-                            int *__restrict__ perm, int *__restrict__ inv_perm) {
+                            const int *__restrict__ perm_tmp, const double *__restrict__ qt,
+                            const double *__restrict__ relD, typename V4<T>::type *__restrict__ part,
+                            int *__restrict__ perm, int *__restrict__ inv_perm, double *__restrict__ qd) {
   int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (warp >= nleaf) return;
   int b = leaf_start[warp], e = leaf_start[warp + 1];
@@ -277,6 +311,22 @@ __global__ void k_leaf_sort(int nleaf, const int *__restrict__ leaf_start, const
     part[b + rank] = part_tmp[a];
     perm[b + rank] = key;
     inv_perm[key] = b + rank;
+  }
+  __syncwarp();
+  double v[5] = {0, 0, 0, 0, 0};
+  for (int a = b + lane; a < e; a += 32) {
+    const int i = perm[a];
+    const double q = qt[i], rx = relD[3 * (size_t)i], ry = relD[3 * (size_t)i + 1], rz = relD[3 * (size_t)i + 2];
+    v[0] += q;
+    v[1] = fma(q, rx, v[1]);
+    v[2] = fma(q, ry, v[2]);
+    v[3] = fma(q, rz, v[3]);
+    v[4] = fma(q, rx * rx + ry * ry + rz * rz, v[4]);
+  }
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffff, v[k], o);
+    if (lane == 0) qd[(size_t)warp * kQD + k] = v[k];
   }
 }
 
@@ -450,6 +500,7 @@ template <typename T>
 __global__ void k_lattice(int K, int ld, double L, const double *__restrict__ lat, const double *__restrict__ lat_h3,
                           const double *__restrict__ mom, const T *__restrict__ Mroot, T *__restrict__ Lroot,
                           double *__restrict__ Lh3) {
+  // one warp per output row, spread over the GPU (the FP64 rate per SM is low)
   extern __shared__ double ms[];
   for (int k = threadIdx.x; k < K; k += blockDim.x) ms[k] = (double)Mroot[k];
   __syncthreads();
@@ -466,16 +517,25 @@ __global__ void k_lattice(int K, int ld, double L, const double *__restrict__ la
     }
   }
   __syncthreads();
-  for (int r = threadIdx.x; r < K; r += blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (r < K) {
     double s = 0, s3 = 0;
-    for (int k = 0; k < K; ++k) {
-      s += lat[(size_t)r * K + k] * ms[k];
-      s3 += lat_h3[(size_t)r * K + k] * ms[k];
+    for (int k = lane; k < K; k += 32) {
+      s = fma(lat[(size_t)r * K + k], ms[k], s);
+      s3 = fma(lat_h3[(size_t)r * K + k], ms[k], s3);
     }
-    Lroot[r] = (T)s;
-    Lh3[r] = s3;
+    for (int o = 16; o > 0; o >>= 1) {
+      s += __shfl_xor_sync(0xffffffff, s, o);
+      s3 += __shfl_xor_sync(0xffffffff, s3, o);
+    }
+    if (lane == 0) {
+      Lroot[r] = (T)s;
+      Lh3[r] = s3;
+    }
+  } else if (r < ld && lane == 0) {
+    Lroot[r] = T(0);
   }
-  for (int r = K + threadIdx.x; r < ld; r += blockDim.x) Lroot[r] = T(0);
 }
 
 // ---------------------------------------------------------------------------
@@ -568,6 +628,23 @@ __global__ void k_l2p(int nleaf, int P, int ld, T s, const int *__restrict__ lea
 // ---------------------------------------------------------------------------
 constexpr int P2P_THREADS = 128;
 
+// energy accumulator: compensated (Kahan-Babuska) in single precision, plain in FP64
+template <typename T> struct SiteAccE;
+template <> struct SiteAccE<float> {
+  float h = 0.f, l = 0.f;
+  __device__ __forceinline__ void add(float v) {
+    const float s = h + v, bv = s - h;
+    l += (h - (s - bv)) + (v - bv);
+    h = s;
+  }
+  __device__ __forceinline__ double value() const { return (double)h + (double)l; }
+};
+template <> struct SiteAccE<double> {
+  double h = 0.0;
+  __device__ __forceinline__ void add(double v) { h += v; }
+  __device__ __forceinline__ double value() const { return h; }
+};
+
 __device__ __forceinline__ double rinv(double r2) { return 1.0 / sqrt(r2); }
 // hardware reciprocal square root refined by one Newton-Raphson step
 // y' = y (3 - r2 y^2) / 2, which roughly squares the relative error
@@ -592,33 +669,46 @@ __global__ void __launch_bounds__(P2P_THREADS) k_p2p(int nb, double L, double fc
   using V = typename V4<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V *src = reinterpret_cast<V *>(smem_raw);
-  __shared__ int nb_start[27], nb_cnt[27], nb_pre[28];
+  __shared__ int nb_start[27], nb_pre[28];
   __shared__ T red[P2P_THREADS][4];
+  __shared__ T kc[5];
   __shared__ double ered[P2P_THREADS / 32];
   const int leaf = blockIdx.x;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const T s = (T)(L / nb);
   const int ix = (int)d_compact(leaf), iy = (int)d_compact(leaf >> 1), iz = (int)d_compact(leaf >> 2);
   if (tid < 27) {
     int dx = tid % 3 - 1, dy = (tid / 3) % 3 - 1, dz = tid / 9 - 1;
     int n = (int)d_morton(wrapi(ix + dx, nb), wrapi(iy + dy, nb), wrapi(iz + dz, nb));
     nb_start[tid] = leaf_start[n];
-    nb_cnt[tid] = leaf_start[n + 1] - leaf_start[n];
+    nb_pre[tid + 1] = leaf_start[n + 1] - leaf_start[n];
+  }
+  if (tid == 32) {
+    // dipole / background term of the periodic kernel, (2 pi/3V) sum_j q_j |x_i - x_j|^2
+    //   = c2 (Q |a|^2 - 2 a.D + T) with a = x_i - box centre = lc + m (lc: this
+    // leaf's centre, m: the stored offset); per leaf in FP64:
+    //   K0 = c2 (Q |lc|^2 - 2 lc.D + T), K1 = 2 c2 (Q lc - D), K2 = c2 Q,
+    // so the term is K0 + K1.m + K2 |m|^2 and its gradient K1 + 2 K2 m
+    const double Q = mom[0], Dx = mom[1], Dy = mom[2], Dz = mom[3], Tm = mom[4];
+    const double c2 = 2.0 * kPi / (3.0 * L * L * L);
+    const double lcx = (ix + 0.5) * (L / nb) - 0.5 * L, lcy = (iy + 0.5) * (L / nb) - 0.5 * L,
+                 lcz = (iz + 0.5) * (L / nb) - 0.5 * L;
+    kc[0] = (T)(c2 * (Q * (lcx * lcx + lcy * lcy + lcz * lcz) - 2.0 * (lcx * Dx + lcy * Dy + lcz * Dz) + Tm));
+    kc[1] = (T)(2.0 * c2 * (Q * lcx - Dx));
+    kc[2] = (T)(2.0 * c2 * (Q * lcy - Dy));
+    kc[3] = (T)(2.0 * c2 * (Q * lcz - Dz));
+    kc[4] = (T)(c2 * Q);
   }
   __syncthreads();
   if (tid == 0) {
     nb_pre[0] = 0;
-    for (int k = 0; k < 27; ++k) nb_pre[k + 1] = nb_pre[k] + nb_cnt[k];
+    for (int k = 0; k < 27; ++k) nb_pre[k + 1] += nb_pre[k];
   }
   __syncthreads();
   const int tb = leaf_start[leaf], te = leaf_start[leaf + 1], nt = te - tb;
   const int nsrc_total = nb_pre[27];
-  // centre of the system box relative to this leaf centre, for the r^2 term
-  const double Q = mom[0], Dx = mom[1], Dy = mom[2], Dz = mom[3], Tm = mom[4];
-  const double vol = L * L * L, c2 = 2.0 * kPi / (3.0 * vol);
-  const double lcx = (ix + 0.5) * (L / nb) - 0.5 * L, lcy = (iy + 0.5) * (L / nb) - 0.5 * L,
-               lcz = (iz + 0.5) * (L / nb) - 0.5 * L;
-  double e_acc = 0.0;
+  const T fc = (T)fcoul;
+  SiteAccE<T> e_acc;
   // process targets in groups so that (target, chunk) pairs fill the block
   int nchunk = P2P_THREADS / max(1, min(nt, P2P_THREADS));
   int tgroup = P2P_THREADS / nchunk;
@@ -630,13 +720,19 @@ __global__ void __launch_bounds__(P2P_THREADS) k_p2p(int nb, double L, double fc
     for (int s0 = 0; s0 < nsrc_total; s0 += P2P_MAXSRC) {
       int ns = min(P2P_MAXSRC, nsrc_total - s0);
       __syncthreads();
-      for (int i = tid; i < ns; i += P2P_THREADS) {
-        int g = s0 + i, k = 0;
-        while (nb_pre[k + 1] <= g) ++k;
-        V v = part[nb_start[k] + (g - nb_pre[k])];
-        int dx = k % 3 - 1, dy = (k / 3) % 3 - 1, dz = k / 9 - 1;
-        v.x += dx * s; v.y += dy * s; v.z += dz * s;
-        src[i] = v;
+      // stage the sources, shifted to this leaf's frame: warp w copies the
+      // neighbour leaves w, w + 4, ...
+      for (int k = warp; k < 27; k += P2P_THREADS / 32) {
+        const int b = nb_pre[k] - s0, cnt = nb_pre[k + 1] - nb_pre[k];
+        const T ox = (T)(k % 3 - 1) * s, oy = (T)((k / 3) % 3 - 1) * s, oz = (T)(k / 9 - 1) * s;
+        for (int i = lane; i < cnt; i += 32) {
+          const int d = b + i;
+          if (d >= 0 && d < ns) {
+            V v = part[nb_start[k] + i];
+            v.x += ox; v.y += oy; v.z += oz;
+            src[d] = v;
+          }
+        }
       }
       __syncthreads();
       // self: neighbour k = 13 is the leaf itself, at source index nb_pre[13] + ta
@@ -644,12 +740,13 @@ __global__ void __launch_bounds__(P2P_THREADS) k_p2p(int nb, double L, double fc
       int per = (ns + nchunk - 1) / nchunk;
       int jb = ck * per, je = min(ns, jb + per);
       if (tv) {
+#pragma unroll 4
         for (int j = jb; j < je; ++j) {
           V v = src[j];
           T rx = me.x - v.x, ry = me.y - v.y, rz = me.z - v.z;
           T r2 = rx * rx + ry * ry + rz * rz;
-          if (j == self) continue;
           T ri = rinv(r2);
+          ri = (j == self) ? T(0) : ri;
           T qr = v.w * ri;
           f += qr;
           T g3 = qr * ri * ri;
@@ -664,18 +761,20 @@ __global__ void __launch_bounds__(P2P_THREADS) k_p2p(int nb, double L, double fc
         int o = tid + c2i * tgroup;
         f += red[o][0]; gx += red[o][1]; gy += red[o][2]; gz += red[o][3];
       }
-      int a = tb + ta;
-      double ff = (double)f + (double)phi_s[a];
-      double g0 = (double)gx + (double)grad_s[3 * (size_t)a], g1 = (double)gy + (double)grad_s[3 * (size_t)a + 1],
-             g2 = (double)gz + (double)grad_s[3 * (size_t)a + 2];
-      // dipole / background term of the periodic kernel: (2 pi/3V) sum_j q_j |x_i - x_j|^2
-      double ax = lcx + (double)me.x, ay = lcy + (double)me.y, az = lcz + (double)me.z;
-      ff += c2 * (Q * (ax * ax + ay * ay + az * az) - 2.0 * (ax * Dx + ay * Dy + az * Dz) + Tm);
-      g0 += 2.0 * c2 * (Q * ax - Dx); g1 += 2.0 * c2 * (Q * ay - Dy); g2 += 2.0 * c2 * (Q * az - Dz);
-      ff *= fcoul; g0 *= fcoul; g1 *= fcoul; g2 *= fcoul;
-      double q = (double)me.w;
-      phi_s[a] = (T)ff;
-      e_acc += 0.5 * q * ff;
+      const int a = tb + ta;
+      // near + far field, then the dipole / background term (in the working
+      // precision from the FP64 per-leaf constants)
+      T ff = f + phi_s[a];
+      T g0 = gx + grad_s[3 * (size_t)a], g1 = gy + grad_s[3 * (size_t)a + 1], g2 = gz + grad_s[3 * (size_t)a + 2];
+      const T mx = me.x, my = me.y, mz = me.z;
+      ff += kc[0] + kc[1] * mx + kc[2] * my + kc[3] * mz + kc[4] * (mx * mx + my * my + mz * mz);
+      g0 += kc[1] + T(2) * kc[4] * mx;
+      g1 += kc[2] + T(2) * kc[4] * my;
+      g2 += kc[3] + T(2) * kc[4] * mz;
+      ff *= fc; g0 *= fc; g1 *= fc; g2 *= fc;
+      const T q = me.w;
+      phi_s[a] = ff;
+      e_acc.add(T(0.5) * q * ff);
       int io = perm[a];
       if (forces) {
         forces[3 * (size_t)io + 0] = (FT)(-q * g0);
@@ -685,8 +784,9 @@ __global__ void __launch_bounds__(P2P_THREADS) k_p2p(int nb, double L, double fc
     }
     __syncthreads();
   }
-  for (int o = 16; o > 0; o >>= 1) e_acc += __shfl_xor_sync(0xffffffff, e_acc, o);
-  if ((tid & 31) == 0) ered[tid >> 5] = e_acc;
+  double ev = e_acc.value();
+  for (int o = 16; o > 0; o >>= 1) ev += __shfl_xor_sync(0xffffffff, ev, o);
+  if (lane == 0) ered[warp] = ev;
   __syncthreads();
   if (tid == 0) {
     double v = 0;
@@ -799,49 +899,26 @@ __global__ void k_site(int S, double L, double fcoul, int Pmax, const int *__res
 }
 
 // ---------------------------------------------------------------------------
-// 8. FP64 charge and dipole (about the box centre) of every box: leaves from the
-//    atoms (original FP64 positions), parents by exact translation.  They feed
-//    the l <= 1 terms of the per-site-atom potential below.
+// 8. FP64 charge, dipole and second moment (about the box centre) of every box
+//    above the leaves by exact translation of the children's:
+//    Q = sum Q_c, D = sum (D_c + Q_c o_c), T = sum (T_c + 2 o_c.D_c + Q_c |o_c|^2),
+//    o_c = child centre - parent centre.  The root's values are the moments
+//    of the whole box about its centre used by the dipole / background term.
 // ---------------------------------------------------------------------------
-template <typename XT>
-__global__ void k_qd_leaf(int nleaf, int nb, double L, const int *__restrict__ leaf_start, const int *__restrict__ perm,
-                          const XT *__restrict__ x, const double *__restrict__ qt, double *__restrict__ qd) {
-  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-  if (warp >= nleaf) return;
-  const double s = L / nb;
-  const int ix = (int)d_compact(warp), iy = (int)d_compact(warp >> 1), iz = (int)d_compact(warp >> 2);
-  const double c[3] = {(ix + 0.5) * s, (iy + 0.5) * s, (iz + 0.5) * s};
-  double v[4] = {0, 0, 0, 0};
-  for (int a = leaf_start[warp] + lane; a < leaf_start[warp + 1]; a += 32) {
-    int i = perm[a];
-    double q = qt[i];
-    v[0] += q;
-    for (int k = 0; k < 3; ++k) {
-      double w = (double)x[3 * (size_t)i + k];
-      w -= floor(w / L) * L;
-      if (w >= L) w -= L;
-      if (w < 0.0) w = 0.0;
-      v[1 + k] += q * (w - c[k]);
-    }
-  }
-  for (int k = 0; k < 4; ++k) {
-    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffff, v[k], o);
-    if (lane == 0) qd[(size_t)warp * 4 + k] = v[k];
-  }
-}
-
 __global__ void k_qd_up(int nparent, double s_child, const double *__restrict__ child, double *__restrict__ parent) {
   int P = blockIdx.x * blockDim.x + threadIdx.x;
   if (P >= nparent) return;
-  double v[4] = {0, 0, 0, 0};
+  double v[5] = {0, 0, 0, 0, 0};
   for (int c = 0; c < 8; ++c) {
-    const double *ch = child + (size_t)(8 * P + c) * 4;
-    double off[3] = {((c & 1) ? 0.5 : -0.5) * s_child, ((c & 2) ? 0.5 : -0.5) * s_child,
-                     ((c & 4) ? 0.5 : -0.5) * s_child};
+    const double *ch = child + (size_t)(8 * P + c) * kQD;
+    const double off[3] = {((c & 1) ? 0.5 : -0.5) * s_child, ((c & 2) ? 0.5 : -0.5) * s_child,
+                           ((c & 4) ? 0.5 : -0.5) * s_child};
     v[0] += ch[0];
+    v[4] += ch[4] + 2.0 * (off[0] * ch[1] + off[1] * ch[2] + off[2] * ch[3]) +
+            ch[0] * (off[0] * off[0] + off[1] * off[1] + off[2] * off[2]);
     for (int k = 0; k < 3; ++k) v[1 + k] += ch[1 + k] + ch[0] * off[k];
   }
-  for (int k = 0; k < 4; ++k) parent[(size_t)P * 4 + k] = v[k];
+  for (int k = 0; k < 5; ++k) parent[(size_t)P * kQD + k] = v[k];
 }
 
 // ---------------------------------------------------------------------------
@@ -1204,7 +1281,7 @@ __global__ void __launch_bounds__(kSiteThreads, 3) k_site_phi(
           const double wy = (((int)d_compact(box >> 1) + 0.5) * s + ny * L) - cen[1];
           const double wz = (((int)d_compact(box >> 2) + 0.5) * s + nz * L) - cen[2];
           const double B2 = wx * wx + wy * wy + wz * wz, Bi = rinv_dd(B2);
-          const double Q = qd[row * 4], px = qd[row * 4 + 1], py = qd[row * 4 + 2], pz = qd[row * 4 + 3];
+          const double Q = qd[row * kQD], px = qd[row * kQD + 1], py = qd[row * kQD + 2], pz = qd[row * kQD + 3];
           const double pw = px * wx + py * wy + pz * wz;
           base += Q * Bi - pw * (Bi * Bi * Bi);  // at c the box centre is at -w
           rw[tid][0] = (T)wx; rw[tid][1] = (T)wy; rw[tid][2] = (T)wz;
@@ -1444,23 +1521,27 @@ static cudaError_t eval_t(mahi_ctx *h, const XT *x, const double *lam, double *e
   const int64_t N = h->N;
   const int K = h->K, ld = h->ld, P = h->p;
   T *M = (T *)h->Mexp, *Lx = (T *)h->Lexp;
+  const double *mom = h->box_qd;  // root box row: Q, D, T of the system about the box centre
   h->launches = 0;
   mark(h, 0);
   MAHI_CK(cudaMemsetAsync(h->leaf_count, 0, sizeof(int) * nleaf, st));
-  k_bin<XT><<<h->n_moment_blocks, 256, 0, st>>>(x, N, h->L, nb, lam, h->qA, h->dq, h->site_of, h->leaf_of, h->slot,
-                                                 h->leaf_count, h->qt, h->moments_part);
-  k_reduce_partials<<<5, 256, 0, st>>>(h->moments_part, h->n_moment_blocks, 5, h->moments, 1.0);
-  h->launches += 2;
+  {
+    const double s_l = h->L / nb;
+    float lf = (float)h->L;
+    if ((double)lf < h->L) lf = nextafterf(lf, INFINITY);  // smallest float >= L
+    k_bin<T, XT><<<h->n_moment_blocks, 256, 0, st>>>(x, N, h->L, s_l, nb / h->L, lf, nb, lam, h->qA, h->dq, h->site_of,
+                                                      h->leaf_of, h->slot, h->leaf_count, h->qt, (V *)h->vtmp, h->relD);
+  }
+  h->launches += 1;
   mark(h, 1);
   k_scan<<<1, 1024, 0, st>>>(h->leaf_count, nleaf, h->leaf_start);
   int gb = (int)((N + 255) / 256);
-  k_scatter<T, XT><<<gb, 256, 0, st>>>(x, N, h->L, nb, h->leaf_of, h->slot, h->leaf_start, h->qt, (V *)h->part_tmp,
-                                       h->perm_tmp);
+  k_scatter<T><<<gb, 256, 0, st>>>(N, h->leaf_of, h->slot, h->leaf_start, (const V *)h->vtmp, (V *)h->part_tmp,
+                                   h->perm_tmp);
   k_leaf_sort<T><<<(nleaf * 32 + 255) / 256, 256, 0, st>>>(nleaf, h->leaf_start, (const V *)h->part_tmp, h->perm_tmp,
-                                                          (V *)h->part, h->perm, h->inv_perm);
-  k_qd_leaf<XT><<<(nleaf * 32 + 255) / 256, 256, 0, st>>>(nleaf, nb, h->L, h->leaf_start, h->perm, x, h->qt,
-                                                          h->box_qd + h->level_off[h->d] * 4);
-  h->launches += 4;
+                                                          h->qt, h->relD, (V *)h->part, h->perm, h->inv_perm,
+                                                          h->box_qd + h->level_off[h->d] * kQD);
+  h->launches += 3;
   MAHI_CK(cudaGetLastError());
   mark(h, 2);
   const double s_leaf = h->L / nb;
@@ -1474,12 +1555,12 @@ static cudaError_t eval_t(mahi_ctx *h, const XT *x, const double *lam, double *e
     MAHI_CK(launch_gemm<T>(mp, K, ld, M + h->level_off[l + 1] * ld, M + h->level_off[l] * ld, (const T *)h->ops_m2m,
                            st));
     const int np = 1 << (3 * l);
-    k_qd_up<<<(np + 127) / 128, 128, 0, st>>>(np, h->L / (1 << (l + 1)), h->box_qd + h->level_off[l + 1] * 4,
-                                              h->box_qd + h->level_off[l] * 4);
+    k_qd_up<<<(np + 127) / 128, 128, 0, st>>>(np, h->L / (1 << (l + 1)), h->box_qd + h->level_off[l + 1] * kQD,
+                                              h->box_qd + h->level_off[l] * kQD);
     h->launches += 2;
   }
   mark(h, 4);
-  k_lattice<T><<<1, 256, sizeof(double) * K, st>>>(K, ld, h->L, h->ops_lat, h->ops_lat_h3, h->moments, M, Lx,
+  k_lattice<T><<<(ld + 3) / 4, 128, sizeof(double) * K, st>>>(K, ld, h->L, h->ops_lat, h->ops_lat_h3, mom, M, Lx,
                                                     h->L_h3);
   h->launches += 1;
   MAHI_CK(cudaGetLastError());
@@ -1517,7 +1598,7 @@ static cudaError_t eval_t(mahi_ctx *h, const XT *x, const double *lam, double *e
     size_t sm = sizeof(V) * P2P_MAXSRC;
     if (sm > 48 * 1024) MAHI_CK(cudaFuncSetAttribute(k_p2p<T, XT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     k_p2p<T, XT><<<nleaf, P2P_THREADS, sm, st>>>(nb, h->L, coulomb_constant(), h->leaf_start, (const V *)h->part,
-                                                 h->perm, h->moments, (T *)h->phi_s, (const T *)h->grad_s, forces,
+                                                 h->perm, mom, (T *)h->phi_s, (const T *)h->grad_s, forces,
                                                  h->energy_part);
     h->launches += 1;
     MAHI_CK(cudaGetLastError());
@@ -1533,7 +1614,7 @@ static cudaError_t eval_t(mahi_ctx *h, const XT *x, const double *lam, double *e
     const int G = std::max(1, std::min(kSiteChunksMax, (4 * 3 * h->num_sms + h->S - 1) / std::max(1, h->S)));
     MAHI_CK(launch_site_phi<T>(P, G, smp, st, h->S, G, h->site_ptr, h->site_atoms, h->d, P, ld, lds, nbmax, h->L,
                                h->d_level_off, h->leaf_start, h->inv_perm, (const V *)h->part, M, h->box_qd,
-                               h->moments, h->L_h3, h->phi_part, h->tc_error_site));
+                               mom, h->L_h3, h->phi_part, h->tc_error_site));
     k_site_phi_sum<<<(h->n_site_atoms + 127) / 128, 128, 0, st>>>(h->n_site_atoms, G, coulomb_constant(),
                                                                    h->phi_part, h->phi_site);
     k_site<T, XT, XT><<<(h->S + 3) / 4, 128, 0, st>>>(h->S, h->L, coulomb_constant(), kSiteDegree, h->site_ptr,
