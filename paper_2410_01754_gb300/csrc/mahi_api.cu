@@ -41,7 +41,7 @@ static cudaError_t dalloc(P **p, size_t bytes) {
 static void free_all(mahi_ctx *h) {
   void *bufs[] = {h->qA, h->dq, h->site_of, h->qt, h->leaf_of, h->slot, h->leaf_count, h->leaf_start, h->perm,
                   h->perm_tmp, h->inv_perm, h->part, h->part_tmp, h->Mexp, h->Lexp, h->phi_s, h->grad_s,
-                  h->ops_m2m, h->ops_l2l, h->ops_m2l, h->ops_lat, h->eta, h->eta_x, h->eta_y, h->eta_z,
+                  h->ops_m2m, h->ops_l2l, h->ops_m2l, h->gemm_ws, h->ops_lat, h->eta, h->eta_x, h->eta_y, h->eta_z,
                   h->m2l_list, h->m2l_off, h->site_ptr, h->site_atoms,
                   h->energy_part, h->site_energy, h->tc_ops, h->tc_partial, h->tc_msrc, h->tc_level_off, h->tc_units, h->tc_error, h->d_x_stage,
                   h->d_lam_stage, h->d_E_stage, h->d_dEdl_stage, h->d_F_stage, h->ops_lat_h3, h->L_h3,
@@ -59,6 +59,19 @@ static cudaError_t upload_ops_t(const std::vector<std::vector<double>> &ops, int
   for (size_t t = 0; t < ops.size(); ++t)
     for (int n = 0; n < K; ++n)
       for (int k = 0; k < K; ++k) tmp[t * (size_t)ld * ld + (size_t)k * ld + n] = (T)ops[t][(size_t)n * K + k];
+  cudaError_t e = dalloc(dst, tmp.size() * sizeof(T));
+  if (e != cudaSuccess) return e;
+  return cudaMemcpy(*dst, tmp.data(), tmp.size() * sizeof(T), cudaMemcpyHostToDevice);
+}
+
+// L2L operators side by side for the dense GEMM: wide[k][c * ld + n] = T'_c[n][k]
+template <typename T>
+static cudaError_t upload_ops_wide(const std::vector<std::vector<double>> &ops, int K, int ld, void **dst) {
+  const size_t W = ops.size() * (size_t)ld;
+  std::vector<T> tmp((size_t)ld * W, T(0));
+  for (size_t t = 0; t < ops.size(); ++t)
+    for (int n = 0; n < K; ++n)
+      for (int k = 0; k < K; ++k) tmp[(size_t)k * W + t * ld + n] = (T)ops[t][(size_t)n * K + k];
   cudaError_t e = dalloc(dst, tmp.size() * sizeof(T));
   if (e != cudaSuccess) return e;
   return cudaMemcpy(*dst, tmp.data(), tmp.size() * sizeof(T), cudaMemcpyHostToDevice);
@@ -158,6 +171,8 @@ int mahi_create(double box_L_nm, int64_t n_atoms, int32_t n_sites, int32_t order
   AL(h->Mexp, (size_t)h->nbox_total * h->ld * ts); AL(h->Lexp, (size_t)h->nbox_total * h->ld * ts);
   AL(h->phi_s, N * ts); AL(h->grad_s, N * 3 * ts);
   h->n_moment_blocks = (int)std::min<int64_t>(4 * 152, (N + 255) / 256);
+  h->gemm_ws_elems = gemm_workspace_elems(h->d, h->ld, h->num_sms);
+  if (h->gemm_ws_elems) AL(h->gemm_ws, h->gemm_ws_elems * ts);
   AL(h->energy_part, (size_t)h->nleaf * 8); AL(h->site_energy, (size_t)std::max(1, n_sites) * 8);
   {
     cudaError_t e = cudaMemset(h->Lexp, 0, (size_t)h->nbox_total * h->ld * ts);
@@ -189,11 +204,11 @@ int mahi_create(double box_L_nm, int64_t n_atoms, int32_t n_sites, int32_t order
     const int ldp = h->ld;
     if (f64) {
       if ((e = upload_ops_t<double>(m2m, K, ldp, &h->ops_m2m)) != cudaSuccess) return fail(e, "ops");
-      if ((e = upload_ops_t<double>(l2l, K, ldp, &h->ops_l2l)) != cudaSuccess) return fail(e, "ops");
+      if ((e = upload_ops_wide<double>(l2l, K, ldp, &h->ops_l2l)) != cudaSuccess) return fail(e, "ops");
       if ((e = upload_ops_t<double>(m2l, K, ldp, &h->ops_m2l)) != cudaSuccess) return fail(e, "ops");
     } else {
       if ((e = upload_ops_t<float>(m2m, K, ldp, &h->ops_m2m)) != cudaSuccess) return fail(e, "ops");
-      if ((e = upload_ops_t<float>(l2l, K, ldp, &h->ops_l2l)) != cudaSuccess) return fail(e, "ops");
+      if ((e = upload_ops_wide<float>(l2l, K, ldp, &h->ops_l2l)) != cudaSuccess) return fail(e, "ops");
       if (precision != MAHI_MIXED)
         if ((e = upload_ops_t<float>(m2l, K, ldp, &h->ops_m2l)) != cudaSuccess) return fail(e, "ops");
     }
@@ -214,6 +229,9 @@ int mahi_create(double box_L_nm, int64_t n_atoms, int32_t n_sites, int32_t order
     // gradient coefficients
     const int P = kSiteDegree;
     const std::vector<double> &eta = lattice_coeffs(P, 1);
+    // A_ii = lim_{r->0} A(r) - 1/r: the 26 first-shell images plus H_1(0) (the
+    // r^2 term vanishes); H_1(0) is the degree-0 coefficient
+    h->site_aii = (6.0 + 12.0 / std::sqrt(2.0) + 8.0 / std::sqrt(3.0) + eta[0]) / box_L_nm;
     std::vector<double> ex((size_t)(P + 1) * (P + 1), 0.0), ey(ex), ez(ex);
     gradient_coeffs(P, eta.data(), ex.data(), ey.data(), ez.data());
     std::vector<std::vector<double>> v1{eta}, v2{ex}, v3{ey}, v4v{ez};

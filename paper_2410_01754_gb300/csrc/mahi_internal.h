@@ -101,6 +101,8 @@ struct mahi_ctx {
   void *Mexp = nullptr, *Lexp = nullptr;      // expansions, all levels
   void *phi_s = nullptr, *grad_s = nullptr;   // sorted potential / gradient
   void *ops_m2m = nullptr, *ops_l2l = nullptr, *ops_m2l = nullptr;
+  void *gemm_ws = nullptr;                    // K-split partials of the M2M / L2L GEMMs
+  size_t gemm_ws_elems = 0;
   double *ops_lat = nullptr;                  // FP64 root operator (images 2..3 + H_3)
   double *ops_lat_h3 = nullptr;               // FP64 H_3 part alone (site-atom path)
   double *L_h3 = nullptr;                     // root local of H_3 (K doubles)
@@ -109,6 +111,8 @@ struct mahi_ctx {
   double *phi_part = nullptr;                 // its per-part partial sums
   int64_t *d_level_off = nullptr;             // device copy of level_off
   double *eta = nullptr, *eta_x = nullptr, *eta_y = nullptr, *eta_z = nullptr;  // degree 2p
+  double site_aii = 0.0;                      // self term A_ii of the periodic kernel (1/nm)
+  float site_theta = 0.40f;                   // separation ratio of the site-potential traversal
   int *m2l_list = nullptr;                    // [8][189] offset ids
   int *m2l_off = nullptr;                     // [316][3]
   int *site_ptr = nullptr, *site_atoms = nullptr;
@@ -140,6 +144,7 @@ int enqueue_eval(mahi_ctx *h, const void *x, int x_is_fp64, const double *lambda
                  void *forces, double *dEdl);
 int enqueue_potential(mahi_ctx *h, double *phi);
 int upload_tables();
+size_t gemm_workspace_elems(int d, int ld, int num_sms);
 const char *stage_name(int i);
 int num_stages();
 // tensor-core M2L (mahi_m2l_tc.cu)

@@ -368,6 +368,58 @@ __global__ void k_p2m(int nleaf, int P, int ld, T inv_s, const int *__restrict__
   for (int k = lane; k < ld; k += 32) out[k] = acc[k];
 }
 
+// P2M with the lane reduction done through shared memory: each lane writes the
+// K coefficients q conj(R_lm(u)) of its atom into a row of a 32 x Ks buffer
+// (Ks = K rounded up to odd, so row writes do not share banks), then lane j
+// sums the columns j, j + 32, ... over the rows in row order.  Same sums in the
+// same order for every run; no shuffle chains.
+template <typename T>
+__global__ void k_p2m_t(int nleaf, int P, int ld, int Ks, T inv_s, const int *__restrict__ leaf_start,
+                        const typename V4<T>::type *__restrict__ part, T *__restrict__ M) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int warp = blockIdx.x * (blockDim.x >> 5) + wib;
+  if (warp >= nleaf) return;
+  T *buf = reinterpret_cast<T *>(smem_raw) + (size_t)wib * 32 * Ks;
+  T *row = buf + (size_t)lane * Ks;
+  constexpr int kMaxCols = (kMaxOrderMixed + 1) * (kMaxOrderMixed + 1) / 32 + 1;
+  T acc[kMaxCols];
+#pragma unroll
+  for (int r = 0; r < kMaxCols; ++r) acc[r] = T(0);
+  const int K = (P + 1) * (P + 1);
+  const int b = leaf_start[warp], e = leaf_start[warp + 1];
+  for (int base = b; base < e; base += 32) {
+    const int a = base + lane;
+    const int na = min(32, e - base);
+    if (a < e) {
+      const typename V4<T>::type pt = part[a];
+      const T q = pt.w;
+      rt_columns<T>(P, pt.x * inv_s, pt.y * inv_s, pt.z * inv_s, [&](int l, int m, T re, T im) {
+        const int k = ridx(l, m);
+        row[k] = q * re;
+        if (m > 0) row[k + 1] = -q * im;  // conj
+      });
+    }
+    __syncwarp();
+#pragma unroll
+    for (int r = 0; r < kMaxCols; ++r) {
+      const int k = lane + 32 * r;
+      if (k < K) {
+        T v = acc[r];
+        for (int i = 0; i < na; ++i) v += buf[(size_t)i * Ks + k];
+        acc[r] = v;
+      }
+    }
+    __syncwarp();
+  }
+  T *out = M + (size_t)warp * ld;
+#pragma unroll
+  for (int r = 0; r < kMaxCols; ++r) {
+    const int k = lane + 32 * r;
+    if (k < ld) out[k] = (k < K) ? acc[r] : T(0);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // 3. Gather-GEMM for M2M, L2L and (SIMT) M2L.  A tile of TR output rows shares
 //    one operator per term; out[row] (+)= sum_terms op[term] * in[src(row, term)].
@@ -493,6 +545,142 @@ __global__ void __launch_bounds__(256) k_gather_gemm(GemmMap mp, int K, int ld, 
 }
 
 // ---------------------------------------------------------------------------
+// 3b. Dense GEMM for M2M and L2L (Fig. "fmm_scheme" steps 2 and 4).  Children
+//     of a parent P are the consecutive rows 8P..8P+7 of the next level, so
+//       M2M: M_l[P] = sum_c T_c M_{l+1}[8P+c]   is  C[nP x ld]  = A[nP x 8ld] B[8ld x ld]
+//       L2L: L_l[8P+c] += T'_c L_{l-1}[P]        is  C[nP x 8ld] += A[nP x ld] B'[ld x 8ld]
+//     with A and C plain row-major views of the expansion arrays and B the
+//     stacked (transposed, zero-padded) operators.  64 x 64 tiles, K steps of
+//     16, 256 threads with 4 x 4 outputs each, register-staged double buffer.
+// ---------------------------------------------------------------------------
+constexpr int GB_M = 64, GB_N = 64, GB_K = 16;
+
+// blockIdx.z = split of the K range (nsplit = gridDim.z); with more than one
+// split, split z writes its partial product to W[z] (M x N) and k_gemm_reduce
+// adds the splits in order
+template <typename T, bool ACC>
+__global__ void __launch_bounds__(256) k_gemm(int M, int N, int Kd, const T *__restrict__ A, int lda,
+                                              const T *__restrict__ B, int ldb, T *__restrict__ C, int ldc,
+                                              T *__restrict__ W) {
+  __shared__ __align__(16) T As[2][GB_K][GB_M + 4];  // A tile, k-major
+  __shared__ __align__(16) T Bs[2][GB_K][GB_N];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int m0 = blockIdx.y * GB_M, n0 = blockIdx.x * GB_N;
+  // global -> register staging: 4 consecutive elements per thread and matrix
+  const int ar = tid >> 2, ak = (tid & 3) * 4;   // A: row ar, k ak..ak+3
+  const int bk = tid >> 4, bn = (tid & 15) * 4;  // B: row bk, n bn..bn+3
+  T ra[4], rb[4];
+  auto load = [&](int k0) {
+    const int gm = m0 + ar;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) ra[e] = (gm < M) ? A[(size_t)gm * lda + k0 + ak + e] : T(0);
+    const int gn = n0 + bn;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) rb[e] = (gn + e < N) ? B[(size_t)(k0 + bk) * ldb + gn + e] : T(0);
+  };
+  auto store = [&](int stg) {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) As[stg][ak + e][ar] = ra[e];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) Bs[stg][bk][bn + e] = rb[e];
+  };
+  T acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+  const int nkt = Kd / GB_K, z = blockIdx.z, nz = gridDim.z;
+  const int kt0 = (int)((int64_t)z * nkt / nz), kt1 = (int)((int64_t)(z + 1) * nkt / nz);
+  load(kt0 * GB_K);
+  store(0);
+  __syncthreads();
+  for (int kt = kt0; kt < kt1; ++kt) {
+    const int stg = (kt - kt0) & 1;
+    if (kt + 1 < kt1) load((kt + 1) * GB_K);
+#pragma unroll
+    for (int kk = 0; kk < GB_K; ++kk) {
+      T av[4], bv[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) av[i] = As[stg][kk][ty * 4 + i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) bv[j] = Bs[stg][kk][tx * 4 + j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+    }
+    if (kt + 1 < kt1) store(stg ^ 1);
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int gm = m0 + ty * 4 + i;
+    if (gm >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int gn = n0 + tx * 4 + j;
+      if (gn >= N) continue;
+      if (nz > 1) {
+        W[((size_t)z * M + gm) * N + gn] = acc[i][j];
+      } else {
+        T *c = C + (size_t)gm * ldc + gn;
+        if (ACC) *c += acc[i][j];
+        else *c = acc[i][j];
+      }
+    }
+  }
+}
+
+template <typename T, bool ACC>
+__global__ void k_gemm_reduce(int M, int N, int nz, const T *__restrict__ W, T *__restrict__ C, int ldc) {
+  const int64_t n = (int64_t)M * N;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    T v = W[e];
+    for (int z = 1; z < nz; ++z) v += W[(size_t)z * n + e];
+    T *c = C + (e / N) * ldc + (e % N);
+    if (ACC) *c += v;
+    else *c = v;
+  }
+}
+
+// K splits that give about four blocks per SM (the coarse levels have few
+// output tiles and long K loops)
+static inline int gemm_splits(int M, int N, int Kd, int num_sms) {
+  const int tiles = ((N + GB_N - 1) / GB_N) * ((M + GB_M - 1) / GB_M);
+  const int nkt = Kd / GB_K;
+  return std::max(1, std::min(nkt, (4 * num_sms + tiles - 1) / tiles));
+}
+
+template <typename T, bool ACC>
+static cudaError_t launch_dense_gemm(int M, int N, int Kd, const T *A, int lda, const T *B, int ldb, T *C, int ldc,
+                                     T *W, size_t w_elems, int num_sms, cudaStream_t st, int &launches) {
+  if (Kd % GB_K) return cudaErrorInvalidValue;
+  int nz = gemm_splits(M, N, Kd, num_sms);
+  if ((size_t)nz * M * N > w_elems) nz = 1;
+  dim3 grid((N + GB_N - 1) / GB_N, (M + GB_M - 1) / GB_M, nz);
+  k_gemm<T, ACC><<<grid, 256, 0, st>>>(M, N, Kd, A, lda, B, ldb, C, ldc, W);
+  ++launches;
+  if (nz > 1) {
+    const int64_t n = (int64_t)M * N;
+    k_gemm_reduce<T, ACC><<<(int)std::min<int64_t>(4 * num_sms, (n + 255) / 256), 256, 0, st>>>(M, N, nz, W, C, ldc);
+    ++launches;
+  }
+  return cudaGetLastError();
+}
+
+// workspace (elements) for the K splits of every M2M and L2L GEMM of a tree
+size_t gemm_workspace_elems(int d, int ld, int num_sms) {
+  size_t w = 0;
+  for (int l = 0; l < d; ++l) {  // M2M into level l, L2L out of level l
+    const int M = 1 << (3 * l);
+    const int a = gemm_splits(M, ld, 8 * ld, num_sms), b = gemm_splits(M, 8 * ld, ld, num_sms);
+    if (a > 1) w = std::max(w, (size_t)a * M * ld);
+    if (b > 1) w = std::max(w, (size_t)b * M * 8 * ld);
+  }
+  return w;
+}
+
+// ---------------------------------------------------------------------------
 // 4. Root lattice operator (FP64): L^_root = Lambda M^_root, with the monopole
 //    and dipole of the root multipole taken from the FP64 moments.
 // ---------------------------------------------------------------------------
@@ -549,7 +737,8 @@ __global__ void k_lattice(int K, int ld, double L, const double *__restrict__ la
 // (from d/dz R_lm = R_{l-1,m}, d/dx R_lm = (R_{l-1,m+1} - R_{l-1,m-1})/2,
 //  d/dy R_lm = -i (R_{l-1,m-1} + R_{l-1,m+1})/2 and the basis scale ratios).
 template <typename T>
-__device__ __forceinline__ void gradient_row_coeffs(int P, const T *c, T *cx, T *cy, T *cz) {
+__device__ __forceinline__ void gradient_row_coeffs(int P, const T *c, T *cx, T *cy, T *cz, int lane = 0,
+                                                    int nlanes = 1) {
   auto get = [&](int l, int m, T &re, T &im) {
     if (l < 0 || m > l || -m > l) { re = T(0); im = T(0); return; }
     int am = m < 0 ? -m : m;
@@ -557,23 +746,28 @@ __device__ __forceinline__ void gradient_row_coeffs(int P, const T *c, T *cx, T 
     else { re = c[l * l + 2 * am - 1]; im = c[l * l + 2 * am]; }
     if (m < 0) { im = -im; if (am & 1) { re = -re; im = -im; } }
   };
-  for (int l = 0; l <= P - 1; ++l)
-    for (int m = 0; m <= l; ++m) {
-      T zr, zi, ar, ai, br, bi;
-      get(l + 1, m, zr, zi);
-      get(l + 1, m - 1, ar, ai);
-      get(l + 1, m + 1, br, bi);
-      T fz = sqrt(T((l + 1 + m) * (l + 1 - m)));
-      T fa = sqrt(T((l - m + 2) * (l - m + 1))), fb = sqrt(T((l + m + 2) * (l + m + 1)));
-      zr *= fz; zi *= fz; ar *= fa; ai *= fa; br *= fb; bi *= fb;
-      T xr = T(0.5) * (ar - br), xi = T(0.5) * (ai - bi);
-      T yr = T(-0.5) * (bi + ai), yi = T(0.5) * (br + ar);
-      if (m == 0) { cz[l * l] = zr; cx[l * l] = xr; cy[l * l] = yr; }
-      else {
-        int k = l * l + 2 * m - 1;
-        cz[k] = zr; cz[k + 1] = zi; cx[k] = xr; cx[k + 1] = xi; cy[k] = yr; cy[k + 1] = yi;
-      }
+  // entries (l, m), 0 <= m <= l < P, in triangular order t = l(l+1)/2 + m,
+  // dealt round-robin to the calling lanes
+  const int nt = P * (P + 1) / 2;
+  int l = 0, t0 = 0;  // l of entry t and the first entry of row l
+  for (int t = lane; t < nt; t += nlanes) {
+    while (t >= t0 + l + 1) { t0 += l + 1; ++l; }
+    const int m = t - t0;
+    T zr, zi, ar, ai, br, bi;
+    get(l + 1, m, zr, zi);
+    get(l + 1, m - 1, ar, ai);
+    get(l + 1, m + 1, br, bi);
+    T fz = sqrt(T((l + 1 + m) * (l + 1 - m)));
+    T fa = sqrt(T((l - m + 2) * (l - m + 1))), fb = sqrt(T((l + m + 2) * (l + m + 1)));
+    zr *= fz; zi *= fz; ar *= fa; ai *= fa; br *= fb; bi *= fb;
+    T xr = T(0.5) * (ar - br), xi = T(0.5) * (ai - bi);
+    T yr = T(-0.5) * (bi + ai), yi = T(0.5) * (br + ar);
+    if (m == 0) { cz[l * l] = zr; cx[l * l] = xr; cy[l * l] = yr; }
+    else {
+      int k = l * l + 2 * m - 1;
+      cz[k] = zr; cz[k + 1] = zi; cx[k] = xr; cx[k + 1] = xi; cy[k] = yr; cy[k + 1] = yi;
     }
+  }
 }
 
 template <typename T>
@@ -590,7 +784,7 @@ __global__ void k_l2p(int nleaf, int P, int ld, T s, const int *__restrict__ lea
   const T *Lv = Lleaf + (size_t)warp * ld;
   for (int k = lane; k < K; k += 32) c[k] = Lv[k];
   __syncwarp();
-  if (lane == 0) gradient_row_coeffs<T>(P, c, cx, cy, cz);
+  gradient_row_coeffs<T>(P, c, cx, cy, cz, lane, 32);
   __syncwarp();
   int b = leaf_start[warp], e = leaf_start[warp + 1];
   T inv_s = T(1) / s;
@@ -637,11 +831,22 @@ template <> struct SiteAccE<float> {
     l += (h - (s - bv)) + (v - bv);
     h = s;
   }
+  // sum over the warp (butterfly, same order on every run), still compensated
+  __device__ __forceinline__ void warp_reduce() {
+    for (int o = 16; o > 0; o >>= 1) {
+      const float oh = __shfl_xor_sync(0xffffffff, h, o), ol = __shfl_xor_sync(0xffffffff, l, o);
+      l += ol;
+      add(oh);
+    }
+  }
   __device__ __forceinline__ double value() const { return (double)h + (double)l; }
 };
 template <> struct SiteAccE<double> {
   double h = 0.0;
   __device__ __forceinline__ void add(double v) { h += v; }
+  __device__ __forceinline__ void warp_reduce() {
+    for (int o = 16; o > 0; o >>= 1) h += __shfl_xor_sync(0xffffffff, h, o);
+  }
   __device__ __forceinline__ double value() const { return h; }
 };
 
@@ -652,6 +857,10 @@ __device__ __forceinline__ float rinv(float r2) {
   float y = rsqrtf(r2);
   return y * fmaf(-0.5f * r2, y * y, 1.5f);
 }
+// near-field pair kernel: the hardware estimate alone (relative error below
+// 2^-22, under the single-precision rounding of the accumulated sums)
+__device__ __forceinline__ float rinv_fast(float r2) { return rsqrtf(r2); }
+__device__ __forceinline__ double rinv_fast(double r2) { return 1.0 / sqrt(r2); }
 constexpr int P2P_MAXSRC = 2048;
 // FP64 1/sqrt(r2): single-precision seed and one FP64 Newton-Raphson step; the
 // seed's relative error e (about 2^-23) becomes 1.5 e^2 after the step
@@ -670,7 +879,7 @@ __global__ void __launch_bounds__(P2P_THREADS) k_p2p(int nb, double L, double fc
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V *src = reinterpret_cast<V *>(smem_raw);
   __shared__ int nb_start[27], nb_pre[28];
-  __shared__ T red[P2P_THREADS][4];
+  __shared__ T red[P2P_THREADS][4], red2[P2P_THREADS][4];
   __shared__ T kc[5];
   __shared__ double ered[P2P_THREADS / 32];
   const int leaf = blockIdx.x;
@@ -709,14 +918,18 @@ __global__ void __launch_bounds__(P2P_THREADS) k_p2p(int nb, double L, double fc
   const int nsrc_total = nb_pre[27];
   const T fc = (T)fcoul;
   SiteAccE<T> e_acc;
-  // process targets in groups so that (target, chunk) pairs fill the block
-  int nchunk = P2P_THREADS / max(1, min(nt, P2P_THREADS));
-  int tgroup = P2P_THREADS / nchunk;
-  for (int t0 = 0; t0 < nt; t0 += tgroup) {
-    int ta = t0 + tid % tgroup, ck = tid / tgroup;
-    bool tv = ta < nt;
-    V me = tv ? part[tb + ta] : V{0, 0, 0, 0};
-    T f = 0, gx = 0, gy = 0, gz = 0;
+  // threads = (target pair, source chunk): every thread holds two targets, so
+  // each staged source serves two pairs; as many chunks as fill the block
+  const int npr = (nt + 1) >> 1;
+  const int nchunk = P2P_THREADS / max(1, min(npr, P2P_THREADS));
+  const int tgroup = P2P_THREADS / nchunk;
+  for (int t0 = 0; t0 < npr; t0 += tgroup) {
+    const int tp = t0 + tid % tgroup, ck = tid / tgroup;
+    const int ta0 = 2 * t0 + (tid % tgroup), ta1 = ta0 + min(tgroup, npr - t0);  // this round's targets
+    const bool tv0 = tp < npr && ta0 < nt, tv1 = tp < npr && ta1 < nt;
+    const V me0 = tv0 ? part[tb + ta0] : V{0, 0, 0, 0};
+    const V me1 = tv1 ? part[tb + ta1] : V{0, 0, 0, 0};
+    T f0 = 0, gx0 = 0, gy0 = 0, gz0 = 0, f1 = 0, gx1 = 0, gy1 = 0, gz1 = 0;
     for (int s0 = 0; s0 < nsrc_total; s0 += P2P_MAXSRC) {
       int ns = min(P2P_MAXSRC, nsrc_total - s0);
       __syncthreads();
@@ -736,31 +949,46 @@ __global__ void __launch_bounds__(P2P_THREADS) k_p2p(int nb, double L, double fc
       }
       __syncthreads();
       // self: neighbour k = 13 is the leaf itself, at source index nb_pre[13] + ta
-      int self = (nb_pre[13] + ta) - s0;
-      int per = (ns + nchunk - 1) / nchunk;
-      int jb = ck * per, je = min(ns, jb + per);
-      if (tv) {
+      const int self0 = (nb_pre[13] + ta0) - s0, self1 = (nb_pre[13] + ta1) - s0;
+      const int per = (ns + nchunk - 1) / nchunk;
+      const int jb = ck * per, je = min(ns, jb + per);
+      if (tv0) {
 #pragma unroll 4
         for (int j = jb; j < je; ++j) {
-          V v = src[j];
-          T rx = me.x - v.x, ry = me.y - v.y, rz = me.z - v.z;
-          T r2 = rx * rx + ry * ry + rz * rz;
-          T ri = rinv(r2);
-          ri = (j == self) ? T(0) : ri;
-          T qr = v.w * ri;
-          f += qr;
-          T g3 = qr * ri * ri;
-          gx -= g3 * rx; gy -= g3 * ry; gz -= g3 * rz;
+          const V v = src[j];
+          const T rx0 = me0.x - v.x, ry0 = me0.y - v.y, rz0 = me0.z - v.z;
+          const T rx1 = me1.x - v.x, ry1 = me1.y - v.y, rz1 = me1.z - v.z;
+          const T r20 = rx0 * rx0 + ry0 * ry0 + rz0 * rz0, r21 = rx1 * rx1 + ry1 * ry1 + rz1 * rz1;
+          const T ri0 = (j == self0) ? T(0) : rinv_fast(r20);
+          const T ri1 = (j == self1 || !tv1) ? T(0) : rinv_fast(r21);
+          const T qr0 = v.w * ri0, qr1 = v.w * ri1;
+          f0 += qr0;
+          f1 += qr1;
+          const T g30 = qr0 * ri0 * ri0, g31 = qr1 * ri1 * ri1;
+          gx0 -= g30 * rx0; gy0 -= g30 * ry0; gz0 -= g30 * rz0;
+          gx1 -= g31 * rx1; gy1 -= g31 * ry1; gz1 -= g31 * rz1;
         }
       }
     }
-    red[tid][0] = f; red[tid][1] = gx; red[tid][2] = gy; red[tid][3] = gz;
+    // chunk partial sums of both targets, then one thread per target finishes
+    red[tid][0] = f0; red[tid][1] = gx0; red[tid][2] = gy0; red[tid][3] = gz0;
+    red2[tid][0] = f1; red2[tid][1] = gx1; red2[tid][2] = gy1; red2[tid][3] = gz1;
     __syncthreads();
-    if (ck == 0 && tv) {
-      for (int c2i = 1; c2i < nchunk; ++c2i) {
-        int o = tid + c2i * tgroup;
-        f += red[o][0]; gx += red[o][1]; gy += red[o][2]; gz += red[o][3];
+    const int nr = min(2 * tgroup, nt - 2 * t0);  // targets of this round
+    for (int tt = tid; tt < nr; tt += P2P_THREADS) {
+      // target ta = 2 t0 + tt: first of the pair tt (tt < w) or second of the
+      // pair tt - w, w = pairs in this round
+      const int w = min(tgroup, npr - t0);
+      const bool second = tt >= w;
+      const int p = second ? tt - w : tt;
+      const int ta = 2 * t0 + tt;
+      T f = 0, gx = 0, gy = 0, gz = 0;
+      for (int c2i = 0; c2i < nchunk; ++c2i) {
+        const int o = p + c2i * tgroup;
+        const T *r = second ? red2[o] : red[o];
+        f += r[0]; gx += r[1]; gy += r[2]; gz += r[3];
       }
+      const V me = part[tb + ta];
       const int a = tb + ta;
       // near + far field, then the dipole / background term (in the working
       // precision from the FP64 per-leaf constants)
@@ -784,9 +1012,8 @@ __global__ void __launch_bounds__(P2P_THREADS) k_p2p(int nb, double L, double fc
     }
     __syncthreads();
   }
-  double ev = e_acc.value();
-  for (int o = 16; o > 0; o >>= 1) ev += __shfl_xor_sync(0xffffffff, ev, o);
-  if (lane == 0) ered[warp] = ev;
+  e_acc.warp_reduce();
+  if (lane == 0) ered[warp] = e_acc.value();
   __syncthreads();
   if (tid == 0) {
     double v = 0;
@@ -796,87 +1023,136 @@ __global__ void __launch_bounds__(P2P_THREADS) k_p2p(int nb, double L, double fc
 }
 
 // ---------------------------------------------------------------------------
-// 7. Per-site HI correction (FP64).  One warp per site.  For every ordered pair
-//    (i, j) of the site: A(r) = sum_{|n|_inf<=1} 1/|r+nL| (without r+nL = 0)
-//    + H(r) + (2 pi/3V)|r|^2, r = minimum image of x_i - x_j, H from the
-//    lattice coefficients (degree adapted to |r|).  This is the paper's
-//    C_P2P + C_L + C_D for a two-form site (first shell direct, lattice part,
-//    dipole/background part).  Then
+// 7. Per-site HI correction (FP64).  One warp per site.  For every pair (i, j)
+//    of the site: A(r) = sum_{|n|_inf<=1} 1/|r+nL| + H(r) + (2 pi/3V)|r|^2,
+//    r = minimum image of x_i - x_j, H from the lattice coefficients (degree
+//    adapted to |r|); the self term A_ii (the same limit without 1/|r|) is a
+//    constant of the box.  This is the paper's C_P2P + C_L + C_D for a two-form
+//    site (first shell direct, lattice part, dipole/background part).  Then
 //      k_s = f sum D_i D_j A_ij,  g_s = sum D_i phi~_i,
 //      dE/dlam = g + (1/2 - lam) k,  E += 1/2 lam(1-lam) k,
 //      F_i -= lam(1-lam) f sum_{j != i} D_i D_j grad A(r_ij).
+//    Sites of up to kSiteSymMax atoms evaluate each unordered pair once and
+//    gather the forces per atom in a fixed order; larger sites evaluate the
+//    ordered pairs of one atom per lane.
 // ---------------------------------------------------------------------------
 constexpr int kMaxSiteAtoms = 64;
+constexpr int kSiteSymMax = 16;
+constexpr int kSiteSymPairs = kSiteSymMax * (kSiteSymMax - 1) / 2;
+
+// A(r) and grad A(r) for r != 0 (nm), FP64
+__device__ __forceinline__ void site_pair_kernel(const double r[3], double L, double c2, int Pmax,
+                                                 const double *__restrict__ eta, const double *__restrict__ eta_x,
+                                                 const double *__restrict__ eta_y, const double *__restrict__ eta_z,
+                                                 double &A, double g[3]) {
+  double a = 0.0, g0 = 0.0, g1 = 0.0, g2 = 0.0;
+  for (int nx = -1; nx <= 1; ++nx)
+    for (int ny = -1; ny <= 1; ++ny)
+      for (int nz = -1; nz <= 1; ++nz) {
+        const double d0 = r[0] + nx * L, d1 = r[1] + ny * L, d2 = r[2] + nz * L;
+        const double ri = rsqrt_dp(d0 * d0 + d1 * d1 + d2 * d2);
+        a += ri;
+        const double g3 = ri * ri * ri;
+        g0 -= g3 * d0; g1 -= g3 * d1; g2 -= g3 * d2;
+      }
+  const double iL = 1.0 / L;
+  const double u[3] = {r[0] * iL, r[1] * iL, r[2] * iL};
+  const float un = (float)sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+  // (|u| / 1.9)^P < 1e-17: the series of H converges for |u| < 1.9
+  const int P = min(Pmax, max(4, (int)ceilf(-39.2f / logf(un / 1.9f)) + 1));
+  double H = 0, hx = 0, hy = 0, hz = 0;
+  // H lives on even degrees; its gradient coefficients on odd degrees (< P)
+  r_columns(P, u[0], u[1], u[2], [&](int l, int m, double re, double im) {
+    const int k = ridx(l, m);
+    const double w = (m == 0) ? 1.0 : 2.0;
+    if (!(l & 1)) {
+      H += (m == 0) ? eta[k] * re : w * (eta[k] * re + eta[k + 1] * im);
+    } else if (l < P) {
+      hx += (m == 0) ? eta_x[k] * re : w * (eta_x[k] * re + eta_x[k + 1] * im);
+      hy += (m == 0) ? eta_y[k] * re : w * (eta_y[k] * re + eta_y[k + 1] * im);
+      hz += (m == 0) ? eta_z[k] * re : w * (eta_z[k] * re + eta_z[k + 1] * im);
+    }
+  });
+  A = a + H * iL + c2 * (r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+  g[0] = g0 + hx * iL * iL + 2.0 * c2 * r[0];
+  g[1] = g1 + hy * iL * iL + 2.0 * c2 * r[1];
+  g[2] = g2 + hz * iL * iL + 2.0 * c2 * r[2];
+}
+
+template <typename XT>
+__device__ __forceinline__ void site_pair_r(const XT *__restrict__ x, int i, int j, double L, double r[3]) {
+  for (int a = 0; a < 3; ++a) {
+    double v = (double)x[3 * (size_t)i + a] - (double)x[3 * (size_t)j + a];
+    v -= L * rint(v / L);
+    r[a] = v;
+  }
+}
 
 template <typename T, typename XT, typename FT>
-__global__ void k_site(int S, double L, double fcoul, int Pmax, const int *__restrict__ site_ptr,
+__global__ void k_site(int S, double L, double fcoul, int Pmax, double aii, const int *__restrict__ site_ptr,
                        const int *__restrict__ site_atoms, const XT *__restrict__ x, const double *__restrict__ dq,
                        const double *__restrict__ lam, const double *__restrict__ phi_site,
                        const double *__restrict__ eta, const double *__restrict__ eta_x,
                        const double *__restrict__ eta_y, const double *__restrict__ eta_z,
                        double *__restrict__ dEdl, double *__restrict__ site_energy, FT *__restrict__ forces) {
   __shared__ double fsh[4][kMaxSiteAtoms][3];
+  __shared__ double gbuf[4][kSiteSymPairs][3];
   const int wib = threadIdx.x >> 5;
   int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (warp >= S) return;
   const int b = site_ptr[warp], e = site_ptr[warp + 1], n = e - b;
   const double V = L * L * L, c2 = 2.0 * kPi / (3.0 * V);
   const double lw = lam[warp] * (1.0 - lam[warp]);
-  for (int k = lane; k < n * 3; k += 32) fsh[wib][k / 3][k % 3] = 0.0;
-  __syncwarp();
   double ksum = 0.0, gsum = 0.0;
-  for (int pi = lane; pi < n * n; pi += 32) {
-    const int ia = pi / n, ja = pi % n;
-    const int i = site_atoms[b + ia], j = site_atoms[b + ja];
-    const double Di = dq[i], Dj = dq[j];
-    double r[3];
-    for (int a = 0; a < 3; ++a) {
-      double v = (double)x[3 * (size_t)i + a] - (double)x[3 * (size_t)j + a];
-      v -= L * rint(v / L);
-      r[a] = (ia == ja) ? 0.0 : v;
+  // self terms and the charge-interpolation derivative
+  for (int ia = lane; ia < n; ia += 32) {
+    const double Di = dq[site_atoms[b + ia]];
+    ksum += Di * Di * aii;
+    gsum += Di * phi_site[b + ia];
+  }
+  if (n <= kSiteSymMax) {
+    const int np = n * (n - 1) / 2;
+    for (int p = lane; p < np; p += 32) {
+      int ia = 0, rem = p;
+      while (rem >= n - 1 - ia) { rem -= n - 1 - ia; ++ia; }
+      const int ja = ia + 1 + rem;
+      const int i = site_atoms[b + ia], j = site_atoms[b + ja];
+      double r[3], A, g[3];
+      site_pair_r(x, i, j, L, r);
+      site_pair_kernel(r, L, c2, Pmax, eta, eta_x, eta_y, eta_z, A, g);
+      ksum += 2.0 * dq[i] * dq[j] * A;
+      gbuf[wib][p][0] = g[0]; gbuf[wib][p][1] = g[1]; gbuf[wib][p][2] = g[2];
     }
-    double A = 0.0, g0 = 0.0, g1 = 0.0, g2 = 0.0;
-    for (int nx = -1; nx <= 1; ++nx)
-      for (int ny = -1; ny <= 1; ++ny)
-        for (int nz = -1; nz <= 1; ++nz) {
-          if (ia == ja && nx == 0 && ny == 0 && nz == 0) continue;
-          double d0 = r[0] + nx * L, d1 = r[1] + ny * L, d2 = r[2] + nz * L;
-          double ri = 1.0 / sqrt(d0 * d0 + d1 * d1 + d2 * d2);
-          A += ri;
-          double g3 = ri * ri * ri;
-          g0 -= g3 * d0; g1 -= g3 * d1; g2 -= g3 * d2;
-        }
-    double u[3] = {r[0] / L, r[1] / L, r[2] / L};
-    double un = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
-    int P = 0;
-    if (un > 0.0) {
-      int need = (int)ceil(-39.2 / log(un / 1.9)) + 1;  // (|u|/1.9)^P < 1e-17
-      P = min(Pmax, max(4, need));
-    }
-    double H = 0, hx = 0, hy = 0, hz = 0;
-    // H lives on even degrees; its gradient coefficients on odd degrees (< P)
-    r_columns(P, u[0], u[1], u[2], [&](int l, int m, double re, double im) {
-      const int k = ridx(l, m);
-      const double w = (m == 0) ? 1.0 : 2.0;
-      if (!(l & 1)) {
-        H += (m == 0) ? eta[k] * re : w * (eta[k] * re + eta[k + 1] * im);
-      } else if (l < P) {
-        hx += (m == 0) ? eta_x[k] * re : w * (eta_x[k] * re + eta_x[k + 1] * im);
-        hy += (m == 0) ? eta_y[k] * re : w * (eta_y[k] * re + eta_y[k + 1] * im);
-        hz += (m == 0) ? eta_z[k] * re : w * (eta_z[k] * re + eta_z[k + 1] * im);
+    __syncwarp();
+    for (int ia = lane; ia < n; ia += 32) {
+      const double Di = dq[site_atoms[b + ia]];
+      double f0 = 0.0, f1 = 0.0, f2 = 0.0;
+      for (int ja = 0; ja < n; ++ja) {
+        if (ja == ia) continue;
+        const int lo = min(ia, ja), hi = max(ia, ja);
+        const int p = lo * (2 * n - lo - 1) / 2 + (hi - lo - 1);
+        // gbuf holds grad A at r = x_lo - x_hi; at x_hi - x_lo it changes sign
+        const double w = (ia == lo ? 1.0 : -1.0) * lw * fcoul * Di * dq[site_atoms[b + ja]];
+        f0 -= w * gbuf[wib][p][0]; f1 -= w * gbuf[wib][p][1]; f2 -= w * gbuf[wib][p][2];
       }
-    });
-    A += H / L + c2 * (r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
-    g0 += hx / (L * L) + 2.0 * c2 * r[0];
-    g1 += hy / (L * L) + 2.0 * c2 * r[1];
-    g2 += hz / (L * L) + 2.0 * c2 * r[2];
-    ksum += Di * Dj * A;
-    if (ia == ja) gsum += Di * phi_site[b + ia];
-    else {
-      double w = lw * fcoul * Di * Dj;
-      atomicAdd(&fsh[wib][ia][0], -w * g0);
-      atomicAdd(&fsh[wib][ia][1], -w * g1);
-      atomicAdd(&fsh[wib][ia][2], -w * g2);
+      fsh[wib][ia][0] = f0; fsh[wib][ia][1] = f1; fsh[wib][ia][2] = f2;
+    }
+  } else {
+    for (int ia = lane; ia < n; ia += 32) {
+      const int i = site_atoms[b + ia];
+      const double Di = dq[i];
+      double f0 = 0.0, f1 = 0.0, f2 = 0.0;
+      for (int ja = 0; ja < n; ++ja) {
+        if (ja == ia) continue;
+        const int j = site_atoms[b + ja];
+        double r[3], A, g[3];
+        site_pair_r(x, i, j, L, r);
+        site_pair_kernel(r, L, c2, Pmax, eta, eta_x, eta_y, eta_z, A, g);
+        ksum += Di * dq[j] * A;
+        const double w = lw * fcoul * Di * dq[j];
+        f0 -= w * g[0]; f1 -= w * g[1]; f2 -= w * g[2];
+      }
+      fsh[wib][ia][0] = f0; fsh[wib][ia][1] = f1; fsh[wib][ia][2] = f2;
     }
   }
   for (int o = 16; o > 0; o >>= 1) {
@@ -952,7 +1228,7 @@ __device__ __forceinline__ T m2p_high(int P, const T *__restrict__ M, T ux, T uy
 // |n|_inf <= 3 (beyond them the H_3 lattice expansion takes over).  With R the
 // radius of the site's atoms about their centroid c, a box of edge s at
 // distance D from c is used through its multipole (M2P at every atom) only if
-// its circumradius (sqrt(3)/2) s < theta (D - R), so every multipole term
+// its circumradius (sqrt(3)/2) s < theta (D - R) (theta = 0.4 by default), so every multipole term
 // converges at least like theta^(p+1) at every atom; otherwise it is opened,
 // and unseparated leaves are summed directly.
 //
@@ -971,7 +1247,6 @@ __device__ __forceinline__ T m2p_high(int P, const T *__restrict__ M, T ux, T uy
 // The batches of separated boxes and leaves are dealt round-robin to G blocks
 // per site; each block repeats the (cheap) classification and writes its own
 // partial sum, so results are bitwise reproducible.
-constexpr float kSiteTheta = 0.35f;
 constexpr int kFrontier = 1536;            // frontier / list entries per buffer
 constexpr int kSiteThreads = 128;
 constexpr int kSiteBatchMax = 64;
@@ -1151,7 +1426,7 @@ __global__ void __launch_bounds__(kSiteThreads, 3) k_site_phi(
     int lds, int nbmax, double L, const int64_t *__restrict__ level_off, const int *__restrict__ leaf_start,
     const int *__restrict__ inv_perm, const typename V4<T>::type *__restrict__ part, const T *__restrict__ M,
     const double *__restrict__ qd, const double *__restrict__ mom, const double *__restrict__ Lh3,
-    double *__restrict__ phi_part, int *__restrict__ err) {
+    double *__restrict__ phi_part, int *__restrict__ err, float theta) {
   using V = typename V4<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   int *fa = reinterpret_cast<int *>(smem_raw);          // frontier (current)
@@ -1230,7 +1505,7 @@ __global__ void __launch_bounds__(kSiteThreads, 3) k_site_phi(
   const T Rf = (T)cen[3];
   for (int l = 0; l <= d && n0 > 0; ++l) {
     const double s = L / (double)(1 << l);
-    const T a_l = (T)(0.86602540378443865 * s), th = (T)kSiteTheta, is = (T)(1.0 / s);
+    const T a_l = (T)(0.86602540378443865 * s), th = (T)theta, is = (T)(1.0 / s);
     int nsep = 0, n1 = 0;
     for (int t0 = 0; t0 < n0; t0 += blockDim.x) {
       const int t = t0 + tid;
@@ -1545,19 +1820,28 @@ static cudaError_t eval_t(mahi_ctx *h, const XT *x, const double *lam, double *e
   MAHI_CK(cudaGetLastError());
   mark(h, 2);
   const double s_leaf = h->L / nb;
-  k_p2m<T><<<(nleaf * 32 + 127) / 128, 128, 4 * sizeof(T) * ld, st>>>(
-      nleaf, P, ld, (T)(1.0 / s_leaf), h->leaf_start, (const V *)h->part, M + h->level_off[h->d] * ld);
+  {
+    const int Ks = K | 1;
+    const size_t per_warp = 32 * (size_t)Ks * sizeof(T);
+    if (sizeof(T) == 4 && P <= kMaxOrderMixed && 2 * per_warp <= 48 * 1024) {
+      k_p2m_t<T><<<(nleaf + 1) / 2, 64, 2 * per_warp, st>>>(nleaf, P, ld, Ks, (T)(1.0 / s_leaf), h->leaf_start,
+                                                          (const V *)h->part, M + h->level_off[h->d] * ld);
+    } else {
+      k_p2m<T><<<(nleaf * 32 + 127) / 128, 128, 4 * sizeof(T) * ld, st>>>(
+          nleaf, P, ld, (T)(1.0 / s_leaf), h->leaf_start, (const V *)h->part, M + h->level_off[h->d] * ld);
+    }
+  }
   h->launches += 1;
   MAHI_CK(cudaGetLastError());
   mark(h, 3);
   for (int l = h->d - 1; l >= 0; --l) {
-    GemmMap mp{0, l, 1 << (3 * l), nullptr, nullptr};
-    MAHI_CK(launch_gemm<T>(mp, K, ld, M + h->level_off[l + 1] * ld, M + h->level_off[l] * ld, (const T *)h->ops_m2m,
-                           st));
+    MAHI_CK((launch_dense_gemm<T, false>(1 << (3 * l), ld, 8 * ld, M + h->level_off[l + 1] * ld, 8 * ld,
+                                          (const T *)h->ops_m2m, ld, M + h->level_off[l] * ld, ld, (T *)h->gemm_ws,
+                                          h->gemm_ws_elems, h->num_sms, st, h->launches)));
     const int np = 1 << (3 * l);
     k_qd_up<<<(np + 127) / 128, 128, 0, st>>>(np, h->L / (1 << (l + 1)), h->box_qd + h->level_off[l + 1] * kQD,
                                               h->box_qd + h->level_off[l] * kQD);
-    h->launches += 2;
+    h->launches += 1;
   }
   mark(h, 4);
   k_lattice<T><<<(ld + 3) / 4, 128, sizeof(double) * K, st>>>(K, ld, h->L, h->ops_lat, h->ops_lat_h3, mom, M, Lx,
@@ -1578,10 +1862,9 @@ static cudaError_t eval_t(mahi_ctx *h, const XT *x, const double *lam, double *e
   }
   mark(h, 6);
   for (int l = 1; l <= h->d; ++l) {
-    GemmMap mp{1, l, 1 << (3 * l), nullptr, nullptr};
-    MAHI_CK(launch_gemm<T>(mp, K, ld, Lx + h->level_off[l - 1] * ld, Lx + h->level_off[l] * ld, (const T *)h->ops_l2l,
-                           st));
-    h->launches += 1;
+    MAHI_CK((launch_dense_gemm<T, true>(1 << (3 * (l - 1)), 8 * ld, ld, Lx + h->level_off[l - 1] * ld, ld,
+                                         (const T *)h->ops_l2l, 8 * ld, Lx + h->level_off[l] * ld, 8 * ld,
+                                         (T *)h->gemm_ws, h->gemm_ws_elems, h->num_sms, st, h->launches)));
   }
   mark(h, 7);
   {
@@ -1614,10 +1897,11 @@ static cudaError_t eval_t(mahi_ctx *h, const XT *x, const double *lam, double *e
     const int G = std::max(1, std::min(kSiteChunksMax, (4 * 3 * h->num_sms + h->S - 1) / std::max(1, h->S)));
     MAHI_CK(launch_site_phi<T>(P, G, smp, st, h->S, G, h->site_ptr, h->site_atoms, h->d, P, ld, lds, nbmax, h->L,
                                h->d_level_off, h->leaf_start, h->inv_perm, (const V *)h->part, M, h->box_qd,
-                               mom, h->L_h3, h->phi_part, h->tc_error_site));
+                               mom, h->L_h3, h->phi_part, h->tc_error_site, h->site_theta));
     k_site_phi_sum<<<(h->n_site_atoms + 127) / 128, 128, 0, st>>>(h->n_site_atoms, G, coulomb_constant(),
                                                                    h->phi_part, h->phi_site);
-    k_site<T, XT, XT><<<(h->S + 3) / 4, 128, 0, st>>>(h->S, h->L, coulomb_constant(), kSiteDegree, h->site_ptr,
+    k_site<T, XT, XT><<<(h->S + 3) / 4, 128, 0, st>>>(h->S, h->L, coulomb_constant(), kSiteDegree, h->site_aii,
+                                                      h->site_ptr,
                                                       h->site_atoms, x, h->dq, lam, h->phi_site, h->eta, h->eta_x,
                                                       h->eta_y, h->eta_z, dEdl, h->site_energy, forces);
     h->launches += 3;
