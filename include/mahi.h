@@ -101,6 +101,26 @@ int mahi_eval(mahi_t h, const void *x, int32_t x_is_fp64, const double *lambda, 
 int mahi_eval_host(mahi_t h, const void *x_host, int32_t x_is_fp64, const double *lambda_host,
                    double *energy_host, void *forces_host, double *dEdlambda_host);
 
+/* Backward pass of the HI energy of the LAST mahi_eval on this handle (for
+ * reverse-mode differentiation, e.g. a torch.autograd.Function).  With
+ * g = dLoss/dE (device, 1 float64) it writes, each output optional (NULL):
+ *   dx       device, n_atoms x 3 (x dtype):  -g F   (F = the forces output of
+ *            that evaluation, passed back in `forces`; dE/dx = -F)
+ *   dlambda  device, n_sites float64:        g dE/dlambda (passed back in
+ *            `dEdlambda`)
+ *   dEdqA, dEdqB  device, n_atoms float64:   g dE/dqA_i, g dE/dqB_i with
+ *       dE/dqA_i = (1 - l) phi~_i - l (1 - l) psi_i,  dE/dqB_i = l phi~_i + l (1 - l) psi_i
+ *   for an atom of a site with lambda l (`lambda`: the same device array as in
+ *   that evaluation), psi_i = f sum_{j in s} D_j A(x_i - x_j) (self term
+ *   included), and dE/dqA_i = phi~_i, dE/dqB_i = 0 for environment atoms
+ *   (they carry qA only).  These follow from E = E(q~) + sum_s 1/2 l_s (1 - l_s) k_s
+ *   (Eqs. "DeltaFQIHI", "Udiff") with q~ = (1 - l) qA + l qB.
+ * One kernel, enqueued on the handle's stream.  The potentials it uses are
+ * overwritten by the next mahi_eval.  MAHI_ERR_INVALID_ARG if an output is
+ * requested without its input; MAHI_ERR_STATE before mahi_set_charges. */
+int mahi_backward(mahi_t h, const double *grad_energy, const void *forces, const double *dEdlambda,
+                  const double *lambda, int32_t x_is_fp64, void *dx, double *dlambda, double *dEdqA, double *dEdqB);
+
 /* Charge-scaled potential phi~ (kJ/mol/e, float64, original atom order) of the
  * last evaluation into a device buffer of n_atoms doubles (enqueued). */
 int mahi_get_potential(mahi_t h, double *phi_device);

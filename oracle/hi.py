@@ -115,6 +115,37 @@ def hi_eval(sys, rc=None, targets=None, f=F_COULOMB, energy_only_full=False):
     return out
 
 
+def hi_charge_gradients(sys, rc=None, f=F_COULOMB, ref=None):
+    """Derivatives of the HI energy with respect to the two charge sets.
+
+    With q~_i = (1 - lambda_s) qA_i + lambda_s qB_i and D = qB - qA, the energy
+    E = E(q~) + sum_s 1/2 lambda_s (1 - lambda_s) k_s, k_s = f D_s^T A D_s, has
+        dE/dqA_i = (1 - lambda_s) phi~_i - lambda_s (1 - lambda_s) psi_i
+        dE/dqB_i = lambda_s phi~_i + lambda_s (1 - lambda_s) psi_i
+    for an atom of site s, where phi~_i = dE(q~)/dq~_i is the charge-scaled
+    potential and psi_i = f sum_{j in s} A_ij D_j = 1/2 dk_s/dD_i the potential
+    of the site's charge change (self term included).  Environment atoms have
+    q~ = qA: dE/dqA_i = phi~_i, dE/dqB_i = 0.  ``ref`` may pass a hi_eval result
+    (full targets) to reuse its potentials."""
+    x, qA, qB = sys["x"], np.asarray(sys["qA"]), np.asarray(sys["qB"])
+    site_of, lam, L = np.asarray(sys["site_of"]), np.asarray(sys["lam"]), sys["L"]
+    if ref is None:
+        ref = hi_eval(sys, rc=rc, f=f)
+    phi = ref["phi"]
+    dqA = phi.copy()
+    dqB = np.zeros_like(phi)
+    psi = np.zeros_like(phi)
+    dq = qB - qA
+    for s, at in enumerate(site_lists(site_of, lam.shape[0])):
+        if len(at) == 0:
+            continue
+        psi[at] = f * ewald(x[at], dq[at], L, rc=0.5 * L)[0]
+        l = lam[s]
+        dqA[at] = (1.0 - l) * phi[at] - l * (1.0 - l) * psi[at]
+        dqB[at] = l * phi[at] + l * (1.0 - l) * psi[at]
+    return dict(dqA=dqA, dqB=dqB, psi=psi)
+
+
 def energy(x, q, L, rc=None, f=F_COULOMB):
     """Periodic Coulomb energy of one charge vector."""
     return ewald(x, q, L, rc)[2] * f

@@ -32,6 +32,9 @@ _SIGS = {
     "mahi_eval_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "mahi_get_potential": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "mahi_backward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                     ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                     ctypes.c_void_p, ctypes.c_void_p]),
     "mahi_set_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "mahi_stage_times": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float), ctypes.c_int32]),
     "mahi_stage_name": (ctypes.c_char_p, [ctypes.c_int32]),
@@ -132,6 +135,14 @@ def mahi_eval_host(h, x, lam, energy=None, forces=None, dEdlambda=None):
 
 def mahi_get_potential(h, phi):
     _ck(lib().mahi_get_potential(h, _ptr(phi)), "mahi_get_potential")
+
+
+def mahi_backward(h, grad_energy, forces, dEdlambda, lam, dx=None, dlambda=None, dEdqA=None, dEdqB=None):
+    """Backward of the last mahi_eval (device tensors; outputs may be None)."""
+    ref = forces if forces is not None else dx
+    x_is_fp64 = 1 if ref is not None and str(ref.dtype).endswith("float64") else 0
+    _ck(lib().mahi_backward(h, _ptr(grad_energy), _ptr(forces), _ptr(dEdlambda), _ptr(lam), x_is_fp64, _ptr(dx),
+                            _ptr(dlambda), _ptr(dEdqA), _ptr(dEdqB)), "mahi_backward")
 
 
 def mahi_set_timing(h, on=True):

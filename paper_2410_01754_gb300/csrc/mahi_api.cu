@@ -45,7 +45,7 @@ static void free_all(mahi_ctx *h) {
                   h->m2l_list, h->m2l_off, h->site_ptr, h->site_atoms,
                   h->energy_part, h->site_energy, h->tc_ops, h->tc_partial, h->tc_msrc, h->tc_level_off, h->tc_units, h->tc_error, h->d_x_stage,
                   h->d_lam_stage, h->d_E_stage, h->d_dEdl_stage, h->d_F_stage, h->ops_lat_h3, h->L_h3,
-                  h->box_qd, h->vtmp, h->relD, h->phi_site, h->phi_part, h->d_level_off, h->tc_error_site};
+                  h->box_qd, h->vtmp, h->relD, h->phi_site, h->psi_site, h->site_slot, h->phi_part, h->d_level_off, h->tc_error_site};
   for (void *b : bufs)
     if (b) cudaFree(b);
   for (int i = 0; i < 32; ++i)
@@ -329,8 +329,16 @@ int mahi_set_charges(mahi_t h, const double *qA, const double *qB, const int32_t
   if (h->site_ptr) { cudaFree(h->site_ptr); h->site_ptr = nullptr; }
   if (h->site_atoms) { cudaFree(h->site_atoms); h->site_atoms = nullptr; }
   if (h->phi_site) { cudaFree(h->phi_site); h->phi_site = nullptr; }
+  if (h->psi_site) { cudaFree(h->psi_site); h->psi_site = nullptr; }
   if (h->phi_part) { cudaFree(h->phi_part); h->phi_part = nullptr; }
   CK(dalloc(&h->phi_site, std::max<size_t>(1, atoms.size()) * sizeof(double)));
+  CK(dalloc(&h->psi_site, std::max<size_t>(1, atoms.size()) * sizeof(double)));
+  {
+    std::vector<int> slot(N, -1);
+    for (size_t k = 0; k < atoms.size(); ++k) slot[atoms[k]] = (int)k;
+    if (!h->site_slot) CK(dalloc(&h->site_slot, N * sizeof(int)));
+    CK(cudaMemcpy(h->site_slot, slot.data(), N * sizeof(int), cudaMemcpyHostToDevice));
+  }
   CK(dalloc(&h->phi_part, std::max<size_t>(1, atoms.size()) * kSiteChunksMax * sizeof(double)));
   CK(dalloc(&h->site_ptr, (S + 1) * sizeof(int)));
   CK(dalloc(&h->site_atoms, std::max<size_t>(1, atoms.size()) * sizeof(int)));
@@ -352,6 +360,20 @@ int mahi_eval(mahi_t h, const void *x, int32_t x_is_fp64, const double *lambda, 
     // the tensor-core kernel reports bounded-wait timeouts through a flag that
     // is checked lazily at the next synchronising call (mahi_eval_host)
   }
+  return MAHI_OK;
+}
+
+int mahi_backward(mahi_t h, const double *grad_energy, const void *forces, const double *dEdlambda,
+                  const double *lambda, int32_t x_is_fp64, void *dx, double *dlambda, double *dEdqA, double *dEdqB) {
+  if (!h || !grad_energy) return MAHI_ERR_INVALID_ARG;
+  if (!h->charges_set) return MAHI_ERR_STATE;
+  if (dx && !forces) return MAHI_ERR_INVALID_ARG;
+  if (dlambda && h->S > 0 && !dEdlambda) return MAHI_ERR_INVALID_ARG;
+  if ((dEdqA || dEdqB) && h->S > 0 && !lambda) return MAHI_ERR_INVALID_ARG;
+  CK(cudaSetDevice(h->device));
+  if (enqueue_backward(h, grad_energy, forces, dEdlambda, lambda, x_is_fp64 ? 1 : 0, dx, dlambda, dEdqA, dEdqB) != 0)
+    return cuda_fail(cudaGetLastError(), "mahi_backward");
+  h->launches = 1;
   return MAHI_OK;
 }
 

@@ -108,6 +108,8 @@ struct mahi_ctx {
   double *L_h3 = nullptr;                     // root local of H_3 (K doubles)
   double *box_qd = nullptr;                   // FP64 Q, D, T per box (8 doubles), all levels
   double *phi_site = nullptr;                 // refined potential at site atoms
+  double *psi_site = nullptr;                 // f sum_j A_ij D_j at site atoms (charge gradients)
+  int *site_slot = nullptr;                   // N: position in site_atoms, -1 for environment atoms
   double *phi_part = nullptr;                 // its per-part partial sums
   int64_t *d_level_off = nullptr;             // device copy of level_off
   double *eta = nullptr, *eta_x = nullptr, *eta_y = nullptr, *eta_z = nullptr;  // degree 2p
@@ -143,6 +145,8 @@ namespace mahi {
 int enqueue_eval(mahi_ctx *h, const void *x, int x_is_fp64, const double *lambda, double *energy,
                  void *forces, double *dEdl);
 int enqueue_potential(mahi_ctx *h, double *phi);
+int enqueue_backward(mahi_ctx *h, const double *gE, const void *forces, const double *dEdl, const double *lam,
+                     int x_is_fp64, void *dx, double *dlam, double *dqA, double *dqB);
 int upload_tables();
 size_t gemm_workspace_elems(int d, int ld, int num_sms);
 const char *stage_name(int i);

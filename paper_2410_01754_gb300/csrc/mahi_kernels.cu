@@ -1031,7 +1031,8 @@ __global__ void __launch_bounds__(P2P_THREADS) k_p2p(int nb, double L, double fc
 //    site (first shell direct, lattice part, dipole/background part).  Then
 //      k_s = f sum D_i D_j A_ij,  g_s = sum D_i phi~_i,
 //      dE/dlam = g + (1/2 - lam) k,  E += 1/2 lam(1-lam) k,
-//      F_i -= lam(1-lam) f sum_{j != i} D_i D_j grad A(r_ij).
+//      F_i -= lam(1-lam) f sum_{j != i} D_i D_j grad A(r_ij),
+//    and psi_i = f sum_{j in s} A_ij D_j (kept for the charge gradients).
 //    Sites of up to kSiteSymMax atoms evaluate each unordered pair once and
 //    gather the forces per atom in a fixed order; larger sites evaluate the
 //    ordered pairs of one atom per lane.
@@ -1094,9 +1095,10 @@ __global__ void k_site(int S, double L, double fcoul, int Pmax, double aii, cons
                        const double *__restrict__ lam, const double *__restrict__ phi_site,
                        const double *__restrict__ eta, const double *__restrict__ eta_x,
                        const double *__restrict__ eta_y, const double *__restrict__ eta_z,
-                       double *__restrict__ dEdl, double *__restrict__ site_energy, FT *__restrict__ forces) {
+                       double *__restrict__ dEdl, double *__restrict__ site_energy, FT *__restrict__ forces,
+                       double *__restrict__ psi_site) {
   __shared__ double fsh[4][kMaxSiteAtoms][3];
-  __shared__ double gbuf[4][kSiteSymPairs][3];
+  __shared__ double gbuf[4][kSiteSymPairs][4];  // grad A at r = x_lo - x_hi, then A
   const int wib = threadIdx.x >> 5;
   int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (warp >= S) return;
@@ -1121,27 +1123,30 @@ __global__ void k_site(int S, double L, double fcoul, int Pmax, double aii, cons
       site_pair_r(x, i, j, L, r);
       site_pair_kernel(r, L, c2, Pmax, eta, eta_x, eta_y, eta_z, A, g);
       ksum += 2.0 * dq[i] * dq[j] * A;
-      gbuf[wib][p][0] = g[0]; gbuf[wib][p][1] = g[1]; gbuf[wib][p][2] = g[2];
+      gbuf[wib][p][0] = g[0]; gbuf[wib][p][1] = g[1]; gbuf[wib][p][2] = g[2]; gbuf[wib][p][3] = A;
     }
     __syncwarp();
     for (int ia = lane; ia < n; ia += 32) {
       const double Di = dq[site_atoms[b + ia]];
-      double f0 = 0.0, f1 = 0.0, f2 = 0.0;
+      double f0 = 0.0, f1 = 0.0, f2 = 0.0, ps = aii * Di;
       for (int ja = 0; ja < n; ++ja) {
         if (ja == ia) continue;
         const int lo = min(ia, ja), hi = max(ia, ja);
         const int p = lo * (2 * n - lo - 1) / 2 + (hi - lo - 1);
+        const double Dj = dq[site_atoms[b + ja]];
         // gbuf holds grad A at r = x_lo - x_hi; at x_hi - x_lo it changes sign
-        const double w = (ia == lo ? 1.0 : -1.0) * lw * fcoul * Di * dq[site_atoms[b + ja]];
+        const double w = (ia == lo ? 1.0 : -1.0) * lw * fcoul * Di * Dj;
         f0 -= w * gbuf[wib][p][0]; f1 -= w * gbuf[wib][p][1]; f2 -= w * gbuf[wib][p][2];
+        ps += gbuf[wib][p][3] * Dj;
       }
       fsh[wib][ia][0] = f0; fsh[wib][ia][1] = f1; fsh[wib][ia][2] = f2;
+      if (psi_site) psi_site[b + ia] = fcoul * ps;
     }
   } else {
     for (int ia = lane; ia < n; ia += 32) {
       const int i = site_atoms[b + ia];
       const double Di = dq[i];
-      double f0 = 0.0, f1 = 0.0, f2 = 0.0;
+      double f0 = 0.0, f1 = 0.0, f2 = 0.0, ps = aii * Di;
       for (int ja = 0; ja < n; ++ja) {
         if (ja == ia) continue;
         const int j = site_atoms[b + ja];
@@ -1149,10 +1154,12 @@ __global__ void k_site(int S, double L, double fcoul, int Pmax, double aii, cons
         site_pair_r(x, i, j, L, r);
         site_pair_kernel(r, L, c2, Pmax, eta, eta_x, eta_y, eta_z, A, g);
         ksum += Di * dq[j] * A;
+        ps += A * dq[j];
         const double w = lw * fcoul * Di * dq[j];
         f0 -= w * g[0]; f1 -= w * g[1]; f2 -= w * g[2];
       }
       fsh[wib][ia][0] = f0; fsh[wib][ia][1] = f1; fsh[wib][ia][2] = f2;
+      if (psi_site) psi_site[b + ia] = fcoul * ps;
     }
   }
   for (int o = 16; o > 0; o >>= 1) {
@@ -1503,9 +1510,14 @@ __global__ void __launch_bounds__(kSiteThreads, 3) k_site_phi(
   double base = 0.0;  // FP64 charge + dipole values at c of the rows this thread stages
   int n0 = 343, bc = 0;
   const T Rf = (T)cen[3];
+  // the separation test runs in single precision (its 1e-4 safety margin is far
+  // above the rounding of box centres at |x| < 4L); every block of a site
+  // evaluates it identically
+  const float cfx = (float)cen[0], cfy = (float)cen[1], cfz = (float)cen[2], Lf = (float)L;
   for (int l = 0; l <= d && n0 > 0; ++l) {
     const double s = L / (double)(1 << l);
     const T a_l = (T)(0.86602540378443865 * s), th = (T)theta, is = (T)(1.0 / s);
+    const float sf = (float)s;
     int nsep = 0, n1 = 0;
     for (int t0 = 0; t0 < n0; t0 += blockDim.x) {
       const int t = t0 + tid;
@@ -1515,11 +1527,11 @@ __global__ void __launch_bounds__(kSiteThreads, 3) k_site_phi(
         e = fa[t];
         const int box = e >> 9, img = e & 511;
         const int nx = img / 49 - 3, ny = (img / 7) % 7 - 3, nz = img % 7 - 3;
-        const T dx = (T)(cen[0] - (((int)d_compact(box) + 0.5) * s + nx * L)),
-                dy = (T)(cen[1] - (((int)d_compact(box >> 1) + 0.5) * s + ny * L)),
-                dz = (T)(cen[2] - (((int)d_compact(box >> 2) + 0.5) * s + nz * L));
-        const T D = sqrt(dx * dx + dy * dy + dz * dz);
-        if (a_l < th * (D - Rf) * (T)0.9999) kind = 0;
+        const float dx = cfx - (((float)d_compact(box) + 0.5f) * sf + (float)nx * Lf),
+                    dy = cfy - (((float)d_compact(box >> 1) + 0.5f) * sf + (float)ny * Lf),
+                    dz = cfz - (((float)d_compact(box >> 2) + 0.5f) * sf + (float)nz * Lf);
+        const float D = sqrtf(dx * dx + dy * dy + dz * dz);
+        if ((float)a_l < (float)th * (D - (float)Rf) * 0.9999f) kind = 0;
         else if (l == d) kind = 1;
         else kind = 2;
       }
@@ -1903,7 +1915,7 @@ static cudaError_t eval_t(mahi_ctx *h, const XT *x, const double *lam, double *e
     k_site<T, XT, XT><<<(h->S + 3) / 4, 128, 0, st>>>(h->S, h->L, coulomb_constant(), kSiteDegree, h->site_aii,
                                                       h->site_ptr,
                                                       h->site_atoms, x, h->dq, lam, h->phi_site, h->eta, h->eta_x,
-                                                      h->eta_y, h->eta_z, dEdl, h->site_energy, forces);
+                                                      h->eta_y, h->eta_z, dEdl, h->site_energy, forces, h->psi_site);
     h->launches += 3;
   }
   if (energy) {
@@ -1951,6 +1963,79 @@ int upload_tables() {
   if (cudaMemcpyToSymbol(c_udiag, ud, sizeof(ud)) != cudaSuccess) return -1;
   done = true;
   return 0;
+}
+
+// ---------------------------------------------------------------------------
+// Backward of the HI energy (autograd): with g = dLoss/dE,
+//   dx = -g F,  dlambda = g dE/dlambda,
+//   dqA_i = g ((1 - l) phi~_i - l (1 - l) psi_i),  dqB_i = g (l phi~_i + l (1 - l) psi_i)
+// for an atom of a site with lambda l; environment atoms: dqA_i = g phi~_i,
+// dqB_i = 0.  phi~ is the last evaluation's potential (refined at site atoms).
+// ---------------------------------------------------------------------------
+template <typename T, typename FT>
+__global__ void k_backward(int64_t N, int S, const double *__restrict__ gE, const FT *__restrict__ F,
+                           const double *__restrict__ dEdl, const double *__restrict__ lam,
+                           const int *__restrict__ inv_perm, const T *__restrict__ phi_s,
+                           const int *__restrict__ site_of, const int *__restrict__ site_slot,
+                           const double *__restrict__ phi_site, const double *__restrict__ psi_site,
+                           FT *__restrict__ dx, double *__restrict__ dlam, double *__restrict__ dqA,
+                           double *__restrict__ dqB) {
+  const double g = *gE;
+  const FT gf = (FT)g;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += stride) {
+    if (dx) {
+      dx[3 * i + 0] = -gf * F[3 * i + 0];
+      dx[3 * i + 1] = -gf * F[3 * i + 1];
+      dx[3 * i + 2] = -gf * F[3 * i + 2];
+    }
+    if (dqA || dqB) {
+      const int sl = site_slot[i];
+      double a, b;
+      if (sl < 0) {
+        a = g * (double)phi_s[inv_perm[i]];
+        b = 0.0;
+      } else {
+        const double l = lam[site_of[i]], w = l * (1.0 - l), phi = phi_site[sl], psi = psi_site[sl];
+        a = g * ((1.0 - l) * phi - w * psi);
+        b = g * (l * phi + w * psi);
+      }
+      if (dqA) dqA[i] = a;
+      if (dqB) dqB[i] = b;
+    }
+  }
+  if (dlam)
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < S; s += stride) dlam[s] = g * dEdl[s];
+}
+
+int enqueue_backward(mahi_ctx *h, const double *gE, const void *forces, const double *dEdl, const double *lam,
+                     int x_is_fp64, void *dx, double *dlam, double *dqA, double *dqB) {
+  const int grid = (int)std::min<int64_t>(4 * (int64_t)h->num_sms, (h->N + 255) / 256);
+  const bool f64 = h->prec == MAHI_FP64;
+  if (x_is_fp64) {
+    if (f64)
+      k_backward<double, double><<<grid, 256, 0, h->stream>>>(h->N, h->S, gE, (const double *)forces, dEdl, lam,
+                                                              h->inv_perm, (const double *)h->phi_s, h->site_of,
+                                                              h->site_slot, h->phi_site, h->psi_site, (double *)dx,
+                                                              dlam, dqA, dqB);
+    else
+      k_backward<float, double><<<grid, 256, 0, h->stream>>>(h->N, h->S, gE, (const double *)forces, dEdl, lam,
+                                                             h->inv_perm, (const float *)h->phi_s, h->site_of,
+                                                             h->site_slot, h->phi_site, h->psi_site, (double *)dx,
+                                                             dlam, dqA, dqB);
+  } else {
+    if (f64)
+      k_backward<double, float><<<grid, 256, 0, h->stream>>>(h->N, h->S, gE, (const float *)forces, dEdl, lam,
+                                                             h->inv_perm, (const double *)h->phi_s, h->site_of,
+                                                             h->site_slot, h->phi_site, h->psi_site, (float *)dx,
+                                                             dlam, dqA, dqB);
+    else
+      k_backward<float, float><<<grid, 256, 0, h->stream>>>(h->N, h->S, gE, (const float *)forces, dEdl, lam,
+                                                            h->inv_perm, (const float *)h->phi_s, h->site_of,
+                                                            h->site_slot, h->phi_site, h->psi_site, (float *)dx,
+                                                            dlam, dqA, dqB);
+  }
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 int enqueue_eval(mahi_ctx *h, const void *x, int x_is_fp64, const double *lambda, double *energy, void *forces,

@@ -16,13 +16,12 @@
 // so the descriptor strides are LBO = (#row-groups x 128 B) along K and
 // SBO = 128 B along M/N.
 //
-// Warp roles (192 threads): warp 0 allocates TMEM, lane 0 issues the MMAs;
-// warps 1-4 gather A rows with cp.async (one row per thread) whose completion
-// arrives on the stage barrier asynchronously (cp.async.mbarrier.arrive), so
-// the gather of stage i never waits for the MMAs of stage i-1; warp 5 lane 0
-// streams B with cp.async.bulk.  Warps 0-3 drain TMEM in the epilogue.
-// Every wait is bounded: on expiry the CTA records an error, stops issuing
-// work, drains what is in flight and frees its TMEM.
+// Warp roles (448 threads): warp 0 allocates TMEM, lane 0 issues the MMAs;
+// warp 1 lane 0 streams B with cp.async.bulk; warps 2-9 are two groups of A
+// producers taking the even and the odd pipeline items, gathering source rows
+// with cp.async and storing their TF32 hi/lo split in TMEM; warps 10-13 drain
+// TMEM in the epilogue.  Every wait is bounded: on expiry the CTA records an
+// error, stops issuing work, drains what is in flight and frees its TMEM.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -38,9 +37,9 @@ namespace tc {
 constexpr int kRows = 128;       // targets per tile (MMA M)
 constexpr int kKC = 8;           // input coefficients per pipeline stage (one MMA K)
 constexpr int kStagesA = 4;      // A stages in tensor memory
-constexpr int kStagesS = 8;      // A staging slots in shared memory (cp.async, own rows per thread)
+constexpr int kStagesS = 4;      // A staging slots in shared memory per producer group (cp.async)
 constexpr int kStagesB = 12;     // B stages in shared memory (at most; Params::nsb is the count used)
-constexpr int kThreads = 320;
+constexpr int kThreads = 448;     // 14 warps: MMA, B producer, 2 x 4 A producers, 4 epilogue
 constexpr uint32_t kSpinLimit = 1u << 26;
 constexpr int kMaxN = 256;       // MMA N limit: Kp <= 256, order <= 15
 
@@ -223,9 +222,10 @@ __device__ __forceinline__ uint32_t tc_compact(uint32_t x) {
 // warps load each target's source rows from global memory, split them into
 // TF32 hi and lo in registers and store them with tcgen05.st, so shared memory
 // carries only the operator chunks (B).
-// Warp roles: 0 = TMEM owner + MMA issuer (one lane), 1-4 = A producers (row
-// t of both tiles = TMEM lane t), 5 = B producer (bulk copies), 6-9 = epilogue
-// (TMEM -> L).  TMEM columns: [0, 176) tile-0 accumulator, [192, 368) tile-1
+// Warp roles: 0 = TMEM owner + MMA issuer (one lane), 1 = B producer (bulk
+// copies), 2-5 and 6-9 = A producers of the even and odd items (row t of both
+// tiles = TMEM lane t; a warp may touch only its TMEM lane quarter, warp % 4),
+// 10-13 = epilogue (TMEM -> L).  TMEM columns: [0, 176) tile-0 accumulator, [192, 368) tile-1
 // accumulator, [384 + 32 s, 416 + 32 s) A stage s as tile-0 hi | lo, tile-1 hi | lo.
 // ---------------------------------------------------------------------------
 namespace tc {
@@ -349,6 +349,60 @@ __device__ __forceinline__ void arow_issue(const Params &p, const int *s_list, c
   }
 }
 
+// Coalesced variant: the same copies as arow_issue for the 32 rows of this
+// warp, but lane l copies granule (l & 1) of row 16 rh + (l >> 1) (rh = 0, 1)
+// of each tile, so one warp instruction reads 16 whole 32-byte source chunks
+// (512 contiguous bytes where the sources are consecutive) instead of half of
+// 32 chunks.  Row state (source index, validity) is still kept per own row and
+// exchanged by shuffles; the caller must __syncwarp() after its cp.async wait
+// before reading rows written by other lanes.
+__device__ __forceinline__ void arow_issue_coalesced(const Params &p, const int *s_list, const int *s_off, int t,
+                                                     int lane, const ItemIter &it, ARow &a, unsigned char *dst) {
+  const int unit = it.unit, j = it.j, kc = it.kc;
+  if (unit != a.unit) {
+    const int4 u = p.units[unit];
+    a.lev = u.x;
+    a.child = u.y;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      a.valid[h] = t < tile_count(p, u, h);
+      class_target(u.x, u.y, u.z + h * kRows + t, a.bx[h], a.by[h], a.bz[h]);
+    }
+    a.base = p.M + p.level_off[u.x] * p.ld;
+    a.sidx[0] = a.sidx[1] = 0;
+    a.unit = unit;
+    a.j = -1;
+  }
+  const int hb = a.lev - 1;
+  if (j != a.j) {
+    const int oid = s_list[a.child * kListLen + j];
+    const int ox = s_off[oid * 3 + 0], oy = s_off[oid * 3 + 1], oz = s_off[oid * 3 + 2];
+    const int sm = (1 << a.lev) - 1;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      if (!a.valid[h]) continue;
+      const int sx = (a.bx[h] - ox) & sm, sy = (a.by[h] - oy) & sm, sz = (a.bz[h] - oz) & sm;
+      const int cls = (sx & 1) | ((sy & 1) << 1) | ((sz & 1) << 2);
+      a.sidx[h] = ((((int64_t)cls << hb | (sz >> 1)) << hb | (sy >> 1)) << hb) | (sx >> 1);
+    }
+    a.j = j;
+  }
+  const int64_t plane = (int64_t)kc << (3 * hb + 3);
+  const int g = lane & 1, rbase = t & ~31;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    // own row as a signed 32-bit code: source chunk index, or -1 for no row
+    const int mine = a.valid[h] ? (int)a.sidx[h] : -1;
+#pragma unroll
+    for (int rh = 0; rh < 2; ++rh) {
+      const int src = __shfl_sync(0xffffffffu, mine, 16 * rh + (lane >> 1));
+      const int row = rbase + 16 * rh + (lane >> 1);
+      const float *gp = a.base + (plane + (src < 0 ? 0 : src)) * kKC + 4 * g;
+      cp_async16_zfill(dst + ((2 * h + g) * kRows + row) * 16, gp, src < 0 ? 0u : 16u);
+    }
+  }
+}
+
 }  // namespace tc
 
 // Multipoles of levels 1..d rewritten for the M2L gathers: per level, K planes
@@ -395,7 +449,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_m2l_tc(tc::Params prm) {
   unsigned char *sB = smem;                         // [B stage][hi|lo][b_bytes]
   const int nsb = prm.nsb;
   unsigned char *sS = sB + nsb * 2 * b_bytes;       // [slot][4 granules][kRows][16 B] A staging
-  int *s_list = reinterpret_cast<int *>(sS + kStagesS * 4 * kRows * 16);  // [8][189] offset ids
+  int *s_list = reinterpret_cast<int *>(sS + 2 * kStagesS * 4 * kRows * 16);  // [8][189] offset ids
   int *s_off = s_list + 8 * kListLen;                                   // [316][3] offsets
   uint64_t *bars = reinterpret_cast<uint64_t *>(s_off + ((3 * kNumOffsets + 1) & ~1));
   uint64_t *fullA = bars, *emptyA = bars + kStagesA, *fullB = bars + 2 * kStagesA,
@@ -419,7 +473,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_m2l_tc(tc::Params prm) {
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStagesA; ++s) {
-      mbar_init(&fullA[s], kRows);
+      mbar_init(&fullA[s], 4);   // the four warps of the producer group of that item
       mbar_init(&emptyA[s], 1);
     }
     for (int s = 0; s < kStagesB; ++s) {
@@ -443,39 +497,47 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_m2l_tc(tc::Params prm) {
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
-  if (warp >= 1 && warp <= 4) {
-    // ---------------- A producers: row t of both tiles (TMEM lane t) per thread ----------------
-    // each thread copies its own rows into a staging slot kStagesS - 1 items
-    // ahead (cp.async groups, one per item), then splits them into TMEM
+  if (warp >= 2 && warp <= 9) {
+    // ---------------- A producers: two groups of four warps take the even and
+    // the odd items; row t of both tiles (TMEM lane t) per thread ----------------
+    // each group copies its items kStagesS - 1 items ahead into its own staging
+    // ring (cp.async groups, one per item, coalesced across the warp), then
+    // every thread splits its own rows into TF32 hi/lo and stores them in TMEM
+    const int grp = (warp - 2) >> 2;
     const int quarter = warp & 3;
     const int t = quarter * 32 + lane;
     const uint32_t lane_addr = tmem + ((uint32_t)(quarter * 32) << 16);
+    unsigned char *ring = sS + (size_t)grp * kStagesS * 4 * kRows * 16;
     constexpr int D = kStagesS - 1;
+    const int nmine = (nloc - grp + 1) >> 1;        // items 2 jj + grp of this group
     ARow a;
-    ItemIter it;                                    // issue position, D items ahead
+    ItemIter it;                                    // issue position, D items of this group ahead
     iter_begin(prm, k, nA, nit, it);
+    if (grp) iter_next(prm, k, nA, nit, it);
     int slot_i = 0;                                 // staging slot of the next issue
     for (int qq = 0; qq < D; ++qq) {
-      if (qq < nloc) {
-        arow_issue(prm, s_list, s_off, t, it, a, sS + (size_t)slot_i * 4 * kRows * 16);
+      if (qq < nmine) {
+        arow_issue_coalesced(prm, s_list, s_off, t, lane, it, a, ring + (size_t)slot_i * 4 * kRows * 16);
+        iter_next(prm, k, nA, nit, it);
         iter_next(prm, k, nA, nit, it);
       }
       slot_i = slot_i + 1 == kStagesS ? 0 : slot_i + 1;
       cp_async_commit();
     }
-    int slot_c = 0, s = 0;                          // staging slot and TMEM stage of item q
-    uint32_t ph = 0;                                // phase parity of emptyA[s] to wait for
-    for (int q = 0; q < nloc; ++q) {
-      if (q + D < nloc) {
-        arow_issue(prm, s_list, s_off, t, it, a, sS + (size_t)slot_i * 4 * kRows * 16);
+    int slot_c = 0;                                 // staging slot of item jj
+    for (int jj = 0; jj < nmine; ++jj) {
+      const int q = 2 * jj + grp;
+      if (jj + D < nmine) {
+        arow_issue_coalesced(prm, s_list, s_off, t, lane, it, a, ring + (size_t)slot_i * 4 * kRows * 16);
+        iter_next(prm, k, nA, nit, it);
         iter_next(prm, k, nA, nit, it);
       }
       slot_i = slot_i + 1 == kStagesS ? 0 : slot_i + 1;
       cp_async_commit();
       cp_async_wait_group<D>();                     // this thread's copies of item q have landed
-      if (q >= kStagesA && !mbar_wait(&emptyA[s], ph, abort_flag)) break;
-      tc_fence_after();
-      const unsigned char *src = sS + (size_t)slot_c * 4 * kRows * 16 + t * 16;
+      __syncwarp();                                 // ... and those of the other lanes of the warp
+      // split first: it needs only the staging slot, not the TMEM stage
+      const unsigned char *src = ring + (size_t)slot_c * 4 * kRows * 16 + t * 16;
       uint32_t w[32];  // tile-0 hi | tile-0 lo | tile-1 hi | tile-1 lo, 8 columns each
 #pragma unroll
       for (int h = 0; h < 2; ++h)
@@ -488,18 +550,24 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_m2l_tc(tc::Params prm) {
           tf32_split(x.z, hi[2], lo[2]);
           tf32_split(x.w, hi[3], lo[3]);
         }
+      __syncwarp();                                 // staging slot read by all lanes before it is refilled
+      const int s = q % kStagesA;
+      // lane 0 waits for the TMEM stage (its MMAs of item q - kStagesA done)
+      // and the warp follows it; the whole warp leaves together on a timeout
+      // (the TMEM store below is warp-collective)
+      bool ok = true;
+      if (q >= kStagesA && lane == 0) ok = mbar_wait(&emptyA[s], (uint32_t)((q / kStagesA - 1) & 1), abort_flag);
+      if (!__shfl_sync(0xffffffffu, ok, 0)) break;
+      tc_fence_after();
       tmem_st32(lane_addr + kAcol + 32u * (uint32_t)s, w);
       asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
       tc_fence_before();
-      mbar_arrive(&fullA[s]);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&fullA[s]);        // one arrival per warp
       slot_c = slot_c + 1 == kStagesS ? 0 : slot_c + 1;
-      if (++s == kStagesA) {
-        s = 0;
-        if (q + 1 > kStagesA) ph ^= 1u;             // from the third use on
-      }
     }
     cp_async_wait_all();
-  } else if (warp == 5) {
+  } else if (warp == 1) {
     // ---------------- B producer ----------------
     if (lane == 0) {
       const uint32_t img = 2 * b_bytes;  // hi | lo of one (offset, chunk)
@@ -574,12 +642,12 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_m2l_tc(tc::Params prm) {
       if (++sa == kStagesA) { sa = 0; pa ^= 1u; }
       if (++sb == nsb) { sb = 0; pb ^= 1u; }
     }
-  } else if (warp >= 6) {
+  } else if (warp >= 10) {
     // ---------------- epilogue: TMEM -> L rows, one segment at a time ----------------
     const int quarter = warp & 3;                   // TMEM lanes this warp may read
     const int r = quarter * 32 + lane;
     for (int seg = 0; seg < nseg; ++seg) {
-      if (!mbar_wait(accb, seg & 1, abort_flag)) break;
+      if (!__all_sync(0xffffffffu, mbar_wait(accb, seg & 1, abort_flag))) break;  // warp-collective TMEM loads follow
       tc_fence_after();
       const int unit = seg < nA ? k + seg * (int)gridDim.x : prm.nfull + k / prm.q;
       const int4 u = prm.units[unit];
@@ -699,7 +767,7 @@ int tc_build_units(mahi_ctx *h, std::vector<int> &units) {
 // dynamic shared memory of k_m2l_tc with nsb operator stages
 static size_t tc_smem_bytes(int ng, int nsb) {
   const size_t b = (size_t)(tc::kKC / 4) * ng * 128;
-  const size_t stage = (size_t)tc::kStagesS * 4 * tc::kRows * 16;
+  const size_t stage = (size_t)2 * tc::kStagesS * 4 * tc::kRows * 16;
   const size_t tables = sizeof(int) * (8 * kListLen + ((3 * kNumOffsets + 1) & ~1));
   return nsb * 2 * b + stage + tables + (2 * tc::kStagesA + 2 * tc::kStagesB + 2) * 8 + 16;
 }

@@ -36,6 +36,10 @@ CONFIGS = {
     # 333,334 waters (1,000,002 atoms) on a 70^3 lattice, L=21.5 nm, S=512, d=5, p=12
     "C": dict(kind="water", n_water=333334, grid=70, L=21.5, n_sites=512,
               waters_per_site=(2, 4), depth=5, order=12),
+    # 66,667 waters (200,001 atoms) at C's density, L=12.57 nm, S=128, d=4, p=12
+    # (the differentiation workload)
+    "D": dict(kind="water", n_water=66667, grid=41, L=12.57, n_sites=128,
+              waters_per_site=(2, 4), depth=4, order=12),
     # profiler case: a quarter of C's waters (250,002 atoms) in the same box and
     # tree, S=128; the M2L, M2M and L2L work is identical to C's
     "C_quarter": dict(kind="water", n_water=83334, grid=70, L=21.5, n_sites=128,
@@ -270,7 +274,7 @@ def make_water(n_water: int, grid: int, L: float, n_sites: int, seed: int,
 
 
 def make(config: str, seed: int = 1):
-    """Build one of the named workloads ("A", "B", "C", "C_quarter") for a seed."""
+    """Build one of the named workloads ("A", "B", "C", "D", "C_quarter") for a seed."""
     c = dict(CONFIGS[config])
     kind = c.pop("kind")
     if kind == "charges":

@@ -1,0 +1,156 @@
+"""Backward pass (mahi_backward, the autograd function) against the oracle and
+against central finite differences of the GPU energy.
+
+The HI energy is a quadratic polynomial in lambda and in the charges, so its
+central differences there are exact up to rounding.  The GPU energy is the
+FMM's, however, while dE/dlambda and dE/dq at site atoms use the refined
+site-atom potential; the two differ by the FMM's truncation error of the
+potential at the site atoms (a few 1e-3 kJ/mol/e at p = 12), which bounds
+those tolerances.  In x the forces are likewise not the exact gradient of the
+truncated FMM energy."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import hi
+import paper_2410_01754_gb300 as pkg
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA device")]
+
+from paper_2410_01754_gb300.autograd import MahiEnergy  # noqa: E402
+
+
+def _tensors(s, xdt):
+    dev = torch.device("cuda")
+    x = torch.tensor(s["x"], dtype=xdt, device=dev, requires_grad=True)
+    lam = torch.tensor(s["lam"], dtype=torch.float64, device=dev, requires_grad=True)
+    qA = torch.tensor(s["qA"], dtype=torch.float64, device=dev, requires_grad=True)
+    qB = torch.tensor(s["qB"], dtype=torch.float64, device=dev, requires_grad=True)
+    return x, lam, qA, qB
+
+
+@pytest.fixture(scope="module")
+def sysA():
+    s = synth.make("A", 1)
+    ref = hi.hi_eval(s)
+    return s, ref, hi.hi_charge_gradients(s, ref=ref)
+
+
+@pytest.mark.parametrize("prec,xdt,tol,etol", [("fp64", torch.float64, 1e-6, 5e-7), ("mixed", torch.float32, 1e-4, 2e-5)])
+def test_backward_matches_oracle(sysA, prec, xdt, tol, etol):
+    """Config A (3,000 charges, 4 sites) at p = 16: every gradient against the
+    oracle's closed forms, scaled by an upstream gradient of 0.7."""
+    s, ref, cg = sysA
+    me = MahiEnergy(s["L"], s["site_of"], len(s["lam"]), 16 if prec == "fp64" else 15, 3, prec)
+    x, lam, qA, qB = _tensors(s, xdt)
+    E = me.energy(x, lam, qA, qB)
+    (0.7 * E).backward()
+    torch.cuda.synchronize()
+    me.close()
+    # mixed: the tensor-core M2L accumulates toward zero (a few 1e-6 of E here)
+    assert abs(E.item() - ref["E"]) < etol * abs(ref["E"])
+    Fr = ref["F"]
+    dx = x.grad.double().cpu().numpy()
+    assert np.sqrt(((dx + 0.7 * Fr) ** 2).sum() / ((0.7 * Fr) ** 2).sum()) < 10 * tol
+    np.testing.assert_allclose(lam.grad.cpu().numpy(), 0.7 * ref["dEdl"], atol=1e-3)
+    for key, g in (("dqA", qA.grad), ("dqB", qB.grad)):
+        got = g.cpu().numpy()
+        want = 0.7 * cg[key]
+        scale = np.abs(want).max()
+        assert np.abs(got - want).max() < tol * scale, (key, np.abs(got - want).max() / scale)
+
+
+@pytest.fixture(scope="module")
+def sysD():
+    return synth.make("D", 1)
+
+
+def test_autograd_finite_differences_fp64(sysD):
+    """200,001 atoms, 128 sites, p = 12, FP64 path: autograd gradients against
+    central differences of the GPU energy on 64 random coordinates (h = 1e-4 nm),
+    8 lambdas (h = 1e-4) and 8 charges of each set."""
+    s = sysD
+    N, S = len(s["qA"]), len(s["lam"])
+    me = MahiEnergy(s["L"], s["site_of"], S, 12, 4, "fp64")
+    x, lam, qA, qB = _tensors(s, torch.float64)
+    E = me.energy(x, lam, qA, qB)
+    E.backward()
+    gx, gl, gA, gB = (t.grad.clone() for t in (x, lam, qA, qB))
+    rng = np.random.default_rng(5)
+
+    def energy(xx=None, ll=None, a=None, b=None):
+        with torch.no_grad():
+            return me.energy(x if xx is None else xx, lam if ll is None else ll, qA if a is None else a,
+                             qB if b is None else b).item()
+
+    # positions: 64 random (atom, axis) pairs
+    h = 1e-4
+    Fscale = gx.abs().max().item()
+    errs = []
+    for k in rng.choice(N, 64, replace=False):
+        ax = int(rng.integers(3))
+        xp = x.detach().clone(); xp[k, ax] += h
+        xm = x.detach().clone(); xm[k, ax] -= h
+        fd = (energy(xx=xp) - energy(xx=xm)) / (2 * h)
+        errs.append(abs(fd - gx[k, ax].item()))
+    # FMM truncation at p = 12: the forces differ from the gradient of the
+    # truncated energy by ~1e-6 of the largest force
+    assert max(errs) < 2e-5 * Fscale, (max(errs), Fscale)
+    # lambda and charges: exact central differences of a quadratic
+    for k in rng.choice(S, 8, replace=False):
+        lp = lam.detach().clone(); lp[k] += 1e-4
+        lm = lam.detach().clone(); lm[k] -= 1e-4
+        fd = (energy(ll=lp) - energy(ll=lm)) / 2e-4
+        assert fd == pytest.approx(gl[k].item(), abs=1e-2)
+    site_atoms = np.where(s["site_of"] >= 0)[0]
+    for key, t, g in (("qA", qA, gA), ("qB", qB, gB)):
+        for k in list(rng.choice(site_atoms, 6, replace=False)) + list(rng.choice(N, 2, replace=False)):
+            hq = 1e-3
+            tp = t.detach().clone(); tm = t.detach().clone()
+            tp[k] += hq; tm[k] -= hq
+            if s["site_of"][k] < 0:  # environment atoms carry one charge (qA == qB)
+                other = qB if key == "qA" else qA
+                op = other.detach().clone(); om = other.detach().clone()
+                op[k] += hq; om[k] -= hq
+                args_p = dict(a=tp, b=op) if key == "qA" else dict(a=op, b=tp)
+                args_m = dict(a=tm, b=om) if key == "qA" else dict(a=om, b=tm)
+                fd = (energy(**args_p) - energy(**args_m)) / (2 * hq)
+                assert fd == pytest.approx((gA[k] + gB[k]).item(), abs=1e-2)
+            else:
+                fd = (energy(**{"a" if key == "qA" else "b": tp}) - energy(**{"a" if key == "qA" else "b": tm})) / (2 * hq)
+                assert fd == pytest.approx(g[k].item(), abs=1e-2)
+    me.close()
+
+
+def test_autograd_mixed_matches_fp64(sysD):
+    """The mixed path's gradients (single precision with FP64 site terms)
+    against the FP64 path's on the same 200,001-atom system."""
+    s = sysD
+    S = len(s["lam"])
+    out = {}
+    for prec, xdt in (("fp64", torch.float64), ("mixed", torch.float32)):
+        me = MahiEnergy(s["L"], s["site_of"], S, 12, 4, prec)
+        x, lam, qA, qB = _tensors(s, xdt)
+        me.energy(x, lam, qA, qB).backward()
+        torch.cuda.synchronize()
+        out[prec] = [t.grad.double().cpu().numpy() for t in (x, lam, qA, qB)]
+        me.close()
+    a, b = out["fp64"], out["mixed"]
+    assert np.sqrt(((a[0] - b[0]) ** 2).sum() / (a[0] ** 2).sum()) < 1e-4
+    assert np.abs(a[1] - b[1]).max() < 1e-3
+    # charge gradients are potentials: at environment atoms the mixed path's
+    # carries the tensor-core accumulation bias of its far field
+    for k in (2, 3):
+        assert np.abs(a[k] - b[k]).max() < 3e-4 * np.abs(a[k]).max()
+
+
+def test_backward_before_charges_is_an_error():
+    m = pkg.Mahi(2.0, 10, 1, 4, 1, "fp64")
+    g = torch.ones(1, dtype=torch.float64, device="cuda")
+    with pytest.raises(pkg.MahiError) as ei:
+        pkg.mahi_backward(m.h, g, None, None, None)
+    assert ei.value.code == -7
+    m.close()

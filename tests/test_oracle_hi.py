@@ -137,3 +137,36 @@ def test_site_terms_match_pairwise_kernel():
     for a in range(6):
         ref = -sum(D[a] * D[b] * G[a, b] for b in range(6) if b != a)
         np.testing.assert_allclose(fc[a], ref, atol=1e-10)
+
+
+def test_charge_gradients_central_difference_exact():
+    """dE/dqA and dE/dqB against central differences of the HI energy.  E is a
+    quadratic polynomial in the charges, so the central difference is exact up
+    to rounding for any step.  Environment atoms use qA only (dE/dqB = 0)."""
+    s = small_multisite(n=40, S=2)
+    g = hi.hi_charge_gradients(s)
+    h = 0.05
+    for k in (0, 3, 5, 9, 30):  # atoms of site 0, of site 1 and of the environment
+        for key in ("qA", "qB"):
+            sp = dict(s); sp[key] = s[key].copy(); sp[key][k] += h
+            sm = dict(s); sm[key] = s[key].copy(); sm[key][k] -= h
+            d = (hi.hi_eval(sp)["E"] - hi.hi_eval(sm)["E"]) / (2 * h)
+            assert d == pytest.approx(g["d" + key][k], rel=1e-9, abs=1e-9), (k, key)
+
+
+def test_charge_gradients_match_bruteforce_states():
+    """Through Eq. rek_ham_lambda: dE/dqB_i = sum over states with site s in form
+    B of the state weight times that state's potential at i (and likewise for
+    qA with form A); for one site these are lambda phi_B and (1 - lambda) phi_A."""
+    s = paper_random_system()
+    g = hi.hi_charge_gradients(s)
+    lam = s["lam"][0]
+    phiA = oracle.ewald(s["x"], s["qA"], s["L"])[0] * oracle.F_COULOMB
+    phiB = oracle.ewald(s["x"], s["qB"], s["L"])[0] * oracle.F_COULOMB
+    site = s["site_of"] == 0
+    np.testing.assert_allclose(g["dqB"][site], lam * phiB[site], rtol=1e-9, atol=1e-9)
+    np.testing.assert_allclose(g["dqA"][site], (1 - lam) * phiA[site], rtol=1e-9, atol=1e-9)
+    # environment: one charge, weighted over both states
+    env = ~site
+    np.testing.assert_allclose(g["dqA"][env], (1 - lam) * phiA[env] + lam * phiB[env], rtol=1e-9, atol=1e-9)
+    assert not g["dqB"][env].any()
