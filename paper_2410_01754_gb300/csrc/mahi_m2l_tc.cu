@@ -16,11 +16,11 @@
 // so the descriptor strides are LBO = (#row-groups x 128 B) along K and
 // SBO = 128 B along M/N.
 //
-// Warp roles (448 threads): warp 0 allocates TMEM, lane 0 issues the MMAs;
-// warp 1 lane 0 streams B with cp.async.bulk; warps 2-9 are two groups of A
-// producers taking the even and the odd pipeline items, gathering source rows
-// with cp.async and storing their TF32 hi/lo split in TMEM; warps 10-13 drain
-// TMEM in the epilogue.  Every wait is bounded: on expiry the CTA records an
+// Warp roles (480 threads): warp 0 allocates TMEM, and its lane 0 and lane 0
+// of warp 14 issue the MMAs of tile 0 and tile 1; warp 1 lane 0 streams B with
+// cp.async.bulk; warps 2-9 are two groups of A producers taking the even and
+// the odd pipeline items, gathering source rows with cp.async and storing
+// their TF32 hi/lo split in TMEM; warps 10-13 drain TMEM in the epilogue.  Every wait is bounded: on expiry the CTA records an
 // error, stops issuing work, drains what is in flight and frees its TMEM.
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -39,8 +39,9 @@ constexpr int kKC = 8;           // input coefficients per pipeline stage (one M
 constexpr int kStagesA = 4;      // A stages in tensor memory
 constexpr int kStagesS = 4;      // A staging slots in shared memory per producer group (cp.async)
 constexpr int kStagesB = 12;     // B stages in shared memory (at most; Params::nsb is the count used)
-constexpr int kThreads = 448;     // 14 warps: MMA, B producer, 2 x 4 A producers, 4 epilogue
+constexpr int kThreads = 480;     // 15 warps: MMA (tile 0), B producer, 2 x 4 A producers, 4 epilogue, MMA (tile 1)
 constexpr uint32_t kSpinLimit = 1u << 26;
+constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s: no wait of a healthy launch comes near it
 constexpr int kMaxN = 256;       // MMA N limit: Kp <= 256, order <= 15
 
 struct Unit {
@@ -92,10 +93,31 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *b, uint32_t parity) {
   return ok != 0;
 }
 // bounded wait; returns false (and raises the abort flag) on expiry
+__device__ __forceinline__ bool mbar_test(uint64_t *b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// bounded wait: gives up after kWaitNs (or when another role of the CTA gave
+// up), raising the abort flag; returns false then
 __device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity, volatile int *abort_flag) {
+  if (mbar_test(b, parity)) return true;  // non-blocking test first: most waits find the phase complete
+  const uint64_t t0 = global_ns();
   for (uint32_t it = 0; it < tc::kSpinLimit; ++it) {
     if (mbar_try_wait(b, parity)) return true;
     if (*abort_flag) return false;
+    if ((it & 255) == 255 && global_ns() - t0 > tc::kWaitNs) break;
   }
   *abort_flag = 1;
   return false;
@@ -222,10 +244,10 @@ __device__ __forceinline__ uint32_t tc_compact(uint32_t x) {
 // warps load each target's source rows from global memory, split them into
 // TF32 hi and lo in registers and store them with tcgen05.st, so shared memory
 // carries only the operator chunks (B).
-// Warp roles: 0 = TMEM owner + MMA issuer (one lane), 1 = B producer (bulk
-// copies), 2-5 and 6-9 = A producers of the even and odd items (row t of both
-// tiles = TMEM lane t; a warp may touch only its TMEM lane quarter, warp % 4),
-// 10-13 = epilogue (TMEM -> L).  TMEM columns: [0, 176) tile-0 accumulator, [192, 368) tile-1
+// Warp roles: 0 = TMEM owner + tile-0 MMA issuer (one lane), 1 = B producer
+// (bulk copies), 2-5 and 6-9 = A producers of the even and odd items (row t of
+// both tiles = TMEM lane t; a warp may touch only its TMEM lane quarter,
+// warp % 4), 10-13 = epilogue (TMEM -> L), 14 = tile-1 MMA issuer (one lane).  TMEM columns: [0, 176) tile-0 accumulator, [192, 368) tile-1
 // accumulator, [384 + 32 s, 416 + 32 s) A stage s as tile-0 hi | lo, tile-1 hi | lo.
 // ---------------------------------------------------------------------------
 namespace tc {
@@ -455,7 +477,8 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_m2l_tc(tc::Params prm) {
   uint64_t *fullA = bars, *emptyA = bars + kStagesA, *fullB = bars + 2 * kStagesA,
            *emptyB = bars + 2 * kStagesA + kStagesB;
   uint64_t *accb = bars + 2 * kStagesA + 2 * kStagesB, *tfree = accb + 1;
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(tfree + 1);
+  uint64_t *mdone = tfree + 1;                      // [2] last commit of each MMA issuer
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mdone + 2);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -474,14 +497,16 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_m2l_tc(tc::Params prm) {
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStagesA; ++s) {
       mbar_init(&fullA[s], 4);   // the four warps of the producer group of that item
-      mbar_init(&emptyA[s], 1);
+      mbar_init(&emptyA[s], 2);  // one commit per MMA-issuing thread
     }
     for (int s = 0; s < kStagesB; ++s) {
       mbar_init(&fullB[s], 1);
-      mbar_init(&emptyB[s], 1);
+      mbar_init(&emptyB[s], 2);
     }
-    mbar_init(accb, 1);
+    mbar_init(accb, 2);
     mbar_init(tfree, kRows);
+    mbar_init(&mdone[0], 1);
+    mbar_init(&mdone[1], 1);
     *abort_flag = 0;
   }
   for (int e = threadIdx.x; e < 8 * kListLen; e += blockDim.x) s_list[e] = prm.list[e];
@@ -597,14 +622,20 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_m2l_tc(tc::Params prm) {
       for (int i = (issued > nsb ? issued - nsb : 0); i < issued; ++i) {
         uint64_t *b = &fullB[i % nsb];
         const uint32_t par = (i / nsb) & 1;
-        for (uint32_t it = 0; it < kSpinLimit && !mbar_try_wait(b, par); ++it) {
-        }
+        const uint64_t t0 = global_ns();
+        for (uint32_t it = 0; it < kSpinLimit && !mbar_try_wait(b, par); ++it)
+          if ((it & 255) == 255 && global_ns() - t0 > kWaitNs) break;
       }
     }
-  } else if (warp == 0 && lane == 0) {
-    // ---------------- MMA issuer ----------------
+  } else if ((warp == 0 || warp == 14) && lane == 0) {
+    // ---------------- MMA issuers: warp 0 issues tile 0, warp 14 tile 1 ----------------
+    // Each tcgen05.mma of this shape (128 x Kp x 8) runs for about as long as
+    // one thread takes to issue it, so the two tiles are issued by two threads
+    // on different warps; each commits to the stage barriers (count 2).
+    const int mt = warp == 14 ? 1 : 0;
     const uint32_t idesc = idesc_tf32(kRows, ng * 8);
     const uint32_t b_lbo = ng * 128;
+    const uint32_t dt = tmem + (mt ? kAcc1 : 0u), acol = kAcol + 16u * (uint32_t)mt;
     int ntile = 1, sa = 0, sb = 0;
     uint32_t pa = 0, pb = 0;                        // phase parities of fullA[sa], fullB[sb]
     bool first = true, seg_start = true;
@@ -622,17 +653,14 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_m2l_tc(tc::Params prm) {
       if (!mbar_wait(&fullA[sa], pa, abort_flag)) break;
       if (!mbar_wait(&fullB[sb], pb, abort_flag)) break;
       tc_fence_after();
-      const uint32_t bh = sB0 + (uint32_t)sb * 2u * b_bytes, bl = bh + b_bytes;
-      const uint64_t dbh = smem_desc(bh, b_lbo, 128), dbl = smem_desc(bl, b_lbo, 128);
-      const uint32_t acc0 = first ? 0u : 1u;
-      const uint32_t ah0 = tmem + kAcol + 32u * (uint32_t)sa;
-      mma_tf32_ts(tmem, ah0, dbh, idesc, acc0);
-      mma_tf32_ts(tmem, ah0, dbl, idesc, 1u);
-      mma_tf32_ts(tmem, ah0 + 8u, dbh, idesc, 1u);
-      if (ntile == 2) {
-        mma_tf32_ts(tmem + kAcc1, ah0 + 16u, dbh, idesc, acc0);
-        mma_tf32_ts(tmem + kAcc1, ah0 + 16u, dbl, idesc, 1u);
-        mma_tf32_ts(tmem + kAcc1, ah0 + 24u, dbh, idesc, 1u);
+      if (mt < ntile) {
+        const uint32_t bh = sB0 + (uint32_t)sb * 2u * b_bytes, bl = bh + b_bytes;
+        const uint64_t dbh = smem_desc(bh, b_lbo, 128), dbl = smem_desc(bl, b_lbo, 128);
+        const uint32_t acc0 = first ? 0u : 1u;
+        const uint32_t ah = tmem + acol + 32u * (uint32_t)sa;   // hi | lo of this tile
+        mma_tf32_ts(dt, ah, dbh, idesc, acc0);
+        mma_tf32_ts(dt, ah, dbl, idesc, 1u);
+        mma_tf32_ts(dt, ah + 8u, dbh, idesc, 1u);
       }
       first = false;
       mma_commit(&emptyA[sa]);
@@ -642,7 +670,15 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_m2l_tc(tc::Params prm) {
       if (++sa == kStagesA) { sa = 0; pa ^= 1u; }
       if (++sb == nsb) { sb = 0; pb ^= 1u; }
     }
-  } else if (warp >= 10) {
+    // every MMA this thread issued has finished before TMEM can be freed
+    // (also after a timeout, when the stage barriers are no longer awaited)
+    mma_commit(&mdone[mt]);
+    {
+      const uint64_t t0 = global_ns();
+      for (uint32_t it = 0; it < kSpinLimit && !mbar_try_wait(&mdone[mt], 0); ++it)
+        if ((it & 255) == 255 && global_ns() - t0 > kWaitNs) break;
+    }
+  } else if (warp >= 10 && warp <= 13) {
     // ---------------- epilogue: TMEM -> L rows, one segment at a time ----------------
     const int quarter = warp & 3;                   // TMEM lanes this warp may read
     const int r = quarter * 32 + lane;
@@ -769,7 +805,7 @@ static size_t tc_smem_bytes(int ng, int nsb) {
   const size_t b = (size_t)(tc::kKC / 4) * ng * 128;
   const size_t stage = (size_t)2 * tc::kStagesS * 4 * tc::kRows * 16;
   const size_t tables = sizeof(int) * (8 * kListLen + ((3 * kNumOffsets + 1) & ~1));
-  return nsb * 2 * b + stage + tables + (2 * tc::kStagesA + 2 * tc::kStagesB + 2) * 8 + 16;
+  return nsb * 2 * b + stage + tables + (2 * tc::kStagesA + 2 * tc::kStagesB + 4) * 8 + 16;
 }
 
 int tc_m2l(mahi_ctx *h) {
