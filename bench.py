@@ -294,6 +294,88 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def _time_steps(h, x, lam, E, F, g, flush, stream, steps, warmup):
+    """Mean event-timed step (ms) and the median site-stage time (ms)."""
+    import torch
+
+    import paper_2410_01754_gb300 as pkg
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            pkg.mahi_eval(h, x, lam, E, F, g)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for k in range(steps):
+            flush.fill_(float(k))
+            ev[k][0].record(stream)
+            pkg.mahi_eval(h, x, lam, E, F, g)
+            ev[k][1].record(stream)
+        stream.synchronize()
+        ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+        pkg.mahi_set_timing(h, True)
+        site = []
+        for _ in range(3):
+            flush.fill_(1.0)
+            pkg.mahi_eval(h, x, lam, E, F, g)
+            site.append(pkg.mahi_stage_times(h).get("site", 0.0))
+        pkg.mahi_set_timing(h, False)
+    return ms, float(np.median(site))
+
+
+def run_sweep(args):
+    """Overhead of the per-site work over the plain FMM (no sites), the
+    paper's sites / forms and particle-count benchmarks (Secs. "Scaling with
+    Increasing Number of Sites", "Scaling with Increasing Number of Particles"):
+    sites: the 1,000,002-atom water box with S = 0, 1, 8, 64, 256, 512 sites;
+    atoms: water boxes of 3k to 4M atoms at the same density with one site of
+    6-12 atoms per ~4,000 atoms, each against the same box without sites.
+    One JSON line per point (mixed precision, p = 12, depth for ~30 atoms per
+    leaf; L2 flushed between timed steps)."""
+    import math
+
+    import torch
+
+    import paper_2410_01754_gb300 as pkg
+    import synth
+    from paper_2410_01754_gb300 import build as pkg_build
+
+    pkg_build.build()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    spacing = 21.5 / 70  # lattice spacing of the 1M-atom box (0.307 nm)
+    if args.sweep == "sites":
+        pts = [(333334, S) for S in (0, 1, 8, 64, 256, 512)]
+    else:
+        pts = []
+        for nw in (1000, 10667, 83334, 333334, 1333334):
+            pts += [(nw, 0), (nw, max(1, round(3 * nw / 4000)))]
+    base = {}
+    for nw, S in pts:
+        grid = math.ceil((nw * 1.0001) ** (1.0 / 3.0))
+        while grid ** 3 < nw:
+            grid += 1
+        L = round(grid * spacing, 4)
+        d = max(1, min(6, round(math.log(3 * nw / 30.0, 8))))
+        s = synth.make_water(n_water=nw, grid=grid, L=L, n_sites=S, seed=1, depth=d, order=12)
+        N = len(s["qA"])
+        h = pkg.mahi_create(L, N, S, 12, d, "mixed", stream)
+        pkg.mahi_set_charges(h, s["qA"], s["qB"], s["site_of"])
+        x = torch.tensor(s["x"], dtype=torch.float32, device=dev)
+        lam = torch.tensor(s["lam"], dtype=torch.float64, device=dev)
+        E = torch.zeros(1, dtype=torch.float64, device=dev)
+        F = torch.empty_like(x)
+        g = torch.zeros(max(1, S), dtype=torch.float64, device=dev)
+        ms, site_ms = _time_steps(h, x, lam, E, F, g, flush, stream, args.steps, args.warmup)
+        pkg.mahi_destroy(h)
+        if S == 0:
+            base[nw] = ms
+        rec = {"sweep": args.sweep, "n_atoms": N, "n_sites": S, "box_nm": L, "depth": d, "order_p": 12,
+               "precision": "mixed", "ms_per_step": round(ms, 4), "site_stage_ms": round(site_ms, 4),
+               "atoms_per_s": round(N / (ms * 1e-3), 1)}
+        if S > 0 and nw in base:
+            rec["overhead_vs_no_sites"] = round(ms / base[nw] - 1.0, 4)
+        print(json.dumps(rec), flush=True)
+
+
 def cpu_baseline(s, n_targets=8192, atom_frac=1 / 8):
     """The oracle (FP64 Ewald + HI closed form) timed on the host cores on a
     bounded sample, extrapolated to one full evaluation of the workload:
@@ -360,6 +442,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kernels-only", action="store_true",
                     help="time the mixed steps only (for profiler runs); skips stages, e2e, FP64 comparator")
+    ap.add_argument("--sweep", choices=["sites", "atoms"], default=None,
+                    help="overhead of the per-site work over the plain FMM vs sites (1M atoms) or vs atoms")
     ap.add_argument("--case", default=WORKLOAD["config"], choices=[WORKLOAD["config"], "C_quarter"],
                     help="C_quarter: 250,002 atoms in the same box and tree (identical M2L work), for "
                          "profiler captures together with --kernels-only")
@@ -370,6 +454,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.sweep:
+        run_sweep(args)
     else:
         run_ours(args)
 

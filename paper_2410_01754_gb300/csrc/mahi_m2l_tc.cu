@@ -122,6 +122,18 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity, volatile
   *abort_flag = 1;
   return false;
 }
+// bounded wait by non-blocking tests only (no suspension between tests): for
+// the single lanes on the pipeline's critical path
+__device__ __forceinline__ bool mbar_spin(uint64_t *b, uint32_t parity, volatile int *abort_flag) {
+  const uint64_t t0 = global_ns();
+  for (uint32_t it = 0;; ++it) {
+    if (mbar_test(b, parity)) return true;
+    if (*abort_flag) return false;
+    if ((it & 255) == 255 && global_ns() - t0 > tc::kWaitNs) break;
+  }
+  *abort_flag = 1;
+  return false;
+}
 // 16-byte copy; with src_bytes = 0 the destination is zero-filled and nothing is read
 __device__ __forceinline__ void cp_async16_zfill(void *smem, const void *gmem, uint32_t src_bytes) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(smem)), "l"(gmem), "r"(src_bytes)
@@ -497,11 +509,11 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_m2l_tc(tc::Params prm) {
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStagesA; ++s) {
       mbar_init(&fullA[s], 4);   // the four warps of the producer group of that item
-      mbar_init(&emptyA[s], 2);  // one commit per MMA-issuing thread
+      mbar_init(&emptyA[s], 2);  // (unused)
     }
     for (int s = 0; s < kStagesB; ++s) {
       mbar_init(&fullB[s], 1);
-      mbar_init(&emptyB[s], 2);
+      mbar_init(&emptyB[s], 2);  // done ring: one commit per MMA-issuing thread and item
     }
     mbar_init(accb, 2);
     mbar_init(tfree, kRows);
@@ -581,7 +593,12 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_m2l_tc(tc::Params prm) {
       // and the warp follows it; the whole warp leaves together on a timeout
       // (the TMEM store below is warp-collective)
       bool ok = true;
-      if (q >= kStagesA && lane == 0) ok = mbar_wait(&emptyA[s], (uint32_t)((q / kStagesA - 1) & 1), abort_flag);
+      // (item q - kStagesA is done when the done-ring entry of that item has
+      // its phase complete: one commit per MMA issuer and item)
+      if (q >= kStagesA && lane == 0) {
+        const int qd = q - kStagesA;
+        ok = mbar_wait(&emptyB[qd % nsb], (uint32_t)((qd / nsb) & 1), abort_flag);
+      }
       if (!__shfl_sync(0xffffffffu, ok, 0)) break;
       tc_fence_after();
       tmem_st32(lane_addr + kAcol + 32u * (uint32_t)s, w);
@@ -663,8 +680,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_m2l_tc(tc::Params prm) {
         mma_tf32_ts(dt, ah + 8u, dbh, idesc, 1u);
       }
       first = false;
-      mma_commit(&emptyA[sa]);
-      mma_commit(&emptyB[sb]);
+      mma_commit(&emptyB[sb]);  // item done: frees its B stage and its A stage
       seg_start = iter_next(prm, k, nA, nit, it);
       if (seg_start || q == nloc - 1) mma_commit(accb);  // segment complete
       if (++sa == kStagesA) { sa = 0; pa ^= 1u; }
