@@ -182,3 +182,126 @@ def hi_bruteforce(sys, rc=None, f=F_COULOMB):
         l0 = lam.copy(); l0[s] = 0.0
         dEdl[s] = interp(l1) - interp(l0)
     return dict(E=E, dEdl=dEdl, states=EX)
+
+
+# ---------------------------------------------------------------------------
+# Sites with more than two forms (Sec. "Hamiltonian Interpolation Formulation",
+# general formulation Eq. "iter_ham_lambda"; Appendix, Eqs. "lambda_list",
+# "one_site_lambda").  A site with F = 2^m forms has m lambdas; form rho is the
+# binary number whose bit l selects lambda_l (bit set) or 1 - lambda_l, so its
+# weight is lambda~_rho = prod_l (lambda_l if bit l of rho else 1 - lambda_l).
+# ---------------------------------------------------------------------------
+def lambda_tilde(lams):
+    """Weights of the 2^m forms of one site from its m lambdas (bit l <-> lambda_l)."""
+    lams = np.asarray(lams, dtype=np.float64)
+    m = lams.shape[0]
+    w = np.ones(1 << m)
+    for rho in range(1 << m):
+        for l in range(m):
+            w[rho] *= lams[l] if (rho >> l) & 1 else 1.0 - lams[l]
+    return w
+
+
+def dlambda_tilde(lams):
+    """d lambda~_rho / d lambda_l as an (m, 2^m) array: the weight with factor l
+    replaced by +1 (bit set) or -1 (bit clear)."""
+    lams = np.asarray(lams, dtype=np.float64)
+    m = lams.shape[0]
+    d = np.ones((m, 1 << m))
+    for l in range(m):
+        for rho in range(1 << m):
+            for k in range(m):
+                if k == l:
+                    d[l, rho] *= 1.0 if (rho >> k) & 1 else -1.0
+                else:
+                    d[l, rho] *= lams[k] if (rho >> k) & 1 else 1.0 - lams[k]
+    return d
+
+
+def multiform_eval(sys, rc=None, f=F_COULOMB):
+    """HI energy, dE/dlambda and forces for sites with 2^m forms.
+
+    ``sys`` holds x, q_env (charges of environment atoms; site entries unused),
+    site_of, forms (list over sites of (F_s, n_s) arrays: charges of the site's
+    atoms, in increasing atom index, in each form), lams (list over sites of
+    m_s lambdas) and L.  With q~ = sum_rho lambda~_rho q^rho at site atoms, the
+    general formulation equals the charge-scaled energy E(q~) plus, per site,
+        C = f/2 [sum_rho lambda~_rho G_rho,rho - sum_rho,rho' lambda~_rho lambda~_rho' G_rho,rho']
+    with G_rho,rho' = q^rho^T A q^rho' over the site (self term included):
+    cross-site and environment terms are bilinear in the scaled charges and
+    agree between the two.  Derivatives:
+        dE/dlambda_l = sum_rho (d lambda~_rho / d lambda_l)
+                       (q^rho . phi~ + f (1/2 G_rho,rho - (G lambda~)_rho)),
+        F_i = -q~_i grad phi~_i - grad_i C,
+        grad_i C = f [sum_rho lambda~_rho q_i^rho grad_i phi^rho - q~_i grad_i phi^q~]
+    where phi^u is the potential of the site-only charge set u (f = 1)."""
+    x, L = sys["x"], sys["L"]
+    site_of = np.asarray(sys["site_of"])
+    q = np.asarray(sys["q_env"], dtype=np.float64).copy()
+    sites = site_lists(site_of, len(sys["forms"]))
+    lt = [lambda_tilde(l) for l in sys["lams"]]
+    for s, at in enumerate(sites):
+        q[at] = lt[s] @ np.asarray(sys["forms"][s])
+    phi, grad, e = ewald(x, q, L, rc)
+    phi = phi * f
+    grad = grad * f
+    F = -q[:, None] * grad
+    E = e * f
+    dEdl = []
+    for s, at in enumerate(sites):
+        Q = np.asarray(sys["forms"][s], dtype=np.float64)      # (F, n)
+        w = lt[s]
+        xs = x[at]
+        T = np.zeros_like(Q)                                   # A q^rho per form
+        Gr = np.zeros(Q.shape + (3,))                          # grad of phi^rho
+        for r in range(Q.shape[0]):
+            p_r, g_r, _ = ewald(xs, Q[r], L, rc=0.5 * L)
+            T[r] = p_r
+            Gr[r] = g_r
+        G = Q @ T.T
+        E += 0.5 * f * (w @ np.diag(G) - w @ G @ w)
+        pq, gq, _ = ewald(xs, q[at], L, rc=0.5 * L)
+        gradC = f * (np.einsum("r,ri,rik->ik", w, Q, Gr) - q[at][:, None] * gq)
+        F[at] -= gradC
+        dl = dlambda_tilde(sys["lams"][s])
+        per_form = Q @ phi[at] + f * (0.5 * np.diag(G) - G @ w)
+        dEdl.append(dl @ per_form)
+    return dict(E=E, F=F, dEdl=np.concatenate(dEdl) if dEdl else np.zeros(0), qt=q, phi=phi)
+
+
+def multiform_bruteforce(sys, rc=None, f=F_COULOMB):
+    """The multilinear definition (Eq. "rek_ham_lambda" with Eq. "one_site_lambda"
+    per site): E = sum over every choice of one form per site of the product of
+    the forms' weights times the periodic energy of that charge set; dE/dlambda
+    by the exact central difference of this multilinear function."""
+    x, L = sys["x"], sys["L"]
+    site_of = np.asarray(sys["site_of"])
+    sites = site_lists(site_of, len(sys["forms"]))
+    nf = [np.asarray(fm).shape[0] for fm in sys["forms"]]
+    EX = {}
+    for X in itertools.product(*[range(n) for n in nf]):
+        q = np.asarray(sys["q_env"], dtype=np.float64).copy()
+        for s, at in enumerate(sites):
+            q[at] = np.asarray(sys["forms"][s])[X[s]]
+        EX[X] = energy(x, q, L, rc, f)
+
+    def interp(lams):
+        lt = [lambda_tilde(l) for l in lams]
+        tot = 0.0
+        for X, e in EX.items():
+            w = 1.0
+            for s in range(len(X)):
+                w *= lt[s][X[s]]
+            tot += w * e
+        return tot
+
+    lams = [np.asarray(l, dtype=np.float64) for l in sys["lams"]]
+    E = interp(lams)
+    dEdl = []
+    h = 0.25
+    for s in range(len(lams)):
+        for l in range(lams[s].shape[0]):
+            lp = [v.copy() for v in lams]; lp[s][l] += h
+            lm = [v.copy() for v in lams]; lm[s][l] -= h
+            dEdl.append((interp(lp) - interp(lm)) / (2 * h))
+    return dict(E=E, dEdl=np.array(dEdl))

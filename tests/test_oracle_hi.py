@@ -170,3 +170,67 @@ def test_charge_gradients_match_bruteforce_states():
     env = ~site
     np.testing.assert_allclose(g["dqA"][env], (1 - lam) * phiA[env] + lam * phiB[env], rtol=1e-9, atol=1e-9)
     assert not g["dqB"][env].any()
+
+
+def small_multiform(seed=7, n=60, L=1.9, nforms=(4, 2, 8)):
+    """Environment charges plus sites of 3-4 atoms with 2^m forms each."""
+    rng = np.random.default_rng(seed)
+    x = rng.uniform(0, L, (n, 3))
+    q_env = rng.uniform(-1, 1, n)
+    site_of = np.full(n, -1, dtype=np.int32)
+    forms, lams = [], []
+    k = 0
+    for s, F in enumerate(nforms):
+        na = 3 + (s % 2)
+        at = np.arange(k, k + na)
+        k += na
+        site_of[at] = s
+        forms.append(q_env[at][None, :] + rng.uniform(-0.5, 0.5, (F, na)))
+        lams.append(rng.uniform(0, 1, int(np.log2(F))))
+    return dict(x=x, q_env=q_env, site_of=site_of, forms=forms, lams=lams, L=L)
+
+
+def test_lambda_tilde_sums_to_one_and_matches_paper_example():
+    """Eq. constraint (sum of the form weights is 1) and Eq. one_site_lambda for
+    four forms: (1-l1)(1-l0), (1-l1) l0, l1 (1-l0), l1 l0."""
+    l0, l1 = 0.3, 0.8
+    w = hi.lambda_tilde([l0, l1])
+    np.testing.assert_allclose(w, [(1 - l1) * (1 - l0), (1 - l1) * l0, l1 * (1 - l0), l1 * l0], rtol=1e-15)
+    for m in range(1, 5):
+        lams = np.random.default_rng(m).uniform(0, 1, m)
+        assert hi.lambda_tilde(lams).sum() == pytest.approx(1.0, abs=1e-15)
+        d = hi.dlambda_tilde(lams)
+        np.testing.assert_allclose(d.sum(axis=1), 0.0, atol=1e-15)
+
+
+def test_multiform_closed_form_equals_bruteforce():
+    s = small_multiform()
+    cf = hi.multiform_eval(s)
+    bf = hi.multiform_bruteforce(s)
+    assert cf["E"] == pytest.approx(bf["E"], rel=1e-11)
+    np.testing.assert_allclose(cf["dEdl"], bf["dEdl"], rtol=1e-9, atol=1e-9)
+
+
+def test_multiform_two_forms_reduce_to_two_form_path():
+    s = small_multisite(n=50, S=2)
+    sites = hi.site_lists(s["site_of"], 2)
+    mf = dict(x=s["x"], q_env=s["qA"], site_of=s["site_of"], L=s["L"],
+              forms=[np.stack([s["qA"][at], s["qB"][at]]) for at in sites], lams=[[v] for v in s["lam"]])
+    a = hi.multiform_eval(mf)
+    b = hi.hi_eval(s)
+    assert a["E"] == pytest.approx(b["E"], rel=1e-12)
+    np.testing.assert_allclose(a["dEdl"], b["dEdl"], rtol=1e-10)
+    np.testing.assert_allclose(a["F"], b["F"], atol=1e-8)
+
+
+def test_multiform_forces_central_difference():
+    s = small_multiform(n=30, nforms=(4, 2))
+    base = hi.multiform_eval(s)
+    h = 1e-5
+    for k in (0, 2, 4, 20):  # site atoms and an environment atom
+        for ax in range(3):
+            xp = s["x"].copy(); xp[k, ax] += h
+            xm = s["x"].copy(); xm[k, ax] -= h
+            ep = hi.multiform_eval(dict(s, x=xp))["E"]
+            em = hi.multiform_eval(dict(s, x=xm))["E"]
+            assert -(ep - em) / (2 * h) == pytest.approx(base["F"][k, ax], rel=2e-6, abs=1e-5)
