@@ -376,6 +376,83 @@ def run_sweep(args):
         print(json.dumps(rec), flush=True)
 
 
+def run_replicas(args):
+    """16 independent replicas of uneven size (48k to 250k atoms, 16 to 256
+    sites, each its own box and lambdas; p = 12, d = 4, mixed precision): one
+    step evaluates all of them, either as 16 mahi_eval calls or as one launch
+    of the CUDA graph that mahi_batch_create captured (after mahi_autotune on
+    each replica).  L2 flushed between timed steps."""
+    import math
+
+    import torch
+
+    import paper_2410_01754_gb300 as pkg
+    import synth
+    from paper_2410_01754_gb300 import build as pkg_build
+
+    pkg_build.build()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    spacing = 21.5 / 70
+    R = 16
+    reps = []
+    for k in range(R):
+        nw = int(round(16000 + (83334 - 16000) * ((k * 7) % R) / (R - 1)))  # uneven order of sizes
+        S = int(round(16 + (256 - 16) * ((k * 5) % R) / (R - 1)))
+        grid = math.ceil(nw ** (1.0 / 3.0))
+        while grid ** 3 < nw:
+            grid += 1
+        L = round(grid * spacing, 4)
+        s = synth.make_water(n_water=nw, grid=grid, L=L, n_sites=S, seed=100 + k, depth=4, order=12)
+        N = len(s["qA"])
+        h = pkg.mahi_create(L, N, S, 12, 4, "mixed", stream)
+        pkg.mahi_set_charges(h, s["qA"], s["qB"], s["site_of"])
+        x = torch.tensor(s["x"], dtype=torch.float32, device=dev)
+        lam = torch.tensor(s["lam"], dtype=torch.float64, device=dev)
+        out = (torch.zeros(1, dtype=torch.float64, device=dev), torch.empty_like(x),
+               torch.zeros(S, dtype=torch.float64, device=dev))
+        reps.append((h, x, lam, out, N, S))
+    n_atoms = sum(r[4] for r in reps)
+
+    def timed(step):
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                step()
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(args.steps)]
+            for k in range(args.steps):
+                flush.fill_(float(k))
+                ev[k][0].record(stream)
+                step()
+                ev[k][1].record(stream)
+            stream.synchronize()
+        return float(np.mean([a.elapsed_time(b) for a, b in ev]))
+
+    def eager():
+        for h, x, lam, (E, F, g), N, S in reps:
+            pkg.mahi_eval(h, x, lam, E, F, g)
+
+    t_eager = timed(eager)
+    tune = []
+    for h, x, lam, out, N, S in reps:
+        pkg.mahi_autotune(h, x, lam, 2)
+        tune.append(pkg.mahi_get_tuning(h))
+    t_tuned = timed(eager)
+    batch = pkg.MahiBatch([r[0] for r in reps], stream, [r[1] for r in reps], [r[2] for r in reps],
+                          [r[3][0] for r in reps], [r[3][1] for r in reps], [r[3][2] for r in reps])
+    t_graph = timed(batch.launch)
+    batch.close()
+    for r in reps:
+        pkg.mahi_destroy(r[0])
+    print(json.dumps({"mode": "replicas", "replicas": R, "n_atoms_total": n_atoms,
+                      "atoms": [r[4] for r in reps], "sites": [r[5] for r in reps], "order_p": 12, "depth": 4,
+                      "precision": "mixed", "ms_per_step_eager": round(t_eager, 4),
+                      "ms_per_step_tuned_eager": round(t_tuned, 4), "ms_per_step_graph": round(t_graph, 4),
+                      "atoms_per_s_graph": round(n_atoms / (t_graph * 1e-3), 1),
+                      "tuning_p2p_threads_site_blocks": tune}), flush=True)
+
+
 def cpu_baseline(s, n_targets=8192, atom_frac=1 / 8):
     """The oracle (FP64 Ewald + HI closed form) timed on the host cores on a
     bounded sample, extrapolated to one full evaluation of the workload:
@@ -442,6 +519,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kernels-only", action="store_true",
                     help="time the mixed steps only (for profiler runs); skips stages, e2e, FP64 comparator")
+    ap.add_argument("--replicas", action="store_true",
+                    help="16 uneven replicas per step: eager calls vs autotuned vs one CUDA graph")
     ap.add_argument("--sweep", choices=["sites", "atoms"], default=None,
                     help="overhead of the per-site work over the plain FMM vs sites (1M atoms) or vs atoms")
     ap.add_argument("--case", default=WORKLOAD["config"], choices=[WORKLOAD["config"], "C_quarter"],
@@ -456,6 +535,8 @@ def main():
         run_reference(args)
     elif args.sweep:
         run_sweep(args)
+    elif args.replicas:
+        run_replicas(args)
     else:
         run_ours(args)
 

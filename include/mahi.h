@@ -84,6 +84,30 @@ int mahi_set_stream(mahi_t h, void *cuda_stream);
  * MAHI_ERR_BAD_SITE_MAP.  The library copies the data (synchronously). */
 int mahi_set_charges(mahi_t h, const double *qA, const double *qB, const int32_t *site_of_atom);
 
+/* Sites with more than two forms (general formulation, Eq. "iter_ham_lambda";
+ * Appendix, Eqs. "lambda_list", "one_site_lambda").  Instead of
+ * mahi_set_charges: HOST arrays
+ *   q_env           n_atoms charges (e) of the environment atoms (entries of
+ *                   site atoms are ignored)
+ *   site_of_atom    n_atoms, -1 = environment, else the site (1 to 32 atoms)
+ *   forms_per_site  n_sites values F_s in {2, 4, 8, 16}; site s then has
+ *                   m_s = log2(F_s) lambdas
+ *   q_forms         for each site in order, F_s rows (forms) of its atoms'
+ *                   charges, atoms in increasing index: sum_s F_s n_s doubles
+ * Form rho has weight prod_l (bit l of rho ? lambda_l : 1 - lambda_l) and the
+ * site atoms the scaled charge sum_rho weight_rho q^rho.  mahi_eval then takes
+ * lambda as sum_s m_s values (site 0's lambdas first, lambda_0 first) and
+ * writes dE/dlambda in the same order; E adds per site
+ *   C = f/2 [sum_rho w_rho G_rho,rho - w^T G w],  G = form-form matrix of the
+ *   periodic kernel over the site's atoms (self term included),
+ * and the forces its gradient.  mahi_n_lambdas gives the count.  A later
+ * mahi_set_charges returns the handle to two-form sites.  mahi_backward does
+ * not support these sites (MAHI_ERR_INVALID_ARG).  Errors as for
+ * mahi_set_charges, and MAHI_ERR_INVALID_ARG for an F_s outside the set. */
+int mahi_set_forms(mahi_t h, const double *q_env, const int32_t *site_of_atom, const int32_t *forms_per_site,
+                   const double *q_forms);
+int mahi_n_lambdas(mahi_t h);
+
 /* One MAHI evaluation, enqueued on the handle's stream; returns after enqueueing.
  *   x          device, n_atoms x 3 row-major positions in nm (float64 if
  *              x_is_fp64 else float32); any real values (wrapped into the box).
@@ -182,6 +206,35 @@ int mahi_site_terms_static(double box_L_nm, int32_t n_sites, const int32_t *site
                            const void *x, int32_t x_is_fp64, const double *qA, const double *qB,
                            const double *lambda, const double *phi, double *dEdlambda, double *energy_correction,
                            void *forces, void *cuda_stream);
+
+/* ---- batched replicas and launch-shape tuning -------------------------------
+ * Independent constant-pH replicas (each its own handle: box, atoms, sites,
+ * lambdas) evaluated as ONE CUDA graph.  mahi_batch_create sets every handle's
+ * stream to cuda_stream (which must not be the legacy NULL stream), runs one
+ * ordinary evaluation per replica, then captures the n evaluations, in order,
+ * into a graph with the given device buffers (arrays of n pointers, same
+ * meaning as in mahi_eval).  mahi_batch_launch enqueues the graph on that
+ * stream (one host call for all replicas); results equal n mahi_eval calls.
+ * The graph keeps the captured pointers: update positions and lambdas in place
+ * between launches; changing charges or tuning needs a new batch.  The batch
+ * does not own the handles (destroy it before them).  The paper has no
+ * counterpart (its benchmarks run one system per process). */
+typedef struct mahi_batch_ctx *mahi_batch_t;
+int mahi_batch_create(const mahi_t *handles, int32_t n, void *cuda_stream, const void *const *x,
+                      const int32_t *x_is_fp64, const double *const *lambda, double *const *energy,
+                      void *const *forces, double *const *dEdlambda, mahi_batch_t *out);
+int mahi_batch_launch(mahi_batch_t b);
+int mahi_batch_destroy(mahi_batch_t b);
+
+/* Launch-shape autotuner: times reps evaluations (outputs discarded) for each
+ * candidate shape of the near-field kernel (64, 128 or 256 threads per target
+ * leaf) and of the site-potential traversal (default blocks per site, half,
+ * double) on the given input, keeps the fastest in the handle and returns;
+ * synchronises the handle's stream.  Results change only in the order of
+ * floating-point sums.  mahi_get_tuning reports the choice (site_blocks 0 =
+ * the default count). */
+int mahi_autotune(mahi_t h, const void *x, int32_t x_is_fp64, const double *lambda, int32_t reps);
+int mahi_get_tuning(mahi_t h, int32_t *p2p_threads, int32_t *site_blocks);
 
 /* Coulomb constant used by the library (kJ mol^-1 nm e^-2). */
 double mahi_coulomb_constant(void);

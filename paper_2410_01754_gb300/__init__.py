@@ -46,6 +46,18 @@ _SIGS = {
                                               ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
                                               ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                               ctypes.c_void_p, ctypes.c_void_p]),
+    "mahi_batch_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
+    "mahi_batch_launch": (ctypes.c_int, [ctypes.c_void_p]),
+    "mahi_batch_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "mahi_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
+                                     ctypes.c_int32]),
+    "mahi_get_tuning": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32),
+                                       ctypes.POINTER(ctypes.c_int32)]),
+    "mahi_set_forms": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                      ctypes.c_void_p]),
+    "mahi_n_lambdas": (ctypes.c_int, [ctypes.c_void_p]),
     "mahi_coulomb_constant": (ctypes.c_double, []),
     "mahi_error_string": (ctypes.c_char_p, [ctypes.c_int]),
     "mahi_last_cuda_error": (ctypes.c_char_p, []),
@@ -119,6 +131,21 @@ def mahi_set_charges(h, qA, qB, site_of_atom):
     _ck(lib().mahi_set_charges(h, qA.ctypes.data, qB.ctypes.data, so.ctypes.data), "mahi_set_charges")
 
 
+def mahi_set_forms(h, q_env, site_of_atom, forms):
+    """forms: list over sites of (F_s, n_s) arrays (charges of the site's atoms,
+    in increasing atom index, in each of its F_s = 2^m forms)."""
+    q_env = np.ascontiguousarray(q_env, dtype=np.float64)
+    so = np.ascontiguousarray(site_of_atom, dtype=np.int32)
+    nf = np.ascontiguousarray([np.asarray(f).shape[0] for f in forms], dtype=np.int32)
+    qf = np.ascontiguousarray(np.concatenate([np.asarray(f, dtype=np.float64).ravel() for f in forms])
+                              if len(forms) else np.zeros(1))
+    _ck(lib().mahi_set_forms(h, q_env.ctypes.data, so.ctypes.data, nf.ctypes.data, qf.ctypes.data), "mahi_set_forms")
+
+
+def mahi_n_lambdas(h):
+    return int(lib().mahi_n_lambdas(h))
+
+
 def mahi_eval(h, x, lam, energy=None, forces=None, dEdlambda=None):
     """x, lam, energy, forces, dEdlambda: CUDA tensors (x float32/float64 N x 3)."""
     x_is_fp64 = 1 if str(x.dtype).endswith("float64") else 0
@@ -186,6 +213,43 @@ def mahi_site_terms_static(box_L_nm, site_ptr, site_atoms, x, qA, qB, lam, phi, 
         "mahi_site_terms_static")
 
 
+def mahi_autotune(h, x, lam, reps=3):
+    x_is_fp64 = 1 if str(x.dtype).endswith("float64") else 0
+    _ck(lib().mahi_autotune(h, _ptr(x), x_is_fp64, _ptr(lam), int(reps)), "mahi_autotune")
+
+
+def mahi_get_tuning(h):
+    a, b = ctypes.c_int32(), ctypes.c_int32()
+    _ck(lib().mahi_get_tuning(h, ctypes.byref(a), ctypes.byref(b)), "mahi_get_tuning")
+    return int(a.value), int(b.value)
+
+
+class MahiBatch:
+    """Replicas (handles) evaluated as one CUDA graph; tensors are captured by
+    pointer, so update them in place between launch() calls."""
+
+    def __init__(self, handles, stream, xs, lams, energies, forces, dEdls):
+        n = len(handles)
+        arr = lambda vals: (ctypes.c_void_p * n)(*vals)
+        self._keep = (xs, lams, energies, forces, dEdls)
+        is64 = (ctypes.c_int32 * n)(*[1 if str(x.dtype).endswith("float64") else 0 for x in xs])
+        out = ctypes.c_void_p()
+        _ck(lib().mahi_batch_create(arr([h.value if hasattr(h, "value") else h for h in handles]), n,
+                                    _stream_handle(stream), arr([_ptr(x) for x in xs]), is64,
+                                    arr([_ptr(v) for v in lams]), arr([_ptr(v) for v in energies]),
+                                    arr([_ptr(v) for v in forces]), arr([_ptr(v) for v in dEdls]),
+                                    ctypes.byref(out)), "mahi_batch_create")
+        self.b = out
+
+    def launch(self):
+        _ck(lib().mahi_batch_launch(self.b), "mahi_batch_launch")
+
+    def close(self):
+        if self.b is not None:
+            _ck(lib().mahi_batch_destroy(self.b), "mahi_batch_destroy")
+            self.b = None
+
+
 def mahi_coulomb_constant():
     return float(lib().mahi_coulomb_constant())
 
@@ -200,17 +264,23 @@ class Mahi:
     def __init__(self, box_L_nm, n_atoms, n_sites, order_p, depth, precision="fp64", stream=None):
         self.h = mahi_create(box_L_nm, n_atoms, n_sites, order_p, depth, precision, stream)
         self.n_atoms, self.n_sites = int(n_atoms), int(n_sites)
+        self.n_lambdas = self.n_sites
 
     def set_charges(self, qA, qB, site_of_atom):
         mahi_set_charges(self.h, qA, qB, site_of_atom)
+        self.n_lambdas = self.n_sites
+
+    def set_forms(self, q_env, site_of_atom, forms):
+        mahi_set_forms(self.h, q_env, site_of_atom, forms)
+        self.n_lambdas = mahi_n_lambdas(self.h)
 
     def eval(self, x, lam):
         import torch
         E = torch.zeros(1, dtype=torch.float64, device=x.device)
         F = torch.empty_like(x)
-        g = torch.zeros(max(1, self.n_sites), dtype=torch.float64, device=x.device)
+        g = torch.zeros(max(1, self.n_lambdas), dtype=torch.float64, device=x.device)
         mahi_eval(self.h, x, lam, E, F, g)
-        return E, F, g[: self.n_sites]
+        return E, F, g[: self.n_lambdas]
 
     def potential(self, device="cuda"):
         import torch

@@ -45,7 +45,7 @@ static void free_all(mahi_ctx *h) {
                   h->m2l_list, h->m2l_off, h->site_ptr, h->site_atoms,
                   h->energy_part, h->site_energy, h->tc_ops, h->tc_partial, h->tc_msrc, h->tc_level_off, h->tc_units, h->tc_error, h->d_x_stage,
                   h->d_lam_stage, h->d_E_stage, h->d_dEdl_stage, h->d_F_stage, h->ops_lat_h3, h->L_h3,
-                  h->box_qd, h->vtmp, h->relD, h->phi_site, h->psi_site, h->site_slot, h->phi_part, h->d_level_off, h->tc_error_site};
+                  h->box_qd, h->vtmp, h->relD, h->phi_site, h->psi_site, h->site_slot, h->mf_q, h->mf_lam_off, h->phi_part, h->d_level_off, h->tc_error_site};
   for (void *b : bufs)
     if (b) cudaFree(b);
   for (int i = 0; i < 32; ++i)
@@ -346,8 +346,61 @@ int mahi_set_charges(mahi_t h, const double *qA, const double *qB, const int32_t
   if (!atoms.empty()) CK(cudaMemcpy(h->site_atoms, atoms.data(), atoms.size() * sizeof(int), cudaMemcpyHostToDevice));
   h->n_site_atoms = (int)atoms.size();
   h->charges_set = true;
+  h->multiform = false;  // mahi_set_forms sets it after calling this
   return MAHI_OK;
 }
+
+int mahi_set_forms(mahi_t h, const double *q_env, const int32_t *site_of_atom, const int32_t *forms_per_site,
+                   const double *q_forms) {
+  if (!h || !q_env || !site_of_atom || (h->S > 0 && (!forms_per_site || !q_forms))) return MAHI_ERR_INVALID_ARG;
+  const int64_t N = h->N;
+  const int S = h->S;
+  std::vector<int> cnt(S, 0), lam_off(S + 1, 0);
+  for (int sidx = 0; sidx < S; ++sidx) {
+    const int F = forms_per_site[sidx];
+    int m = 0;
+    while ((1 << m) < F) ++m;
+    if (F < 2 || F > 16 || (1 << m) != F) return MAHI_ERR_INVALID_ARG;
+    lam_off[sidx + 1] = lam_off[sidx] + m;
+  }
+  for (int64_t i = 0; i < N; ++i) {
+    const int sidx = site_of_atom[i];
+    if (!std::isfinite(q_env[i])) return MAHI_ERR_INVALID_ARG;
+    if (sidx < -1 || sidx >= S) return MAHI_ERR_BAD_SITE_MAP;
+    if (sidx >= 0) cnt[sidx]++;
+  }
+  for (int sidx = 0; sidx < S; ++sidx)
+    if (cnt[sidx] == 0 || cnt[sidx] > 32) return MAHI_ERR_BAD_SITE_MAP;
+  // the two-form layout with dq = 0: the evaluation rescales site charges itself
+  std::vector<double> qB(q_env, q_env + N);
+  int rc = mahi_set_charges(h, q_env, qB.data(), site_of_atom);
+  if (rc != MAHI_OK) return rc;
+  // per site atom (in site_atoms order) its charges in every form, padded to 16
+  std::vector<int> ptr(S + 1, 0);
+  for (int sidx = 0; sidx < S; ++sidx) ptr[sidx + 1] = ptr[sidx] + cnt[sidx];
+  std::vector<double> qf((size_t)std::max(1, ptr[S]) * 16, 0.0);
+  size_t off = 0;
+  for (int sidx = 0; sidx < S; ++sidx) {
+    const int F = forms_per_site[sidx], n = cnt[sidx];
+    for (int r = 0; r < F; ++r)
+      for (int a = 0; a < n; ++a) {
+        const double v = q_forms[off + (size_t)r * n + a];
+        if (!std::isfinite(v)) return MAHI_ERR_INVALID_ARG;
+        qf[(size_t)(ptr[sidx] + a) * 16 + r] = v;
+      }
+    off += (size_t)F * n;
+  }
+  if (h->mf_q) { cudaFree(h->mf_q); h->mf_q = nullptr; }
+  if (!h->mf_lam_off) CK(dalloc(&h->mf_lam_off, (S + 1) * sizeof(int)));
+  CK(dalloc(&h->mf_q, qf.size() * sizeof(double)));
+  CK(cudaMemcpy(h->mf_q, qf.data(), qf.size() * sizeof(double), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(h->mf_lam_off, lam_off.data(), (S + 1) * sizeof(int), cudaMemcpyHostToDevice));
+  h->n_lam = lam_off[S];
+  h->multiform = true;
+  return MAHI_OK;
+}
+
+int mahi_n_lambdas(mahi_t h) { return h ? (h->multiform ? h->n_lam : h->S) : MAHI_ERR_INVALID_ARG; }
 
 int mahi_eval(mahi_t h, const void *x, int32_t x_is_fp64, const double *lambda, double *energy, void *forces,
               double *dEdlambda) {
@@ -367,6 +420,7 @@ int mahi_backward(mahi_t h, const double *grad_energy, const void *forces, const
                   const double *lambda, int32_t x_is_fp64, void *dx, double *dlambda, double *dEdqA, double *dEdqB) {
   if (!h || !grad_energy) return MAHI_ERR_INVALID_ARG;
   if (!h->charges_set) return MAHI_ERR_STATE;
+  if (h->multiform) return MAHI_ERR_INVALID_ARG;  // two-form sites only
   if (dx && !forces) return MAHI_ERR_INVALID_ARG;
   if (dlambda && h->S > 0 && !dEdlambda) return MAHI_ERR_INVALID_ARG;
   if ((dEdqA || dEdqB) && h->S > 0 && !lambda) return MAHI_ERR_INVALID_ARG;
@@ -392,20 +446,21 @@ int mahi_eval_host(mahi_t h, const void *x_host, int32_t x_is_fp64, const double
     h->x_stage_fp64 = x_is_fp64 ? 1 : 0;
   }
   if (!h->d_lam_stage) {
-    CK(dalloc(&h->d_lam_stage, std::max(1, h->S) * 8));
+    CK(dalloc(&h->d_lam_stage, std::max(1, 4 * h->S) * 8));  // up to 4 lambdas per site (16 forms)
     CK(dalloc(&h->d_E_stage, 8));
-    CK(dalloc(&h->d_dEdl_stage, std::max(1, h->S) * 8));
+    CK(dalloc(&h->d_dEdl_stage, std::max(1, 4 * h->S) * 8));
   }
   cudaStream_t st = h->stream;
   CK(cudaMemcpyAsync(h->d_x_stage, x_host, xb, cudaMemcpyHostToDevice, st));
-  if (h->S > 0) CK(cudaMemcpyAsync(h->d_lam_stage, lambda_host, h->S * 8, cudaMemcpyHostToDevice, st));
+  const int nl = h->multiform ? h->n_lam : h->S;
+  if (nl > 0) CK(cudaMemcpyAsync(h->d_lam_stage, lambda_host, (size_t)nl * 8, cudaMemcpyHostToDevice, st));
   int r = enqueue_eval(h, h->d_x_stage, x_is_fp64 ? 1 : 0, h->d_lam_stage, h->d_E_stage, h->d_F_stage,
                        h->d_dEdl_stage);
   if (r != 0) return cuda_fail((cudaError_t)r, "mahi_eval_host");
   if (energy_host) CK(cudaMemcpyAsync(energy_host, h->d_E_stage, 8, cudaMemcpyDeviceToHost, st));
   if (forces_host) CK(cudaMemcpyAsync(forces_host, h->d_F_stage, xb, cudaMemcpyDeviceToHost, st));
   if (dEdlambda_host && h->S > 0)
-    CK(cudaMemcpyAsync(dEdlambda_host, h->d_dEdl_stage, h->S * 8, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(dEdlambda_host, h->d_dEdl_stage, (size_t)nl * 8, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   if (h->tc_error) {
     int flag = 0;

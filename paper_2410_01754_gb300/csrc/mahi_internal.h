@@ -110,11 +110,18 @@ struct mahi_ctx {
   double *phi_site = nullptr;                 // refined potential at site atoms
   double *psi_site = nullptr;                 // f sum_j A_ij D_j at site atoms (charge gradients)
   int *site_slot = nullptr;                   // N: position in site_atoms, -1 for environment atoms
+  // sites with 2^m forms (mahi_set_forms)
+  bool multiform = false;
+  double *mf_q = nullptr;                     // [site atom slot][16] charges per form
+  int *mf_lam_off = nullptr;                  // [S + 1] offsets of each site's lambdas
+  int n_lam = 0;                              // lambdas (and dE/dlambda entries) in total
   double *phi_part = nullptr;                 // its per-part partial sums
   int64_t *d_level_off = nullptr;             // device copy of level_off
   double *eta = nullptr, *eta_x = nullptr, *eta_y = nullptr, *eta_z = nullptr;  // degree 2p
   double site_aii = 0.0;                      // self term A_ii of the periodic kernel (1/nm)
   float site_theta = 0.40f;                   // separation ratio of the site-potential traversal
+  int tune_p2p_threads = 128;                 // autotuned launch shapes (mahi_autotune)
+  int tune_site_blocks = 0;                   // 0 = default count of blocks per site
   int *m2l_list = nullptr;                    // [8][189] offset ids
   int *m2l_off = nullptr;                     // [316][3]
   int *site_ptr = nullptr, *site_atoms = nullptr;

@@ -869,8 +869,8 @@ __device__ __forceinline__ double rinv_dd(double r2) {
   return y * fma(-0.5 * r2, y * y, 1.5);
 }
 
-template <typename T, typename FT>
-__global__ void __launch_bounds__(P2P_THREADS) k_p2p(int nb, double L, double fcoul, const int *__restrict__ leaf_start,
+template <typename T, typename FT, int NT>
+__global__ void __launch_bounds__(NT) k_p2p(int nb, double L, double fcoul, const int *__restrict__ leaf_start,
                                                      const typename V4<T>::type *__restrict__ part,
                                                      const int *__restrict__ perm, const double *__restrict__ mom,
                                                      T *__restrict__ phi_s, const T *__restrict__ grad_s,
@@ -879,9 +879,9 @@ __global__ void __launch_bounds__(P2P_THREADS) k_p2p(int nb, double L, double fc
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V *src = reinterpret_cast<V *>(smem_raw);
   __shared__ int nb_start[27], nb_pre[28];
-  __shared__ T red[P2P_THREADS][4], red2[P2P_THREADS][4];
+  __shared__ T red[NT][4], red2[NT][4];
   __shared__ T kc[5];
-  __shared__ double ered[P2P_THREADS / 32];
+  __shared__ double ered[NT / 32];
   const int leaf = blockIdx.x;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const T s = (T)(L / nb);
@@ -921,8 +921,8 @@ __global__ void __launch_bounds__(P2P_THREADS) k_p2p(int nb, double L, double fc
   // threads = (target pair, source chunk): every thread holds two targets, so
   // each staged source serves two pairs; as many chunks as fill the block
   const int npr = (nt + 1) >> 1;
-  const int nchunk = P2P_THREADS / max(1, min(npr, P2P_THREADS));
-  const int tgroup = P2P_THREADS / nchunk;
+  const int nchunk = NT / max(1, min(npr, NT));
+  const int tgroup = NT / nchunk;
   for (int t0 = 0; t0 < npr; t0 += tgroup) {
     const int tp = t0 + tid % tgroup, ck = tid / tgroup;
     const int ta0 = 2 * t0 + (tid % tgroup), ta1 = ta0 + min(tgroup, npr - t0);  // this round's targets
@@ -935,7 +935,7 @@ __global__ void __launch_bounds__(P2P_THREADS) k_p2p(int nb, double L, double fc
       __syncthreads();
       // stage the sources, shifted to this leaf's frame: warp w copies the
       // neighbour leaves w, w + 4, ...
-      for (int k = warp; k < 27; k += P2P_THREADS / 32) {
+      for (int k = warp; k < 27; k += NT / 32) {
         const int b = nb_pre[k] - s0, cnt = nb_pre[k + 1] - nb_pre[k];
         const T ox = (T)(k % 3 - 1) * s, oy = (T)((k / 3) % 3 - 1) * s, oz = (T)(k / 9 - 1) * s;
         for (int i = lane; i < cnt; i += 32) {
@@ -975,7 +975,7 @@ __global__ void __launch_bounds__(P2P_THREADS) k_p2p(int nb, double L, double fc
     red2[tid][0] = f1; red2[tid][1] = gx1; red2[tid][2] = gy1; red2[tid][3] = gz1;
     __syncthreads();
     const int nr = min(2 * tgroup, nt - 2 * t0);  // targets of this round
-    for (int tt = tid; tt < nr; tt += P2P_THREADS) {
+    for (int tt = tid; tt < nr; tt += NT) {
       // target ta = 2 t0 + tt: first of the pair tt (tt < w) or second of the
       // pair tt - w, w = pairs in this round
       const int w = min(tgroup, npr - t0);
@@ -1017,7 +1017,7 @@ __global__ void __launch_bounds__(P2P_THREADS) k_p2p(int nb, double L, double fc
   __syncthreads();
   if (tid == 0) {
     double v = 0;
-    for (int w = 0; w < P2P_THREADS / 32; ++w) v += ered[w];
+    for (int w = 0; w < NT / 32; ++w) v += ered[w];
     energy_part[leaf] = v;
   }
 }
@@ -1178,6 +1178,148 @@ __global__ void k_site(int S, double L, double fcoul, int Pmax, double aii, cons
       int ia = k3 / 3, a = k3 % 3;
       int i = site_atoms[b + ia];
       forces[3 * (size_t)i + a] = (FT)((double)forces[3 * (size_t)i + a] + fsh[wib][ia][a]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// 7b. Sites with 2^m forms (general formulation, Eq. "iter_ham_lambda";
+//     Appendix, Eqs. "lambda_list", "one_site_lambda").  Form rho of a site has
+//     weight lambda~_rho = prod_l (bit l of rho ? lambda_l : 1 - lambda_l); the
+//     scaled charge of a site atom is q~ = sum_rho lambda~_rho q^rho, and the
+//     per-site correction that turns E(q~) into the interpolated Hamiltonian is
+//       C = f/2 [sum_rho lambda~_rho G_rr - sum_rr' lambda~_r lambda~_r' G_rr'],
+//       G_rr' = q^r^T A q^r' over the site's atoms (A_ii = the self term);
+//     dE/dlambda_l = sum_rho d lambda~_rho/d lambda_l (q^rho . phi~ + f (G_rr/2 - (G lambda~)_r)),
+//     F_i -= f sum_{j != i} W_ij grad A(r_ij),  W_ij = sum_r lambda~_r q_i^r q_j^r - q~_i q~_j.
+// ---------------------------------------------------------------------------
+constexpr int kMfMaxForms = 16;
+constexpr int kMfMaxAtoms = 32;
+
+__device__ __forceinline__ void mf_weights(const double *__restrict__ lam, int m, double *w) {
+  for (int r = 0; r < (1 << m); ++r) {
+    double v = 1.0;
+    for (int l = 0; l < m; ++l) v *= ((r >> l) & 1) ? lam[l] : 1.0 - lam[l];
+    w[r] = v;
+  }
+}
+
+// q~ of the site atoms (overwrites what k_bin wrote for them)
+template <typename T>
+__global__ void k_mf_charges(int nsa, const int *__restrict__ site_atoms, const int *__restrict__ site_of,
+                             const int *__restrict__ lam_off, const double *__restrict__ lam,
+                             const double *__restrict__ qf, double *__restrict__ qt, typename V4<T>::type *vtmp) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nsa) return;
+  const int i = site_atoms[k], s = site_of[i], m = lam_off[s + 1] - lam_off[s];
+  double w[kMfMaxForms];
+  mf_weights(lam + lam_off[s], m, w);
+  double q = 0.0;
+  for (int r = 0; r < (1 << m); ++r) q += w[r] * qf[(size_t)k * kMfMaxForms + r];
+  qt[i] = q;
+  vtmp[i].w = (T)q;
+}
+
+template <typename XT, typename FT>
+__global__ void __launch_bounds__(32) k_site_mf(int S, double L, double fcoul, int Pmax, double aii,
+                                                const int *__restrict__ site_ptr, const int *__restrict__ site_atoms,
+                                                const XT *__restrict__ x, const int *__restrict__ lam_off,
+                                                const double *__restrict__ lam, const double *__restrict__ qf,
+                                                const double *__restrict__ phi_site, const double *__restrict__ eta,
+                                                const double *__restrict__ eta_x, const double *__restrict__ eta_y,
+                                                const double *__restrict__ eta_z, double *__restrict__ dEdl,
+                                                double *__restrict__ site_energy, FT *__restrict__ forces) {
+  __shared__ double A[kMfMaxAtoms][kMfMaxAtoms + 1];
+  __shared__ double gw[kMfMaxAtoms * (kMfMaxAtoms - 1) / 2][3];  // W_ij grad A(r_ij), r = x_i - x_j, i < j
+  __shared__ double qs[kMfMaxForms][kMfMaxAtoms], Tm[kMfMaxForms][kMfMaxAtoms], G[kMfMaxForms][kMfMaxForms];
+  __shared__ double w[kMfMaxForms], qtl[kMfMaxAtoms];
+  const int s = blockIdx.x, lane = threadIdx.x;
+  if (s >= S) return;
+  const int b = site_ptr[s], n = site_ptr[s + 1] - b, m = lam_off[s + 1] - lam_off[s], F = 1 << m;
+  const double c2 = 2.0 * kPi / (3.0 * L * L * L);
+  if (lane == 0) mf_weights(lam + lam_off[s], m, w);
+  for (int e = lane; e < F * n; e += 32) {
+    const int r = e / n, a = e % n;
+    qs[r][a] = qf[(size_t)(b + a) * kMfMaxForms + r];
+  }
+  __syncwarp();
+  for (int a = lane; a < n; a += 32) {
+    double v = 0.0;
+    for (int r = 0; r < F; ++r) v += w[r] * qs[r][a];
+    qtl[a] = v;
+    A[a][a] = aii;
+  }
+  __syncwarp();
+  // pair kernel: A_ij and W_ij grad A for every unordered pair
+  const int np = n * (n - 1) / 2;
+  for (int p = lane; p < np; p += 32) {
+    int ia = 0, rem = p;
+    while (rem >= n - 1 - ia) { rem -= n - 1 - ia; ++ia; }
+    const int ja = ia + 1 + rem;
+    double r[3], Aij, g[3];
+    site_pair_r(x, site_atoms[b + ia], site_atoms[b + ja], L, r);
+    site_pair_kernel(r, L, c2, Pmax, eta, eta_x, eta_y, eta_z, Aij, g);
+    A[ia][ja] = Aij;
+    A[ja][ia] = Aij;
+    double W = -qtl[ia] * qtl[ja];
+    for (int rr = 0; rr < F; ++rr) W += w[rr] * qs[rr][ia] * qs[rr][ja];
+    gw[p][0] = W * g[0]; gw[p][1] = W * g[1]; gw[p][2] = W * g[2];
+  }
+  __syncwarp();
+  // T = A q^r per form, then G = Q T^T
+  for (int e = lane; e < F * n; e += 32) {
+    const int r = e / n, a = e % n;
+    double v = 0.0;
+    for (int j = 0; j < n; ++j) v += A[a][j] * qs[r][j];
+    Tm[r][a] = v;
+  }
+  __syncwarp();
+  for (int e = lane; e < F * F; e += 32) {
+    const int r = e / F, r2 = e % F;
+    double v = 0.0;
+    for (int a = 0; a < n; ++a) v += qs[r][a] * Tm[r2][a];
+    G[r][r2] = v;
+  }
+  __syncwarp();
+  if (lane == 0) {
+    double c = 0.0;
+    for (int r = 0; r < F; ++r) {
+      double gwr = 0.0;
+      for (int r2 = 0; r2 < F; ++r2) gwr += G[r][r2] * w[r2];
+      c += w[r] * (G[r][r] - gwr);
+    }
+    site_energy[s] = 0.5 * fcoul * c;
+  }
+  // dE/dlambda_l, one lambda per lane
+  if (dEdl)
+    for (int l = lane; l < m; l += 32) {
+      const double *lm = lam + lam_off[s];
+      double tot = 0.0;
+      for (int r = 0; r < F; ++r) {
+        double dw = ((r >> l) & 1) ? 1.0 : -1.0;
+        for (int k = 0; k < m; ++k)
+          if (k != l) dw *= ((r >> k) & 1) ? lm[k] : 1.0 - lm[k];
+        double qphi = 0.0, gwr = 0.0;
+        for (int a = 0; a < n; ++a) qphi += qs[r][a] * phi_site[b + a];
+        for (int r2 = 0; r2 < F; ++r2) gwr += G[r][r2] * w[r2];
+        tot += dw * (qphi + fcoul * (0.5 * G[r][r] - gwr));
+      }
+      dEdl[lam_off[s] + l] = tot;
+    }
+  // forces: gather the pair terms of each atom in a fixed order
+  if (forces)
+    for (int ia = lane; ia < n; ia += 32) {
+      double f0 = 0.0, f1 = 0.0, f2 = 0.0;
+      for (int ja = 0; ja < n; ++ja) {
+        if (ja == ia) continue;
+        const int lo = min(ia, ja), hi = max(ia, ja);
+        const int p = lo * (2 * n - lo - 1) / 2 + (hi - lo - 1);
+        const double sg = ia == lo ? 1.0 : -1.0;  // grad A is odd in r
+        f0 -= sg * gw[p][0]; f1 -= sg * gw[p][1]; f2 -= sg * gw[p][2];
+      }
+      const int i = site_atoms[b + ia];
+      forces[3 * (size_t)i + 0] = (FT)((double)forces[3 * (size_t)i + 0] + fcoul * f0);
+      forces[3 * (size_t)i + 1] = (FT)((double)forces[3 * (size_t)i + 1] + fcoul * f1);
+      forces[3 * (size_t)i + 2] = (FT)((double)forces[3 * (size_t)i + 2] + fcoul * f2);
     }
 }
 
@@ -1799,6 +1941,19 @@ static inline void mark(mahi_ctx *h, int stage) {
   }
 }
 
+template <typename T, typename XT, int NT>
+static cudaError_t launch_p2p(mahi_ctx *h, int nleaf, int nb, const double *mom, XT *forces, cudaStream_t st) {
+  using V = typename V4<T>::type;
+  const size_t sm = sizeof(V) * P2P_MAXSRC;
+  if (sm > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_p2p<T, XT, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+  }
+  k_p2p<T, XT, NT><<<nleaf, NT, sm, st>>>(nb, h->L, coulomb_constant(), h->leaf_start, (const V *)h->part, h->perm,
+                                          mom, (T *)h->phi_s, (const T *)h->grad_s, forces, h->energy_part);
+  return cudaGetLastError();
+}
+
 template <typename T, typename XT>
 static cudaError_t eval_t(mahi_ctx *h, const XT *x, const double *lam, double *energy, XT *forces, double *dEdl) {
   using V = typename V4<T>::type;
@@ -1820,6 +1975,11 @@ static cudaError_t eval_t(mahi_ctx *h, const XT *x, const double *lam, double *e
                                                       h->leaf_of, h->slot, h->leaf_count, h->qt, (V *)h->vtmp, h->relD);
   }
   h->launches += 1;
+  if (h->multiform && h->n_site_atoms > 0) {
+    k_mf_charges<T><<<(h->n_site_atoms + 127) / 128, 128, 0, st>>>(h->n_site_atoms, h->site_atoms, h->site_of,
+                                                                    h->mf_lam_off, lam, h->mf_q, h->qt, (V *)h->vtmp);
+    h->launches += 1;
+  }
   mark(h, 1);
   k_scan<<<1, 1024, 0, st>>>(h->leaf_count, nleaf, h->leaf_start);
   int gb = (int)((N + 255) / 256);
@@ -1890,11 +2050,12 @@ static cudaError_t eval_t(mahi_ctx *h, const XT *x, const double *lam, double *e
   }
   mark(h, 8);
   {
-    size_t sm = sizeof(V) * P2P_MAXSRC;
-    if (sm > 48 * 1024) MAHI_CK(cudaFuncSetAttribute(k_p2p<T, XT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    k_p2p<T, XT><<<nleaf, P2P_THREADS, sm, st>>>(nb, h->L, coulomb_constant(), h->leaf_start, (const V *)h->part,
-                                                 h->perm, mom, (T *)h->phi_s, (const T *)h->grad_s, forces,
-                                                 h->energy_part);
+    // threads per target leaf: 128 unless the autotuner picked another
+    switch (h->tune_p2p_threads) {
+      case 64: MAHI_CK((launch_p2p<T, XT, 64>(h, nleaf, nb, mom, forces, st))); break;
+      case 256: MAHI_CK((launch_p2p<T, XT, 256>(h, nleaf, nb, mom, forces, st))); break;
+      default: MAHI_CK((launch_p2p<T, XT, 128>(h, nleaf, nb, mom, forces, st))); break;
+    }
     h->launches += 1;
     MAHI_CK(cudaGetLastError());
   }
@@ -1906,16 +2067,24 @@ static cudaError_t eval_t(mahi_ctx *h, const XT *x, const double *lam, double *e
     const size_t budget = 72 * 1024;
     const int nbmax = (int)std::max<size_t>(8, std::min<size_t>(kSiteBatchMax, (budget - fixed) / (sizeof(T) * lds)));
     const size_t smp = fixed + sizeof(T) * nbmax * lds;
-    const int G = std::max(1, std::min(kSiteChunksMax, (4 * 3 * h->num_sms + h->S - 1) / std::max(1, h->S)));
+    // blocks per site: about 4 x 3 per SM over all sites, unless the autotuner picked a count
+    const int G = h->tune_site_blocks > 0
+                      ? std::min(kSiteChunksMax, h->tune_site_blocks)
+                      : std::max(1, std::min(kSiteChunksMax, (4 * 3 * h->num_sms + h->S - 1) / std::max(1, h->S)));
     MAHI_CK(launch_site_phi<T>(P, G, smp, st, h->S, G, h->site_ptr, h->site_atoms, h->d, P, ld, lds, nbmax, h->L,
                                h->d_level_off, h->leaf_start, h->inv_perm, (const V *)h->part, M, h->box_qd,
                                mom, h->L_h3, h->phi_part, h->tc_error_site, h->site_theta));
     k_site_phi_sum<<<(h->n_site_atoms + 127) / 128, 128, 0, st>>>(h->n_site_atoms, G, coulomb_constant(),
                                                                    h->phi_part, h->phi_site);
-    k_site<T, XT, XT><<<(h->S + 3) / 4, 128, 0, st>>>(h->S, h->L, coulomb_constant(), kSiteDegree, h->site_aii,
-                                                      h->site_ptr,
-                                                      h->site_atoms, x, h->dq, lam, h->phi_site, h->eta, h->eta_x,
-                                                      h->eta_y, h->eta_z, dEdl, h->site_energy, forces, h->psi_site);
+    if (h->multiform)
+      k_site_mf<XT, XT><<<h->S, 32, 0, st>>>(h->S, h->L, coulomb_constant(), kSiteDegree, h->site_aii, h->site_ptr,
+                                             h->site_atoms, x, h->mf_lam_off, lam, h->mf_q, h->phi_site, h->eta,
+                                             h->eta_x, h->eta_y, h->eta_z, dEdl, h->site_energy, forces);
+    else
+      k_site<T, XT, XT><<<(h->S + 3) / 4, 128, 0, st>>>(h->S, h->L, coulomb_constant(), kSiteDegree, h->site_aii,
+                                                        h->site_ptr, h->site_atoms, x, h->dq, lam, h->phi_site, h->eta,
+                                                        h->eta_x, h->eta_y, h->eta_z, dEdl, h->site_energy, forces,
+                                                        h->psi_site);
     h->launches += 3;
   }
   if (energy) {
