@@ -870,7 +870,7 @@ __device__ __forceinline__ double rinv_dd(double r2) {
 }
 
 template <typename T, typename FT, int NT>
-__global__ void __launch_bounds__(NT) k_p2p(int nb, double L, double fcoul, const int *__restrict__ leaf_start,
+__global__ void __launch_bounds__(NT) k_p2p(int nb, double L, T s_leaf, T fc_t, const int *__restrict__ leaf_start,
                                                      const typename V4<T>::type *__restrict__ part,
                                                      const int *__restrict__ perm, const double *__restrict__ mom,
                                                      T *__restrict__ phi_s, const T *__restrict__ grad_s,
@@ -884,7 +884,7 @@ __global__ void __launch_bounds__(NT) k_p2p(int nb, double L, double fcoul, cons
   __shared__ double ered[NT / 32];
   const int leaf = blockIdx.x;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const T s = (T)(L / nb);
+  const T s = s_leaf;  // leaf edge (the host divides once)
   const int ix = (int)d_compact(leaf), iy = (int)d_compact(leaf >> 1), iz = (int)d_compact(leaf >> 2);
   if (tid < 27) {
     int dx = tid % 3 - 1, dy = (tid / 3) % 3 - 1, dz = tid / 9 - 1;
@@ -916,7 +916,7 @@ __global__ void __launch_bounds__(NT) k_p2p(int nb, double L, double fcoul, cons
   __syncthreads();
   const int tb = leaf_start[leaf], te = leaf_start[leaf + 1], nt = te - tb;
   const int nsrc_total = nb_pre[27];
-  const T fc = (T)fcoul;
+  const T fc = fc_t;
   SiteAccE<T> e_acc;
   // threads = (target pair, source chunk): every thread holds two targets, so
   // each staged source serves two pairs; as many chunks as fill the block
@@ -1847,11 +1847,17 @@ __global__ void k_site_phi_sum(int nsa, int nparts, double fcoul, const double *
   phi_site[k] = fcoul * v;
 }
 
-__global__ void k_final_energy(const double *__restrict__ epart, int nb, const double *__restrict__ site_e, int S,
-                               double *__restrict__ out) {
-  double v = 0;
-  for (int i = threadIdx.x; i < nb; i += blockDim.x) v += epart[i];
-  for (int i = threadIdx.x; i < S; i += blockDim.x) v += site_e[i];
+__global__ void __launch_bounds__(1024) k_final_energy(const double *__restrict__ epart, int nb,
+                                                      const double *__restrict__ site_e, int S, double *__restrict__ out) {
+  // four independent partial sums per thread (loads in flight together),
+  // combined in a fixed order
+  double v4[4] = {0, 0, 0, 0};
+  const int stride = blockDim.x;
+  int i = threadIdx.x, k = 0;
+#pragma unroll 8
+  for (; i < nb; i += stride, ++k) v4[k & 3] += epart[i];
+  double v = (v4[0] + v4[1]) + (v4[2] + v4[3]);
+  for (int j = threadIdx.x; j < S; j += stride) v += site_e[j];
   __shared__ double red[32];
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffff, v, o);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
@@ -1949,7 +1955,8 @@ static cudaError_t launch_p2p(mahi_ctx *h, int nleaf, int nb, const double *mom,
     cudaError_t e = cudaFuncSetAttribute(k_p2p<T, XT, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
   }
-  k_p2p<T, XT, NT><<<nleaf, NT, sm, st>>>(nb, h->L, coulomb_constant(), h->leaf_start, (const V *)h->part, h->perm,
+  k_p2p<T, XT, NT><<<nleaf, NT, sm, st>>>(nb, h->L, (T)(h->L / nb), (T)coulomb_constant(), h->leaf_start,
+                                          (const V *)h->part, h->perm,
                                           mom, (T *)h->phi_s, (const T *)h->grad_s, forces, h->energy_part);
   return cudaGetLastError();
 }
@@ -2088,7 +2095,7 @@ static cudaError_t eval_t(mahi_ctx *h, const XT *x, const double *lam, double *e
     h->launches += 3;
   }
   if (energy) {
-    k_final_energy<<<1, 256, 0, st>>>(h->energy_part, nleaf, h->site_energy, h->S, energy);
+    k_final_energy<<<1, 1024, 0, st>>>(h->energy_part, nleaf, h->site_energy, h->S, energy);
     h->launches += 1;
   }
   MAHI_CK(cudaGetLastError());
