@@ -173,7 +173,13 @@ int mahi_create(double box_L_nm, int64_t n_atoms, int32_t n_sites, int32_t order
   h->n_moment_blocks = (int)std::min<int64_t>(4 * 152, (N + 255) / 256);
   h->gemm_ws_elems = gemm_workspace_elems(h->d, h->ld, h->num_sms);
   if (h->gemm_ws_elems) AL(h->gemm_ws, h->gemm_ws_elems * ts);
-  AL(h->energy_part, (size_t)h->nleaf * 8); AL(h->site_energy, (size_t)std::max(1, n_sites) * 8);
+  // leaf energy partials, then the final sum's block sums and its ticket
+  AL(h->energy_part, ((size_t)h->nleaf + kFinalBlocks + 1) * 8);
+  AL(h->site_energy, (size_t)std::max(1, n_sites) * 8);
+  {
+    cudaError_t e0 = cudaMemset(h->energy_part + h->nleaf + kFinalBlocks, 0, 8);
+    if (e0 != cudaSuccess) return fail(e0, "memset");
+  }
   {
     cudaError_t e = cudaMemset(h->Lexp, 0, (size_t)h->nbox_total * h->ld * ts);
     if (e != cudaSuccess) return fail(e, "memset");

@@ -21,6 +21,7 @@ constexpr int kLatticeShell = 3;       // images |n|_inf <= 3 exactly, beyond by
 constexpr int kSiteDegree = 40;        // degree of H_1 in the per-site correction
 constexpr int kSiteChunksMax = 16;   // blocks sharing one site in the site-potential traversal
 constexpr double kPi = 3.14159265358979323846264338327950288;
+constexpr int kFinalBlocks = 64;  // blocks of the final energy sum
 
 // Coulomb constant N_A e^2 / (4 pi eps0) in kJ mol^-1 nm e^-2 (CODATA 2018).
 double coulomb_constant();

@@ -77,6 +77,7 @@ template <typename T, class CB>
 __device__ __forceinline__ void rt_columns(int P, T x, T y, T z, CB cb) {
   const T r2 = x * x + y * y + z * z;
   T dre = T(1), dim = T(0);
+#pragma unroll
   for (int m = 0; m <= P; ++m) {
     if (m > 0) {
       const T f = -tab_diag<T>(m);
@@ -85,6 +86,7 @@ __device__ __forceinline__ void rt_columns(int P, T x, T y, T z, CB cb) {
     }
     T pr = T(0), pi = T(0), cr = dre, ci = dim;
     cb(m, m, cr, ci);
+#pragma unroll
     for (int l = m + 1; l <= P; ++l) {
       const int k = l * (l + 1) / 2 + m;
       const T a = tab_a<T>(k) * z, b = tab_b<T>(k) * r2;
@@ -292,16 +294,11 @@ __global__ void k_scatter(int64_t N, const int *__restrict__ leaf_of, const int 
   perm_tmp[pos] = (int)i;
 }
 
-// Order the atoms of every leaf by original index (deterministic layout), then
-// the FP64 charge Q, dipole D and second moment T = sum q |x - c|^2 of the leaf
-// about its centre c, summed in that order.  These feed the l <= 1 terms of the
-// site-atom potential and, through exact translation up the tree, the
-// dipole / background term of the periodic kernel.
+// Order the atoms of every leaf by original index (deterministic layout).
 template <typename T>
 __global__ void k_leaf_sort(int nleaf, const int *__restrict__ leaf_start, const typename V4<T>::type *__restrict__ part_tmp,
-                            const int *__restrict__ perm_tmp, const double *__restrict__ qt,
-                            const double *__restrict__ relD, typename V4<T>::type *__restrict__ part,
-                            int *__restrict__ perm, int *__restrict__ inv_perm, double *__restrict__ qd) {
+                            const int *__restrict__ perm_tmp, typename V4<T>::type *__restrict__ part,
+                            int *__restrict__ perm, int *__restrict__ inv_perm) {
   int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (warp >= nleaf) return;
   int b = leaf_start[warp], e = leaf_start[warp + 1];
@@ -312,9 +309,24 @@ __global__ void k_leaf_sort(int nleaf, const int *__restrict__ leaf_start, const
     perm[b + rank] = key;
     inv_perm[key] = b + rank;
   }
-  __syncwarp();
+}
+
+// The FP64 charge Q, dipole D and second moment T = sum q |x - c|^2 of every
+// leaf about its centre c, summed over its atoms in the sorted order.  These
+// feed the l <= 1 terms of the site-atom potential and, through exact
+// translation up the tree, the dipole / background term of the periodic
+// kernel.  One thread per leaf: FP64 issues at a small fraction of the FP32
+// rate on GB300, and a warp-wide FP64 reduction per leaf would cost far more
+// instructions than the sums themselves.
+__global__ void k_leaf_moments(int nleaf, const int *__restrict__ leaf_start, const int *__restrict__ perm,
+                               const double *__restrict__ qt, const double *__restrict__ relD,
+                               double *__restrict__ qd) {
+  const int leaf = blockIdx.x * blockDim.x + threadIdx.x;
+  if (leaf >= nleaf) return;
+  const int b = leaf_start[leaf], e = leaf_start[leaf + 1];
   double v[5] = {0, 0, 0, 0, 0};
-  for (int a = b + lane; a < e; a += 32) {
+#pragma unroll 4
+  for (int a = b; a < e; ++a) {
     const int i = perm[a];
     const double q = qt[i], rx = relD[3 * (size_t)i], ry = relD[3 * (size_t)i + 1], rz = relD[3 * (size_t)i + 2];
     v[0] += q;
@@ -324,10 +336,7 @@ __global__ void k_leaf_sort(int nleaf, const int *__restrict__ leaf_start, const
     v[4] = fma(q, rx * rx + ry * ry + rz * rz, v[4]);
   }
 #pragma unroll
-  for (int k = 0; k < 5; ++k) {
-    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffff, v[k], o);
-    if (lane == 0) qd[(size_t)warp * kQD + k] = v[k];
-  }
+  for (int k = 0; k < 5; ++k) qd[(size_t)leaf * kQD + k] = v[k];
 }
 
 // ---------------------------------------------------------------------------
@@ -372,10 +381,12 @@ __global__ void k_p2m(int nleaf, int P, int ld, T inv_s, const int *__restrict__
 // K coefficients q conj(R_lm(u)) of its atom into a row of a 32 x Ks buffer
 // (Ks = K rounded up to odd, so row writes do not share banks), then lane j
 // sums the columns j, j + 32, ... over the rows in row order.  Same sums in the
-// same order for every run; no shuffle chains.
-template <typename T>
-__global__ void k_p2m_t(int nleaf, int P, int ld, int Ks, T inv_s, const int *__restrict__ leaf_start,
+// same order for every run; no shuffle chains.  PP > 0 makes the order a
+// compile-time constant (the harmonic recursion is then unrolled).
+template <typename T, int PP>
+__global__ void k_p2m_t(int nleaf, int Pr, int ld, int Ks, T inv_s, const int *__restrict__ leaf_start,
                         const typename V4<T>::type *__restrict__ part, T *__restrict__ M) {
+  const int P = PP > 0 ? PP : Pr;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int warp = blockIdx.x * (blockDim.x >> 5) + wib;
@@ -631,12 +642,22 @@ __global__ void __launch_bounds__(256) k_gemm(int M, int N, int Kd, const T *__r
   }
 }
 
+// The coarse levels have few elements and up to ~80 splits, so the loads of
+// eight splits are issued together (the sum itself stays in split order).
 template <typename T, bool ACC>
 __global__ void k_gemm_reduce(int M, int N, int nz, const T *__restrict__ W, T *__restrict__ C, int ldc) {
   const int64_t n = (int64_t)M * N;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
     T v = W[e];
-    for (int z = 1; z < nz; ++z) v += W[(size_t)z * n + e];
+    int z = 1;
+    for (; z + 8 <= nz; z += 8) {
+      T w[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) w[u] = W[(size_t)(z + u) * n + e];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v += w[u];
+    }
+    for (; z < nz; ++z) v += W[(size_t)z * n + e];
     T *c = C + (e / N) * ldc + (e % N);
     if (ACC) *c += v;
     else *c = v;
@@ -738,12 +759,12 @@ __global__ void k_lattice(int K, int ld, double L, const double *__restrict__ la
 //  d/dy R_lm = -i (R_{l-1,m-1} + R_{l-1,m+1})/2 and the basis scale ratios).
 template <typename T>
 __device__ __forceinline__ void gradient_row_coeffs(int P, const T *c, T *cx, T *cy, T *cz, int lane = 0,
-                                                    int nlanes = 1) {
+                                                    int nlanes = 1, int stride = 1) {
   auto get = [&](int l, int m, T &re, T &im) {
     if (l < 0 || m > l || -m > l) { re = T(0); im = T(0); return; }
     int am = m < 0 ? -m : m;
-    if (am == 0) { re = c[l * l]; im = T(0); }
-    else { re = c[l * l + 2 * am - 1]; im = c[l * l + 2 * am]; }
+    if (am == 0) { re = c[stride * (l * l)]; im = T(0); }
+    else { re = c[stride * (l * l + 2 * am - 1)]; im = c[stride * (l * l + 2 * am)]; }
     if (m < 0) { im = -im; if (am & 1) { re = -re; im = -im; } }
   };
   // entries (l, m), 0 <= m <= l < P, in triangular order t = l(l+1)/2 + m,
@@ -762,47 +783,56 @@ __device__ __forceinline__ void gradient_row_coeffs(int P, const T *c, T *cx, T 
     zr *= fz; zi *= fz; ar *= fa; ai *= fa; br *= fb; bi *= fb;
     T xr = T(0.5) * (ar - br), xi = T(0.5) * (ai - bi);
     T yr = T(-0.5) * (bi + ai), yi = T(0.5) * (br + ar);
-    if (m == 0) { cz[l * l] = zr; cx[l * l] = xr; cy[l * l] = yr; }
+    if (m == 0) { cz[stride * (l * l)] = zr; cx[stride * (l * l)] = xr; cy[stride * (l * l)] = yr; }
     else {
-      int k = l * l + 2 * m - 1;
-      cz[k] = zr; cz[k + 1] = zi; cx[k] = xr; cx[k + 1] = xi; cy[k] = yr; cy[k + 1] = yi;
+      const int k = stride * (l * l + 2 * m - 1);
+      cz[k] = zr; cz[k + stride] = zi; cx[k] = xr; cx[k + stride] = xi; cy[k] = yr; cy[k + stride] = yi;
     }
   }
 }
 
-template <typename T>
-__global__ void k_l2p(int nleaf, int P, int ld, T s, const int *__restrict__ leaf_start,
+// The leaf's local coefficients and the three gradient rows are kept
+// interleaved per coefficient, so one vector load of shared memory serves the
+// potential and the gradient of a term; PP > 0 makes the order a compile-time
+// constant (the harmonic recursion is then unrolled; six blocks of four warps
+// per SM measured fastest, with a few registers spilled).
+template <typename T, int PP>
+__global__ void __launch_bounds__(128, 6) k_l2p(int nleaf, int Pr, int ld, T s, const int *__restrict__ leaf_start,
                       const typename V4<T>::type *__restrict__ part, const T *__restrict__ Lleaf,
                       T *__restrict__ phi, T *__restrict__ grad) {
+  using V = typename V4<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int P = PP > 0 ? PP : Pr;
   const int K = (P + 1) * (P + 1);
   const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  T *c = reinterpret_cast<T *>(smem_raw) + (size_t)wib * 4 * K;
-  T *cx = c + K, *cy = cx + K, *cz = cy + K;
+  V *cc = reinterpret_cast<V *>(smem_raw) + (size_t)wib * K;  // {c, cx, cy, cz} per coefficient
+  T *cf = reinterpret_cast<T *>(cc);
   int warp = blockIdx.x * (blockDim.x >> 5) + wib;
   if (warp >= nleaf) return;
   const T *Lv = Lleaf + (size_t)warp * ld;
-  for (int k = lane; k < K; k += 32) c[k] = Lv[k];
+  for (int k = lane; k < K; k += 32) cf[4 * k] = Lv[k];
   __syncwarp();
-  gradient_row_coeffs<T>(P, c, cx, cy, cz, lane, 32);
+  gradient_row_coeffs<T>(P, cf, cf + 1, cf + 2, cf + 3, lane, 32, 4);
   __syncwarp();
   int b = leaf_start[warp], e = leaf_start[warp + 1];
   T inv_s = T(1) / s;
   for (int a = b + lane; a < e; a += 32) {
-    typename V4<T>::type pt = part[a];
+    V pt = part[a];
     T f = 0, gx = 0, gy = 0, gz = 0;
     // sum over m of X_lm conj(R_lm) = X_l0 R_l0 + 2 sum_{m>0} (Xr Rr + Xi Ri)
     rt_columns<T>(P, pt.x * inv_s, pt.y * inv_s, pt.z * inv_s, [&](int l, int m, T re, T im) {
       const int k = ridx(l, m);
+      const V c0 = cc[k];
       if (m == 0) {
-        f += c[k] * re;
-        if (l < P) { gx += cx[k] * re; gy += cy[k] * re; gz += cz[k] * re; }
+        f += c0.x * re;
+        if (l < P) { gx += c0.y * re; gy += c0.z * re; gz += c0.w * re; }
       } else {
-        f += T(2) * (c[k] * re + c[k + 1] * im);
+        const V c1 = cc[k + 1];
+        f += T(2) * (c0.x * re + c1.x * im);
         if (l < P) {
-          gx += T(2) * (cx[k] * re + cx[k + 1] * im);
-          gy += T(2) * (cy[k] * re + cy[k + 1] * im);
-          gz += T(2) * (cz[k] * re + cz[k + 1] * im);
+          gx += T(2) * (c0.y * re + c1.y * im);
+          gy += T(2) * (c0.z * re + c1.z * im);
+          gz += T(2) * (c0.w * re + c1.w * im);
         }
       }
     });
@@ -861,7 +891,9 @@ __device__ __forceinline__ float rinv(float r2) {
 // 2^-22, under the single-precision rounding of the accumulated sums)
 __device__ __forceinline__ float rinv_fast(float r2) { return rsqrtf(r2); }
 __device__ __forceinline__ double rinv_fast(double r2) { return 1.0 / sqrt(r2); }
-constexpr int P2P_MAXSRC = 2048;
+// staged sources per pass (16 KB in single precision): leaves of ~30 atoms
+// give ~800 sources, so one pass is the rule and more blocks fit on an SM
+constexpr int P2P_MAXSRC = 1024;
 // FP64 1/sqrt(r2): single-precision seed and one FP64 Newton-Raphson step; the
 // seed's relative error e (about 2^-23) becomes 1.5 e^2 after the step
 __device__ __forceinline__ double rinv_dd(double r2) {
@@ -870,7 +902,7 @@ __device__ __forceinline__ double rinv_dd(double r2) {
 }
 
 template <typename T, typename FT, int NT>
-__global__ void __launch_bounds__(NT) k_p2p(int nb, double L, T s_leaf, T fc_t, const int *__restrict__ leaf_start,
+__global__ void __launch_bounds__(NT) k_p2p(int nb, T c2, T half_L, T s_leaf, T fc_t, const int *__restrict__ leaf_start,
                                                      const typename V4<T>::type *__restrict__ part,
                                                      const int *__restrict__ perm, const double *__restrict__ mom,
                                                      T *__restrict__ phi_s, const T *__restrict__ grad_s,
@@ -895,18 +927,22 @@ __global__ void __launch_bounds__(NT) k_p2p(int nb, double L, T s_leaf, T fc_t, 
   if (tid == 32) {
     // dipole / background term of the periodic kernel, (2 pi/3V) sum_j q_j |x_i - x_j|^2
     //   = c2 (Q |a|^2 - 2 a.D + T) with a = x_i - box centre = lc + m (lc: this
-    // leaf's centre, m: the stored offset); per leaf in FP64:
-    //   K0 = c2 (Q |lc|^2 - 2 lc.D + T), K1 = 2 c2 (Q lc - D), K2 = c2 Q,
-    // so the term is K0 + K1.m + K2 |m|^2 and its gradient K1 + 2 K2 m
-    const double Q = mom[0], Dx = mom[1], Dy = mom[2], Dz = mom[3], Tm = mom[4];
-    const double c2 = 2.0 * kPi / (3.0 * L * L * L);
-    const double lcx = (ix + 0.5) * (L / nb) - 0.5 * L, lcy = (iy + 0.5) * (L / nb) - 0.5 * L,
-                 lcz = (iz + 0.5) * (L / nb) - 0.5 * L;
-    kc[0] = (T)(c2 * (Q * (lcx * lcx + lcy * lcy + lcz * lcz) - 2.0 * (lcx * Dx + lcy * Dy + lcz * Dz) + Tm));
-    kc[1] = (T)(2.0 * c2 * (Q * lcx - Dx));
-    kc[2] = (T)(2.0 * c2 * (Q * lcy - Dy));
-    kc[3] = (T)(2.0 * c2 * (Q * lcz - Dz));
-    kc[4] = (T)(c2 * Q);
+    // leaf's centre, m: the stored offset); per leaf, in the working precision
+    // from the FP64 box moments (c2 = 2 pi / 3V from the host):
+    //   K0 = A |lc|^2 - B.lc + C, K1 = 2 A lc - B, K2 = A,
+    //   A = c2 Q, B = 2 c2 D, C = c2 T,
+    // so the term is K0 + K1.m + K2 |m|^2 and its gradient K1 + 2 K2 m.  (No
+    // FP64 arithmetic per leaf: on GB300 FP64 issues at a small fraction of the
+    // FP32 rate, and one thread of every block would hold the others.)
+    const T A = c2 * (T)mom[0], C = c2 * (T)mom[4];
+    const T Bx = T(2) * c2 * (T)mom[1], By = T(2) * c2 * (T)mom[2], Bz = T(2) * c2 * (T)mom[3];
+    const T lcx = ((T)ix + T(0.5)) * s - half_L, lcy = ((T)iy + T(0.5)) * s - half_L,
+            lcz = ((T)iz + T(0.5)) * s - half_L;
+    kc[0] = A * (lcx * lcx + lcy * lcy + lcz * lcz) - (Bx * lcx + By * lcy + Bz * lcz) + C;
+    kc[1] = T(2) * A * lcx - Bx;
+    kc[2] = T(2) * A * lcy - By;
+    kc[3] = T(2) * A * lcz - Bz;
+    kc[4] = A;
   }
   __syncthreads();
   if (tid == 0) {
@@ -1847,25 +1883,41 @@ __global__ void k_site_phi_sum(int nsa, int nparts, double fcoul, const double *
   phi_site[k] = fcoul * v;
 }
 
-__global__ void __launch_bounds__(1024) k_final_energy(const double *__restrict__ epart, int nb,
-                                                      const double *__restrict__ site_e, int S, double *__restrict__ out) {
-  // four independent partial sums per thread (loads in flight together),
-  // combined in a fixed order
-  double v4[4] = {0, 0, 0, 0};
-  const int stride = blockDim.x;
-  int i = threadIdx.x, k = 0;
-#pragma unroll 8
-  for (; i < nb; i += stride, ++k) v4[k & 3] += epart[i];
-  double v = (v4[0] + v4[1]) + (v4[2] + v4[3]);
-  for (int j = threadIdx.x; j < S; j += stride) v += site_e[j];
-  __shared__ double red[32];
+// Total energy: kFinalBlocks blocks each sum a contiguous range of the leaf
+// partials (block 0 also the site terms) in a fixed order; the block that
+// finishes last adds the block sums in block order and re-arms the ticket.
+// FP64 issues at a small fraction of the FP32 rate on GB300, so the sum is
+// spread over many SMs instead of one.
+__global__ void __launch_bounds__(256) k_final_energy(const double *__restrict__ epart, int nb,
+                                                     const double *__restrict__ site_e, int S, double *blk,
+                                                     unsigned int *ticket, double *__restrict__ out) {
+  const int per = (nb + (int)gridDim.x - 1) / (int)gridDim.x;
+  const int b0 = min(nb, (int)blockIdx.x * per), b1 = min(nb, b0 + per);
+  double v2[2] = {0, 0};
+  int k = 0;
+  for (int i = b0 + (int)threadIdx.x; i < b1; i += blockDim.x, ++k) v2[k & 1] += epart[i];
+  double v = v2[0] + v2[1];
+  if (blockIdx.x == 0)
+    for (int j = threadIdx.x; j < S; j += blockDim.x) v += site_e[j];
+  __shared__ double red[8];
+  __shared__ bool last;
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffff, v, o);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
   __syncthreads();
   if (threadIdx.x == 0) {
     double s = 0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
-    *out = s;
+    blk[blockIdx.x] = s;
+    __threadfence();
+    last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    __threadfence();
+    double e = 0;
+    for (int b = 0; b < (int)gridDim.x; ++b) e += reinterpret_cast<volatile double *>(blk)[b];
+    *out = e;
+    *ticket = 0u;
   }
 }
 
@@ -1955,7 +2007,8 @@ static cudaError_t launch_p2p(mahi_ctx *h, int nleaf, int nb, const double *mom,
     cudaError_t e = cudaFuncSetAttribute(k_p2p<T, XT, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
   }
-  k_p2p<T, XT, NT><<<nleaf, NT, sm, st>>>(nb, h->L, (T)(h->L / nb), (T)coulomb_constant(), h->leaf_start,
+  k_p2p<T, XT, NT><<<nleaf, NT, sm, st>>>(nb, (T)(2.0 * kPi / (3.0 * h->L * h->L * h->L)), (T)(0.5 * h->L),
+                                          (T)(h->L / nb), (T)coulomb_constant(), h->leaf_start,
                                           (const V *)h->part, h->perm,
                                           mom, (T *)h->phi_s, (const T *)h->grad_s, forces, h->energy_part);
   return cudaGetLastError();
@@ -1993,9 +2046,10 @@ static cudaError_t eval_t(mahi_ctx *h, const XT *x, const double *lam, double *e
   k_scatter<T><<<gb, 256, 0, st>>>(N, h->leaf_of, h->slot, h->leaf_start, (const V *)h->vtmp, (V *)h->part_tmp,
                                    h->perm_tmp);
   k_leaf_sort<T><<<(nleaf * 32 + 255) / 256, 256, 0, st>>>(nleaf, h->leaf_start, (const V *)h->part_tmp, h->perm_tmp,
-                                                          h->qt, h->relD, (V *)h->part, h->perm, h->inv_perm,
-                                                          h->box_qd + h->level_off[h->d] * kQD);
-  h->launches += 3;
+                                                          (V *)h->part, h->perm, h->inv_perm);
+  k_leaf_moments<<<(nleaf + 127) / 128, 128, 0, st>>>(nleaf, h->leaf_start, h->perm, h->qt, h->relD,
+                                                       h->box_qd + h->level_off[h->d] * kQD);
+  h->launches += 4;
   MAHI_CK(cudaGetLastError());
   mark(h, 2);
   const double s_leaf = h->L / nb;
@@ -2003,8 +2057,14 @@ static cudaError_t eval_t(mahi_ctx *h, const XT *x, const double *lam, double *e
     const int Ks = K | 1;
     const size_t per_warp = 32 * (size_t)Ks * sizeof(T);
     if (sizeof(T) == 4 && P <= kMaxOrderMixed && 2 * per_warp <= 48 * 1024) {
-      k_p2m_t<T><<<(nleaf + 1) / 2, 64, 2 * per_warp, st>>>(nleaf, P, ld, Ks, (T)(1.0 / s_leaf), h->leaf_start,
-                                                          (const V *)h->part, M + h->level_off[h->d] * ld);
+      if (P == 12)
+        k_p2m_t<T, 12><<<(nleaf + 1) / 2, 64, 2 * per_warp, st>>>(nleaf, P, ld, Ks, (T)(1.0 / s_leaf),
+                                                                  h->leaf_start, (const V *)h->part,
+                                                                  M + h->level_off[h->d] * ld);
+      else
+        k_p2m_t<T, 0><<<(nleaf + 1) / 2, 64, 2 * per_warp, st>>>(nleaf, P, ld, Ks, (T)(1.0 / s_leaf),
+                                                                 h->leaf_start, (const V *)h->part,
+                                                                 M + h->level_off[h->d] * ld);
     } else {
       k_p2m<T><<<(nleaf * 32 + 127) / 128, 128, 4 * sizeof(T) * ld, st>>>(
           nleaf, P, ld, (T)(1.0 / s_leaf), h->leaf_start, (const V *)h->part, M + h->level_off[h->d] * ld);
@@ -2049,9 +2109,15 @@ static cudaError_t eval_t(mahi_ctx *h, const XT *x, const double *lam, double *e
   {
     size_t per_warp = sizeof(T) * 4 * (size_t)K;
     int wpb = (int)std::max<size_t>(1, std::min<size_t>(4, (40 * 1024) / per_warp));
-    k_l2p<T><<<(nleaf + wpb - 1) / wpb, 32 * wpb, per_warp * wpb, st>>>(
-        nleaf, P, ld, (T)s_leaf, h->leaf_start, (const V *)h->part, Lx + h->level_off[h->d] * ld, (T *)h->phi_s,
-        (T *)h->grad_s);
+    const dim3 gl((nleaf + wpb - 1) / wpb), bl(32 * wpb);
+    const T sl = (T)s_leaf;
+    const T *Ll = Lx + h->level_off[h->d] * ld;
+    if (P == 12)
+      k_l2p<T, 12><<<gl, bl, per_warp * wpb, st>>>(nleaf, P, ld, sl, h->leaf_start, (const V *)h->part, Ll,
+                                                    (T *)h->phi_s, (T *)h->grad_s);
+    else
+      k_l2p<T, 0><<<gl, bl, per_warp * wpb, st>>>(nleaf, P, ld, sl, h->leaf_start, (const V *)h->part, Ll,
+                                                   (T *)h->phi_s, (T *)h->grad_s);
     h->launches += 1;
     MAHI_CK(cudaGetLastError());
   }
@@ -2095,7 +2161,9 @@ static cudaError_t eval_t(mahi_ctx *h, const XT *x, const double *lam, double *e
     h->launches += 3;
   }
   if (energy) {
-    k_final_energy<<<1, 1024, 0, st>>>(h->energy_part, nleaf, h->site_energy, h->S, energy);
+    double *blk = h->energy_part + nleaf;  // kFinalBlocks block sums, then the ticket
+    k_final_energy<<<kFinalBlocks, 256, 0, st>>>(h->energy_part, nleaf, h->site_energy, h->S, blk,
+                                                 reinterpret_cast<unsigned int *>(blk + kFinalBlocks), energy);
     h->launches += 1;
   }
   MAHI_CK(cudaGetLastError());
