@@ -1439,22 +1439,24 @@ constexpr int kSiteBatchMax = 64;
 __device__ __forceinline__ int pack_entry(int box, int img) { return (box << 9) | img; }
 
 // block-wide exclusive prefix of `cnt` (per thread) in thread order; returns the
-// offset of this thread and writes the total to *total
-__device__ __forceinline__ int block_scan(int cnt, int *wsum, int *total) {
+// offset of this thread and writes the total to *total.  One barrier per call:
+// the warp totals alternate between the two halves of wsum (flip `parity`
+// every call), so a call never overwrites totals the previous one still reads.
+__device__ __forceinline__ int block_scan(int cnt, int *wsum, int parity, int *total) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  int *ws = wsum + 32 * parity;
   int x = cnt;
   for (int o = 1; o < 32; o <<= 1) {
     const int y = __shfl_up_sync(0xffffffff, x, o);
     if (lane >= o) x += y;
   }
-  if (lane == 31) wsum[w] = x;
+  if (lane == 31) ws[w] = x;
   __syncthreads();
   int off = 0, tot = 0;
   for (int k = 0; k < nw; ++k) {
-    if (k < w) off += wsum[k];
-    tot += wsum[k];
+    if (k < w) off += ws[k];
+    tot += ws[k];
   }
-  __syncthreads();
   *total = tot;
   return off + x - cnt;
 }
@@ -1623,7 +1625,7 @@ __global__ void __launch_bounds__(kSiteThreads, 3) k_site_phi(
   __shared__ T rw[kSiteBatchMax][3], rp[kSiteBatchMax][3], rQ[kSiteBatchMax], rB[kSiteBatchMax],
       rBi[kSiteBatchMax], rpw[kSiteBatchMax];
   __shared__ V me[kMaxSiteAtoms];
-  __shared__ int sa_s[kMaxSiteAtoms], aI[kMaxSiteAtoms][3], brow_s[kSiteBatchMax], bimg[kSiteBatchMax], wsum[32];
+  __shared__ int sa_s[kMaxSiteAtoms], aI[kMaxSiteAtoms][3], brow_s[kSiteBatchMax], bimg[kSiteBatchMax], wsum[64];
   const int site = blockIdx.x / G, g = blockIdx.x % G, tid = threadIdx.x;
   if (site >= S) return;
   const int b0 = site_ptr[site], n = site_ptr[site + 1] - b0;
@@ -1686,7 +1688,7 @@ __global__ void __launch_bounds__(kSiteThreads, 3) k_site_phi(
   const int nbatch = (nslot <= nbmax) ? nslot * (nbmax / nslot) : nbmax;
   SiteAcc<T> acc0, acc1;
   double base = 0.0;  // FP64 charge + dipole values at c of the rows this thread stages
-  int n0 = 343, bc = 0;
+  int n0 = 343, bc = 0, scan_par = 0;
   const T Rf = (T)cen[3];
   // the separation test runs in single precision (its 1e-4 safety margin is far
   // above the rounding of box centres at |x| < 4L); every block of a site
@@ -1713,17 +1715,21 @@ __global__ void __launch_bounds__(kSiteThreads, 3) k_site_phi(
         else if (l == d) kind = 1;
         else kind = 2;
       }
+      // one scan for both lists: separated / direct entries in the low 16
+      // bits, the 8 children of an opened box in the high 16 (a chunk of at
+      // most 1024 threads adds at most 8192 children)
       int tot;
-      const int osep = block_scan(kind == 0 || kind == 1 ? 1 : 0, wsum, &tot);
+      const int off = block_scan((kind == 0 || kind == 1) ? 1 : (kind == 2 ? (8 << 16) : 0), wsum, scan_par, &tot);
+      scan_par ^= 1;
+      const int osep = off & 0xffff, oopen = off >> 16;
       if ((kind == 0 || kind == 1) && nsep + osep < kFrontier) sep[nsep + osep] = (kind == 1) ? (e | (1 << 31)) : e;
-      nsep += tot;
-      const int oopen = block_scan(kind == 2 ? 8 : 0, wsum, &tot);
+      nsep += tot & 0xffff;
       if (kind == 2) {
         const int box = e >> 9, img = e & 511;
         for (int c = 0; c < 8; ++c)
           if (n1 + oopen + c < kFrontier) fb[n1 + oopen + c] = pack_entry(8 * box + c, img);
       }
-      n1 += tot;
+      n1 += tot >> 16;
     }
     if (nsep > kFrontier || n1 > kFrontier) {
       if (tid == 0) atomicExch(err, 1);
@@ -1758,16 +1764,18 @@ __global__ void __launch_bounds__(kSiteThreads, 3) k_site_phi(
         }
         bimg[tid] = img;
       }
-      __syncthreads();
+      // the multipole rows of the batch (row index straight from the list, so
+      // this needs no barrier after the per-row values above)
       if (P >= 2) {
         constexpr int EPV = 16 / sizeof(T);
         const int per_row = ld / EPV;
         for (int q = tid; q < nbx * per_row; q += blockDim.x) {
           const int r = q / per_row, e2 = q % per_row;
-          if (brow_s[r] >= 0)
-            reinterpret_cast<float4 *>(Ms + (size_t)r * lds)[e2] =
-                reinterpret_cast<const float4 *>(M + (size_t)brow_s[r] * ld)[e2];
+          const int er = sep[b + r];
+          if (er >= 0)
+            cpa16(Ms + (size_t)r * lds + (size_t)e2 * EPV, M + (size_t)(level_off[l] + (er >> 9)) * ld + (size_t)e2 * EPV);
         }
+        asm volatile("cp.async.wait_all;" ::: "memory");
       }
       __syncthreads();
       if (my_p >= 0) {
