@@ -50,6 +50,11 @@ static void free_all(mahi_ctx *h) {
     if (b) cudaFree(b);
   for (int i = 0; i < 32; ++i)
     if (h->ev[i]) cudaEventDestroy(h->ev[i]);
+  for (int i = 0; i < 2; ++i) {
+    if (h->fork_ev[i]) cudaEventDestroy(h->fork_ev[i]);
+    if (h->join_ev[i]) cudaEventDestroy(h->join_ev[i]);
+  }
+  if (h->side) cudaStreamDestroy(h->side);
 }
 
 // SIMT operator layout: transposed and zero padded, opT[term][k][n], k, n < ld.
@@ -281,6 +286,14 @@ int mahi_create(double box_L_nm, int64_t n_atoms, int32_t n_sites, int32_t order
   for (int i = 0; i < 32; ++i) {
     cudaError_t e = cudaEventCreate(&h->ev[i]);
     if (e != cudaSuccess) return fail(e, "event");
+  }
+  {
+    cudaError_t e = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking);
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+      e = cudaEventCreateWithFlags(&h->fork_ev[i], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->join_ev[i], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) return fail(e, "side stream");
   }
 #undef AL
   (void)K;

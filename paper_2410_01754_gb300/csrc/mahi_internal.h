@@ -146,6 +146,11 @@ struct mahi_ctx {
 
   cudaEvent_t ev[32] = {};
   int n_ev = 0;
+  // side stream for work that does not depend on the main chain (box moments
+  // during P2M/M2M, the site-atom potential during L2L/L2P/P2P), forked and
+  // joined with events inside every evaluation
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork_ev[2] = {}, join_ev[2] = {};
 };
 
 namespace mahi {

@@ -22,7 +22,7 @@ namespace mahi {
 
 template <typename T> struct V4;
 template <> struct V4<float> { using type = float4; };
-template <> struct V4<double> { using type = double4; };
+template <> struct V4<double> { using type = double4_16a; };  // 32 bytes, 16-byte aligned
 
 __device__ __forceinline__ uint32_t d_spread(uint32_t v) {
   uint32_t x = v & 0x3ff;
@@ -850,7 +850,6 @@ __global__ void __launch_bounds__(128, 6) k_l2p(int nleaf, int Pr, int ld, T s, 
 //    leaf centre.  Writes forces (original order), per-block energy partials,
 //    and the total potential phi~ back into phi_s (sorted order).
 // ---------------------------------------------------------------------------
-constexpr int P2P_THREADS = 128;
 
 // energy accumulator: compensated (Kahan-Babuska) in single precision, plain in FP64
 template <typename T> struct SiteAccE;
@@ -881,15 +880,23 @@ template <> struct SiteAccE<double> {
 };
 
 __device__ __forceinline__ double rinv(double r2) { return 1.0 / sqrt(r2); }
+// the hardware reciprocal square root as one instruction: subnormal inputs
+// flush to zero (squared distances here are never subnormal), so no
+// input-scaling fix-up is emitted around it
+__device__ __forceinline__ float rsqrt_ftz(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
 // hardware reciprocal square root refined by one Newton-Raphson step
 // y' = y (3 - r2 y^2) / 2, which roughly squares the relative error
 __device__ __forceinline__ float rinv(float r2) {
-  float y = rsqrtf(r2);
+  float y = rsqrt_ftz(r2);
   return y * fmaf(-0.5f * r2, y * y, 1.5f);
 }
 // near-field pair kernel: the hardware estimate alone (relative error below
 // 2^-22, under the single-precision rounding of the accumulated sums)
-__device__ __forceinline__ float rinv_fast(float r2) { return rsqrtf(r2); }
+__device__ __forceinline__ float rinv_fast(float r2) { return rsqrt_ftz(r2); }
 __device__ __forceinline__ double rinv_fast(double r2) { return 1.0 / sqrt(r2); }
 // staged sources per pass (16 KB in single precision): leaves of ~30 atoms
 // give ~800 sources, so one pass is the rule and more blocks fit on an SM
@@ -897,7 +904,7 @@ constexpr int P2P_MAXSRC = 1024;
 // FP64 1/sqrt(r2): single-precision seed and one FP64 Newton-Raphson step; the
 // seed's relative error e (about 2^-23) becomes 1.5 e^2 after the step
 __device__ __forceinline__ double rinv_dd(double r2) {
-  const double y = (double)rsqrtf((float)r2);
+  const double y = (double)rsqrt_ftz((float)r2);
   return y * fma(-0.5 * r2, y * y, 1.5);
 }
 
@@ -1535,7 +1542,7 @@ __device__ __forceinline__ void pair_pot(const SiteTarget<float> &m, float sx, f
   two_sum(px, py, s1, t1);
   two_sum(s1, pz, s2, t2);
   const float r2l = (t1 + t2) + (qx + qy + qz) + 2.0f * (hx * ex + hy * ey + hz * ez);
-  const float y0 = rsqrtf(s2);
+  const float y0 = rsqrt_ftz(s2);
   const float t = y0 * y0, te = fmaf(y0, y0, -t);
   const float u = s2 * t, ue = fmaf(s2, t, -u);
   const float res = ((1.0f - u) - ue) - fmaf(s2, te, r2l * t);
@@ -2055,9 +2062,19 @@ static cudaError_t eval_t(mahi_ctx *h, const XT *x, const double *lam, double *e
                                    h->perm_tmp);
   k_leaf_sort<T><<<(nleaf * 32 + 255) / 256, 256, 0, st>>>(nleaf, h->leaf_start, (const V *)h->part_tmp, h->perm_tmp,
                                                           (V *)h->part, h->perm, h->inv_perm);
-  k_leaf_moments<<<(nleaf + 127) / 128, 128, 0, st>>>(nleaf, h->leaf_start, h->perm, h->qt, h->relD,
-                                                       h->box_qd + h->level_off[h->d] * kQD);
-  h->launches += 4;
+  // FP64 box moments (leaves, then up the tree) on the side stream, while the
+  // main stream runs P2M and the M2M GEMMs; joined before the lattice step
+  MAHI_CK(cudaEventRecord(h->fork_ev[0], st));
+  MAHI_CK(cudaStreamWaitEvent(h->side, h->fork_ev[0], 0));
+  k_leaf_moments<<<(nleaf + 127) / 128, 128, 0, h->side>>>(nleaf, h->leaf_start, h->perm, h->qt, h->relD,
+                                                            h->box_qd + h->level_off[h->d] * kQD);
+  for (int l = h->d - 1; l >= 0; --l) {
+    const int np = 1 << (3 * l);
+    k_qd_up<<<(np + 127) / 128, 128, 0, h->side>>>(np, h->L / (1 << (l + 1)), h->box_qd + h->level_off[l + 1] * kQD,
+                                                   h->box_qd + h->level_off[l] * kQD);
+  }
+  MAHI_CK(cudaEventRecord(h->join_ev[0], h->side));
+  h->launches += 4 + h->d;
   MAHI_CK(cudaGetLastError());
   mark(h, 2);
   const double s_leaf = h->L / nb;
@@ -2085,11 +2102,8 @@ static cudaError_t eval_t(mahi_ctx *h, const XT *x, const double *lam, double *e
     MAHI_CK((launch_dense_gemm<T, false>(1 << (3 * l), ld, 8 * ld, M + h->level_off[l + 1] * ld, 8 * ld,
                                           (const T *)h->ops_m2m, ld, M + h->level_off[l] * ld, ld, (T *)h->gemm_ws,
                                           h->gemm_ws_elems, h->num_sms, st, h->launches)));
-    const int np = 1 << (3 * l);
-    k_qd_up<<<(np + 127) / 128, 128, 0, st>>>(np, h->L / (1 << (l + 1)), h->box_qd + h->level_off[l + 1] * kQD,
-                                              h->box_qd + h->level_off[l] * kQD);
-    h->launches += 1;
   }
+  MAHI_CK(cudaStreamWaitEvent(st, h->join_ev[0], 0));  // box moments (mom) done
   mark(h, 4);
   k_lattice<T><<<(ld + 3) / 4, 128, sizeof(double) * K, st>>>(K, ld, h->L, h->ops_lat, h->ops_lat_h3, mom, M, Lx,
                                                     h->L_h3);
@@ -2108,6 +2122,30 @@ static cudaError_t eval_t(mahi_ctx *h, const XT *x, const double *lam, double *e
     }
   }
   mark(h, 6);
+  if (h->S > 0) {
+    // The site-atom potential needs only the multipoles, the box moments and
+    // the lattice part, so it runs on the side stream alongside L2L, L2P and
+    // P2P (it fills the SMs the coarse L2L levels leave idle); joined before
+    // the per-site terms.
+    MAHI_CK(cudaEventRecord(h->fork_ev[1], st));
+    MAHI_CK(cudaStreamWaitEvent(h->side, h->fork_ev[1], 0));
+    // rows of staged multipoles: as many as keep three blocks per SM
+    const int lds = ld + 16 / (int)sizeof(T);
+    const size_t fixed = sizeof(int) * 3 * kFrontier;
+    const size_t budget = 72 * 1024;
+    const int nbmax = (int)std::max<size_t>(8, std::min<size_t>(kSiteBatchMax, (budget - fixed) / (sizeof(T) * lds)));
+    const size_t smp = fixed + sizeof(T) * nbmax * lds;
+    // blocks per site: about 4 x 3 per SM over all sites, unless the autotuner picked a count
+    const int G = h->tune_site_blocks > 0
+                      ? std::min(kSiteChunksMax, h->tune_site_blocks)
+                      : std::max(1, std::min(kSiteChunksMax, (4 * 3 * h->num_sms + h->S - 1) / std::max(1, h->S)));
+    MAHI_CK(launch_site_phi<T>(P, G, smp, h->side, h->S, G, h->site_ptr, h->site_atoms, h->d, P, ld, lds, nbmax, h->L,
+                               h->d_level_off, h->leaf_start, h->inv_perm, (const V *)h->part, M, h->box_qd,
+                               mom, h->L_h3, h->phi_part, h->tc_error_site, h->site_theta));
+    k_site_phi_sum<<<(h->n_site_atoms + 127) / 128, 128, 0, h->side>>>(h->n_site_atoms, G, coulomb_constant(),
+                                                                        h->phi_part, h->phi_site);
+    MAHI_CK(cudaEventRecord(h->join_ev[1], h->side));
+  }
   for (int l = 1; l <= h->d; ++l) {
     MAHI_CK((launch_dense_gemm<T, true>(1 << (3 * (l - 1)), 8 * ld, ld, Lx + h->level_off[l - 1] * ld, ld,
                                          (const T *)h->ops_l2l, 8 * ld, Lx + h->level_off[l] * ld, 8 * ld,
@@ -2142,21 +2180,7 @@ static cudaError_t eval_t(mahi_ctx *h, const XT *x, const double *lam, double *e
   }
   mark(h, 9);
   if (h->S > 0) {
-    // rows of staged multipoles: as many as keep three blocks per SM
-    const int lds = ld + 16 / (int)sizeof(T);
-    const size_t fixed = sizeof(int) * 3 * kFrontier;
-    const size_t budget = 72 * 1024;
-    const int nbmax = (int)std::max<size_t>(8, std::min<size_t>(kSiteBatchMax, (budget - fixed) / (sizeof(T) * lds)));
-    const size_t smp = fixed + sizeof(T) * nbmax * lds;
-    // blocks per site: about 4 x 3 per SM over all sites, unless the autotuner picked a count
-    const int G = h->tune_site_blocks > 0
-                      ? std::min(kSiteChunksMax, h->tune_site_blocks)
-                      : std::max(1, std::min(kSiteChunksMax, (4 * 3 * h->num_sms + h->S - 1) / std::max(1, h->S)));
-    MAHI_CK(launch_site_phi<T>(P, G, smp, st, h->S, G, h->site_ptr, h->site_atoms, h->d, P, ld, lds, nbmax, h->L,
-                               h->d_level_off, h->leaf_start, h->inv_perm, (const V *)h->part, M, h->box_qd,
-                               mom, h->L_h3, h->phi_part, h->tc_error_site, h->site_theta));
-    k_site_phi_sum<<<(h->n_site_atoms + 127) / 128, 128, 0, st>>>(h->n_site_atoms, G, coulomb_constant(),
-                                                                   h->phi_part, h->phi_site);
+    MAHI_CK(cudaStreamWaitEvent(st, h->join_ev[1], 0));  // site-atom potential done
     if (h->multiform)
       k_site_mf<XT, XT><<<h->S, 32, 0, st>>>(h->S, h->L, coulomb_constant(), kSiteDegree, h->site_aii, h->site_ptr,
                                              h->site_atoms, x, h->mf_lam_off, lam, h->mf_q, h->phi_site, h->eta,
