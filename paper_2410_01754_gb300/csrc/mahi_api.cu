@@ -45,15 +45,15 @@ static void free_all(mahi_ctx *h) {
                   h->m2l_list, h->m2l_off, h->site_ptr, h->site_atoms,
                   h->energy_part, h->site_energy, h->tc_ops, h->tc_partial, h->tc_msrc, h->tc_level_off, h->tc_units, h->tc_error, h->d_x_stage,
                   h->d_lam_stage, h->d_E_stage, h->d_dEdl_stage, h->d_F_stage, h->ops_lat_h3, h->L_h3,
-                  h->box_qd, h->vtmp, h->relD, h->phi_site, h->psi_site, h->site_slot, h->mf_q, h->mf_lam_off, h->phi_part, h->d_level_off, h->tc_error_site};
+                  h->box_qd, h->vtmp, h->relD, h->phi_site, h->psi_site, h->site_pairs, h->site_slot, h->mf_q, h->mf_lam_off, h->phi_part, h->d_level_off, h->tc_error_site};
   for (void *b : bufs)
     if (b) cudaFree(b);
   for (int i = 0; i < 32; ++i)
     if (h->ev[i]) cudaEventDestroy(h->ev[i]);
-  for (int i = 0; i < 2; ++i) {
+  for (int i = 0; i < 3; ++i)
     if (h->fork_ev[i]) cudaEventDestroy(h->fork_ev[i]);
+  for (int i = 0; i < 2; ++i)
     if (h->join_ev[i]) cudaEventDestroy(h->join_ev[i]);
-  }
   if (h->side) cudaStreamDestroy(h->side);
 }
 
@@ -289,10 +289,8 @@ int mahi_create(double box_L_nm, int64_t n_atoms, int32_t n_sites, int32_t order
   }
   {
     cudaError_t e = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking);
-    for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
-      e = cudaEventCreateWithFlags(&h->fork_ev[i], cudaEventDisableTiming);
-      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->join_ev[i], cudaEventDisableTiming);
-    }
+    for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&h->fork_ev[i], cudaEventDisableTiming);
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&h->join_ev[i], cudaEventDisableTiming);
     if (e != cudaSuccess) return fail(e, "side stream");
   }
 #undef AL
@@ -349,9 +347,11 @@ int mahi_set_charges(mahi_t h, const double *qA, const double *qB, const int32_t
   if (h->site_atoms) { cudaFree(h->site_atoms); h->site_atoms = nullptr; }
   if (h->phi_site) { cudaFree(h->phi_site); h->phi_site = nullptr; }
   if (h->psi_site) { cudaFree(h->psi_site); h->psi_site = nullptr; }
+  if (h->site_pairs) { cudaFree(h->site_pairs); h->site_pairs = nullptr; }
   if (h->phi_part) { cudaFree(h->phi_part); h->phi_part = nullptr; }
   CK(dalloc(&h->phi_site, std::max<size_t>(1, atoms.size()) * sizeof(double)));
   CK(dalloc(&h->psi_site, std::max<size_t>(1, atoms.size()) * sizeof(double)));
+  CK(dalloc(&h->site_pairs, std::max<size_t>(1, (size_t)S * kSiteSymPairs * 4) * sizeof(double)));
   {
     std::vector<int> slot(N, -1);
     for (size_t k = 0; k < atoms.size(); ++k) slot[atoms[k]] = (int)k;

@@ -22,6 +22,9 @@ constexpr int kSiteDegree = 40;        // degree of H_1 in the per-site correcti
 constexpr int kSiteChunksMax = 16;   // blocks sharing one site in the site-potential traversal
 constexpr double kPi = 3.14159265358979323846264338327950288;
 constexpr int kFinalBlocks = 64;  // blocks of the final energy sum
+// sites of up to kSiteSymMax atoms evaluate each unordered pair once
+constexpr int kSiteSymMax = 16;
+constexpr int kSiteSymPairs = kSiteSymMax * (kSiteSymMax - 1) / 2;
 
 // Coulomb constant N_A e^2 / (4 pi eps0) in kJ mol^-1 nm e^-2 (CODATA 2018).
 double coulomb_constant();
@@ -110,6 +113,7 @@ struct mahi_ctx {
   double *box_qd = nullptr;                   // FP64 Q, D, T per box (8 doubles), all levels
   double *phi_site = nullptr;                 // refined potential at site atoms
   double *psi_site = nullptr;                 // f sum_j A_ij D_j at site atoms (charge gradients)
+  double *site_pairs = nullptr;               // [S][kSiteSymPairs][4]: grad A, A of every site pair
   int *site_slot = nullptr;                   // N: position in site_atoms, -1 for environment atoms
   // sites with 2^m forms (mahi_set_forms)
   bool multiform = false;
@@ -150,7 +154,7 @@ struct mahi_ctx {
   // during P2M/M2M, the site-atom potential during L2L/L2P/P2P), forked and
   // joined with events inside every evaluation
   cudaStream_t side = nullptr;
-  cudaEvent_t fork_ev[2] = {}, join_ev[2] = {};
+  cudaEvent_t fork_ev[3] = {}, join_ev[2] = {};
 };
 
 namespace mahi {

@@ -1081,8 +1081,6 @@ __global__ void __launch_bounds__(NT) k_p2p(int nb, T c2, T half_L, T s_leaf, T 
 //    ordered pairs of one atom per lane.
 // ---------------------------------------------------------------------------
 constexpr int kMaxSiteAtoms = 64;
-constexpr int kSiteSymMax = 16;
-constexpr int kSiteSymPairs = kSiteSymMax * (kSiteSymMax - 1) / 2;
 
 // A(r) and grad A(r) for r != 0 (nm), FP64
 __device__ __forceinline__ void site_pair_kernel(const double r[3], double L, double c2, int Pmax,
@@ -1132,6 +1130,35 @@ __device__ __forceinline__ void site_pair_r(const XT *__restrict__ x, int i, int
   }
 }
 
+// The FP64 pair terms (grad A, A) of every unordered pair of every site of
+// up to kSiteSymMax atoms, one pair per thread and one block per site.  They
+// depend only on the positions, so they are computed at the start of an
+// evaluation on the side stream, where the FP64 pipe is otherwise idle, and
+// k_site reads them back; pairs[site][p] with p the pair index of k_site.
+template <typename XT>
+__global__ void __launch_bounds__(64) k_site_pairs(double L, int Pmax, const int *__restrict__ site_ptr,
+                                                   const int *__restrict__ site_atoms, const XT *__restrict__ x,
+                                                   const double *__restrict__ eta, const double *__restrict__ eta_x,
+                                                   const double *__restrict__ eta_y, const double *__restrict__ eta_z,
+                                                   double *__restrict__ pairs) {
+  const int site = blockIdx.x;
+  const int b = site_ptr[site], n = site_ptr[site + 1] - b;
+  if (n > kSiteSymMax) return;  // larger sites evaluate their ordered pairs in k_site
+  const double V = L * L * L, c2 = 2.0 * kPi / (3.0 * V);
+  const int np = n * (n - 1) / 2;
+  for (int p = threadIdx.x; p < np; p += blockDim.x) {
+    int ia = 0, rem = p;
+    while (rem >= n - 1 - ia) { rem -= n - 1 - ia; ++ia; }
+    const int ja = ia + 1 + rem;
+    double r[3], A, g[3];
+    site_pair_r(x, site_atoms[b + ia], site_atoms[b + ja], L, r);
+    site_pair_kernel(r, L, c2, Pmax, eta, eta_x, eta_y, eta_z, A, g);
+    double *o = pairs + ((size_t)site * kSiteSymPairs + p) * 4;
+    o[0] = g[0]; o[1] = g[1]; o[2] = g[2]; o[3] = A;
+  }
+}
+
+// pairs: the terms of k_site_pairs, or null to evaluate them here
 template <typename T, typename XT, typename FT>
 __global__ void k_site(int S, double L, double fcoul, int Pmax, double aii, const int *__restrict__ site_ptr,
                        const int *__restrict__ site_atoms, const XT *__restrict__ x, const double *__restrict__ dq,
@@ -1139,7 +1166,7 @@ __global__ void k_site(int S, double L, double fcoul, int Pmax, double aii, cons
                        const double *__restrict__ eta, const double *__restrict__ eta_x,
                        const double *__restrict__ eta_y, const double *__restrict__ eta_z,
                        double *__restrict__ dEdl, double *__restrict__ site_energy, FT *__restrict__ forces,
-                       double *__restrict__ psi_site) {
+                       double *__restrict__ psi_site, const double *__restrict__ pairs) {
   __shared__ double fsh[4][kMaxSiteAtoms][3];
   __shared__ double gbuf[4][kSiteSymPairs][4];  // grad A at r = x_lo - x_hi, then A
   const int wib = threadIdx.x >> 5;
@@ -1162,9 +1189,15 @@ __global__ void k_site(int S, double L, double fcoul, int Pmax, double aii, cons
       while (rem >= n - 1 - ia) { rem -= n - 1 - ia; ++ia; }
       const int ja = ia + 1 + rem;
       const int i = site_atoms[b + ia], j = site_atoms[b + ja];
-      double r[3], A, g[3];
-      site_pair_r(x, i, j, L, r);
-      site_pair_kernel(r, L, c2, Pmax, eta, eta_x, eta_y, eta_z, A, g);
+      double A, g[3];
+      if (pairs) {
+        const double *o = pairs + ((size_t)warp * kSiteSymPairs + p) * 4;
+        g[0] = o[0]; g[1] = o[1]; g[2] = o[2]; A = o[3];
+      } else {
+        double r[3];
+        site_pair_r(x, i, j, L, r);
+        site_pair_kernel(r, L, c2, Pmax, eta, eta_x, eta_y, eta_z, A, g);
+      }
       ksum += 2.0 * dq[i] * dq[j] * A;
       gbuf[wib][p][0] = g[0]; gbuf[wib][p][1] = g[1]; gbuf[wib][p][2] = g[2]; gbuf[wib][p][3] = A;
     }
@@ -2041,6 +2074,15 @@ static cudaError_t eval_t(mahi_ctx *h, const XT *x, const double *lam, double *e
   const double *mom = h->box_qd;  // root box row: Q, D, T of the system about the box centre
   h->launches = 0;
   mark(h, 0);
+  if (h->S > 0 && !h->multiform) {
+    // the sites' FP64 pair terms need only the positions: side stream, from
+    // the start (the FP64 pipe is idle during binning, P2M and M2M)
+    MAHI_CK(cudaEventRecord(h->fork_ev[2], st));
+    MAHI_CK(cudaStreamWaitEvent(h->side, h->fork_ev[2], 0));
+    k_site_pairs<XT><<<h->S, 64, 0, h->side>>>(h->L, kSiteDegree, h->site_ptr, h->site_atoms, x, h->eta, h->eta_x,
+                                               h->eta_y, h->eta_z, h->site_pairs);
+    h->launches += 1;
+  }
   MAHI_CK(cudaMemsetAsync(h->leaf_count, 0, sizeof(int) * nleaf, st));
   {
     const double s_l = h->L / nb;
@@ -2189,7 +2231,7 @@ static cudaError_t eval_t(mahi_ctx *h, const XT *x, const double *lam, double *e
       k_site<T, XT, XT><<<(h->S + 3) / 4, 128, 0, st>>>(h->S, h->L, coulomb_constant(), kSiteDegree, h->site_aii,
                                                         h->site_ptr, h->site_atoms, x, h->dq, lam, h->phi_site, h->eta,
                                                         h->eta_x, h->eta_y, h->eta_z, dEdl, h->site_energy, forces,
-                                                        h->psi_site);
+                                                        h->psi_site, h->site_pairs);
     h->launches += 3;
   }
   if (energy) {
