@@ -113,7 +113,7 @@ int mahi_n_lambdas(mahi_t h);
  * pair terms, the box moments, the site-atom potential); they are forked from
  * and joined back to the handle's stream with events inside the call, so the
  * outputs are complete in the handle's stream order, work queued on that
- * stream before the call is seen, and the call can be captured in a CUDA graph. */
+ * stream before the call is seen, and the call can be captured in a CUDA graph.
  *   x          device, n_atoms x 3 row-major positions in nm (float64 if
  *              x_is_fp64 else float32); any real values (wrapped into the box).
  *   lambda     device, n_sites float64 in [0, 1].
