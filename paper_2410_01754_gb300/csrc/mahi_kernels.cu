@@ -431,6 +431,76 @@ __global__ void k_p2m_t(int nleaf, int Pr, int ld, int Ks, T inv_s, const int *_
   }
 }
 
+// P2M for a compile-time order with a 32 x 33 staging buffer per warp
+// instead of 32 x K: every lane (atom) produces its K coefficients
+// q conj(R_lm(u)) in the recursion's order (m outer, l inner; re, then im for
+// m > 0) and writes them into the buffer 32 at a time; after each 32 the warp
+// adds up the buffer's columns (lane j: production index 32 c + j, sum over
+// the 32 atoms in lane order).  Lanes without an atom carry charge 0 and add
+// exact zeros.  The small buffer lets ~50 warps run per SM instead of 10.
+__device__ __forceinline__ int p2m_prod_ridx(int P, int p) {
+  for (int m = 0; m <= P; ++m) {
+    const int per = (P - m + 1) * (m > 0 ? 2 : 1);
+    if (p < per) return m > 0 ? ridx(m + p / 2, m) + (p & 1) : ridx(m + p, 0);
+    p -= per;
+  }
+  return -1;
+}
+
+template <typename T, int PP>
+__global__ void __launch_bounds__(128) k_p2m_c(int nleaf, int ld, T inv_s, const int *__restrict__ leaf_start,
+                                               const typename V4<T>::type *__restrict__ part, T *__restrict__ M) {
+  using V = typename V4<T>::type;
+  constexpr int K = (PP + 1) * (PP + 1);
+  constexpr int NC = (K + 31) / 32;
+  __shared__ T buf[4][32][33];
+  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int warp = blockIdx.x * 4 + wib;
+  if (warp >= nleaf) return;  // whole warps only
+  T(*bw)[33] = buf[wib];
+  T acc[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) acc[c] = T(0);
+  const int b = leaf_start[warp], e = leaf_start[warp + 1];
+  for (int base = b; base < e; base += 32) {
+    const int a = base + lane;
+    const V pt = (a < e) ? part[a] : V{0, 0, 0, 0};
+    const T q = pt.w;
+    int pidx = 0;  // production index (a constant at every call site once unrolled)
+    auto put = [&](T v) {
+      bw[lane][pidx & 31] = v;
+      if ((pidx & 31) == 31) {
+        __syncwarp();
+        T sum = T(0);
+#pragma unroll 8
+        for (int i = 0; i < 32; ++i) sum += bw[i][lane];
+        acc[pidx >> 5] += sum;
+        __syncwarp();
+      }
+      ++pidx;
+    };
+    rt_columns<T>(PP, pt.x * inv_s, pt.y * inv_s, pt.z * inv_s, [&](int l, int m, T re, T im) {
+      put(q * re);
+      if (m > 0) put(-q * im);  // conj
+    });
+    if constexpr (K % 32 != 0) {  // the last, partial group of 32
+      __syncwarp();
+      T sum = T(0);
+#pragma unroll 8
+      for (int i = 0; i < 32; ++i) sum += bw[i][lane];
+      if (lane < K % 32) acc[NC - 1] += sum;
+      __syncwarp();
+    }
+  }
+  T *out = M + (size_t)warp * ld;
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    const int p = 32 * c + lane;
+    if (p < K) out[p2m_prod_ridx(PP, p)] = acc[c];
+  }
+  for (int k = K + lane; k < ld; k += 32) out[k] = T(0);
+}
+
 // ---------------------------------------------------------------------------
 // 3. Gather-GEMM for M2M, L2L and (SIMT) M2L.  A tile of TR output rows shares
 //    one operator per term; out[row] (+)= sum_terms op[term] * in[src(row, term)].
@@ -2125,9 +2195,8 @@ static cudaError_t eval_t(mahi_ctx *h, const XT *x, const double *lam, double *e
     const size_t per_warp = 32 * (size_t)Ks * sizeof(T);
     if (sizeof(T) == 4 && P <= kMaxOrderMixed && 2 * per_warp <= 48 * 1024) {
       if (P == 12)
-        k_p2m_t<T, 12><<<(nleaf + 1) / 2, 64, 2 * per_warp, st>>>(nleaf, P, ld, Ks, (T)(1.0 / s_leaf),
-                                                                  h->leaf_start, (const V *)h->part,
-                                                                  M + h->level_off[h->d] * ld);
+        k_p2m_c<T, 12><<<(nleaf + 3) / 4, 128, 0, st>>>(nleaf, ld, (T)(1.0 / s_leaf), h->leaf_start,
+                                                        (const V *)h->part, M + h->level_off[h->d] * ld);
       else
         k_p2m_t<T, 0><<<(nleaf + 1) / 2, 64, 2 * per_warp, st>>>(nleaf, P, ld, Ks, (T)(1.0 / s_leaf),
                                                                  h->leaf_start, (const V *)h->part,
