@@ -253,7 +253,9 @@ def run_ours(args):
     translations = 189 * sum(8 ** l for l in range(1, WORKLOAD["depth"] + 1))
     m2l_flop = 2.0 * K * K * translations
     m2l_ms = stages.get("m2l")
-    peak_tf32 = peaks["bf16_tflops_sustained"] * TF32_PER_BF16
+    # the M2L is timed inside a ~5 ms step whose timed loop lasts well under a
+    # second: the burst figure applies
+    peak_tf32 = peaks["bf16_tflops"] * TF32_PER_BF16
     achieved = m2l_flop / (m2l_ms * 1e-3) / 1e12 if m2l_ms else None
     traffic = None
     tpath = os.path.join(ROOT, "profiles", "m2l_tc_traffic.json")
@@ -281,13 +283,14 @@ def run_ours(args):
         "roofline": {"bound": "tensor", "kernel": "k_m2l_tc (+ source layout and remainder reduce)", "achieved": round(achieved, 2) if achieved else None,
                      "peak": round(peak_tf32, 1), "unit": "TFLOP/s",
                      "frac": round(achieved / peak_tf32, 4) if achieved else None, "traffic": traffic,
-                     "peak_source": f"{src} bf16 sustained x {TF32_PER_BF16:.4f} (nominal tf32/bf16)",
+                     "peak_source": f"{src} bf16 burst x {TF32_PER_BF16:.4f} (nominal tf32/bf16)",
                      "algorithmic_flop_per_launch": m2l_flop, "tensor_flop_per_launch": 3 * m2l_flop},
         "clocks": clocks,
         "wall_s_timed": round(t_wall, 3),
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(s)
+        out["cpu_baseline"]["validation"] = cpu_baseline_validation()
     if rank == 0:
         print(json.dumps(out), flush=True)
     if dist:
@@ -480,9 +483,29 @@ def cpu_baseline(s, n_targets=8192, atom_frac=1 / 8):
     full_s = t_sf / atom_frac + (t_rec + t_real) * N / n_targets
     return {"value": round(full_s * 1e3, 1), "unit": "ms", "cores": oracle.num_threads(), "kind": "oracle",
             "sample": f"Ewald structure factors over {atom_frac:.4f} of the atoms plus real- and reciprocal-space "
-                      f"sums at {n_targets} target atoms of the 1,000,002-atom system, extrapolated linearly to "
-                      f"one full E/F/dE/dlambda evaluation (rc={rc:.2f} nm)",
+                      f"sums at {n_targets} target atoms of the {N:,}-atom system, extrapolated linearly to "
+                      f"one full E/F/dE/dlambda evaluation (rc={rc:.2f} nm); a model, checked in "
+                      f"'validation' against a full evaluation of a smaller system",
             "measured_s": round(t_sf * 2 + t_rec + t_real, 2)}
+
+
+def cpu_baseline_validation():
+    """The sampling model of cpu_baseline checked on a system the oracle can
+    evaluate in full: the 96,000-atom, 32-site water box (p = 10, d = 4
+    workload).  One complete oracle evaluation (HI energy, every force, every
+    dE/dlambda) is timed on the host cores, next to the model's prediction from
+    the same kind of sample (an eighth of the atoms, 8,192 targets)."""
+    import oracle
+    import synth
+    from oracle import hi
+    s = synth.make("B", 1)
+    t0 = time.perf_counter()
+    hi.hi_eval(s)
+    full = time.perf_counter() - t0
+    model = cpu_baseline(s)["value"] * 1e-3
+    return {"workload": "water_96k_32sites", "n_atoms": len(s["qA"]), "cores": oracle.num_threads(),
+            "measured_full_s": round(full, 2), "model_s": round(model, 2),
+            "model_over_measured": round(model / full, 3)}
 
 
 def run_reference(args):

@@ -55,8 +55,27 @@ enum {
   MAHI_ERR_CUDA = -4,        /* a CUDA call failed; see mahi_last_cuda_error    */
   MAHI_ERR_TIMEOUT = -5,     /* a bounded device wait gave up                   */
   MAHI_ERR_NO_DEVICE = -6,   /* no usable sm_100-class device                   */
-  MAHI_ERR_STATE = -7        /* call order: charges not set                     */
+  MAHI_ERR_STATE = -7,       /* call order: charges not set                     */
+  MAHI_ERR_SITE_OVERFLOW = -8/* a site's traversal lists outgrew their capacity */
 };
+
+/* Device-side failures.  Two conditions are detected inside the kernels of an
+ * evaluation and recorded in a status word of the handle (host-mapped memory,
+ * written by the device only on failure):
+ *   MAHI_ERR_TIMEOUT        a bounded wait of the tensor-core M2L gave up (the
+ *                           kernel then drains its copies, frees its tensor
+ *                           memory and returns; the local expansions of that
+ *                           evaluation are incomplete);
+ *   MAHI_ERR_SITE_OVERFLOW  the separation-controlled traversal of a site (the
+ *                           refined site-atom potential) had more boxes at one
+ *                           level than its list capacity (MAHI_OPT_SITE_LIST_CAP);
+ *                           that site's dE/dlambda is incomplete.
+ * Outputs of an evaluation that failed this way are not valid.  Because
+ * mahi_eval returns once work is enqueued, such a failure is reported by the
+ * next call that sees it: mahi_get_status (which synchronises), mahi_eval_host
+ * (which synchronises), or the next mahi_eval, which then returns the code
+ * without enqueueing anything.  Reporting clears the status word. */
+int mahi_get_status(mahi_t h);
 
 /* Create a solver for n_atoms atoms in a cubic periodic box of edge box_L_nm,
  * n_sites two-form titratable sites, multipole order order_p (expansions have
@@ -78,11 +97,23 @@ int mahi_destroy(mahi_t h);
 int mahi_set_stream(mahi_t h, void *cuda_stream);
 
 /* Charges of the two forms and the site map (Sec. "Hamiltonian Interpolation
- * Formulation": sites, forms).  HOST arrays of length n_atoms: qA, qB (e) and
- * site_of_atom (-1 = environment, else 0..n_sites-1).  Environment atoms must
- * have qA == qB and every site must own at least one atom, else
- * MAHI_ERR_BAD_SITE_MAP.  The library copies the data (synchronously). */
+ * Formulation": sites, forms).  Arrays of length n_atoms, each in host or
+ * device memory (detected per pointer): qA, qB (float64, e) and site_of_atom
+ * (int32, -1 = environment, else 0..n_sites-1).  Environment atoms must have
+ * qA == qB and every site must own 1 to 64 atoms, else MAHI_ERR_BAD_SITE_MAP.
+ * The library copies the data; the call synchronises the handle's stream (the
+ * site map is validated and indexed on the host). */
 int mahi_set_charges(mahi_t h, const double *qA, const double *qB, const int32_t *site_of_atom);
+
+/* New charges for the same site map, without a host round trip (for loops that
+ * change the charges every step, e.g. charge gradients through autograd).
+ * qA, qB: DEVICE arrays of n_atoms float64 (e).  Enqueued on the handle's
+ * stream (one kernel, no synchronisation); the arrays may be reused once the
+ * stream reaches the next evaluation.  Environment atoms carry qA only (their
+ * qB is ignored, as the two forms of an environment atom are the same charge).
+ * MAHI_ERR_STATE before mahi_set_charges; MAHI_ERR_INVALID_ARG for sites with
+ * more than two forms (mahi_set_forms). */
+int mahi_update_charges(mahi_t h, const double *qA, const double *qB);
 
 /* Sites with more than two forms (general formulation, Eq. "iter_ham_lambda";
  * Appendix, Eqs. "lambda_list", "one_site_lambda").  Instead of
@@ -150,14 +181,48 @@ int mahi_eval_host(mahi_t h, const void *x_host, int32_t x_is_fp64, const double
 int mahi_backward(mahi_t h, const double *grad_energy, const void *forces, const double *dEdlambda,
                   const double *lambda, int32_t x_is_fp64, void *dx, double *dlambda, double *dEdqA, double *dEdqB);
 
+/* Solver options (each has a default; value 0 restores it).
+ *   MAHI_OPT_SITE_THETA     separation ratio theta of the site-atom traversal:
+ *       a box of circumradius a is used through its multipole at a site of
+ *       radius R at distance D only if a < theta (D - R), so each multipole
+ *       term converges at least like theta^(p+1).  Default
+ *       theta(p) = min(0.4, 0.4^(13/(p+1))): the truncation bound of p = 12 at
+ *       theta = 0.4 held at every order.  Range (0, 0.7].
+ *   MAHI_OPT_SITE_LIST_CAP  boxes per level of one site's traversal (list
+ *       capacity, 64 to 12288).  Default: 1536 at theta >= 0.4, else grown
+ *       with the number of boxes a theta-ball holds.  A site that needs more
+ *       fails with MAHI_ERR_SITE_OVERFLOW.
+ *   MAHI_OPT_WAIT_LIMIT_MS  limit of every bounded device wait of the
+ *       tensor-core M2L (default 2000 ms, range 1 to 60000).
+ *   MAHI_OPT_WATCHDOG_SELFTEST  1: every following evaluation's tensor-core
+ *       M2L makes its first wait on a barrier that nothing completes, so that
+ *       the wait runs out after the wait limit and the evaluation reports
+ *       MAHI_ERR_TIMEOUT (a test of the watchdog path; no fault is caused).
+ *       0: off (default).
+ * MAHI_ERR_INVALID_ARG for an unknown option or a value out of range. */
+enum {
+  MAHI_OPT_SITE_THETA = 1,
+  MAHI_OPT_SITE_LIST_CAP = 2,
+  MAHI_OPT_WAIT_LIMIT_MS = 3,
+  MAHI_OPT_WATCHDOG_SELFTEST = 4
+};
+int mahi_set_option(mahi_t h, int32_t option, double value);
+/* Current value of an option (the effective one for defaults). */
+double mahi_get_option(mahi_t h, int32_t option);
+
 /* Charge-scaled potential phi~ (kJ/mol/e, float64, original atom order) of the
  * last evaluation into a device buffer of n_atoms doubles (enqueued). */
 int mahi_get_potential(mahi_t h, double *phi_device);
 
-/* Stage timing (CUDA events on the handle's stream).  mahi_set_timing(h, 1)
- * turns recording on; mahi_stage_times fills up to n floats (ms) of the last
- * evaluation in the order of mahi_stage_name(i) and returns the stage count.
- * It synchronises the stream. */
+/* Stage timing (CUDA events).  mahi_set_timing(h, 1) turns recording on;
+ * mahi_stage_times fills up to n floats (ms) of the last evaluation in the
+ * order of mahi_stage_name(i) and returns the stage count.  The first ten are
+ * consecutive intervals on the handle's stream (bin, sort, p2m, m2m, lattice,
+ * m2l, l2l, l2p, p2p, site); the last two are the internal side stream's work,
+ * which overlaps them: side_site_pairs (the sites' FP64 pair terms, from the
+ * start of the evaluation) and side_site_potential (the refined site-atom
+ * potential, after the M2L), 0 when there are no sites.  It synchronises the
+ * streams.  Timing is meant for eager evaluations, not for captured ones. */
 int mahi_set_timing(mahi_t h, int32_t on);
 int mahi_stage_times(mahi_t h, float *ms, int32_t n);
 const char *mahi_stage_name(int32_t i);
@@ -189,10 +254,15 @@ int mahi_lattice_eval(double box_L_nm, int32_t order_p, int32_t shell, int64_t n
  * potential phi~ with their own solver).  It runs the per-site stage of
  * mahi_eval (k_s, dE/dlambda, energy and force corrections) on
  * caller-provided inputs; its only scratch is a file-scope device array.
+ *   n_atoms     length of the per-atom arrays below (>= 1 when n_sites > 0)
  *   site_ptr    device, n_sites + 1 int32 (CSR offsets into site_atoms)
  *   site_atoms  device, site_ptr[n_sites] int32 atom indices; every site has
- *               1..64 atoms (a malformed site yields NaN in its outputs)
- *   x           device, positions (float64 if x_is_fp64 else float32), n x 3
+ *               1..64 atoms with indices in [0, n_atoms).  A malformed site
+ *               (offsets out of order or beyond site_ptr[n_sites], a size
+ *               outside 1..64, an atom index out of range) is checked before
+ *               any per-atom array is read: its dE/dlambda and its energy
+ *               slot become NaN and none of its atoms is touched.
+ *   x           device, positions (float64 if x_is_fp64 else float32), n_atoms x 3
  *   qA, qB      device float64 charges of the two forms (indexed by atom)
  *   lambda      device, n_sites float64
  *   phi         device float64 charge-scaled potential phi~ (kJ/mol/e) per atom,
@@ -207,7 +277,8 @@ int mahi_lattice_eval(double box_L_nm, int32_t order_p, int32_t shell, int64_t n
  * synchronously; make it before any stream capture.  Later calls only enqueue
  * kernels on cuda_stream.  Calls share the scratch: calls that overlap on the
  * GPU race. */
-int mahi_site_terms_static(double box_L_nm, int32_t n_sites, const int32_t *site_ptr, const int32_t *site_atoms,
+int mahi_site_terms_static(double box_L_nm, int64_t n_atoms, int32_t n_sites, const int32_t *site_ptr,
+                           const int32_t *site_atoms,
                            const void *x, int32_t x_is_fp64, const double *qA, const double *qB,
                            const double *lambda, const double *phi, double *dEdlambda, double *energy_correction,
                            void *forces, void *cuda_stream);

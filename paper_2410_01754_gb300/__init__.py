@@ -17,6 +17,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libmahi.so")
 
 MAHI_FP64, MAHI_MIXED, MAHI_MIXED_SIMT = 0, 1, 2
+MAHI_ERR_TIMEOUT, MAHI_ERR_SITE_OVERFLOW = -5, -8
+OPTIONS = {"site_theta": 1, "site_list_cap": 2, "wait_limit_ms": 3, "watchdog_selftest": 4}
 PRECISIONS = {"fp64": MAHI_FP64, "mixed": MAHI_MIXED, "mixed_simt": MAHI_MIXED_SIMT}
 
 _lib = None
@@ -42,10 +44,15 @@ _SIGS = {
     "mahi_lattice_coeffs": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p]),
     "mahi_lattice_eval": (ctypes.c_int, [ctypes.c_double, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64,
                                          ctypes.c_void_p, ctypes.c_void_p]),
-    "mahi_site_terms_static": (ctypes.c_int, [ctypes.c_double, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+    "mahi_site_terms_static": (ctypes.c_int, [ctypes.c_double, ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p,
+                                              ctypes.c_void_p,
                                               ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
                                               ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                               ctypes.c_void_p, ctypes.c_void_p]),
+    "mahi_get_status": (ctypes.c_int, [ctypes.c_void_p]),
+    "mahi_update_charges": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "mahi_set_option": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_double]),
+    "mahi_get_option": (ctypes.c_double, [ctypes.c_void_p, ctypes.c_int32]),
     "mahi_batch_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                          ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
@@ -124,11 +131,43 @@ def mahi_set_stream(h, stream):
     _ck(lib().mahi_set_stream(h, _stream_handle(stream)), "mahi_set_stream")
 
 
+def _host_or_device(a, dtype):
+    """numpy arrays are passed as host memory, contiguous CUDA tensors by pointer."""
+    if hasattr(a, "data_ptr") and getattr(a, "is_cuda", False):
+        want = "torch.float64" if dtype == np.float64 else "torch.int32"
+        if str(a.dtype) != want or not a.is_contiguous():
+            raise TypeError(f"device array must be a contiguous {want} tensor")
+        return a, a.data_ptr()
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    return arr, arr.ctypes.data
+
+
 def mahi_set_charges(h, qA, qB, site_of_atom):
-    qA = np.ascontiguousarray(qA, dtype=np.float64)
-    qB = np.ascontiguousarray(qB, dtype=np.float64)
-    so = np.ascontiguousarray(site_of_atom, dtype=np.int32)
-    _ck(lib().mahi_set_charges(h, qA.ctypes.data, qB.ctypes.data, so.ctypes.data), "mahi_set_charges")
+    """qA, qB (float64) and site_of_atom (int32): numpy arrays or CUDA tensors."""
+    ka, pa = _host_or_device(qA, np.float64)
+    kb, pb = _host_or_device(qB, np.float64)
+    ks, ps = _host_or_device(site_of_atom, np.int32)
+    _ck(lib().mahi_set_charges(h, pa, pb, ps), "mahi_set_charges")
+
+
+def mahi_update_charges(h, qA, qB):
+    """New charges (contiguous float64 CUDA tensors) for the same site map; enqueued."""
+    _ck(lib().mahi_update_charges(h, _ptr(qA), _ptr(qB)), "mahi_update_charges")
+
+
+def mahi_get_status(h):
+    """Synchronises the handle's stream; returns 0 or the code of a device-side failure."""
+    return int(lib().mahi_get_status(h))
+
+
+def mahi_set_option(h, option, value):
+    opt = OPTIONS[option] if isinstance(option, str) else int(option)
+    _ck(lib().mahi_set_option(h, opt, float(value)), "mahi_set_option")
+
+
+def mahi_get_option(h, option):
+    opt = OPTIONS[option] if isinstance(option, str) else int(option)
+    return float(lib().mahi_get_option(h, opt))
 
 
 def mahi_set_forms(h, q_env, site_of_atom, forms):
@@ -206,8 +245,10 @@ def mahi_site_terms_static(box_L_nm, site_ptr, site_atoms, x, qA, qB, lam, phi, 
                            energy_correction=None, forces=None, stream=None):
     """Allocation-free per-site HI terms (device tensors in, device tensors out)."""
     n_sites = int(site_ptr.numel()) - 1
+    n_atoms = int(x.shape[0])
     x_is_fp64 = 1 if str(x.dtype).endswith("float64") else 0
-    _ck(lib().mahi_site_terms_static(float(box_L_nm), n_sites, _ptr(site_ptr), _ptr(site_atoms), _ptr(x), x_is_fp64,
+    _ck(lib().mahi_site_terms_static(float(box_L_nm), n_atoms, n_sites, _ptr(site_ptr), _ptr(site_atoms), _ptr(x),
+                                     x_is_fp64,
                                      _ptr(qA), _ptr(qB), _ptr(lam), _ptr(phi), _ptr(dEdlambda),
                                      _ptr(energy_correction), _ptr(forces), _stream_handle(stream)),
         "mahi_site_terms_static")
@@ -269,6 +310,18 @@ class Mahi:
     def set_charges(self, qA, qB, site_of_atom):
         mahi_set_charges(self.h, qA, qB, site_of_atom)
         self.n_lambdas = self.n_sites
+
+    def update_charges(self, qA, qB):
+        mahi_update_charges(self.h, qA, qB)
+
+    def set_option(self, option, value):
+        mahi_set_option(self.h, option, value)
+
+    def get_option(self, option):
+        return mahi_get_option(self.h, option)
+
+    def status(self):
+        return mahi_get_status(self.h)
 
     def set_forms(self, q_env, site_of_atom, forms):
         mahi_set_forms(self.h, q_env, site_of_atom, forms)

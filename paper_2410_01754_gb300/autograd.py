@@ -19,7 +19,7 @@ from . import Mahi, mahi_backward
 class _Fn(torch.autograd.Function):
     @staticmethod
     def forward(ctx, x, lam, qA, qB, owner):
-        owner._sync_charges(qA, qB)
+        owner._sync_charges(qA, qB, x.device)
         E, F, g = owner.solver.eval(x.contiguous(), lam.contiguous())
         owner._evals += 1
         ctx.owner = owner
@@ -50,20 +50,29 @@ class MahiEnergy:
     """Differentiable HI energy of a fixed system layout.
 
     site_of: host int array (-1 = environment, else the site index); charges are
-    passed per call (device tensors of n_atoms float64) and uploaded when they
-    change.  Environment atoms must have qA == qB; their gradient goes to qA."""
+    passed per call (device tensors of n_atoms float64).  The first call hands
+    them to mahi_set_charges (which validates the site map); later changes go
+    through mahi_update_charges, a device-side copy enqueued on the solver's
+    stream (no host round trip).  Environment atoms must have qA == qB; their
+    gradient goes to qA."""
 
     def __init__(self, box_L_nm, site_of, n_sites, order_p, depth, precision="mixed", stream=None):
         self.site_of = np.ascontiguousarray(site_of, dtype=np.int32)
         self.solver = Mahi(box_L_nm, len(self.site_of), n_sites, order_p, depth, precision, stream)
         self._key = None
+        self._keep = None
         self._evals = 0
 
-    def _sync_charges(self, qA, qB):
+    def _sync_charges(self, qA, qB, device):
         key = (qA.data_ptr(), qA._version, qB.data_ptr(), qB._version)
         if key != self._key:
-            self.solver.set_charges(qA.detach().double().cpu().numpy(), qB.detach().double().cpu().numpy(),
-                                    self.site_of)
+            a = qA.detach().to(device=device, dtype=torch.float64).contiguous()
+            b = qB.detach().to(device=device, dtype=torch.float64).contiguous()
+            if self._key is None:
+                self.solver.set_charges(a, b, self.site_of)
+            else:
+                self.solver.update_charges(a, b)
+            self._keep = (a, b)   # alive until the stream has read them
             self._key = key
 
     def energy(self, x, lam, qA, qB):

@@ -18,11 +18,29 @@ using namespace mahi;
 static std::mutex g_err_mu;
 static char g_cuda_err[512] = "";
 
-static int cuda_fail(cudaError_t e, const char *what) {
+namespace mahi {
+int cuda_fail(cudaError_t e, const char *what) {
   std::lock_guard<std::mutex> lk(g_err_mu);
   snprintf(g_cuda_err, sizeof(g_cuda_err), "%s: %s (%d)", what, cudaGetErrorString(e), (int)e);
   return MAHI_ERR_CUDA;
 }
+
+float default_site_theta(int p) {
+  // theta^(p+1) = 0.4^13: the M2P truncation bound that theta = 0.4 gives at p = 12
+  const double t = std::pow(0.4, 13.0 / (p + 1.0));
+  return (float)std::min(0.4, t);
+}
+
+int default_site_list_cap(float theta) {
+  if (theta >= 0.4f) return 1536;
+  // children of the boxes opened at one level: 8 x the lattice points in a
+  // ball of radius (sqrt(3)/2) / theta plus 1.5 box edges (site radius, margin)
+  const double r = 0.86602540378443865 / theta + 1.5;
+  int cap = (int)std::ceil(8.0 * 4.0 / 3.0 * kPi * r * r * r);
+  cap = (cap + 255) / 256 * 256;
+  return std::max(1536, std::min(kSiteListCapMax, cap));
+}
+}  // namespace mahi
 
 #define CK(call)                                      \
   do {                                                \
@@ -43,11 +61,12 @@ static void free_all(mahi_ctx *h) {
                   h->perm_tmp, h->inv_perm, h->part, h->part_tmp, h->Mexp, h->Lexp, h->phi_s, h->grad_s,
                   h->ops_m2m, h->ops_l2l, h->ops_m2l, h->gemm_ws, h->ops_lat, h->eta, h->eta_x, h->eta_y, h->eta_z,
                   h->m2l_list, h->m2l_off, h->site_ptr, h->site_atoms,
-                  h->energy_part, h->site_energy, h->tc_ops, h->tc_partial, h->tc_msrc, h->tc_level_off, h->tc_units, h->tc_error, h->d_x_stage,
+                  h->energy_part, h->site_energy, h->tc_ops, h->tc_partial, h->tc_msrc, h->tc_level_off, h->tc_units, h->d_x_stage,
                   h->d_lam_stage, h->d_E_stage, h->d_dEdl_stage, h->d_F_stage, h->ops_lat_h3, h->L_h3,
-                  h->box_qd, h->vtmp, h->relD, h->phi_site, h->psi_site, h->site_pairs, h->site_slot, h->mf_q, h->mf_lam_off, h->phi_part, h->d_level_off, h->tc_error_site};
+                  h->box_qd, h->vtmp, h->relD, h->phi_site, h->psi_site, h->site_pairs, h->site_slot, h->mf_q, h->mf_lam_off, h->phi_part, h->d_level_off};
   for (void *b : bufs)
     if (b) cudaFree(b);
+  if (h->status_host) cudaFreeHost(h->status_host);
   for (int i = 0; i < 32; ++i)
     if (h->ev[i]) cudaEventDestroy(h->ev[i]);
   for (int i = 0; i < 3; ++i)
@@ -95,6 +114,29 @@ static cudaError_t upload_ops(const std::vector<std::vector<double>> &ops, void 
   return cudaMemcpy(*dst, tmp.data(), n * sizeof(T), cudaMemcpyHostToDevice);
 }
 
+// true for device (or managed) memory, false for host memory (pinned or pageable)
+static bool is_device_ptr(const void *p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// host view of an array that may live on the device (copied when it does)
+template <typename T>
+static int host_view(const T *p, int64_t n, std::vector<T> &buf, const T **out) {
+  if (!is_device_ptr(p)) {
+    *out = p;
+    return MAHI_OK;
+  }
+  buf.resize((size_t)n);
+  CK(cudaMemcpy(buf.data(), p, (size_t)n * sizeof(T), cudaMemcpyDeviceToHost));
+  *out = buf.data();
+  return MAHI_OK;
+}
+
 extern "C" {
 
 double mahi_coulomb_constant(void) { return coulomb_constant(); }
@@ -109,6 +151,7 @@ const char *mahi_error_string(int code) {
     case MAHI_ERR_TIMEOUT: return "a bounded device wait gave up";
     case MAHI_ERR_NO_DEVICE: return "no usable sm_103 (GB300) CUDA device";
     case MAHI_ERR_STATE: return "charges not set";
+    case MAHI_ERR_SITE_OVERFLOW: return "a site's traversal lists outgrew their capacity (raise MAHI_OPT_SITE_LIST_CAP)";
     default: return "unknown error";
   }
 }
@@ -229,8 +272,19 @@ int mahi_create(double box_L_nm, int64_t n_atoms, int32_t n_sites, int32_t order
     if ((e = upload_ops<double>(lat3, &tmp)) != cudaSuccess) return fail(e, "ops");
     h->ops_lat_h3 = (double *)tmp;
     AL(h->L_h3, sizeof(double) * K);
-    AL(h->tc_error_site, 16);
-    cudaMemset(h->tc_error_site, 0, 16);
+    // status word: host-mapped, so that a failure recorded by a kernel can be
+    // read without a synchronisation
+    {
+      void *hp = nullptr, *dp = nullptr;
+      if ((e = cudaHostAlloc(&hp, sizeof(int) * kStatusWords, cudaHostAllocMapped)) != cudaSuccess)
+        return fail(e, "status word");
+      h->status_host = (int *)hp;
+      std::memset(hp, 0, sizeof(int) * kStatusWords);
+      if ((e = cudaHostGetDevicePointer(&dp, hp, 0)) != cudaSuccess) return fail(e, "status word");
+      h->status_dev = (int *)dp;
+    }
+    h->site_theta = default_site_theta(order_p);
+    h->site_list_cap = default_site_list_cap(h->site_theta);
     AL(h->box_qd, sizeof(double) * 8 * h->nbox_total);
     AL(h->d_level_off, sizeof(int64_t) * (kMaxDepth + 2));
     if ((e = cudaMemcpy(h->d_level_off, h->level_off, sizeof(int64_t) * (kMaxDepth + 2), cudaMemcpyHostToDevice)) !=
@@ -273,8 +327,6 @@ int mahi_create(double box_L_nm, int64_t n_atoms, int32_t n_sites, int32_t order
       if ((e = cudaMemcpy(h->tc_units, units.data(), units.size() * sizeof(int), cudaMemcpyHostToDevice)) !=
           cudaSuccess)
         return fail(e, "tc units");
-      AL(h->tc_error, 16);
-      cudaMemset(h->tc_error, 0, 16);
       AL(h->tc_partial, (size_t)h->num_sms * 2 * 128 * h->ld * sizeof(float));  // remainder-unit partial tiles
       AL(h->tc_msrc, (size_t)h->nbox_total * h->ld * sizeof(float));            // M2L source layout
       AL(h->tc_level_off, sizeof(int64_t) * (kMaxDepth + 2));
@@ -313,10 +365,19 @@ int mahi_set_stream(mahi_t h, void *cuda_stream) {
   return MAHI_OK;
 }
 
-int mahi_set_charges(mahi_t h, const double *qA, const double *qB, const int32_t *site_of_atom) {
-  if (!h || !qA || !qB || !site_of_atom) return MAHI_ERR_INVALID_ARG;
+int mahi_set_charges(mahi_t h, const double *qA_in, const double *qB_in, const int32_t *site_in) {
+  if (!h || !qA_in || !qB_in || !site_in) return MAHI_ERR_INVALID_ARG;
   const int64_t N = h->N;
   const int S = h->S;
+  CK(cudaSetDevice(h->device));
+  std::vector<double> bufA, bufB;
+  std::vector<int32_t> bufS;
+  const double *qA = nullptr, *qB = nullptr;
+  const int32_t *site_of_atom = nullptr;
+  int rc0 = host_view(qA_in, N, bufA, &qA);
+  if (rc0 == MAHI_OK) rc0 = host_view(qB_in, N, bufB, &qB);
+  if (rc0 == MAHI_OK) rc0 = host_view(site_in, N, bufS, &site_of_atom);
+  if (rc0 != MAHI_OK) return rc0;
   std::vector<int> cnt(S, 0);
   std::vector<double> dq(N);
   for (int64_t i = 0; i < N; ++i) {
@@ -421,18 +482,85 @@ int mahi_set_forms(mahi_t h, const double *q_env, const int32_t *site_of_atom, c
 
 int mahi_n_lambdas(mahi_t h) { return h ? (h->multiform ? h->n_lam : h->S) : MAHI_ERR_INVALID_ARG; }
 
+// Reads and clears the status word (no synchronisation: only what the device
+// has written so far is seen).
+static int take_status(mahi_t h) {
+  volatile int *st = h->status_host;
+  int rc = MAHI_OK;
+  if (st[kStatusM2LTimeout]) rc = MAHI_ERR_TIMEOUT;
+  else if (st[kStatusSiteOverflow]) rc = MAHI_ERR_SITE_OVERFLOW;
+  if (rc != MAHI_OK)
+    for (int i = 0; i < kStatusWords; ++i) st[i] = 0;
+  return rc;
+}
+
+int mahi_get_status(mahi_t h) {
+  if (!h) return MAHI_ERR_INVALID_ARG;
+  CK(cudaSetDevice(h->device));
+  CK(cudaStreamSynchronize(h->stream));
+  return take_status(h);
+}
+
 int mahi_eval(mahi_t h, const void *x, int32_t x_is_fp64, const double *lambda, double *energy, void *forces,
               double *dEdlambda) {
   if (!h || !x || (h->S > 0 && !lambda)) return MAHI_ERR_INVALID_ARG;
   if (!h->charges_set) return MAHI_ERR_STATE;
+  // a failure of an earlier evaluation that the device has reported by now
+  {
+    const int st = take_status(h);
+    if (st != MAHI_OK) return st;
+  }
   CK(cudaSetDevice(h->device));
   int r = enqueue_eval(h, x, x_is_fp64 ? 1 : 0, lambda, energy, forces, dEdlambda);
   if (r != 0) return cuda_fail((cudaError_t)r, "mahi_eval");
-  if (h->tc_error && h->prec == MAHI_MIXED) {
-    // the tensor-core kernel reports bounded-wait timeouts through a flag that
-    // is checked lazily at the next synchronising call (mahi_eval_host)
-  }
   return MAHI_OK;
+}
+
+int mahi_update_charges(mahi_t h, const double *qA, const double *qB) {
+  if (!h || !qA || !qB) return MAHI_ERR_INVALID_ARG;
+  if (!h->charges_set) return MAHI_ERR_STATE;
+  if (h->multiform) return MAHI_ERR_INVALID_ARG;
+  CK(cudaSetDevice(h->device));
+  if (enqueue_update_charges(h, qA, qB) != 0) return cuda_fail(cudaGetLastError(), "mahi_update_charges");
+  return MAHI_OK;
+}
+
+int mahi_set_option(mahi_t h, int32_t option, double value) {
+  if (!h || !std::isfinite(value)) return MAHI_ERR_INVALID_ARG;
+  switch (option) {
+    case MAHI_OPT_SITE_THETA:
+      if (value < 0.0 || value > 0.7) return MAHI_ERR_INVALID_ARG;
+      h->site_theta_set = value > 0.0;
+      h->site_theta = h->site_theta_set ? (float)value : default_site_theta(h->p);
+      if (!h->site_list_cap_set) h->site_list_cap = default_site_list_cap(h->site_theta);
+      return MAHI_OK;
+    case MAHI_OPT_SITE_LIST_CAP:
+      if (value != 0.0 && (value < 64 || value > kSiteListCapMax || value != std::floor(value)))
+        return MAHI_ERR_INVALID_ARG;
+      h->site_list_cap_set = value > 0.0;
+      h->site_list_cap = h->site_list_cap_set ? (int)value : default_site_list_cap(h->site_theta);
+      return MAHI_OK;
+    case MAHI_OPT_WAIT_LIMIT_MS:
+      if (value < 0.0 || (value > 0.0 && value < 1.0) || value > 60000.0) return MAHI_ERR_INVALID_ARG;
+      h->wait_limit_ns = value > 0.0 ? (uint64_t)(value * 1e6) : 2000000000ull;
+      return MAHI_OK;
+    case MAHI_OPT_WATCHDOG_SELFTEST:
+      if (value != 0.0 && value != 1.0) return MAHI_ERR_INVALID_ARG;
+      h->watchdog_selftest = (int)value;
+      return MAHI_OK;
+    default: return MAHI_ERR_INVALID_ARG;
+  }
+}
+
+double mahi_get_option(mahi_t h, int32_t option) {
+  if (!h) return -1.0;
+  switch (option) {
+    case MAHI_OPT_SITE_THETA: return h->site_theta;
+    case MAHI_OPT_SITE_LIST_CAP: return h->site_list_cap;
+    case MAHI_OPT_WAIT_LIMIT_MS: return (double)h->wait_limit_ns * 1e-6;
+    case MAHI_OPT_WATCHDOG_SELFTEST: return h->watchdog_selftest;
+    default: return -1.0;
+  }
 }
 
 int mahi_backward(mahi_t h, const double *grad_energy, const void *forces, const double *dEdlambda,
@@ -454,6 +582,10 @@ int mahi_eval_host(mahi_t h, const void *x_host, int32_t x_is_fp64, const double
                    void *forces_host, double *dEdlambda_host) {
   if (!h || !x_host || (h->S > 0 && !lambda_host)) return MAHI_ERR_INVALID_ARG;
   if (!h->charges_set) return MAHI_ERR_STATE;
+  {
+    const int st0 = take_status(h);
+    if (st0 != MAHI_OK) return st0;
+  }
   const size_t xs = x_is_fp64 ? 8 : 4;
   const size_t xb = (size_t)h->N * 3 * xs;
   if (h->x_stage_fp64 != (x_is_fp64 ? 1 : 0)) {
@@ -481,17 +613,7 @@ int mahi_eval_host(mahi_t h, const void *x_host, int32_t x_is_fp64, const double
   if (dEdlambda_host && h->S > 0)
     CK(cudaMemcpyAsync(dEdlambda_host, h->d_dEdl_stage, (size_t)nl * 8, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
-  if (h->tc_error) {
-    int flag = 0;
-    CK(cudaMemcpy(&flag, h->tc_error, sizeof(int), cudaMemcpyDeviceToHost));
-    if (flag) return MAHI_ERR_TIMEOUT;
-  }
-  {
-    int flag = 0;
-    CK(cudaMemcpy(&flag, h->tc_error_site, sizeof(int), cudaMemcpyDeviceToHost));
-    if (flag) return MAHI_ERR_INVALID_ARG;  // site traversal frontier overflowed
-  }
-  return MAHI_OK;
+  return take_status(h);
 }
 
 int mahi_get_potential(mahi_t h, double *phi_device) {
@@ -514,6 +636,15 @@ int mahi_stage_times(mahi_t h, float *ms, int32_t n) {
     float t = 0;
     CK(cudaEventElapsedTime(&t, h->ev[i], h->ev[i + 1]));
     ms[i] = t;
+  }
+  // the side-stream intervals follow the main-stream stages (0 when not run)
+  if (ns == num_stages()) {
+    CK(cudaStreamSynchronize(h->side));
+    for (int k = 0; k < 2; ++k, ++ns) {
+      float t = 0;
+      if (h->side_timed & (1 << k)) CK(cudaEventElapsedTime(&t, h->ev[kSideEv + 2 * k], h->ev[kSideEv + 2 * k + 1]));
+      if (ns < n) ms[ns] = t;
+    }
   }
   return ns;
 }

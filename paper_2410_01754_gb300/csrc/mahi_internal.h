@@ -29,6 +29,21 @@ constexpr int kSiteSymPairs = kSiteSymMax * (kSiteSymMax - 1) / 2;
 // Coulomb constant N_A e^2 / (4 pi eps0) in kJ mol^-1 nm e^-2 (CODATA 2018).
 double coulomb_constant();
 
+// Records a failed CUDA call for mahi_last_cuda_error and returns MAHI_ERR_CUDA.
+int cuda_fail(cudaError_t e, const char *what);
+
+// Slots of the per-handle device status word (host-mapped, set by kernels on failure).
+constexpr int kStatusM2LTimeout = 0;   // a bounded wait of the tensor-core M2L gave up
+constexpr int kStatusSiteOverflow = 1; // a site traversal list outgrew its capacity
+constexpr int kStatusWords = 4;
+// Default separation ratio of the site-atom traversal at order p (truncation
+// bound theta^(p+1) of p = 12, theta = 0.4 kept at every order, never above 0.4)
+float default_site_theta(int p);
+// Default list capacity of the site traversal for a separation ratio theta
+int default_site_list_cap(float theta);
+constexpr int kSiteListCapMax = 12288;
+constexpr int kSideEv = 24;            // first of the four side-stream timing events of a handle
+
 // Number of real coefficients of an order-p expansion and the padded row stride.
 inline int ncoef(int p) { return (p + 1) * (p + 1); }
 inline int nstride(int p) { return ((ncoef(p) + 15) / 16) * 16; }
@@ -125,6 +140,13 @@ struct mahi_ctx {
   double *eta = nullptr, *eta_x = nullptr, *eta_y = nullptr, *eta_z = nullptr;  // degree 2p
   double site_aii = 0.0;                      // self term A_ii of the periodic kernel (1/nm)
   float site_theta = 0.40f;                   // separation ratio of the site-potential traversal
+  bool site_theta_set = false;                // set by mahi_set_option (else the default rule)
+  int site_list_cap = 1536;                   // boxes per level of one site's traversal
+  bool site_list_cap_set = false;
+  uint64_t wait_limit_ns = 2000000000ull;     // bounded device waits of the tensor-core M2L
+  int watchdog_selftest = 0;                  // 1: the M2L's first wait is on a barrier nothing completes
+  int *status_host = nullptr;                 // kStatusWords ints, host-mapped pinned memory
+  int *status_dev = nullptr;                  // the same words as seen from the device
   int tune_p2p_threads = 128;                 // autotuned launch shapes (mahi_autotune)
   int tune_site_blocks = 0;                   // 0 = default count of blocks per site
   int *m2l_list = nullptr;                    // [8][189] offset ids
@@ -140,8 +162,6 @@ struct mahi_ctx {
   int64_t *tc_level_off = nullptr;            // device copy of level_off
   int *tc_units = nullptr;
   int tc_nunits = 0;
-  int *tc_error = nullptr;
-  int *tc_error_site = nullptr;               // frontier overflow flag of the site traversal
   // host staging for mahi_eval_host
   void *d_x_stage = nullptr;
   double *d_lam_stage = nullptr, *d_E_stage = nullptr, *d_dEdl_stage = nullptr;
@@ -150,6 +170,7 @@ struct mahi_ctx {
 
   cudaEvent_t ev[32] = {};
   int n_ev = 0;
+  int side_timed = 0;                         // bit k: side-stream interval k recorded
   // side stream for work that does not depend on the main chain (box moments
   // during P2M/M2M, the site-atom potential during L2L/L2P/P2P), forked and
   // joined with events inside every evaluation
@@ -162,6 +183,7 @@ namespace mahi {
 int enqueue_eval(mahi_ctx *h, const void *x, int x_is_fp64, const double *lambda, double *energy,
                  void *forces, double *dEdl);
 int enqueue_potential(mahi_ctx *h, double *phi);
+int enqueue_update_charges(mahi_ctx *h, const double *qA, const double *qB);
 int enqueue_backward(mahi_ctx *h, const double *gE, const void *forces, const double *dEdl, const double *lam,
                      int x_is_fp64, void *dx, double *dlam, double *dqA, double *dqB);
 int upload_tables();

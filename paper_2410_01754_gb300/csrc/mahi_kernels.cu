@@ -1542,7 +1542,6 @@ __device__ __forceinline__ T m2p_high(int P, const T *__restrict__ M, T ux, T uy
 // The batches of separated boxes and leaves are dealt round-robin to G blocks
 // per site; each block repeats the (cheap) classification and writes its own
 // partial sum, so results are bitwise reproducible.
-constexpr int kFrontier = 1536;            // frontier / list entries per buffer
 constexpr int kSiteThreads = 128;
 constexpr int kSiteBatchMax = 64;
 
@@ -1723,13 +1722,13 @@ __global__ void __launch_bounds__(kSiteThreads, 3) k_site_phi(
     int lds, int nbmax, double L, const int64_t *__restrict__ level_off, const int *__restrict__ leaf_start,
     const int *__restrict__ inv_perm, const typename V4<T>::type *__restrict__ part, const T *__restrict__ M,
     const double *__restrict__ qd, const double *__restrict__ mom, const double *__restrict__ Lh3,
-    double *__restrict__ phi_part, int *__restrict__ err, float theta) {
+    double *__restrict__ phi_part, int *__restrict__ err, float theta, int fcap) {
   using V = typename V4<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   int *fa = reinterpret_cast<int *>(smem_raw);          // frontier (current)
-  int *fb = fa + kFrontier;                             // frontier (next)
-  int *sep = fb + kFrontier;                            // separated boxes / direct leaves of this level
-  T *Ms = reinterpret_cast<T *>(sep + kFrontier);       // [nbmax][lds] staged multipole rows
+  int *fb = fa + fcap;                                  // frontier (next)
+  int *sep = fb + fcap;                                 // separated boxes / direct leaves of this level
+  T *Ms = reinterpret_cast<T *>(sep + fcap);            // [nbmax][lds] staged multipole rows
   __shared__ double pa[kMaxSiteAtoms][3], cen[4], base_s[kSiteBatchMax], res_s[kSiteThreads][2];
   __shared__ T pu[kMaxSiteAtoms][3], puu[kMaxSiteAtoms];
   __shared__ T rw[kSiteBatchMax][3], rp[kSiteBatchMax][3], rQ[kSiteBatchMax], rB[kSiteBatchMax],
@@ -1788,7 +1787,8 @@ __global__ void __launch_bounds__(kSiteThreads, 3) k_site_phi(
     pu[a][0] = (T)ux; pu[a][1] = (T)uy; pu[a][2] = (T)uz;
     puu[a] = (T)(ux * ux + uy * uy + uz * uz);
   }
-  for (int t = tid; t < 343; t += blockDim.x) fa[t] = pack_entry(0, t);  // root images
+  for (int t = tid; t < 343 && t < fcap; t += blockDim.x) fa[t] = pack_entry(0, t);  // root images
+  if (fcap < 343 && tid == 0) *(volatile int *)err = 1;  // capacity below the root images
   __syncthreads();
   // thread -> (atom pair, slot), fixed for the whole traversal; a slot takes
   // the rows slot, slot + nslot, ... of every batch
@@ -1798,7 +1798,7 @@ __global__ void __launch_bounds__(kSiteThreads, 3) k_site_phi(
   const int nbatch = (nslot <= nbmax) ? nslot * (nbmax / nslot) : nbmax;
   SiteAcc<T> acc0, acc1;
   double base = 0.0;  // FP64 charge + dipole values at c of the rows this thread stages
-  int n0 = 343, bc = 0, scan_par = 0;
+  int n0 = min(343, fcap), bc = 0, scan_par = 0;
   const T Rf = (T)cen[3];
   // the separation test runs in single precision (its 1e-4 safety margin is far
   // above the rounding of box centres at |x| < 4L); every block of a site
@@ -1832,19 +1832,21 @@ __global__ void __launch_bounds__(kSiteThreads, 3) k_site_phi(
       const int off = block_scan((kind == 0 || kind == 1) ? 1 : (kind == 2 ? (8 << 16) : 0), wsum, scan_par, &tot);
       scan_par ^= 1;
       const int osep = off & 0xffff, oopen = off >> 16;
-      if ((kind == 0 || kind == 1) && nsep + osep < kFrontier) sep[nsep + osep] = (kind == 1) ? (e | (1 << 31)) : e;
+      if ((kind == 0 || kind == 1) && nsep + osep < fcap) sep[nsep + osep] = (kind == 1) ? (e | (1 << 31)) : e;
       nsep += tot & 0xffff;
       if (kind == 2) {
         const int box = e >> 9, img = e & 511;
         for (int c = 0; c < 8; ++c)
-          if (n1 + oopen + c < kFrontier) fb[n1 + oopen + c] = pack_entry(8 * box + c, img);
+          if (n1 + oopen + c < fcap) fb[n1 + oopen + c] = pack_entry(8 * box + c, img);
       }
       n1 += tot >> 16;
     }
-    if (nsep > kFrontier || n1 > kFrontier) {
-      if (tid == 0) atomicExch(err, 1);
-      nsep = min(nsep, kFrontier);
-      n1 = min(n1, kFrontier);
+    if (nsep > fcap || n1 > fcap) {
+      // list capacity exceeded: recorded in the handle's status word; the
+      // traversal goes on with the entries that fit (all accesses stay in bounds)
+      if (tid == 0) *(volatile int *)err = 1;
+      nsep = min(nsep, fcap);
+      n1 = min(n1, fcap);
     }
     __syncthreads();
     for (int b = 0; b < nsep; b += nbatch, ++bc) {
@@ -2049,8 +2051,12 @@ __global__ void k_unpermute_phi(int64_t N, const int *__restrict__ inv_perm, con
 // ---------------------------------------------------------------------------
 // orchestration
 // ---------------------------------------------------------------------------
-static const char *kStageNames[] = {"bin", "sort", "p2m", "m2m", "lattice", "m2l", "l2l", "l2p", "p2p", "site"};
-const char *stage_name(int i) { return (i >= 0 && i < 10) ? kStageNames[i] : "?"; }
+// main-stream intervals, then the two side-stream intervals (overlapping the
+// main stream: the sites' FP64 pair terms during binning/P2M/M2M, the refined
+// site-atom potential during L2L/L2P/P2P)
+static const char *kStageNames[] = {"bin", "sort", "p2m", "m2m", "lattice", "m2l", "l2l", "l2p", "p2p", "site",
+                                    "side_site_pairs", "side_site_potential"};
+const char *stage_name(int i) { return (i >= 0 && i < 12) ? kStageNames[i] : "?"; }
 int num_stages() { return 10; }
 
 #define MAHI_CK(call)                                   \
@@ -2111,9 +2117,16 @@ static cudaError_t launch_gemm(const GemmMap &mp, int K, int ld, const T *in, T 
 }
 
 static inline void mark(mahi_ctx *h, int stage) {
-  if (h->timing && stage < 31) {
+  if (h->timing && stage < 20) {
     cudaEventRecord(h->ev[stage], h->stream);
     h->n_ev = stage + 1;
+  }
+}
+// side-stream interval k (0: site pair terms, 1: site-atom potential) start / end
+static inline void mark_side(mahi_ctx *h, int k, int end) {
+  if (h->timing) {
+    cudaEventRecord(h->ev[kSideEv + 2 * k + end], h->side);
+    h->side_timed |= 1 << k;
   }
 }
 
@@ -2143,14 +2156,17 @@ static cudaError_t eval_t(mahi_ctx *h, const XT *x, const double *lam, double *e
   T *M = (T *)h->Mexp, *Lx = (T *)h->Lexp;
   const double *mom = h->box_qd;  // root box row: Q, D, T of the system about the box centre
   h->launches = 0;
+  h->side_timed = 0;
   mark(h, 0);
   if (h->S > 0 && !h->multiform) {
     // the sites' FP64 pair terms need only the positions: side stream, from
     // the start (the FP64 pipe is idle during binning, P2M and M2M)
     MAHI_CK(cudaEventRecord(h->fork_ev[2], st));
     MAHI_CK(cudaStreamWaitEvent(h->side, h->fork_ev[2], 0));
+    mark_side(h, 0, 0);
     k_site_pairs<XT><<<h->S, 64, 0, h->side>>>(h->L, kSiteDegree, h->site_ptr, h->site_atoms, x, h->eta, h->eta_x,
                                                h->eta_y, h->eta_z, h->site_pairs);
+    mark_side(h, 0, 1);
     h->launches += 1;
   }
   MAHI_CK(cudaMemsetAsync(h->leaf_count, 0, sizeof(int) * nleaf, st));
@@ -2240,10 +2256,11 @@ static cudaError_t eval_t(mahi_ctx *h, const XT *x, const double *lam, double *e
     // the per-site terms.
     MAHI_CK(cudaEventRecord(h->fork_ev[1], st));
     MAHI_CK(cudaStreamWaitEvent(h->side, h->fork_ev[1], 0));
+    mark_side(h, 1, 0);
     // rows of staged multipoles: as many as keep three blocks per SM
     const int lds = ld + 16 / (int)sizeof(T);
-    const size_t fixed = sizeof(int) * 3 * kFrontier;
-    const size_t budget = 72 * 1024;
+    const size_t fixed = sizeof(int) * 3 * (size_t)h->site_list_cap;
+    const size_t budget = std::max<size_t>(72 * 1024, fixed + 8 * sizeof(T) * lds);
     const int nbmax = (int)std::max<size_t>(8, std::min<size_t>(kSiteBatchMax, (budget - fixed) / (sizeof(T) * lds)));
     const size_t smp = fixed + sizeof(T) * nbmax * lds;
     // blocks per site: about 4 x 3 per SM over all sites, unless the autotuner picked a count
@@ -2252,9 +2269,11 @@ static cudaError_t eval_t(mahi_ctx *h, const XT *x, const double *lam, double *e
                       : std::max(1, std::min(kSiteChunksMax, (4 * 3 * h->num_sms + h->S - 1) / std::max(1, h->S)));
     MAHI_CK(launch_site_phi<T>(P, G, smp, h->side, h->S, G, h->site_ptr, h->site_atoms, h->d, P, ld, lds, nbmax, h->L,
                                h->d_level_off, h->leaf_start, h->inv_perm, (const V *)h->part, M, h->box_qd,
-                               mom, h->L_h3, h->phi_part, h->tc_error_site, h->site_theta));
+                               mom, h->L_h3, h->phi_part, h->status_dev + kStatusSiteOverflow, h->site_theta,
+                               h->site_list_cap));
     k_site_phi_sum<<<(h->n_site_atoms + 127) / 128, 128, 0, h->side>>>(h->n_site_atoms, G, coulomb_constant(),
                                                                         h->phi_part, h->phi_site);
+    mark_side(h, 1, 1);
     MAHI_CK(cudaEventRecord(h->join_ev[1], h->side));
   }
   for (int l = 1; l <= h->d; ++l) {
@@ -2436,6 +2455,24 @@ int enqueue_eval(mahi_ctx *h, const void *x, int x_is_fp64, const double *lambda
     else e = eval_t<float, float>(h, (const float *)x, lambda, energy, (float *)forces, dEdl);
   }
   return e == cudaSuccess ? 0 : (int)e;
+}
+
+// new charges for the same site map: qA as given, D = qB - qA on site atoms,
+// 0 on environment atoms (they carry qA only)
+__global__ void k_update_charges(int64_t N, const double *__restrict__ qA_in, const double *__restrict__ qB_in,
+                                 const int *__restrict__ site_of, double *__restrict__ qA, double *__restrict__ dq) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += stride) {
+    const double a = qA_in[i];
+    qA[i] = a;
+    dq[i] = site_of[i] >= 0 ? qB_in[i] - a : 0.0;
+  }
+}
+
+int enqueue_update_charges(mahi_ctx *h, const double *qA, const double *qB) {
+  const int grid = (int)std::min<int64_t>(4 * (int64_t)h->num_sms, (h->N + 255) / 256);
+  k_update_charges<<<grid, 256, 0, h->stream>>>(h->N, qA, qB, h->site_of, h->qA, h->dq);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 __global__ void k_patch_site_phi(int nsa, const int *__restrict__ site_atoms, const double *__restrict__ phi_site,

@@ -41,7 +41,7 @@ constexpr int kStagesS = 4;      // A staging slots in shared memory per produce
 constexpr int kStagesB = 12;     // B stages in shared memory (at most; Params::nsb is the count used)
 constexpr int kThreads = 480;     // 15 warps: MMA (tile 0), B producer, 2 x 4 A producers, 4 epilogue, MMA (tile 1)
 constexpr uint32_t kSpinLimit = 1u << 26;
-constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s: no wait of a healthy launch comes near it
+constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s: drains of work in flight (they end in microseconds)
 constexpr int kMaxN = 256;       // MMA N limit: Kp <= 256, order <= 15
 
 struct Unit {
@@ -56,7 +56,9 @@ struct Params {
   const int *list;              // [8][189] offset ids
   const int *off;               // [316][3]
   const int64_t *level_off;     // [kMaxDepth + 2]
-  int *error;
+  int *error;                   // status word slot (host-mapped), set to 1 when a wait gave up
+  uint64_t wait_ns;             // limit of every bounded pipeline wait
+  int selftest;                 // 1: the tile-0 issuer first waits on a barrier nothing completes
   int ld, nch, ngroups;         // row stride, K chunks, N row groups (Kp/8)
   int nunits;
   int nfull, nrem, q;           // units done whole (round-robin), remainder units, slices per remainder unit
@@ -109,27 +111,15 @@ __device__ __forceinline__ uint64_t global_ns() {
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
-// bounded wait: gives up after kWaitNs (or when another role of the CTA gave
+// bounded wait: gives up after lim ns (or when another role of the CTA gave
 // up), raising the abort flag; returns false then
-__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity, volatile int *abort_flag) {
+__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity, volatile int *abort_flag, uint64_t lim) {
   if (mbar_test(b, parity)) return true;  // non-blocking test first: most waits find the phase complete
   const uint64_t t0 = global_ns();
   for (uint32_t it = 0; it < tc::kSpinLimit; ++it) {
     if (mbar_try_wait(b, parity)) return true;
     if (*abort_flag) return false;
-    if ((it & 255) == 255 && global_ns() - t0 > tc::kWaitNs) break;
-  }
-  *abort_flag = 1;
-  return false;
-}
-// bounded wait by non-blocking tests only (no suspension between tests): for
-// the single lanes on the pipeline's critical path
-__device__ __forceinline__ bool mbar_spin(uint64_t *b, uint32_t parity, volatile int *abort_flag) {
-  const uint64_t t0 = global_ns();
-  for (uint32_t it = 0;; ++it) {
-    if (mbar_test(b, parity)) return true;
-    if (*abort_flag) return false;
-    if ((it & 255) == 255 && global_ns() - t0 > tc::kWaitNs) break;
+    if ((it & 255) == 255 && global_ns() - t0 > lim) break;
   }
   *abort_flag = 1;
   return false;
@@ -486,7 +476,8 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_m2l_tc(tc::Params prm) {
   int *s_list = reinterpret_cast<int *>(sS + 2 * kStagesS * 4 * kRows * 16);  // [8][189] offset ids
   int *s_off = s_list + 8 * kListLen;                                   // [316][3] offsets
   uint64_t *bars = reinterpret_cast<uint64_t *>(s_off + ((3 * kNumOffsets + 1) & ~1));
-  uint64_t *fullA = bars, *emptyA = bars + kStagesA, *fullB = bars + 2 * kStagesA,
+  // idle[0] is a barrier that nothing arrives on (the watchdog self-test waits on it)
+  uint64_t *fullA = bars, *idle = bars + kStagesA, *fullB = bars + 2 * kStagesA,
            *emptyB = bars + 2 * kStagesA + kStagesB;
   uint64_t *accb = bars + 2 * kStagesA + 2 * kStagesB, *tfree = accb + 1;
   uint64_t *mdone = tfree + 1;                      // [2] last commit of each MMA issuer
@@ -509,7 +500,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_m2l_tc(tc::Params prm) {
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStagesA; ++s) {
       mbar_init(&fullA[s], 4);   // the four warps of the producer group of that item
-      mbar_init(&emptyA[s], 2);  // (unused)
+      mbar_init(&idle[s], 1);    // never arrived on
     }
     for (int s = 0; s < kStagesB; ++s) {
       mbar_init(&fullB[s], 1);
@@ -597,7 +588,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_m2l_tc(tc::Params prm) {
       // its phase complete: one commit per MMA issuer and item)
       if (q >= kStagesA && lane == 0) {
         const int qd = q - kStagesA;
-        ok = mbar_wait(&emptyB[qd % nsb], (uint32_t)((qd / nsb) & 1), abort_flag);
+        ok = mbar_wait(&emptyB[qd % nsb], (uint32_t)((qd / nsb) & 1), abort_flag, prm.wait_ns);
       }
       if (!__shfl_sync(0xffffffffu, ok, 0)) break;
       tc_fence_after();
@@ -618,7 +609,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_m2l_tc(tc::Params prm) {
       ItemIter it;
       iter_begin(prm, k, nA, nit, it);
       for (int q = 0; q < nloc; ++q) {
-        if (q >= nsb && !mbar_wait(&emptyB[s], ph, abort_flag)) break;
+        if (q >= nsb && !mbar_wait(&emptyB[s], ph, abort_flag, prm.wait_ns)) break;
         if (it.unit != ucur) {
           child = prm.units[it.unit].y;
           ucur = it.unit;
@@ -659,16 +650,18 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_m2l_tc(tc::Params prm) {
     ItemIter it;
     iter_begin(prm, k, nA, nit, it);
     const uint32_t sB0 = smem_u32(sB);
-    for (int q = 0; q < nloc; ++q) {
+    // watchdog self-test: a wait that runs out before any MMA is issued
+    const bool go = !(prm.selftest && mt == 0) || mbar_wait(&idle[0], 0, abort_flag, prm.wait_ns);
+    for (int q = 0; go && q < nloc; ++q) {
       if (seg_start) {
         // new segment: the accumulators must have been drained by the epilogue
-        if (it.seg >= 1 && !mbar_wait(tfree, (it.seg - 1) & 1, abort_flag)) break;
+        if (it.seg >= 1 && !mbar_wait(tfree, (it.seg - 1) & 1, abort_flag, prm.wait_ns)) break;
         tc_fence_after();
         first = true;
         ntile = tile_count(prm, prm.units[it.unit], 1) > 0 ? 2 : 1;
       }
-      if (!mbar_wait(&fullA[sa], pa, abort_flag)) break;
-      if (!mbar_wait(&fullB[sb], pb, abort_flag)) break;
+      if (!mbar_wait(&fullA[sa], pa, abort_flag, prm.wait_ns)) break;
+      if (!mbar_wait(&fullB[sb], pb, abort_flag, prm.wait_ns)) break;
       tc_fence_after();
       if (mt < ntile) {
         const uint32_t bh = sB0 + (uint32_t)sb * 2u * b_bytes, bl = bh + b_bytes;
@@ -699,7 +692,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_m2l_tc(tc::Params prm) {
     const int quarter = warp & 3;                   // TMEM lanes this warp may read
     const int r = quarter * 32 + lane;
     for (int seg = 0; seg < nseg; ++seg) {
-      if (!__all_sync(0xffffffffu, mbar_wait(accb, seg & 1, abort_flag))) break;  // warp-collective TMEM loads follow
+      if (!__all_sync(0xffffffffu, mbar_wait(accb, seg & 1, abort_flag, prm.wait_ns))) break;  // warp-collective TMEM loads follow
       tc_fence_after();
       const int unit = seg < nA ? k + seg * (int)gridDim.x : prm.nfull + k / prm.q;
       const int4 u = prm.units[unit];
@@ -729,7 +722,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_m2l_tc(tc::Params prm) {
   __syncwarp();
   tc_fence_before();
   __syncthreads();
-  if (*abort_flag && threadIdx.x == 0) atomicExch(prm.error, 1);
+  if (*abort_flag && threadIdx.x == 0) *(volatile int *)prm.error = 1;
   if (warp == 0) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
@@ -837,7 +830,9 @@ int tc_m2l(mahi_ctx *h) {
   prm.list = h->m2l_list;
   prm.off = h->m2l_off;
   prm.level_off = h->tc_level_off;
-  prm.error = h->tc_error;
+  prm.error = h->status_dev + kStatusM2LTimeout;
+  prm.wait_ns = h->wait_limit_ns;
+  prm.selftest = h->watchdog_selftest;
   prm.ld = h->ld;
   prm.nch = h->ld / tc::kKC;
   prm.ngroups = h->ld / 8;

@@ -11,15 +11,18 @@
 // same per-site arithmetic as the k_site stage of mahi_eval.
 //
 // Scratch: g_site_energy, kStaticMaxSites doubles (32 KiB), plus the tables of
-// the first-shell lattice function (4 x 41^2 doubles); every GPU that loads the
-// library holds them until the process exits.  All calls share the scratch and
-// keep the last call's contents; calls whose work overlaps on the GPU race.
+// the first-shell lattice function (4 x 41^2 doubles, filled from the host
+// planner's coefficients, the same ones mahi_create uploads); every GPU that
+// loads the library holds them until the process exits.  All calls share the
+// scratch and keep the last call's contents; calls whose work overlaps on the
+// GPU race.  Every site is validated (offsets, size, atom indices) before any
+// per-atom array is touched.
 #include <cuda_runtime.h>
 
 #include <cmath>
-#include <complex>
 #include <cstring>
 #include <mutex>
+#include <vector>
 
 #include "mahi_internal.h"
 
@@ -40,115 +43,18 @@ bool g_ready[kMaxDevices] = {};
 double *g_energy_ptr[kMaxDevices] = {};
 double *g_eta_ptr[kMaxDevices] = {};
 
-using cd = std::complex<double>;
-constexpr int tri(int l, int m) { return l * (l + 1) / 2 + m; }
-
-// Fixed-size (heap-free) host evaluation of the scaled regular harmonics R_lm,
-// m >= 0, at a point; out has tri(P, P) + 1 entries.
-void regular_fixed(int P, const double r[3], cd *out) {
-  const double x = r[0], y = r[1], z = r[2], r2 = x * x + y * y + z * z;
-  out[0] = 1.0;
-  for (int m = 0; m <= P; ++m) {
-    if (m > 0) out[tri(m, m)] = -cd(x, y) / (2.0 * m) * out[tri(m - 1, m - 1)];
-    if (m + 1 <= P) out[tri(m + 1, m)] = z * out[tri(m, m)];
-    for (int l = m + 2; l <= P; ++l)
-      out[tri(l, m)] = ((2.0 * l - 1.0) * z * out[tri(l - 1, m)] - r2 * out[tri(l - 2, m)]) / double((l + m) * (l - m));
-  }
-}
-
-// H_1(r) for the unit box by Ewald splitting (first image shell removed, no
-// singular term), as in the library's lattice coefficients.
-double lattice_h1(const double r[3]) {
-  const double a = 2.6, two_over_sqrtpi = 1.12837916709551257390;
-  double s = 0.0;
-  for (int nx = -4; nx <= 4; ++nx)
-    for (int ny = -4; ny <= 4; ++ny)
-      for (int nz = -4; nz <= 4; ++nz) {
-        const double dx = r[0] + nx, dy = r[1] + ny, dz = r[2] + nz, d = std::sqrt(dx * dx + dy * dy + dz * dz);
-        const bool near = std::abs(nx) <= 1 && std::abs(ny) <= 1 && std::abs(nz) <= 1;
-        if (near) s -= (d > 0.0) ? std::erf(a * d) / d : two_over_sqrtpi * a;
-        else if (d < 2.45) s += std::erfc(a * d) / d;
-      }
-  double rec = 0.0;
-  for (int mx = -6; mx <= 6; ++mx)
-    for (int my = -6; my <= 6; ++my)
-      for (int mz = -6; mz <= 6; ++mz) {
-        const int m2 = mx * mx + my * my + mz * mz;
-        if (m2 == 0 || m2 > 36) continue;
-        const double k2 = 4.0 * kPi * kPi * m2;
-        rec += std::exp(-k2 / (4.0 * a * a)) / k2 * std::cos(2.0 * kPi * (mx * r[0] + my * r[1] + mz * r[2]));
-      }
-  return s + 4.0 * kPi * rec - kPi / (a * a) - (2.0 * kPi / 3.0) * (r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
-}
-
-// Coefficients of H_1 (degree kStaticDeg, real layout) and of its gradient
-// (degree kStaticDeg - 1), into fixed host buffers: projection on the sphere
-// |r| = 1.2 with Gauss-Legendre x trapezoid quadrature.
+// Coefficients of the first-shell lattice function H_1 (degree kStaticDeg, real
+// layout) and of its gradient (degree kStaticDeg - 1) from the library's host
+// planner: the same tables the evaluation path uploads.
 void h1_tables(double (*tab)[kStaticCoef]) {
-  static cd acc[tri(kStaticDeg, kStaticDeg) + 1];
-  static cd R[tri(kStaticDeg, kStaticDeg) + 1];
-  static double gx[kStaticDeg + 64], gw[kStaticDeg + 64];
-  const int P = kStaticDeg, nt = P + 64, np = 2 * nt;
-  const double rho = 1.2;
-  for (int i = 0; i < nt; ++i) {  // Gauss-Legendre nodes by Newton iteration
-    double z = std::cos(kPi * (i + 0.75) / (nt + 0.5)), pp = 0.0;
-    for (int it = 0; it < 100; ++it) {
-      double p1 = 1.0, p2 = 0.0;
-      for (int j = 1; j <= nt; ++j) { const double p3 = p2; p2 = p1; p1 = ((2.0 * j - 1.0) * z * p2 - (j - 1.0) * p3) / j; }
-      pp = nt * (z * p1 - p2) / (z * z - 1.0);
-      const double dz = p1 / pp;
-      z -= dz;
-      if (std::abs(dz) < 1e-16) break;
-    }
-    gx[i] = z;
-    gw[i] = 2.0 / ((1.0 - z * z) * pp * pp);
-  }
-  for (auto &v : acc) v = 0.0;
-  for (int it = 0; it < nt; ++it) {
-    const double ct = gx[it], st = std::sqrt(std::max(0.0, 1.0 - ct * ct));
-    for (int jp = 0; jp < np; ++jp) {
-      const double ph = 2.0 * kPi * jp / np;
-      const double s[3] = {st * std::cos(ph), st * std::sin(ph), ct};
-      const double r[3] = {rho * s[0], rho * s[1], rho * s[2]};
-      const double h = lattice_h1(r) * gw[it] * (2.0 * kPi / np);
-      regular_fixed(P, s, R);
-      for (int k = 0; k <= tri(P, P); ++k) acc[k] += h * R[k];
-    }
-  }
+  const std::vector<double> &eta = lattice_coeffs(kStaticDeg, 1);
   std::memset(tab, 0, sizeof(double) * 4 * kStaticCoef);
-  double lf[2 * kStaticDeg + 2];
-  lf[0] = 0.0;
-  for (int i = 1; i < 2 * kStaticDeg + 2; ++i) lf[i] = lf[i - 1] + std::log((double)i);
-  for (int l = 0; l <= P; l += 2)
-    for (int m = 0; m <= l; m += 4) {
-      if (l == 2) continue;  // cubic symmetry: even l, m = 0 mod 4, real
-      const double logN = std::log(4.0 * kPi / (2.0 * l + 1.0)) - lf[l + m] - lf[l - m];
-      const double v = acc[tri(l, m)].real() / std::exp(l * std::log(rho) + logN);
-      tab[0][m == 0 ? l * l : l * l + 2 * m - 1] = v;
-    }
-  // gradient maps: d/dz conj R_lm = conj R_{l-1,m}; d/dx = (conj R_{l-1,m+1} - conj R_{l-1,m-1})/2;
-  // d/dy = i (conj R_{l-1,m-1} + conj R_{l-1,m+1})/2
-  auto get = [&](int l, int m) -> cd {
-    if (l < 0 || m > l || -m > l) return 0.0;
-    const int am = m < 0 ? -m : m;
-    cd v = am == 0 ? cd(tab[0][l * l], 0.0) : cd(tab[0][l * l + 2 * am - 1], tab[0][l * l + 2 * am]);
-    if (m < 0) { v = std::conj(v); if (am & 1) v = -v; }
-    return v;
-  };
-  for (int l = 0; l <= P - 1; ++l)
-    for (int m = 0; m <= l; ++m) {
-      const cd zc = get(l + 1, m), xc = 0.5 * (get(l + 1, m - 1) - get(l + 1, m + 1)),
-               yc = cd(0, 0.5) * (get(l + 1, m + 1) + get(l + 1, m - 1));
-      const cd g3[3] = {xc, yc, zc};
-      for (int a = 0; a < 3; ++a) {
-        if (m == 0) tab[1 + a][l * l] = g3[a].real();
-        else { tab[1 + a][l * l + 2 * m - 1] = g3[a].real(); tab[1 + a][l * l + 2 * m] = g3[a].imag(); }
-      }
-    }
+  std::memcpy(tab[0], eta.data(), sizeof(double) * kStaticCoef);
+  gradient_coeffs(kStaticDeg, eta.data(), tab[1], tab[2], tab[3]);
 }
 
 template <typename XT, typename FT>
-__global__ void k_site_static(int S, double L, double fcoul, const int *__restrict__ site_ptr,
+__global__ void k_site_static(int S, int64_t n_atoms, double L, double fcoul, const int *__restrict__ site_ptr,
                               const int *__restrict__ site_atoms, const XT *__restrict__ x,
                               const double *__restrict__ qA, const double *__restrict__ qB,
                               const double *__restrict__ lam, const double *__restrict__ phi,
@@ -158,8 +64,19 @@ __global__ void k_site_static(int S, double L, double fcoul, const int *__restri
   const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int site = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (site >= S) return;
-  const int b = site_ptr[site], n = site_ptr[site + 1] - b;
-  if (n < 1 || n > kStaticMaxSiteAtoms) {  // malformed site: flag it, touch nothing else
+  // validate the site before any per-atom array is read: offsets in order and
+  // within site_ptr[S], 1..64 atoms, every atom index in [0, n_atoms)
+  const int b = site_ptr[site], n = site_ptr[site + 1] - b, total = site_ptr[S];
+  bool bad = b < 0 || n < 1 || n > kStaticMaxSiteAtoms || b + n > total;
+  if (!bad) {
+    bool mine = false;
+    for (int a = lane; a < n; a += 32) {
+      const int i = site_atoms[b + a];
+      mine = mine || i < 0 || (int64_t)i >= n_atoms;
+    }
+    bad = __any_sync(0xffffffffu, mine);
+  }
+  if (bad) {  // malformed site: flag it, touch nothing else
     if (lane == 0) {
       if (dEdl) dEdl[site] = nan("");
       site_energy[site] = nan("");
@@ -273,14 +190,15 @@ __global__ void k_sum_static(int S, const double *__restrict__ site_energy, doub
 }  // namespace
 }  // namespace mahi
 
-extern "C" int mahi_site_terms_static(double box_L_nm, int32_t n_sites, const int32_t *site_ptr,
+extern "C" int mahi_site_terms_static(double box_L_nm, int64_t n_atoms, int32_t n_sites, const int32_t *site_ptr,
                                       const int32_t *site_atoms, const void *x, int32_t x_is_fp64, const double *qA,
                                       const double *qB, const double *lambda, const double *phi, double *dEdlambda,
                                       double *energy_correction, void *forces, void *cuda_stream) {
   using namespace mahi;
   if (!(box_L_nm > 0.0) || !std::isfinite(box_L_nm) || n_sites < 0) return MAHI_ERR_INVALID_ARG;
   if (n_sites > kStaticMaxSites) return MAHI_ERR_INVALID_ARG;  // beyond the static scratch
-  if (n_sites > 0 && (!site_ptr || !site_atoms || !x || !qA || !qB || !lambda || !phi)) return MAHI_ERR_INVALID_ARG;
+  if (n_sites > 0 && (n_atoms < 1 || !site_ptr || !site_atoms || !x || !qA || !qB || !lambda || !phi))
+    return MAHI_ERR_INVALID_ARG;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return MAHI_ERR_NO_DEVICE;
   {
@@ -290,28 +208,36 @@ extern "C" int mahi_site_terms_static(double box_L_nm, int32_t n_sites, const in
     if (!g_ready[dev]) {
       static double tab[4][kStaticCoef];
       h1_tables(tab);
-      if (cudaMemcpyToSymbol(g_eta, tab, sizeof(tab)) != cudaSuccess) return MAHI_ERR_CUDA;
+      cudaError_t e = cudaMemcpyToSymbol(g_eta, tab, sizeof(tab));
+      if (e != cudaSuccess) return cuda_fail(e, "mahi_site_terms_static: lattice tables");
       void *p = nullptr;
-      if (cudaGetSymbolAddress(&p, g_site_energy) != cudaSuccess) return MAHI_ERR_CUDA;
+      if ((e = cudaGetSymbolAddress(&p, g_site_energy)) != cudaSuccess)
+        return cuda_fail(e, "mahi_site_terms_static: scratch address");
       g_energy_ptr[dev] = static_cast<double *>(p);
-      if (cudaGetSymbolAddress(&p, g_eta) != cudaSuccess) return MAHI_ERR_CUDA;
+      if ((e = cudaGetSymbolAddress(&p, g_eta)) != cudaSuccess)
+        return cuda_fail(e, "mahi_site_terms_static: table address");
       g_eta_ptr[dev] = static_cast<double *>(p);
       g_ready[dev] = true;
     }
   }
   cudaStream_t st = (cudaStream_t)cuda_stream;
-  const double f = coulomb_constant();
+  double f = coulomb_constant();
+  double L = box_L_nm;
+  int S = n_sites;
+  int64_t na = n_atoms;
+  double *eta = g_eta_ptr[dev], *sen = g_energy_ptr[dev];
   if (n_sites > 0) {
-    const int blocks = (n_sites + 3) / 4;
-    if (x_is_fp64)
-      k_site_static<double, double><<<blocks, 128, 0, st>>>(n_sites, box_L_nm, f, site_ptr, site_atoms,
-                                                            (const double *)x, qA, qB, lambda, phi, g_eta_ptr[dev],
-                                                            g_energy_ptr[dev], dEdlambda, (double *)forces);
-    else
-      k_site_static<float, float><<<blocks, 128, 0, st>>>(n_sites, box_L_nm, f, site_ptr, site_atoms,
-                                                          (const float *)x, qA, qB, lambda, phi, g_eta_ptr[dev],
-                                                          g_energy_ptr[dev], dEdlambda, (float *)forces);
+    // launched through cudaLaunchKernel so that the error returned is this launch's own
+    void *args[] = {&S, &na, &L, &f, (void *)&site_ptr, (void *)&site_atoms, (void *)&x, (void *)&qA, (void *)&qB,
+                    (void *)&lambda, (void *)&phi, &eta, &sen, &dEdlambda, &forces};
+    const void *fn = x_is_fp64 ? (const void *)k_site_static<double, double> : (const void *)k_site_static<float, float>;
+    const cudaError_t e = cudaLaunchKernel(fn, dim3((n_sites + 3) / 4), dim3(128), args, 0, st);
+    if (e != cudaSuccess) return cuda_fail(e, "mahi_site_terms_static: site kernel");
   }
-  if (energy_correction) k_sum_static<<<1, 256, 0, st>>>(n_sites, g_energy_ptr[dev], energy_correction);
-  return cudaGetLastError() == cudaSuccess ? MAHI_OK : MAHI_ERR_CUDA;
+  if (energy_correction) {
+    void *args[] = {&S, &sen, &energy_correction};
+    const cudaError_t e = cudaLaunchKernel((const void *)k_sum_static, dim3(1), dim3(256), args, 0, st);
+    if (e != cudaSuccess) return cuda_fail(e, "mahi_site_terms_static: energy sum");
+  }
+  return MAHI_OK;
 }

@@ -25,10 +25,16 @@ def run_gpu(s, prec, p=None, d=None, x_dtype="float64", evals=1):
 
 
 def errors(res, ref, idx=None):
+    """Force error as relative RMS (Frel) and as the worst single atom,
+    |F_i - F_ref,i| / rms_i |F_ref,i| (Fmax, at atom Fmax_atom, an index into
+    the compared atoms); worst |d dE/dlambda| in kJ/mol; relative energy."""
     F = res["F"] if idx is None else res["F"][idx]
     Fr = ref["F"]
+    per = np.sqrt(((F - Fr) ** 2).sum(axis=1))
+    rms = np.sqrt((Fr ** 2).sum(axis=1).mean())
     out = dict(
         Frel=float(np.sqrt(((F - Fr) ** 2).sum() / (Fr ** 2).sum())),
+        Fmax=float(per.max() / rms), Fmax_atom=int(per.argmax()),
         dEdl=float(np.abs(res["dEdl"] - ref["dEdl"]).max()) if len(ref["dEdl"]) else 0.0,
     )
     if ref.get("E") is not None:

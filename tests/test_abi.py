@@ -38,7 +38,7 @@ def test_coulomb_constant_matches_oracle():
 
 
 def test_error_strings():
-    for c in range(0, -8, -1):
+    for c in range(0, -9, -1):
         assert pkg.mahi_error_string(c)
 
 

@@ -1,12 +1,16 @@
 """The allocation-free per-site entry point (mahi_site_terms_static) against
-the library's own evaluation.
+the library's own evaluation and the oracle.
 
 It exists for callers that cannot allocate device memory where they need the
 per-site terms (stream capture, externally owned memory pools, other solvers
 producing the charge-scaled potential).  Given the potential that mahi_eval
 used (mahi_get_potential), it must reproduce mahi_eval's dE/dlambda, and its
-energy and force corrections must match the closed forms, on two calls in a
-row (its scratch is reused).  Collected last on purpose."""
+energy and force corrections must match the oracle's intra-site terms
+(k_s = f D^T A D over the site's atoms and their pair forces), on two calls
+in a row (its scratch is reused).  A call captured into a CUDA graph must give
+the same bits (nothing on its path may allocate or synchronise), and a site
+with an atom index out of range must come back as NaN without any access.
+Collected last on purpose."""
 import numpy as np
 import pytest
 
@@ -61,19 +65,19 @@ def test_static_site_terms_match_eval(prec, xdt):
     assert np.array_equal(d1, d2) and e1 == e2 and np.array_equal(f1, f2)
     # dE/dlambda of the allocation-free path equals mahi_eval's
     np.testing.assert_allclose(d1, ref_dEdl, rtol=1e-12, atol=1e-9)
-    # energy correction = sum_s 1/2 lam (1 - lam) k_s with k_s from the same outputs
+    # energy and force corrections against the oracle's intra-site terms:
+    # sum_s 1/2 lam (1 - lam) f k_s, and the pair forces of each site
     dq = s["qB"] - s["qA"]
-    phin = phi.cpu().numpy()
-    gs = np.array([np.sum(dq[atoms[ptr[k]:ptr[k + 1]]] * phin[atoms[ptr[k]:ptr[k + 1]]]) for k in range(S)])
-    ks = (d1 - gs) / (0.5 - s["lam"])
-    assert e1 == pytest.approx(float(np.sum(0.5 * s["lam"] * (1 - s["lam"]) * ks)), rel=1e-9)
-    # force corrections against the oracle's intra-site pair sums
+    e_ref = 0.0
+    tol = 1e-9 if xdt == "float64" else 1e-5   # float32 positions enter the pair distances
     for k in range(S):
         at = atoms[ptr[k]:ptr[k + 1]]
-        _, fc = hi.site_terms(s["x"][at], dq[at], L)
+        xs = np.asarray(x[at.tolist()].double().cpu().numpy())
+        ks, fc = hi.site_terms(xs, dq[at], L)
         w = s["lam"][k] * (1 - s["lam"][k]) * oracle.F_COULOMB
-        tol = 1e-9 if xdt == "float64" else 1e-5
+        e_ref += 0.5 * w * ks
         np.testing.assert_allclose(f1[at], w * fc, rtol=tol, atol=tol * (1 + np.abs(w * fc).max()))
+    assert e1 == pytest.approx(e_ref, rel=1e-9, abs=1e-9)
     # atoms outside the sites are untouched
     mask = np.ones(N, dtype=bool)
     mask[atoms] = False
@@ -91,3 +95,55 @@ def test_static_site_terms_reject_too_many_sites():
     with pytest.raises(pkg.MahiError) as ei:
         pkg.mahi_site_terms_static(3.0, ptr, atoms, x, q, q, lam, q)
     assert ei.value.code == -1
+
+
+def test_static_site_terms_in_a_captured_graph():
+    """One call captured into a CUDA graph on a side stream (after the set-up
+    call): the replay must give the uncaptured call's bits."""
+    s = synth.make_water(n_water=2000, grid=16, L=3.9, n_sites=6, seed=22, depth=3, order=8)
+    N, S, L = len(s["qA"]), len(s["lam"]), s["L"]
+    dev = torch.device("cuda")
+    ptr, atoms = _csr(s["site_of"], S)
+    d_ptr, d_atoms = torch.tensor(ptr, device=dev), torch.tensor(atoms, device=dev)
+    x = torch.tensor(s["x"], dtype=torch.float64, device=dev)
+    qA = torch.tensor(s["qA"], dtype=torch.float64, device=dev)
+    qB = torch.tensor(s["qB"], dtype=torch.float64, device=dev)
+    lam = torch.tensor(s["lam"], dtype=torch.float64, device=dev)
+    phi = torch.linspace(-300.0, 300.0, N, dtype=torch.float64, device=dev)
+    outs = [(torch.zeros(S, dtype=torch.float64, device=dev), torch.zeros(1, dtype=torch.float64, device=dev),
+             torch.zeros((N, 3), dtype=torch.float64, device=dev)) for _ in range(2)]
+    pkg.mahi_site_terms_static(L, d_ptr, d_atoms, x, qA, qB, lam, phi, *outs[0])   # set-up call, uncaptured
+    torch.cuda.synchronize()
+    side = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=side):
+        pkg.mahi_site_terms_static(L, d_ptr, d_atoms, x, qA, qB, lam, phi, *outs[1], stream=side)
+    g.replay()
+    torch.cuda.synchronize()
+    for a, b in zip(outs[0], outs[1]):
+        assert torch.equal(a, b)
+
+
+def test_static_site_terms_flag_an_out_of_range_atom():
+    """A site naming an atom beyond n_atoms gets NaN and is not touched; the
+    other sites are evaluated as usual."""
+    dev = torch.device("cuda")
+    N, L = 40, 3.0
+    rng = np.random.default_rng(3)
+    x = torch.tensor(rng.uniform(0, L, (N, 3)), dtype=torch.float64, device=dev)
+    qA = torch.tensor(rng.uniform(-0.5, 0.5, N), dtype=torch.float64, device=dev)
+    qB = qA + 0.25
+    lam = torch.tensor([0.3, 0.6], dtype=torch.float64, device=dev)
+    phi = torch.zeros(N, dtype=torch.float64, device=dev)
+    ptr = torch.tensor([0, 3, 6], dtype=torch.int32, device=dev)
+    atoms = torch.tensor([1, 2, 3, 4, N + 7, 5], dtype=torch.int32, device=dev)   # site 1 is malformed
+    dEdl = torch.zeros(2, dtype=torch.float64, device=dev)
+    ecor = torch.zeros(1, dtype=torch.float64, device=dev)
+    F = torch.zeros((N, 3), dtype=torch.float64, device=dev)
+    pkg.mahi_site_terms_static(L, ptr, atoms, x, qA, qB, lam, phi, dEdl, ecor, F)
+    torch.cuda.synchronize()
+    d = dEdl.cpu().numpy()
+    assert np.isfinite(d[0]) and np.isnan(d[1]) and np.isnan(ecor.item())
+    Fh = F.cpu().numpy()
+    assert not Fh[[4, 5]].any()             # atoms of the malformed site untouched
+    assert Fh[[1, 2, 3]].any()
