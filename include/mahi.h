@@ -181,7 +181,8 @@ int mahi_eval_host(mahi_t h, const void *x_host, int32_t x_is_fp64, const double
 int mahi_backward(mahi_t h, const double *grad_energy, const void *forces, const double *dEdlambda,
                   const double *lambda, int32_t x_is_fp64, void *dx, double *dlambda, double *dEdqA, double *dEdqB);
 
-/* Solver options (each has a default; value 0 restores it).
+/* Solver options (each has a default; value 0 restores it, except for
+ * MAHI_OPT_M2L_SPLIT_DEGREE, whose default is 2).
  *   MAHI_OPT_SITE_THETA     separation ratio theta of the site-atom traversal:
  *       a box of circumradius a is used through its multipole at a site of
  *       radius R at distance D only if a < theta (D - R), so each multipole
@@ -199,12 +200,26 @@ int mahi_backward(mahi_t h, const double *grad_energy, const void *forces, const
  *       the wait runs out after the wait limit and the evaluation reports
  *       MAHI_ERR_TIMEOUT (a test of the watchdog path; no fault is caused).
  *       0: off (default).
+ *   MAHI_OPT_M2L_SPLIT_DEGREE  MAHI_MIXED only: the tensor-core M2L forms the
+ *       products of the multipole coefficients in the K chunks (8 coefficients
+ *       each) that hold input degrees l <= this value as three TF32 products
+ *       (hi*hi + hi*lo + lo*hi, FP32-level operands), the rest as one (TF32
+ *       operands rounded to nearest, relative rounding 2^-11 per term, on
+ *       terms scaled by (a/R)^l).  Range -1..p: -1 = one product for every
+ *       degree, p = three products throughout, default 2 (the first two
+ *       chunks).  The products accumulate in FP32 in tensor memory, whose
+ *       round-toward-zero additions (about -1 ulp each) bias the locals; fewer
+ *       products per term means fewer additions.  The low degrees carry the
+ *       charge and dipole of the sources, which set the far-field energy of
+ *       charged configurations: one product there gives 1.8e-4 relative energy
+ *       error on the 3,000-charge random system, three give 1.6e-5.
  * MAHI_ERR_INVALID_ARG for an unknown option or a value out of range. */
 enum {
   MAHI_OPT_SITE_THETA = 1,
   MAHI_OPT_SITE_LIST_CAP = 2,
   MAHI_OPT_WAIT_LIMIT_MS = 3,
-  MAHI_OPT_WATCHDOG_SELFTEST = 4
+  MAHI_OPT_WATCHDOG_SELFTEST = 4,
+  MAHI_OPT_M2L_SPLIT_DEGREE = 5
 };
 int mahi_set_option(mahi_t h, int32_t option, double value);
 /* Current value of an option (the effective one for defaults). */

@@ -31,6 +31,8 @@ float default_site_theta(int p) {
   return (float)std::min(0.4, t);
 }
 
+int default_m2l_split_degree(int p) { return std::min(2, p); }
+
 int default_site_list_cap(float theta) {
   if (theta >= 0.4f) return 1536;
   // children of the boxes opened at one level: 8 x the lattice points in a
@@ -284,6 +286,7 @@ int mahi_create(double box_L_nm, int64_t n_atoms, int32_t n_sites, int32_t order
       h->status_dev = (int *)dp;
     }
     h->site_theta = default_site_theta(order_p);
+    h->m2l_split_degree = default_m2l_split_degree(order_p);
     h->site_list_cap = default_site_list_cap(h->site_theta);
     AL(h->box_qd, sizeof(double) * 8 * h->nbox_total);
     AL(h->d_level_off, sizeof(int64_t) * (kMaxDepth + 2));
@@ -548,6 +551,10 @@ int mahi_set_option(mahi_t h, int32_t option, double value) {
       if (value != 0.0 && value != 1.0) return MAHI_ERR_INVALID_ARG;
       h->watchdog_selftest = (int)value;
       return MAHI_OK;
+    case MAHI_OPT_M2L_SPLIT_DEGREE:
+      if (value != std::floor(value) || value < -1.0 || value > h->p) return MAHI_ERR_INVALID_ARG;
+      h->m2l_split_degree = (int)value;
+      return MAHI_OK;
     default: return MAHI_ERR_INVALID_ARG;
   }
 }
@@ -559,6 +566,7 @@ double mahi_get_option(mahi_t h, int32_t option) {
     case MAHI_OPT_SITE_LIST_CAP: return h->site_list_cap;
     case MAHI_OPT_WAIT_LIMIT_MS: return (double)h->wait_limit_ns * 1e-6;
     case MAHI_OPT_WATCHDOG_SELFTEST: return h->watchdog_selftest;
+    case MAHI_OPT_M2L_SPLIT_DEGREE: return h->m2l_split_degree;
     default: return -1.0;
   }
 }

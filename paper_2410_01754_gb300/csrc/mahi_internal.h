@@ -42,6 +42,10 @@ float default_site_theta(int p);
 // Default list capacity of the site traversal for a separation ratio theta
 int default_site_list_cap(float theta);
 constexpr int kSiteListCapMax = 12288;
+// Default input degree up to which the tensor-core M2L uses three TF32 products
+// (above it one product; -1: one product for every degree): 2, i.e. the first
+// two K chunks (coefficients 0..15)
+int default_m2l_split_degree(int p);
 constexpr int kSideEv = 24;            // first of the four side-stream timing events of a handle
 
 // Number of real coefficients of an order-p expansion and the padded row stride.
@@ -145,6 +149,7 @@ struct mahi_ctx {
   bool site_list_cap_set = false;
   uint64_t wait_limit_ns = 2000000000ull;     // bounded device waits of the tensor-core M2L
   int watchdog_selftest = 0;                  // 1: the M2L's first wait is on a barrier nothing completes
+  int m2l_split_degree = 0;                   // tensor-core M2L: three TF32 products up to this input degree
   int *status_host = nullptr;                 // kStatusWords ints, host-mapped pinned memory
   int *status_dev = nullptr;                  // the same words as seen from the device
   int tune_p2p_threads = 128;                 // autotuned launch shapes (mahi_autotune)

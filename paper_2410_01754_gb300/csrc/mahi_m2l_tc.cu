@@ -1,15 +1,16 @@
 // Tensor-core M2L for sm_103a (tcgen05 + TMEM, bulk-async copies, mbarriers).
 //
 // For every level l >= 1 and every target box t, L~_t = sum_{o in list(c(t))}
-// T~_o M~_{t-o} (Fig. "fmm_scheme", step 3; 189 offsets per box).  A CTA owns a
-// tile of up to 128 targets with the same child index c (so they share the
+// T~_o M~_{t-o} (Fig. "fmm_scheme", step 3; 189 offsets per box).  A CTA owns
+// tiles of up to 128 targets with the same child index c (so they share the
 // offset list) and accumulates
 //     D[128 x Kp] = sum_o A_o[128 x Kp] B_o[Kp x Kp]^T
 // in TMEM (fp32, one TMEM lane per target), where row r of A_o is the gathered
 // multipole of target r's source box and B_o = T~_o (rows = output coefficient,
-// K-major).  Three TF32 products per step (hi*hi + hi*lo + lo*hi) keep the
-// result at FP32 accuracy: the multipoles are split into TF32 hi/lo parts once
-// per evaluation, the operators once at creation.
+// K-major).  Operands are TF32: the multipoles are rounded to TF32 hi parts
+// (and lo = remainder) once per evaluation, the operators once at creation.
+// Input coefficients of low degree (the first nsplit K chunks) take three
+// products (hi*hi + hi*lo + lo*hi, FP32-level), the rest one (hi*hi).
 //
 // Shared-memory operand layout: no swizzle, K-major; an 8-row x 16-byte core
 // matrix is 128 contiguous bytes; core matrices are ordered [k-group][row-group],
@@ -20,8 +21,10 @@
 // of warp 14 issue the MMAs of tile 0 and tile 1; warp 1 lane 0 streams B with
 // cp.async.bulk; warps 2-9 are two groups of A producers taking the even and
 // the odd pipeline items, gathering source rows with cp.async and storing
-// their TF32 hi/lo split in TMEM; warps 10-13 drain TMEM in the epilogue.  Every wait is bounded: on expiry the CTA records an
-// error, stops issuing work, drains what is in flight and frees its TMEM.
+// their TF32 parts in TMEM; warps 10-13 drain TMEM in the epilogue.  Every wait
+// is bounded: on expiry the CTA records an error, stops issuing work, drains
+// what is in flight and frees its TMEM.
+
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -35,18 +38,32 @@ namespace mahi {
 
 namespace tc {
 constexpr int kRows = 128;       // targets per tile (MMA M)
-constexpr int kKC = 8;           // input coefficients per pipeline stage (one MMA K)
-constexpr int kStagesA = 4;      // A stages in tensor memory
-constexpr int kStagesS = 4;      // A staging slots in shared memory per producer group (cp.async)
-constexpr int kStagesB = 12;     // B stages in shared memory (at most; Params::nsb is the count used)
+constexpr int kKC = 8;           // input coefficients per K chunk (one MMA K)
+constexpr int kKPI = 2;          // virtual K chunks per pipeline item
+constexpr int kStagesA = 4;      // A stages in tensor memory (32 columns: 2 tiles x 2 chunks x 8)
+constexpr int kStagesS = 3;      // A staging slots in shared memory per producer group (cp.async)
+constexpr int kStagesB = 4;      // B stages in shared memory (at most; Params::nsb is the count used)
+constexpr int kDone = 8;         // done ring: one entry per item pair
 constexpr int kThreads = 480;     // 15 warps: MMA (tile 0), B producer, 2 x 4 A producers, 4 epilogue, MMA (tile 1)
 constexpr uint32_t kSpinLimit = 1u << 26;
 constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s: drains of work in flight (they end in microseconds)
 constexpr int kMaxN = 256;       // MMA N limit: Kp <= 256, order <= 15
+constexpr int kSlotBytes = kKPI * 2 * 2 * kRows * 16;   // A staging slot: [chunk][tile][granule][row] 16 B
 
-struct Unit {
-  int level, child, p0, count;  // targets 8*(p0 + r) + child, r < count
-};
+// A unit is up to two 128-row tiles of one child class c.  Its rows index the
+// class's targets of ALL levels in one sequence (level d first, then d - 1, ...,
+// 1; within a level in the class's grid order), so that the coarse levels,
+// whose classes hold 1, 8, 64, ... targets, share tiles instead of occupying
+// mostly empty ones: int4 {c, r0, n0, n1} = rows r0 .. r0 + n0 - 1 in tile 0
+// and r0 + 128 .. r0 + 127 + n1 in tile 1.  The operators are the same for all
+// levels (scale-normalised expansions), so any mix of levels can share them.
+//
+// Pipeline items.  Per interaction offset j the K dimension is walked as nvc =
+// nch + nsplit virtual chunks: v < nch is the TF32 hi part of chunk v (with the
+// hi*lo operator product too when v < nsplit), v >= nch is the lo part of
+// chunk v - nch (times the operator's hi part).  An item is kKPI consecutive
+// virtual chunks of one offset, so one handshake (A stage, B stage, commit)
+// covers kKPI chunks; ngrp = ceil(nvc / kKPI) items per offset.
 
 struct Params {
   const float *M;               // multipoles in the M2L source layout (see k_m2l_src_layout)
@@ -60,10 +77,13 @@ struct Params {
   uint64_t wait_ns;             // limit of every bounded pipeline wait
   int selftest;                 // 1: the tile-0 issuer first waits on a barrier nothing completes
   int ld, nch, ngroups;         // row stride, K chunks, N row groups (Kp/8)
+  int d;                        // tree depth (levels 1..d hold M2L targets)
+  int nsplit;                   // K chunks 0..nsplit-1: three TF32 products; the rest: one
+  int nvc, ngrp;                // virtual chunks and items per offset
   int nunits;
   int nfull, nrem, q;           // units done whole (round-robin), remainder units, slices per remainder unit
-  int paired;                   // 1: a unit is two 128-target tiles (Kp <= 192); 0: one tile
-  int nsb;                      // B stages that fit in shared memory (4..kStagesB)
+  int paired;                   // 1: a unit has two 128-target tiles (Kp <= 192); 0: one tile
+  int nsb;                      // B stages that fit in shared memory (2..kStagesB)
   float *partial;               // [nrem * q][2][kRows][ld] partial tiles of the remainder units
 };
 }  // namespace tc
@@ -123,6 +143,14 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity, volatile
   }
   *abort_flag = 1;
   return false;
+}
+// two bounded waits whose first (non-blocking) tests are issued together, so
+// that their shared-memory latencies overlap when both phases are complete
+__device__ __forceinline__ bool mbar_wait2(uint64_t *a, uint32_t pa, uint64_t *b, uint32_t pb, volatile int *abort_flag,
+                                           uint64_t lim) {
+  const bool ra = mbar_test(a, pa), rb = mbar_test(b, pb);
+  if (ra && rb) return true;
+  return (ra || mbar_wait(a, pa, abort_flag, lim)) && (rb || mbar_wait(b, pb, abort_flag, lim));
 }
 // 16-byte copy; with src_bytes = 0 the destination is zero-filled and nothing is read
 __device__ __forceinline__ void cp_async16_zfill(void *smem, const void *gmem, uint32_t src_bytes) {
@@ -233,32 +261,34 @@ __device__ __forceinline__ uint32_t tc_compact(uint32_t x) {
 }
 
 // ---------------------------------------------------------------------------
-// the kernel: persistent, one CTA per SM (grid G).  A unit is a pair of
-// 128-target tiles of one level and child class (same offset list, so both
-// tiles use every staged operator chunk: half the operator traffic per flop).
-// CTA k computes the whole units k, k + G, ... below nfull = G * floor(nunits
-// / G), so all CTAs walk the same (offset, K chunk) sequence at the same time
-// and share the operator chunks in L2.  The nrem remainder units are cut along
-// that sequence into q equal slices each, one slice per CTA; slices write
-// partial tiles that k_m2l_tc_reduce adds up in a fixed order.
+// the kernel: persistent, one CTA per SM (grid G).  A unit has two 128-target
+// tiles of one child class (same offset list, so both tiles use every staged
+// operator chunk: half the operator traffic per flop).  CTA k computes the
+// whole units k, k + G, ... below nfull = G * floor(nunits / G), so all CTAs
+// walk the same (offset, chunk) sequence at the same time and share the
+// operator chunks in L2.  The nrem remainder units are cut along that sequence
+// into q equal slices each, one slice per CTA; slices write partial tiles that
+// k_m2l_tc_reduce adds up in a fixed order.
 //
 // The A operand (gathered multipoles) lives in tensor memory: the producer
-// warps load each target's source rows from global memory, split them into
-// TF32 hi and lo in registers and store them with tcgen05.st, so shared memory
-// carries only the operator chunks (B).
+// warps load each target's source rows from global memory, round them to TF32
+// parts in registers and store them with tcgen05.st, so shared memory carries
+// only the operator chunks (B).
 // Warp roles: 0 = TMEM owner + tile-0 MMA issuer (one lane), 1 = B producer
 // (bulk copies), 2-5 and 6-9 = A producers of the even and odd items (row t of
 // both tiles = TMEM lane t; a warp may touch only its TMEM lane quarter,
-// warp % 4), 10-13 = epilogue (TMEM -> L), 14 = tile-1 MMA issuer (one lane).  TMEM columns: [0, 176) tile-0 accumulator, [192, 368) tile-1
-// accumulator, [384 + 32 s, 416 + 32 s) A stage s as tile-0 hi | lo, tile-1 hi | lo.
+// warp % 4), 10-13 = epilogue (TMEM -> L), 14 = tile-1 MMA issuer (one lane).
+// TMEM columns: [0, 176) tile-0 accumulator, [192, 368) tile-1 accumulator,
+// [384 + 32 s, 416 + 32 s) A stage s: tile 0 chunks 0, 1, tile 1 chunks 0, 1
+// (8 columns each).
 // ---------------------------------------------------------------------------
 namespace tc {
 constexpr uint32_t kAcc1 = 192, kAcol = 384;
 
 // Walks the items of CTA k in order without divisions: segment (whole unit
-// or remainder slice), unit, offset j and K chunk kc.
+// or remainder slice), unit, offset j and virtual chunk group g.
 struct ItemIter {
-  int seg, unit, i, i1, j, kc;
+  int seg, unit, i, i1, j, g;
 };
 __device__ __forceinline__ void iter_seg(const Params &p, int k, int nA, int nit, ItemIter &it) {
   if (it.seg < nA) {
@@ -266,14 +296,14 @@ __device__ __forceinline__ void iter_seg(const Params &p, int k, int nA, int nit
     it.i = 0;
     it.i1 = nit;
     it.j = 0;
-    it.kc = 0;
+    it.g = 0;
   } else {
     const int sl = k % p.q;
     it.unit = p.nfull + k / p.q;
     it.i = (int)(((int64_t)sl * nit) / p.q);
     it.i1 = (int)(((int64_t)(sl + 1) * nit) / p.q);
-    it.j = it.i / p.nch;
-    it.kc = it.i - it.j * p.nch;
+    it.j = it.i / p.ngrp;
+    it.g = it.i - it.j * p.ngrp;
   }
 }
 __device__ __forceinline__ void iter_begin(const Params &p, int k, int nA, int nit, ItemIter &it) {
@@ -283,8 +313,8 @@ __device__ __forceinline__ void iter_begin(const Params &p, int k, int nA, int n
 // advance by one item; returns true when a new segment starts
 __device__ __forceinline__ bool iter_next(const Params &p, int k, int nA, int nit, ItemIter &it) {
   ++it.i;
-  if (++it.kc == p.nch) {
-    it.kc = 0;
+  if (++it.g == p.ngrp) {
+    it.g = 0;
     ++it.j;
   }
   if (it.i < it.i1) return false;
@@ -293,13 +323,28 @@ __device__ __forceinline__ bool iter_next(const Params &p, int k, int nA, int ni
   return true;
 }
 
+// K chunk of virtual chunk v and whether it is the lo part
+__device__ __forceinline__ int vchunk(const Params &p, int v, bool &lo) {
+  lo = v >= p.nch;
+  return lo ? v - p.nch : v;
+}
+
 // targets in tile h (0 or 1) of a unit
-__device__ __forceinline__ int tile_count(const Params &p, const int4 &u, int h) {
-  if (h == 0) return u.w;
-  if (!p.paired) return 0;
-  const int per_child = 1 << (3 * (u.x - 1));
-  const int c = per_child - u.z - kRows;
-  return c < 0 ? 0 : (c > kRows ? kRows : c);
+__device__ __forceinline__ int tile_count(const Params &, const int4 &u, int h) { return h == 0 ? u.z : u.w; }
+
+// level and in-class index of merged row r of a class (levels d, d - 1, ..., 1)
+__device__ __forceinline__ int row_level(int d, int r, int &tau) {
+  int start = 0;
+  for (int l = d; l >= 1; --l) {
+    const int n = 1 << (3 * (l - 1));
+    if (r < start + n) {
+      tau = r - start;
+      return l;
+    }
+    start += n;
+  }
+  tau = 0;
+  return 0;
 }
 
 // TF32 round-to-nearest (ties away) on the bit pattern; the remainder is exact
@@ -310,13 +355,15 @@ __device__ __forceinline__ void tf32_split(float x, uint32_t &hi, uint32_t &lo) 
   lo = __float_as_uint(x - __uint_as_float(u));
 }
 
-// the source rows of one producer thread (row t of both tiles), advanced item by item
+// the source rows of one producer thread (row t of both tiles), advanced item by
+// item; each row has its own level
 struct ARow {
-  int unit = -1, j = -1, lev = 1, child = 0;
+  int unit = -1, j = -1, child = 0;
+  int lev[2] = {1, 1};
   int bx[2] = {0, 0}, by[2] = {0, 0}, bz[2] = {0, 0};
   bool valid[2] = {false, false};
-  const float *base = nullptr;
-  int64_t sidx[2] = {0, 0};      // source chunk index within a K plane
+  int rsrc[2] = {0, 0};          // float offset of the source chunk of K plane 0 (current offset j)
+  int rpl[2] = {0, 0};           // floats per K plane at the row's level (8^l chunks of 8)
 };
 
 // target tau of a child class c at level l (parity class c, grid order
@@ -328,101 +375,68 @@ __device__ __forceinline__ void class_target(int l, int c, int tau, int &x, int 
   z = 2 * (tau >> (2 * hb)) + ((c >> 2) & 1);
 }
 
-// issue the cp.async copies of item q for row t of both tiles into staging
-// slot `dst` (4 granules of 16 bytes at dst + (g * kRows + t) * 16; rows past
-// a tile's count are zero-filled)
-__device__ __forceinline__ void arow_issue(const Params &p, const int *s_list, const int *s_off, int t,
-                                           const ItemIter &it, ARow &a, unsigned char *dst) {
-  const int unit = it.unit, j = it.j, kc = it.kc;
-  if (unit != a.unit) {
-    const int4 u = p.units[unit];
-    a.lev = u.x;
-    a.child = u.y;
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      a.valid[h] = t < tile_count(p, u, h);
-      class_target(u.x, u.y, u.z + h * kRows + t, a.bx[h], a.by[h], a.bz[h]);
-    }
-    a.base = p.M + p.level_off[u.x] * p.ld;
-    a.sidx[0] = a.sidx[1] = 0;
-    a.unit = unit;
-    a.j = -1;
-  }
-  const int hb = a.lev - 1;                         // log2 of the half side
-  if (j != a.j) {
-    const int oid = s_list[a.child * kListLen + j];
-    const int ox = s_off[oid * 3 + 0], oy = s_off[oid * 3 + 1], oz = s_off[oid * 3 + 2];
-    const int sm = (1 << a.lev) - 1;
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      if (!a.valid[h]) continue;
-      // source box, periodic wrap (the side is a power of two)
-      const int sx = (a.bx[h] - ox) & sm, sy = (a.by[h] - oy) & sm, sz = (a.bz[h] - oz) & sm;
-      const int cls = (sx & 1) | ((sy & 1) << 1) | ((sz & 1) << 2);
-      a.sidx[h] = ((((int64_t)cls << hb | (sz >> 1)) << hb | (sy >> 1)) << hb) | (sx >> 1);
-    }
-    a.j = j;
-  }
-  const int64_t plane = (int64_t)kc << (3 * hb + 3);  // chunks of one K plane: 8 classes x half^3
-#pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    const uint32_t n = a.valid[h] ? 16u : 0u;
-    const float *g = a.base + (plane + a.sidx[h]) * kKC;
-    cp_async16_zfill(dst + ((2 * h + 0) * kRows + t) * 16, g, n);
-    cp_async16_zfill(dst + ((2 * h + 1) * kRows + t) * 16, g + 4, n);
-  }
-}
-
-// Coalesced variant: the same copies as arow_issue for the 32 rows of this
-// warp, but lane l copies granule (l & 1) of row 16 rh + (l >> 1) (rh = 0, 1)
-// of each tile, so one warp instruction reads 16 whole 32-byte source chunks
-// (512 contiguous bytes where the sources are consecutive) instead of half of
-// 32 chunks.  Row state (source index, validity) is still kept per own row and
-// exchanged by shuffles; the caller must __syncwarp() after its cp.async wait
-// before reading rows written by other lanes.
+// Copies of item (offset j, virtual chunk group g) for the 32 rows of this
+// warp into staging slot `dst` ([chunk k][tile h][granule e][row] of 16 bytes;
+// rows past a tile's count and virtual chunks past nvc are zero-filled).  Lane
+// l copies granule (l & 1) of row 16 rh + (l >> 1) (rh = 0, 1) of each tile, so
+// one warp instruction reads 16 whole 32-byte source chunks (512 contiguous
+// bytes where the sources are consecutive).  Each row's source offset is
+// computed by its own lane and exchanged by shuffles; the caller must
+// __syncwarp() after its cp.async wait before reading rows written by other
+// lanes.
 __device__ __forceinline__ void arow_issue_coalesced(const Params &p, const int *s_list, const int *s_off, int t,
                                                      int lane, const ItemIter &it, ARow &a, unsigned char *dst) {
-  const int unit = it.unit, j = it.j, kc = it.kc;
+  const int unit = it.unit, j = it.j;
   if (unit != a.unit) {
     const int4 u = p.units[unit];
-    a.lev = u.x;
-    a.child = u.y;
+    a.child = u.x;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       a.valid[h] = t < tile_count(p, u, h);
-      class_target(u.x, u.y, u.z + h * kRows + t, a.bx[h], a.by[h], a.bz[h]);
+      int tau = 0;
+      const int l = a.valid[h] ? row_level(p.d, u.y + h * kRows + t, tau) : 1;
+      a.valid[h] = a.valid[h] && l >= 1;
+      a.lev[h] = a.valid[h] ? l : 1;
+      class_target(a.lev[h], a.child, tau, a.bx[h], a.by[h], a.bz[h]);
+      a.rpl[h] = 8 << (3 * a.lev[h]);
     }
-    a.base = p.M + p.level_off[u.x] * p.ld;
-    a.sidx[0] = a.sidx[1] = 0;
     a.unit = unit;
     a.j = -1;
   }
-  const int hb = a.lev - 1;
   if (j != a.j) {
     const int oid = s_list[a.child * kListLen + j];
     const int ox = s_off[oid * 3 + 0], oy = s_off[oid * 3 + 1], oz = s_off[oid * 3 + 2];
-    const int sm = (1 << a.lev) - 1;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       if (!a.valid[h]) continue;
+      // source box, periodic wrap (the side is a power of two), in the class
+      // order of the source layout
+      const int l = a.lev[h], hb = l - 1, sm = (1 << l) - 1;
       const int sx = (a.bx[h] - ox) & sm, sy = (a.by[h] - oy) & sm, sz = (a.bz[h] - oz) & sm;
       const int cls = (sx & 1) | ((sy & 1) << 1) | ((sz & 1) << 2);
-      a.sidx[h] = ((((int64_t)cls << hb | (sz >> 1)) << hb | (sy >> 1)) << hb) | (sx >> 1);
+      const int sidx = (((cls << hb | (sz >> 1)) << hb | (sy >> 1)) << hb) | (sx >> 1);
+      a.rsrc[h] = (int)(p.level_off[l] * p.ld) + sidx * kKC;
     }
     a.j = j;
   }
-  const int64_t plane = (int64_t)kc << (3 * hb + 3);
-  const int g = lane & 1, rbase = t & ~31;
+  const int e = lane & 1, rbase = t & ~31;
 #pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    // own row as a signed 32-bit code: source chunk index, or -1 for no row
-    const int mine = a.valid[h] ? (int)a.sidx[h] : -1;
+  for (int kk = 0; kk < kKPI; ++kk) {
+    const int v = it.g * kKPI + kk;
+    bool lo;
+    const int c = vchunk(p, v, lo);
+    const bool live = v < p.nvc;
 #pragma unroll
-    for (int rh = 0; rh < 2; ++rh) {
-      const int src = __shfl_sync(0xffffffffu, mine, 16 * rh + (lane >> 1));
-      const int row = rbase + 16 * rh + (lane >> 1);
-      const float *gp = a.base + (plane + (src < 0 ? 0 : src)) * kKC + 4 * g;
-      cp_async16_zfill(dst + ((2 * h + g) * kRows + row) * 16, gp, src < 0 ? 0u : 16u);
+    for (int h = 0; h < 2; ++h) {
+      // own row as a signed 32-bit code: float offset of its source chunk, or -1
+      const int mine = (live && a.valid[h]) ? a.rsrc[h] + c * a.rpl[h] : -1;
+#pragma unroll
+      for (int rh = 0; rh < 2; ++rh) {
+        const int src = __shfl_sync(0xffffffffu, mine, 16 * rh + (lane >> 1));
+        const int row = rbase + 16 * rh + (lane >> 1);
+        const float *gp = p.M + (src < 0 ? 0 : src) + 4 * e;
+        cp_async16_zfill(dst + (((kk * 2 + h) * 2 + e) * kRows + row) * 16, gp, src < 0 ? 0u : 16u);
+      }
     }
   }
 }
@@ -469,23 +483,23 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_m2l_tc(tc::Params prm) {
   using namespace tc;
   extern __shared__ __align__(1024) unsigned char smem[];
   const int ng = prm.ngroups;                       // N row groups (Kp / 8)
-  const uint32_t b_bytes = (kKC / 4) * ng * 128;    // hi (or lo) of one B chunk
-  unsigned char *sB = smem;                         // [B stage][hi|lo][b_bytes]
+  const uint32_t b_bytes = (kKC / 4) * ng * 128;    // hi (or lo) of one operator chunk
+  const uint32_t b_stage = kKPI * 2 * b_bytes;      // [chunk][hi|lo] of one item
+  unsigned char *sB = smem;                         // [B stage][chunk][hi|lo][b_bytes]
   const int nsb = prm.nsb;
-  unsigned char *sS = sB + nsb * 2 * b_bytes;       // [slot][4 granules][kRows][16 B] A staging
-  int *s_list = reinterpret_cast<int *>(sS + 2 * kStagesS * 4 * kRows * 16);  // [8][189] offset ids
-  int *s_off = s_list + 8 * kListLen;                                   // [316][3] offsets
+  unsigned char *sS = sB + nsb * b_stage;           // [group][slot] A staging (kSlotBytes each)
+  int *s_list = reinterpret_cast<int *>(sS + 2 * kStagesS * kSlotBytes);   // [8][189] offset ids
+  int *s_off = s_list + 8 * kListLen;                                      // [316][3] offsets
   uint64_t *bars = reinterpret_cast<uint64_t *>(s_off + ((3 * kNumOffsets + 1) & ~1));
   // idle[0] is a barrier that nothing arrives on (the watchdog self-test waits on it)
-  uint64_t *fullA = bars, *idle = bars + kStagesA, *fullB = bars + 2 * kStagesA,
-           *emptyB = bars + 2 * kStagesA + kStagesB;
-  uint64_t *accb = bars + 2 * kStagesA + 2 * kStagesB, *tfree = accb + 1;
+  uint64_t *fullA = bars, *fullB = fullA + kStagesA, *done = fullB + kStagesB, *idle = done + kDone;
+  uint64_t *accb = idle + 1, *tfree = accb + 1;
   uint64_t *mdone = tfree + 1;                      // [2] last commit of each MMA issuer
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mdone + 2);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nit = kListLen * prm.nch;               // stages of one unit
+  const int nit = kListLen * prm.ngrp;              // items of one unit
   const int k = blockIdx.x;
   const int nA = prm.nfull / (int)gridDim.x;        // whole units of this CTA
   int slice_len = 0;
@@ -498,14 +512,10 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_m2l_tc(tc::Params prm) {
   if (nloc == 0) return;                            // uniform over the block
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kStagesA; ++s) {
-      mbar_init(&fullA[s], 4);   // the four warps of the producer group of that item
-      mbar_init(&idle[s], 1);    // never arrived on
-    }
-    for (int s = 0; s < kStagesB; ++s) {
-      mbar_init(&fullB[s], 1);
-      mbar_init(&emptyB[s], 2);  // done ring: one commit per MMA-issuing thread and item
-    }
+    for (int s = 0; s < kStagesA; ++s) mbar_init(&fullA[s], 4);   // the four warps of the item's producer group
+    for (int s = 0; s < kStagesB; ++s) mbar_init(&fullB[s], 1);   // the B producer (plus the copies' bytes)
+    for (int s = 0; s < kDone; ++s) mbar_init(&done[s], 2);       // one commit per MMA issuer and item pair
+    mbar_init(idle, 1);                                           // never arrived on
     mbar_init(accb, 2);
     mbar_init(tfree, kRows);
     mbar_init(&mdone[0], 1);
@@ -530,22 +540,24 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_m2l_tc(tc::Params prm) {
     // the odd items; row t of both tiles (TMEM lane t) per thread ----------------
     // each group copies its items kStagesS - 1 items ahead into its own staging
     // ring (cp.async groups, one per item, coalesced across the warp), then
-    // every thread splits its own rows into TF32 hi/lo and stores them in TMEM
+    // every thread rounds its own rows to the TF32 part of each virtual chunk
+    // and stores them in TMEM
     const int grp = (warp - 2) >> 2;
     const int quarter = warp & 3;
     const int t = quarter * 32 + lane;
     const uint32_t lane_addr = tmem + ((uint32_t)(quarter * 32) << 16);
-    unsigned char *ring = sS + (size_t)grp * kStagesS * 4 * kRows * 16;
+    unsigned char *ring = sS + (size_t)grp * kStagesS * kSlotBytes;
     constexpr int D = kStagesS - 1;
     const int nmine = (nloc - grp + 1) >> 1;        // items 2 jj + grp of this group
     ARow a;
     ItemIter it;                                    // issue position, D items of this group ahead
     iter_begin(prm, k, nA, nit, it);
     if (grp) iter_next(prm, k, nA, nit, it);
+    ItemIter ic = it;                               // position of the item being stored
     int slot_i = 0;                                 // staging slot of the next issue
     for (int qq = 0; qq < D; ++qq) {
       if (qq < nmine) {
-        arow_issue_coalesced(prm, s_list, s_off, t, lane, it, a, ring + (size_t)slot_i * 4 * kRows * 16);
+        arow_issue_coalesced(prm, s_list, s_off, t, lane, it, a, ring + (size_t)slot_i * kSlotBytes);
         iter_next(prm, k, nA, nit, it);
         iter_next(prm, k, nA, nit, it);
       }
@@ -556,7 +568,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_m2l_tc(tc::Params prm) {
     for (int jj = 0; jj < nmine; ++jj) {
       const int q = 2 * jj + grp;
       if (jj + D < nmine) {
-        arow_issue_coalesced(prm, s_list, s_off, t, lane, it, a, ring + (size_t)slot_i * 4 * kRows * 16);
+        arow_issue_coalesced(prm, s_list, s_off, t, lane, it, a, ring + (size_t)slot_i * kSlotBytes);
         iter_next(prm, k, nA, nit, it);
         iter_next(prm, k, nA, nit, it);
       }
@@ -564,31 +576,41 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_m2l_tc(tc::Params prm) {
       cp_async_commit();
       cp_async_wait_group<D>();                     // this thread's copies of item q have landed
       __syncwarp();                                 // ... and those of the other lanes of the warp
-      // split first: it needs only the staging slot, not the TMEM stage
-      const unsigned char *src = ring + (size_t)slot_c * 4 * kRows * 16 + t * 16;
-      uint32_t w[32];  // tile-0 hi | tile-0 lo | tile-1 hi | tile-1 lo, 8 columns each
+      // round first: it needs only the staging slot, not the TMEM stage
+      const unsigned char *src = ring + (size_t)slot_c * kSlotBytes + t * 16;
+      uint32_t w[32];  // tile 0 chunk 0 | tile 0 chunk 1 | tile 1 chunk 0 | tile 1 chunk 1, 8 columns each
 #pragma unroll
-      for (int h = 0; h < 2; ++h)
+      for (int kk = 0; kk < kKPI; ++kk) {
+        bool lo;
+        vchunk(prm, ic.g * kKPI + kk, lo);
 #pragma unroll
-        for (int e = 0; e < 2; ++e) {
-          const float4 x = *reinterpret_cast<const float4 *>(src + (2 * h + e) * kRows * 16);
-          uint32_t *hi = w + 16 * h + 4 * e, *lo = hi + 8;
-          tf32_split(x.x, hi[0], lo[0]);
-          tf32_split(x.y, hi[1], lo[1]);
-          tf32_split(x.z, hi[2], lo[2]);
-          tf32_split(x.w, hi[3], lo[3]);
-        }
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+          for (int e = 0; e < 2; ++e) {
+            const float4 x = *reinterpret_cast<const float4 *>(src + ((kk * 2 + h) * 2 + e) * kRows * 16);
+            uint32_t *o = w + (h * kKPI + kk) * 8 + 4 * e;
+            uint32_t hi4[4], lo4[4];
+            tf32_split(x.x, hi4[0], lo4[0]);
+            tf32_split(x.y, hi4[1], lo4[1]);
+            tf32_split(x.z, hi4[2], lo4[2]);
+            tf32_split(x.w, hi4[3], lo4[3]);
+#pragma unroll
+            for (int c4 = 0; c4 < 4; ++c4) o[c4] = lo ? lo4[c4] : hi4[c4];
+          }
+      }
       __syncwarp();                                 // staging slot read by all lanes before it is refilled
+      iter_next(prm, k, nA, nit, ic);
+      iter_next(prm, k, nA, nit, ic);
       const int s = q % kStagesA;
       // lane 0 waits for the TMEM stage (its MMAs of item q - kStagesA done)
       // and the warp follows it; the whole warp leaves together on a timeout
       // (the TMEM store below is warp-collective)
       bool ok = true;
-      // (item q - kStagesA is done when the done-ring entry of that item has
-      // its phase complete: one commit per MMA issuer and item)
+      // (item q - kStagesA is done when the done-ring entry of its item pair
+      // has its phase complete: one commit per MMA issuer and item pair)
       if (q >= kStagesA && lane == 0) {
-        const int qd = q - kStagesA;
-        ok = mbar_wait(&emptyB[qd % nsb], (uint32_t)((qd / nsb) & 1), abort_flag, prm.wait_ns);
+        const int pd = (q - kStagesA) >> 1;
+        ok = mbar_wait(&done[pd % kDone], (uint32_t)((pd / kDone) & 1), abort_flag, prm.wait_ns);
       }
       if (!__shfl_sync(0xffffffffu, ok, 0)) break;
       tc_fence_after();
@@ -603,27 +625,40 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_m2l_tc(tc::Params prm) {
   } else if (warp == 1) {
     // ---------------- B producer ----------------
     if (lane == 0) {
-      const uint32_t img = 2 * b_bytes;  // hi | lo of one (offset, chunk)
       int issued = 0, ucur = -1, child = 0, s = 0;
-      uint32_t ph = 0;
       ItemIter it;
       iter_begin(prm, k, nA, nit, it);
       for (int q = 0; q < nloc; ++q) {
-        if (q >= nsb && !mbar_wait(&emptyB[s], ph, abort_flag, prm.wait_ns)) break;
+        // stage s was last used by item q - nsb: wait until its item pair is done
+        if (q >= nsb) {
+          const int pd = (q - nsb) >> 1;
+          if (!mbar_wait(&done[pd % kDone], (uint32_t)((pd / kDone) & 1), abort_flag, prm.wait_ns)) break;
+        }
         if (it.unit != ucur) {
-          child = prm.units[it.unit].y;
+          child = prm.units[it.unit].x;
           ucur = it.unit;
         }
         const int oid = s_list[child * kListLen + it.j];
-        const unsigned char *g = prm.ops + ((size_t)oid * prm.nch + it.kc) * img;
-        mbar_arrive_expect_tx(&fullB[s], img);
-        bulk_g2s(sB + (size_t)s * img, g, img, &fullB[s]);
+        // per virtual chunk: hi | lo of the operator chunk for the hi part of a
+        // three-product chunk, else its hi part only
+        uint32_t bytes[kKPI], total = 0;
+        const unsigned char *gsrc[kKPI];
+#pragma unroll
+        for (int kk = 0; kk < kKPI; ++kk) {
+          const int v = it.g * kKPI + kk;
+          bool lo;
+          const int c = vchunk(prm, v, lo);
+          bytes[kk] = v >= prm.nvc ? 0u : ((!lo && c < prm.nsplit) ? 2 * b_bytes : b_bytes);
+          gsrc[kk] = prm.ops + ((size_t)oid * prm.nch + c) * 2 * b_bytes;
+          total += bytes[kk];
+        }
+        mbar_arrive_expect_tx(&fullB[s], total);
+#pragma unroll
+        for (int kk = 0; kk < kKPI; ++kk)
+          if (bytes[kk]) bulk_g2s(sB + (size_t)s * b_stage + kk * 2 * b_bytes, gsrc[kk], bytes[kk], &fullB[s]);
         ++issued;
         iter_next(prm, k, nA, nit, it);
-        if (++s == nsb) {
-          s = 0;
-          if (q + 1 > nsb) ph ^= 1u;                // from the third use on
-        }
+        if (++s == nsb) s = 0;
       }
       // the last copy into each stage is the latest phase of its barrier: wait
       // (bounded) until it has landed before the CTA can retire
@@ -631,19 +666,20 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_m2l_tc(tc::Params prm) {
         uint64_t *b = &fullB[i % nsb];
         const uint32_t par = (i / nsb) & 1;
         const uint64_t t0 = global_ns();
-        for (uint32_t it = 0; it < kSpinLimit && !mbar_try_wait(b, par); ++it)
-          if ((it & 255) == 255 && global_ns() - t0 > kWaitNs) break;
+        for (uint32_t it2 = 0; it2 < kSpinLimit && !mbar_try_wait(b, par); ++it2)
+          if ((it2 & 255) == 255 && global_ns() - t0 > kWaitNs) break;
       }
     }
   } else if ((warp == 0 || warp == 14) && lane == 0) {
     // ---------------- MMA issuers: warp 0 issues tile 0, warp 14 tile 1 ----------------
-    // Each tcgen05.mma of this shape (128 x Kp x 8) runs for about as long as
-    // one thread takes to issue it, so the two tiles are issued by two threads
-    // on different warps; each commits to the stage barriers (count 2).
+    // The issuing thread's fixed cost per item (barrier tests, fences,
+    // bookkeeping) exceeds that of an MMA instruction, so an item carries
+    // kKPI chunks; the two tiles are issued by two threads on different warps,
+    // each committing to the done ring (count 2) once per item pair.
     const int mt = warp == 14 ? 1 : 0;
     const uint32_t idesc = idesc_tf32(kRows, ng * 8);
     const uint32_t b_lbo = ng * 128;
-    const uint32_t dt = tmem + (mt ? kAcc1 : 0u), acol = kAcol + 16u * (uint32_t)mt;
+    const uint32_t dt = tmem + (mt ? kAcc1 : 0u);
     int ntile = 1, sa = 0, sb = 0;
     uint32_t pa = 0, pb = 0;                        // phase parities of fullA[sa], fullB[sb]
     bool first = true, seg_start = true;
@@ -651,7 +687,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_m2l_tc(tc::Params prm) {
     iter_begin(prm, k, nA, nit, it);
     const uint32_t sB0 = smem_u32(sB);
     // watchdog self-test: a wait that runs out before any MMA is issued
-    const bool go = !(prm.selftest && mt == 0) || mbar_wait(&idle[0], 0, abort_flag, prm.wait_ns);
+    const bool go = !(prm.selftest && mt == 0) || mbar_wait(idle, 0, abort_flag, prm.wait_ns);
     for (int q = 0; go && q < nloc; ++q) {
       if (seg_start) {
         // new segment: the accumulators must have been drained by the epilogue
@@ -660,21 +696,26 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_m2l_tc(tc::Params prm) {
         first = true;
         ntile = tile_count(prm, prm.units[it.unit], 1) > 0 ? 2 : 1;
       }
-      if (!mbar_wait(&fullA[sa], pa, abort_flag, prm.wait_ns)) break;
-      if (!mbar_wait(&fullB[sb], pb, abort_flag, prm.wait_ns)) break;
+      if (!mbar_wait2(&fullA[sa], pa, &fullB[sb], pb, abort_flag, prm.wait_ns)) break;
       tc_fence_after();
       if (mt < ntile) {
-        const uint32_t bh = sB0 + (uint32_t)sb * 2u * b_bytes, bl = bh + b_bytes;
-        const uint64_t dbh = smem_desc(bh, b_lbo, 128), dbl = smem_desc(bl, b_lbo, 128);
-        const uint32_t acc0 = first ? 0u : 1u;
-        const uint32_t ah = tmem + acol + 32u * (uint32_t)sa;   // hi | lo of this tile
-        mma_tf32_ts(dt, ah, dbh, idesc, acc0);
-        mma_tf32_ts(dt, ah, dbl, idesc, 1u);
-        mma_tf32_ts(dt, ah + 8u, dbh, idesc, 1u);
+#pragma unroll
+        for (int kk = 0; kk < kKPI; ++kk) {
+          const int v = it.g * kKPI + kk;
+          if (v >= prm.nvc) break;
+          bool lo;
+          const int c = vchunk(prm, v, lo);
+          const uint32_t bh = sB0 + (uint32_t)sb * b_stage + (uint32_t)kk * 2u * b_bytes;
+          const uint64_t dbh = smem_desc(bh, b_lbo, 128);
+          const uint32_t av = tmem + kAcol + 32u * (uint32_t)sa + 16u * (uint32_t)mt + 8u * (uint32_t)kk;
+          mma_tf32_ts(dt, av, dbh, idesc, first ? 0u : 1u);   // hi*hi, or lo*hi for a lo part
+          first = false;
+          if (!lo && c < prm.nsplit) mma_tf32_ts(dt, av, smem_desc(bh + b_bytes, b_lbo, 128), idesc, 1u);  // hi*lo
+        }
       }
-      first = false;
-      mma_commit(&emptyB[sb]);  // item done: frees its B stage and its A stage
       seg_start = iter_next(prm, k, nA, nit, it);
+      // item pair done: frees the B and A stages of its two items
+      if ((q & 1) || q == nloc - 1) mma_commit(&done[(q >> 1) % kDone]);
       if (seg_start || q == nloc - 1) mma_commit(accb);  // segment complete
       if (++sa == kStagesA) { sa = 0; pa ^= 1u; }
       if (++sb == nsb) { sb = 0; pb ^= 1u; }
@@ -684,8 +725,8 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_m2l_tc(tc::Params prm) {
     mma_commit(&mdone[mt]);
     {
       const uint64_t t0 = global_ns();
-      for (uint32_t it = 0; it < kSpinLimit && !mbar_try_wait(&mdone[mt], 0); ++it)
-        if ((it & 255) == 255 && global_ns() - t0 > kWaitNs) break;
+      for (uint32_t it2 = 0; it2 < kSpinLimit && !mbar_try_wait(&mdone[mt], 0); ++it2)
+        if ((it2 & 255) == 255 && global_ns() - t0 > kWaitNs) break;
     }
   } else if (warp >= 10 && warp <= 13) {
     // ---------------- epilogue: TMEM -> L rows, one segment at a time ----------------
@@ -702,9 +743,15 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_m2l_tc(tc::Params prm) {
         if (cnt == 0) continue;                     // uniform over the warp
         const uint32_t taddr = tmem + (h ? kAcc1 : 0u) + ((uint32_t)(quarter * 32) << 16);
         float *Lrow = nullptr;
-        if (r < cnt)
-          Lrow = seg < nA ? prm.L + class_box_row(prm, u.x, u.y, u.z + h * kRows + r) * prm.ld
-                          : prm.partial + (((size_t)k * 2 + h) * kRows + r) * prm.ld;
+        if (r < cnt) {
+          if (seg < nA) {
+            int tau = 0;
+            const int l = row_level(prm.d, u.y + h * kRows + r, tau);
+            Lrow = prm.L + class_box_row(prm, l, u.x, tau) * prm.ld;
+          } else {
+            Lrow = prm.partial + (((size_t)k * 2 + h) * kRows + r) * prm.ld;
+          }
+        }
         for (int c0 = 0; c0 < ng * 8; c0 += 16) {
           float v[16];
           tmem_ld16(taddr + c0, v);
@@ -742,7 +789,9 @@ __global__ void k_m2l_tc_reduce(tc::Params prm) {
     float v = 0.f;
     for (int sl = 0; sl < prm.q; ++sl)
       v += prm.partial[(((size_t)(ru * prm.q + sl) * 2 + h) * tc::kRows + r) * prm.ld + c];
-    prm.L[tc::class_box_row(prm, u.x, u.y, u.z + h * tc::kRows + r) * prm.ld + c] = v;
+    int tau = 0;
+    const int l = tc::row_level(prm.d, u.y + h * tc::kRows + r, tau);
+    prm.L[tc::class_box_row(prm, l, u.x, tau) * prm.ld + c] = v;
   }
 }
 
@@ -794,17 +843,17 @@ static inline bool tc_paired(int ld) { return ld <= (int)tc::kAcc1; }
 int tc_build_units(mahi_ctx *h, std::vector<int> &units) {
   if (h->ld > tc::kMaxN || h->ld % tc::kKC) return -1;
   const int step = (tc_paired(h->ld) ? 2 : 1) * tc::kRows;
+  // targets of one child class over all levels 1..d, in the merged row order
+  int rows = 0;
+  for (int l = 1; l <= h->d; ++l) rows += 1 << (3 * (l - 1));
   units.clear();
-  for (int l = h->d; l >= 1; --l) {
-    const int per_child = 1 << (3 * (l - 1));
-    for (int c = 0; c < 8; ++c)
-      for (int p0 = 0; p0 < per_child; p0 += step) {
-        units.push_back(l);
-        units.push_back(c);
-        units.push_back(p0);
-        units.push_back(std::min(tc::kRows, per_child - p0));
-      }
-  }
+  for (int c = 0; c < 8; ++c)
+    for (int r0 = 0; r0 < rows; r0 += step) {
+      units.push_back(c);
+      units.push_back(r0);
+      units.push_back(std::min(tc::kRows, rows - r0));
+      units.push_back(step > tc::kRows ? std::max(0, std::min(tc::kRows, rows - r0 - tc::kRows)) : 0);
+    }
   h->tc_nunits = (int)units.size() / 4;
   return 0;
 }
@@ -812,9 +861,9 @@ int tc_build_units(mahi_ctx *h, std::vector<int> &units) {
 // dynamic shared memory of k_m2l_tc with nsb operator stages
 static size_t tc_smem_bytes(int ng, int nsb) {
   const size_t b = (size_t)(tc::kKC / 4) * ng * 128;
-  const size_t stage = (size_t)2 * tc::kStagesS * 4 * tc::kRows * 16;
+  const size_t stage = (size_t)2 * tc::kStagesS * tc::kSlotBytes;
   const size_t tables = sizeof(int) * (8 * kListLen + ((3 * kNumOffsets + 1) & ~1));
-  return nsb * 2 * b + stage + tables + (2 * tc::kStagesA + 2 * tc::kStagesB + 4) * 8 + 16;
+  return nsb * tc::kKPI * 2 * b + stage + tables + (tc::kStagesA + tc::kStagesB + tc::kDone + 6) * 8 + 16;
 }
 
 int tc_m2l(mahi_ctx *h) {
@@ -835,12 +884,19 @@ int tc_m2l(mahi_ctx *h) {
   prm.selftest = h->watchdog_selftest;
   prm.ld = h->ld;
   prm.nch = h->ld / tc::kKC;
+  prm.d = h->d;
+  // K chunks holding the coefficients of degrees 0..split degree
+  prm.nsplit = h->m2l_split_degree < 0
+                   ? 0
+                   : std::min(prm.nch, (ncoef(std::min(h->m2l_split_degree, h->p)) + tc::kKC - 1) / tc::kKC);
+  prm.nvc = prm.nch + prm.nsplit;
+  prm.ngrp = (prm.nvc + tc::kKPI - 1) / tc::kKPI;
   prm.ngroups = h->ld / 8;
   prm.nunits = h->tc_nunits;
   prm.paired = tc_paired(h->ld) ? 1 : 0;
-  // as many operator stages as fit (12 at p <= 12, 9 at p = 15)
+  // as many operator stages as fit (4 at p <= 12, 3 at p = 15)
   prm.nsb = tc::kStagesB;
-  while (prm.nsb > 4 && tc_smem_bytes(prm.ngroups, prm.nsb) > 227 * 1024) --prm.nsb;
+  while (prm.nsb > 2 && tc_smem_bytes(prm.ngroups, prm.nsb) > 227 * 1024) --prm.nsb;
   const size_t sm = tc_smem_bytes(prm.ngroups, prm.nsb);
   if (sm > 227 * 1024) return -1;
   if (cudaFuncSetAttribute(k_m2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess) return -1;

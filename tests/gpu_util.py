@@ -4,7 +4,7 @@ import numpy as np
 import paper_2410_01754_gb300 as pkg
 
 
-def run_gpu(s, prec, p=None, d=None, x_dtype="float64", evals=1):
+def run_gpu(s, prec, p=None, d=None, x_dtype="float64", evals=1, options=None):
     import torch
     p = s["order"] if p is None else p
     d = s["depth"] if d is None else d
@@ -12,6 +12,8 @@ def run_gpu(s, prec, p=None, d=None, x_dtype="float64", evals=1):
     m = pkg.Mahi(s["L"], N, S, p, d, prec)
     try:
         m.set_charges(s["qA"], s["qB"], s["site_of"])
+        for k, v in (options or {}).items():
+            m.set_option(k, v)
         x = torch.tensor(s["x"], dtype=getattr(torch, x_dtype), device="cuda")
         lam = torch.tensor(s["lam"], dtype=torch.float64, device="cuda")
         for _ in range(evals):

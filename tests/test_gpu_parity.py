@@ -107,15 +107,18 @@ def test_bitwise_deterministic(prec):
     assert np.array_equal(a["F"], b["F"]) and np.array_equal(a["dEdl"], b["dEdl"])
 
 
+@pytest.mark.parametrize("split", [-1, 2, "p"])
 @pytest.mark.parametrize("p", [8, 12, 13, 15])
-def test_tensor_core_m2l_matches_fp64_path(sysB, p):
-    """Tensor-core M2L (3xTF32) against the FP64 path at the same order: paired
-    128-target tiles up to p = 12, single tiles with fewer operator stages at
-    p = 13 and 15.  Water B at depth 4 has 40 M2L units (fewer than the SMs), so
-    every unit is cut into slices whose partial tiles are reduced."""
+def test_tensor_core_m2l_matches_fp64_path(sysB, p, split):
+    """Tensor-core M2L against the FP64 path at the same order, with one TF32
+    product per term (split -1), three for the first two K chunks (2, the
+    default) and three throughout (p): paired 128-target tiles up to p = 12,
+    single tiles with fewer operator stages at p = 13 and 15.  Water B at depth
+    4 has 24 (paired) or 40 (single) M2L units, fewer than the SMs, so every
+    unit is cut into slices whose partial tiles are reduced."""
     s, _ = sysB
     a = run_gpu(s, "fp64", p=p)
-    b = run_gpu(s, "mixed", p=p)
+    b = run_gpu(s, "mixed", p=p, options={"m2l_split_degree": p if split == "p" else split})
     rel = np.sqrt(((a["F"] - b["F"]) ** 2).sum() / (a["F"] ** 2).sum())
     assert rel < 2e-5, rel
     assert abs(a["E"] - b["E"]) / abs(a["E"]) < 3e-6
@@ -123,7 +126,8 @@ def test_tensor_core_m2l_matches_fp64_path(sysB, p):
 
 
 def test_tensor_core_m2l_full_units():
-    """Depth 5: 160 M2L units, 152 of them whole (one per SM) and 8 sliced."""
+    """Depth 5: each child class holds 4,681 targets over levels 1-5, merged
+    into 19 units of two 128-row tiles, so 152 units: one whole unit per SM."""
     s = synth.make_water(n_water=20000, grid=64, L=12.0, n_sites=4, seed=11, depth=5, order=8)
     a = run_gpu(s, "mixed_simt")
     b = run_gpu(s, "mixed")

@@ -118,8 +118,13 @@ def test_option_defaults_and_range():
             assert m.get_option("site_theta") == pytest.approx(0.3)
             m.set_option("site_theta", 0)
             assert m.get_option("site_theta") == pytest.approx(theta, rel=1e-6)
+            assert m.get_option("m2l_split_degree") == 2
+            m.set_option("m2l_split_degree", p)
+            assert m.get_option("m2l_split_degree") == p
             for opt, bad in [("site_theta", 0.8), ("site_theta", -0.1), ("site_list_cap", 10),
-                             ("site_list_cap", 20000), ("wait_limit_ms", 0.5), ("watchdog_selftest", 2), (99, 1)]:
+                             ("site_list_cap", 20000), ("wait_limit_ms", 0.5), ("watchdog_selftest", 2),
+                             ("m2l_split_degree", -2), ("m2l_split_degree", p + 1), ("m2l_split_degree", 1.5),
+                             (99, 1)]:
                 with pytest.raises(pkg.MahiError) as ei:
                     m.set_option(opt, bad)
                 assert ei.value.code == -1
