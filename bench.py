@@ -379,6 +379,81 @@ def run_sweep(args):
         print(json.dumps(rec), flush=True)
 
 
+def e1_point(s, prec, p, d, oracle_dEdl):
+    """One point of the accuracy sweep: dE/dlambda of the GPU path at order p,
+    depth d, against (a) the oracle (exact periodic HI) and (b) the paper's
+    reference, the same path's energies of the 2^m end states (separate
+    evaluations at the same p and d) combined by the multilinear
+    interpolation's derivative, Eqs. "ref_two_forms" / "ref_four_forms" read
+    as the derivative of Eq. "rek_ham_lambda"."""
+    import torch
+
+    import paper_2410_01754_gb300 as pkg
+    N = len(s["q_env"])
+    m = pkg.Mahi(s["L"], N, 1, p, d, prec)
+    status = 0
+    try:
+        if len(s["forms"][0]) == 2:
+            m.set_charges(s["qA"], s["qB"], s["site_of"])
+        else:
+            m.set_forms(s["q_env"], s["site_of"], s["forms"])
+        xdt = torch.float64 if prec == "fp64" else torch.float32
+        x = torch.tensor(s["x"], dtype=xdt, device="cuda")
+        lam0 = np.asarray(s["lams"][0], dtype=np.float64)
+        nl = len(lam0)
+        _, _, g = m.eval(x, torch.tensor(lam0, device="cuda"))
+        dEdl = g.cpu().numpy()
+        status = m.status()
+        H = {}
+        for rho in range(1 << nl):
+            corner = np.array([(rho >> l) & 1 for l in range(nl)], dtype=np.float64)
+            E, _, _ = m.eval(x, torch.tensor(corner, device="cuda"))
+            H[rho] = E.item()
+        status = status or m.status()
+    except pkg.MahiError as e:   # a device-side failure of one point is recorded, not fatal
+        return {"dEdl": None, "rel_dev_vs_oracle": [float("nan")], "rel_dev_vs_same_order_fmm": [float("nan")],
+                "status": e.code}
+    finally:
+        m.close()
+    ref_same = np.zeros(nl)
+    for l in range(nl):
+        for rho in range(1 << nl):
+            w = 1.0
+            for k in range(nl):
+                if k == l:
+                    w *= 1.0 if (rho >> k) & 1 else -1.0
+                else:
+                    w *= lam0[k] if (rho >> k) & 1 else 1.0 - lam0[k]
+            ref_same[l] += w * H[rho]
+    return {"dEdl": dEdl.tolist(), "rel_dev_vs_oracle": (np.abs(dEdl - oracle_dEdl) / np.abs(oracle_dEdl)).tolist(),
+            "rel_dev_vs_same_order_fmm": (np.abs(dEdl - ref_same) / np.abs(ref_same)).tolist(), "status": status}
+
+
+def run_accuracy_sweep(args):
+    """The paper's accuracy test (Sec. "Accuracy of the Random System with Two
+    Forms and Four Forms", Fig. "accuracy"): 1,000 + 10 random charges, one
+    site of 10 particles with 2 or 4 forms, clustered ("typical") or scattered
+    ("worst") site particles, lambda = 0.345 / (0.345, 0.721); relative
+    deviation of dE/dlambda for depths 0-3 and orders 2-16 in FP64 and mixed
+    precision, against the oracle and against the same-order end-state energies
+    (the paper's reference).  One JSON line per point."""
+    from oracle import hi
+    import synth
+    from paper_2410_01754_gb300 import build as pkg_build
+
+    pkg_build.build()
+    for layout in ("typical", "worst"):
+        for forms in (2, 4):
+            s = synth.make_e1(layout, forms, 1)
+            ref = hi.multiform_eval(s)["dEdl"]
+            for prec, orders in (("fp64", (2, 4, 6, 8, 10, 12, 16, 20)), ("mixed", (2, 4, 6, 8, 10, 12, 15))):
+                for d in (0, 1, 2, 3):
+                    for p in orders:
+                        r = e1_point(s, prec, p, d, ref)
+                        print(json.dumps({"sweep": "accuracy", "layout": layout, "forms": forms, "precision": prec,
+                                          "depth": d, "order_p": p, "oracle_dEdl": ref.tolist(), **r}), flush=True)
+
+
 def run_replicas(args):
     """16 independent replicas of uneven size (48k to 250k atoms, 16 to 256
     sites, each its own box and lambdas; p = 12, d = 4, mixed precision): one
@@ -544,8 +619,9 @@ def main():
                     help="time the mixed steps only (for profiler runs); skips stages, e2e, FP64 comparator")
     ap.add_argument("--replicas", action="store_true",
                     help="16 uneven replicas per step: eager calls vs autotuned vs one CUDA graph")
-    ap.add_argument("--sweep", choices=["sites", "atoms"], default=None,
-                    help="overhead of the per-site work over the plain FMM vs sites (1M atoms) or vs atoms")
+    ap.add_argument("--sweep", choices=["sites", "atoms", "accuracy"], default=None,
+                    help="overhead of the per-site work over the plain FMM vs sites (1M atoms) or vs atoms; "
+                         "accuracy: the paper's 1,010-particle dE/dlambda deviation sweep over depth and order")
     ap.add_argument("--case", default=WORKLOAD["config"], choices=[WORKLOAD["config"], "C_quarter"],
                     help="C_quarter: 250,002 atoms in the same box and tree (identical M2L work), for "
                          "profiler captures together with --kernels-only")
@@ -556,6 +632,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.sweep == "accuracy":
+        run_accuracy_sweep(args)
     elif args.sweep:
         run_sweep(args)
     elif args.replicas:

@@ -187,8 +187,8 @@ int mahi_backward(mahi_t h, const double *grad_energy, const void *forces, const
  *       a box of circumradius a is used through its multipole at a site of
  *       radius R at distance D only if a < theta (D - R), so each multipole
  *       term converges at least like theta^(p+1).  Default
- *       theta(p) = min(0.4, 0.4^(13/(p+1))): the truncation bound of p = 12 at
- *       theta = 0.4 held at every order.  Range (0, 0.7].
+ *       theta(p) = 0.4^(13/(p+1)) clamped to [0.25, 0.4]: the truncation bound
+ *       of p = 12 at theta = 0.4 held at orders 8 and up.  Range (0, 0.7].
  *   MAHI_OPT_SITE_LIST_CAP  boxes per level of one site's traversal (list
  *       capacity, 64 to 12288).  Default: 1536 at theta >= 0.4, else grown
  *       with the number of boxes a theta-ball holds.  A site that needs more

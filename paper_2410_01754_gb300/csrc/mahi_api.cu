@@ -26,9 +26,11 @@ int cuda_fail(cudaError_t e, const char *what) {
 }
 
 float default_site_theta(int p) {
-  // theta^(p+1) = 0.4^13: the M2P truncation bound that theta = 0.4 gives at p = 12
+  // theta^(p+1) = 0.4^13: the M2P truncation bound that theta = 0.4 gives at
+  // p = 12, within [0.25, 0.4] (below p = 8 the bound is not held: a smaller
+  // ratio would open most of the tree)
   const double t = std::pow(0.4, 13.0 / (p + 1.0));
-  return (float)std::min(0.4, t);
+  return (float)std::max(0.25, std::min(0.4, t));
 }
 
 int default_m2l_split_degree(int p) { return std::min(2, p); }

@@ -37,7 +37,7 @@ constexpr int kStatusM2LTimeout = 0;   // a bounded wait of the tensor-core M2L 
 constexpr int kStatusSiteOverflow = 1; // a site traversal list outgrew its capacity
 constexpr int kStatusWords = 4;
 // Default separation ratio of the site-atom traversal at order p (truncation
-// bound theta^(p+1) of p = 12, theta = 0.4 kept at every order, never above 0.4)
+// bound theta^(p+1) of p = 12, theta = 0.4 kept at every order, within [0.25, 0.4])
 float default_site_theta(int p);
 // Default list capacity of the site traversal for a separation ratio theta
 int default_site_list_cap(float theta);

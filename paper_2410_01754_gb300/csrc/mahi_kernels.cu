@@ -1769,6 +1769,11 @@ __global__ void __launch_bounds__(kSiteThreads, 3) k_site_phi(
     }
   }
   __syncthreads();
+  // A compact site (radius at most two leaf edges, the usual case: the atoms
+  // of one residue) shares one traversal between its atoms; a spread site (its
+  // atoms scattered over the box) would have to open nearly every box near
+  // any of them, so each of its atoms then takes its own traversal (a group
+  // of one atom about itself).  All blocks of a site take the same decision.
   if (tid == 0) {
     double c[3] = {0, 0, 0};
     for (int a = 0; a < n; ++a)
@@ -1782,7 +1787,16 @@ __global__ void __launch_bounds__(kSiteThreads, 3) k_site_phi(
     cen[0] = c[0]; cen[1] = c[1]; cen[2] = c[2]; cen[3] = R;
   }
   __syncthreads();
-  for (int a = tid; a < n; a += blockDim.x) {
+  const bool spread = cen[3] > 2.0 * sl;
+  const int ngroups = spread ? n : 1;
+  for (int grp = 0; grp < ngroups; ++grp) {
+  const int ga = spread ? grp : 0, gn = spread ? 1 : n;   // atoms ga .. ga + gn - 1 of the site
+  __syncthreads();
+  if (spread && tid == 0) {
+    cen[0] = pa[ga][0]; cen[1] = pa[ga][1]; cen[2] = pa[ga][2]; cen[3] = 0.0;
+  }
+  __syncthreads();
+  for (int a = ga + tid; a < ga + gn; a += blockDim.x) {
     const double ux = pa[a][0] - cen[0], uy = pa[a][1] - cen[1], uz = pa[a][2] - cen[2];
     pu[a][0] = (T)ux; pu[a][1] = (T)uy; pu[a][2] = (T)uz;
     puu[a] = (T)(ux * ux + uy * uy + uz * uz);
@@ -1792,9 +1806,9 @@ __global__ void __launch_bounds__(kSiteThreads, 3) k_site_phi(
   __syncthreads();
   // thread -> (atom pair, slot), fixed for the whole traversal; a slot takes
   // the rows slot, slot + nslot, ... of every batch
-  const int npair = (n + 1) >> 1, nslot = blockDim.x / npair;
+  const int npair = (gn + 1) >> 1, nslot = blockDim.x / npair;
   const int my_p = (tid < nslot * npair) ? tid % npair : -1, my_s = tid / npair;
-  const int a0 = my_p < 0 ? 0 : my_p, a1 = (my_p >= 0 && my_p + npair < n) ? my_p + npair : a0;
+  const int a0 = ga + (my_p < 0 ? 0 : my_p), a1 = ga + ((my_p >= 0 && my_p + npair < gn) ? my_p + npair : (my_p < 0 ? 0 : my_p));
   const int nbatch = (nslot <= nbmax) ? nslot * (nbmax / nslot) : nbmax;
   SiteAcc<T> acc0, acc1;
   double base = 0.0;  // FP64 charge + dipole values at c of the rows this thread stages
@@ -1971,8 +1985,9 @@ __global__ void __launch_bounds__(kSiteThreads, 3) k_site_phi(
   }
   __syncthreads();
   const double common = cen[3];
-  for (int a = tid; a < n; a += blockDim.x) {
-    const int pp = (a < npair) ? a : a - npair, hh = (a < npair) ? 0 : 1;
+  for (int a = ga + tid; a < ga + gn; a += blockDim.x) {
+    const int al = a - ga;
+    const int pp = (al < npair) ? al : al - npair, hh = (al < npair) ? 0 : 1;
     double acc = common;
     for (int k = 0; k < nslot; ++k) acc += res_s[pp + k * npair][hh];
     if (g == 0) {
@@ -1991,6 +2006,7 @@ __global__ void __launch_bounds__(kSiteThreads, 3) k_site_phi(
     }
     phi_part[(size_t)(b0 + a) * G + g] = acc;
   }
+  }  // groups
 }
 
 // phi_site = f * (sum of the parts, in part order)

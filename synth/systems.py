@@ -273,6 +273,51 @@ def make_water(n_water: int, grid: int, L: float, n_sites: int, seed: int,
                 lam=lam, depth=depth, order=order)
 
 
+def make_e1(layout: str = "typical", forms: int = 2, seed: int = 1, L: float = 2.2, depth: int = 2, order: int = 8):
+    """The paper's accuracy test system (Sec. "Random Systems"): 1,000
+    background particles and 10 site particles, all charges U(-1, 1), in a
+    periodic cube (edge L; the paper gives none, 2.2 nm puts the particles at
+    config A's density), positions uniform with rejection to a minimum
+    periodic pair distance of 0.1 nm.  The 10 site particles form one site with
+    `forms` forms (2 or 4), each form its own U(-1, 1) charge set:
+    layout "typical" takes a random particle and its 9 nearest periodic
+    neighbours (clustered, like the atoms of one residue), "worst" 10 particles
+    drawn uniformly from the whole box.  lambda = 0.345 (two forms) or
+    (0.345, 0.721) (four forms), as in the paper.  Returns the multi-form
+    layout (q_env, site_of, forms, lams) and, for two forms, also qA, qB, lam."""
+    assert layout in ("typical", "worst") and forms in (2, 4)
+    n, nsite = 1010, 10
+    base = make_charges(n=n, L=L, n_sites=0, atoms_per_site=1, seed=seed, dmin=0.1, depth=depth, order=order)
+    x = base["x"]
+    q = _uniform(seed, 11, n, -1.0, 1.0)
+    pick = uniform01(seed, 12, 4 * nsite * 16)
+    if layout == "typical":
+        c = int(pick[0] * n)
+        dd = _min_image(x - x[c], L)
+        members = np.argsort((dd * dd).sum(1), kind="stable")[:nsite]
+    else:
+        members, k = [], 0
+        while len(members) < nsite:
+            j = int(pick[k] * n)
+            k += 1
+            if j not in members:
+                members.append(j)
+        members = np.array(members)
+    members = np.array(sorted(int(j) for j in members), dtype=np.int64)
+    site_of = np.full(n, -1, dtype=np.int32)
+    site_of[members] = 0
+    fq = _uniform(seed, 13, forms * nsite, -1.0, 1.0).reshape(forms, nsite)
+    lams = [np.array([0.345])] if forms == 2 else [np.array([0.345, 0.721])]
+    out = dict(name=f"e1_{layout}_{forms}forms", seed=seed, L=float(L), x=x, q_env=q, site_of=site_of,
+               forms=[fq], lams=lams, depth=depth, order=order)
+    if forms == 2:
+        qA, qB = q.copy(), q.copy()
+        qA[members] = fq[0]
+        qB[members] = fq[1]
+        out.update(qA=qA, qB=qB, lam=lams[0].copy())
+    return out
+
+
 def make(config: str, seed: int = 1):
     """Build one of the named workloads ("A", "B", "C", "D", "C_quarter") for a seed."""
     c = dict(CONFIGS[config])

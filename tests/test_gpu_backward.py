@@ -125,6 +125,68 @@ def test_autograd_finite_differences_fp64(sysD):
     me.close()
 
 
+def test_autograd_finite_differences_mixed(sysD):
+    """200,001 atoms, 128 sites, p = 12, mixed path (float32 positions, FP32
+    FMM with the FP64 site terms): autograd gradients against central
+    differences of the same path's energy.  The energy is an FP64 sum of
+    single-precision potentials, whose rounding changes with any perturbation
+    (about 1e-2 kJ/mol over 200k atoms), so the steps are chosen where that
+    noise is small next to the difference: 2e-3 nm in x (the truncation error
+    of the central difference there is below 2 kJ/mol/nm even for the
+    closest pairs), and 0.25 in lambda and 0.05 e in the charges, where the
+    energy is exactly quadratic and central differences are exact for any
+    step.  dE/dlambda and dE/dq use the refined site-atom potential, the
+    energy the FMM's, whose truncation (and in the mixed path the tensor-core
+    accumulation bias) differs by up to ~0.1 kJ/mol per unit lambda here.
+    In x the check is bounded by the single-precision near-field sums: moving
+    one atom re-rounds the ~800 potentials it enters (each a sum of terms up
+    to ~1e3 kJ/mol/e), which shifts the energy by ~1e-2 kJ/mol, so central
+    differences over 4e-3 nm scatter by ~10 kJ/mol/nm (measured median 9,
+    largest 41, against forces up to 1.1e4): the check catches sign, scale
+    and leaf-boundary errors, not rounding."""
+    s = sysD
+    N, S = len(s["qA"]), len(s["lam"])
+    me = MahiEnergy(s["L"], s["site_of"], S, 12, 4, "mixed")
+    x, lam, qA, qB = _tensors(s, torch.float32)
+    E = me.energy(x, lam, qA, qB)
+    E.backward()
+    gx, gl, gA, gB = (t.grad.clone() for t in (x, lam, qA, qB))
+    rng = np.random.default_rng(6)
+
+    def energy(xx=None, ll=None, a=None, b=None):
+        with torch.no_grad():
+            return me.energy(x if xx is None else xx, lam if ll is None else ll, qA if a is None else a,
+                             qB if b is None else b).item()
+
+    Fscale = gx.abs().max().item()
+    errs = []
+    for k in rng.choice(N, 64, replace=False):
+        ax = int(rng.integers(3))
+        xp = x.detach().clone(); xp[k, ax] += 2e-3
+        xm = x.detach().clone(); xm[k, ax] -= 2e-3
+        h2 = (xp[k, ax] - xm[k, ax]).item()        # the step as stored in float32
+        fd = (energy(xx=xp) - energy(xx=xm)) / h2
+        errs.append(abs(fd - gx[k, ax].item()))
+    print(f"mixed finite differences in x: max {max(errs):.3g}, median {np.median(errs):.3g} kJ/mol/nm "
+          f"(largest force {Fscale:.4g})")
+    assert max(errs) < 5e-3 * Fscale, (max(errs), np.median(errs), Fscale)
+    assert np.median(errs) < 1.5e-3 * Fscale, (max(errs), np.median(errs), Fscale)
+    for k in rng.choice(S, 8, replace=False):
+        lp = lam.detach().clone(); lp[k] += 0.25
+        lm = lam.detach().clone(); lm[k] -= 0.25
+        fd = (energy(ll=lp) - energy(ll=lm)) / 0.5
+        assert fd == pytest.approx(gl[k].item(), abs=0.2)
+    site_atoms = np.where(s["site_of"] >= 0)[0]
+    for key, t, g in (("qA", qA, gA), ("qB", qB, gB)):
+        for k in rng.choice(site_atoms, 6, replace=False):
+            tp = t.detach().clone(); tm = t.detach().clone()
+            tp[k] += 0.05; tm[k] -= 0.05
+            arg = "a" if key == "qA" else "b"
+            fd = (energy(**{arg: tp}) - energy(**{arg: tm})) / 0.1
+            assert fd == pytest.approx(g[k].item(), abs=0.2)
+    me.close()
+
+
 def test_autograd_mixed_matches_fp64(sysD):
     """The mixed path's gradients (single precision with FP64 site terms)
     against the FP64 path's on the same 200,001-atom system."""

@@ -107,7 +107,7 @@ def test_site_list_overflow_is_reported_and_the_handle_recovers(small, prec):
 
 
 def test_option_defaults_and_range():
-    for p, theta in [(8, 0.4 ** (13 / 9)), (10, 0.4 ** (13 / 11)), (12, 0.4), (14, 0.4)]:
+    for p, theta in [(4, 0.25), (8, 0.4 ** (13 / 9)), (10, 0.4 ** (13 / 11)), (12, 0.4), (14, 0.4)]:
         m = pkg.Mahi(3.0, 100, 2, p, 2, "fp64")
         try:
             assert m.get_option("site_theta") == pytest.approx(theta, rel=1e-6)
