@@ -132,9 +132,10 @@ int mahi_update_charges(mahi_t h, const double *qA, const double *qB);
  *   C = f/2 [sum_rho w_rho G_rho,rho - w^T G w],  G = form-form matrix of the
  *   periodic kernel over the site's atoms (self term included),
  * and the forces its gradient.  mahi_n_lambdas gives the count.  A later
- * mahi_set_charges returns the handle to two-form sites.  mahi_backward does
- * not support these sites (MAHI_ERR_INVALID_ARG).  Errors as for
- * mahi_set_charges, and MAHI_ERR_INVALID_ARG for an F_s outside the set. */
+ * mahi_set_charges returns the handle to two-form sites.  Their backward pass
+ * is mahi_backward_forms (mahi_backward returns MAHI_ERR_INVALID_ARG for
+ * them).  Errors as for mahi_set_charges, and MAHI_ERR_INVALID_ARG for an F_s
+ * outside the set. */
 int mahi_set_forms(mahi_t h, const double *q_env, const int32_t *site_of_atom, const int32_t *forms_per_site,
                    const double *q_forms);
 int mahi_n_lambdas(mahi_t h);
@@ -224,6 +225,23 @@ enum {
 int mahi_set_option(mahi_t h, int32_t option, double value);
 /* Current value of an option (the effective one for defaults). */
 double mahi_get_option(mahi_t h, int32_t option);
+
+/* Backward pass for sites with 2^m forms (mahi_set_forms), the counterpart of
+ * mahi_backward.  dx and dlambda as there (dlambda has mahi_n_lambdas entries);
+ * the charge gradients follow the mahi_set_forms layout:
+ *   dEdq_env    device, n_atoms float64: g phi~_i for environment atoms, 0 for
+ *               site atoms (their q_env entries are not used)
+ *   dEdq_forms  device, sum_s F_s n_s float64 (site by site, F_s rows of its
+ *               atoms' entries, as q_forms): g w_r (phi~_i + psi^r_i - sum_r' w_r' psi^r'_i)
+ * with w_r the form weights prod_l (bit l of r ? lambda_l : 1 - lambda_l) and
+ * psi^r_i = f sum_{j in s} A(x_i - x_j) q^r_j (self term included), from
+ * E = E(q~) + sum_s f/2 [sum_r w_r G_rr - w^T G w], G_rr' = q^r^T A q^r'
+ * (Eq. "iter_ham_lambda", Eq. "one_site_lambda").  Uses the last evaluation's
+ * potentials; MAHI_ERR_INVALID_ARG on a two-form handle or an output without
+ * its input; MAHI_ERR_STATE before the charges are set. */
+int mahi_backward_forms(mahi_t h, const double *grad_energy, const void *forces, const double *dEdlambda,
+                        const double *lambda, int32_t x_is_fp64, void *dx, double *dlambda, double *dEdq_env,
+                        double *dEdq_forms);
 
 /* Charge-scaled potential phi~ (kJ/mol/e, float64, original atom order) of the
  * last evaluation into a device buffer of n_atoms doubles (enqueued). */

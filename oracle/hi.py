@@ -269,6 +269,31 @@ def multiform_eval(sys, rc=None, f=F_COULOMB):
     return dict(E=E, F=F, dEdl=np.concatenate(dEdl) if dEdl else np.zeros(0), qt=q, phi=phi)
 
 
+def multiform_charge_gradients(sys, rc=None, f=F_COULOMB, ref=None):
+    """dE/dq_env and dE/dq^rho of the multi-form HI energy (the derivative of
+    multiform_eval's E in the charges; the paper has no charge gradients).
+    With E = E(q~) + sum_s f/2 [sum_rho w_rho G_rho,rho - w^T G w],
+    q~ = sum_rho w_rho q^rho at site atoms and G_rho,rho' = q^rho^T A q^rho':
+      dE/dq_env_i = phi~_i (environment atoms; 0 for site atoms, whose q_env
+                    entries are not used),
+      dE/dq^rho_i = w_rho (phi~_i + f (A q^rho)_i - f (A q~_s)_i)  (site atoms),
+    A over the site's atoms with the self term (the same periodic kernel)."""
+    ref = multiform_eval(sys, rc, f) if ref is None else ref
+    x, L = sys["x"], sys["L"]
+    site_of = np.asarray(sys["site_of"])
+    sites = site_lists(site_of, len(sys["forms"]))
+    dq_env = np.where(site_of < 0, ref["phi"], 0.0)
+    dq_forms = []
+    for s, at in enumerate(sites):
+        Q = np.asarray(sys["forms"][s], dtype=np.float64)
+        w = lambda_tilde(sys["lams"][s])
+        xs = x[at]
+        psi = np.array([ewald(xs, Q[r], L, rc=0.5 * L)[0] for r in range(Q.shape[0])]) * f   # f A q^rho
+        psit = w @ psi
+        dq_forms.append(w[:, None] * (ref["phi"][at][None, :] + psi - psit[None, :]))
+    return dict(dq_env=dq_env, dq_forms=dq_forms)
+
+
 def multiform_bruteforce(sys, rc=None, f=F_COULOMB):
     """The multilinear definition (Eq. "rek_ham_lambda" with Eq. "one_site_lambda"
     per site): E = sum over every choice of one form per site of the product of

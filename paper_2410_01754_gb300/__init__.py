@@ -38,6 +38,9 @@ _SIGS = {
     "mahi_backward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                      ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
                                      ctypes.c_void_p, ctypes.c_void_p]),
+    "mahi_backward_forms": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                           ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                           ctypes.c_void_p, ctypes.c_void_p]),
     "mahi_set_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "mahi_stage_times": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float), ctypes.c_int32]),
     "mahi_stage_name": (ctypes.c_char_p, [ctypes.c_int32]),
@@ -210,6 +213,15 @@ def mahi_backward(h, grad_energy, forces, dEdlambda, lam, dx=None, dlambda=None,
     x_is_fp64 = 1 if ref is not None and str(ref.dtype).endswith("float64") else 0
     _ck(lib().mahi_backward(h, _ptr(grad_energy), _ptr(forces), _ptr(dEdlambda), _ptr(lam), x_is_fp64, _ptr(dx),
                             _ptr(dlambda), _ptr(dEdqA), _ptr(dEdqB)), "mahi_backward")
+
+
+def mahi_backward_forms(h, grad_energy, forces, dEdlambda, lam, dx=None, dlambda=None, dEdq_env=None,
+                        dEdq_forms=None):
+    """Backward of the last mahi_eval on a handle with 2^m-form sites (device tensors)."""
+    ref = forces if forces is not None else dx
+    x_is_fp64 = 1 if ref is not None and str(ref.dtype).endswith("float64") else 0
+    _ck(lib().mahi_backward_forms(h, _ptr(grad_energy), _ptr(forces), _ptr(dEdlambda), _ptr(lam), x_is_fp64,
+                                  _ptr(dx), _ptr(dlambda), _ptr(dEdq_env), _ptr(dEdq_forms)), "mahi_backward_forms")
 
 
 def mahi_set_timing(h, on=True):

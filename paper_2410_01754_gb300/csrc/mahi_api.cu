@@ -67,7 +67,7 @@ static void free_all(mahi_ctx *h) {
                   h->m2l_list, h->m2l_off, h->site_ptr, h->site_atoms,
                   h->energy_part, h->site_energy, h->tc_ops, h->tc_partial, h->tc_msrc, h->tc_level_off, h->tc_units, h->d_x_stage,
                   h->d_lam_stage, h->d_E_stage, h->d_dEdl_stage, h->d_F_stage, h->ops_lat_h3, h->L_h3,
-                  h->box_qd, h->vtmp, h->relD, h->phi_site, h->psi_site, h->site_pairs, h->site_slot, h->mf_q, h->mf_lam_off, h->phi_part, h->d_level_off};
+                  h->box_qd, h->vtmp, h->relD, h->phi_site, h->psi_site, h->site_pairs, h->site_slot, h->mf_q, h->mf_lam_off, h->phi_part, h->d_level_off, h->mf_psi, h->mf_form_off};
   for (void *b : bufs)
     if (b) cudaFree(b);
   if (h->status_host) cudaFreeHost(h->status_host);
@@ -476,10 +476,19 @@ int mahi_set_forms(mahi_t h, const double *q_env, const int32_t *site_of_atom, c
     off += (size_t)F * n;
   }
   if (h->mf_q) { cudaFree(h->mf_q); h->mf_q = nullptr; }
+  if (h->mf_psi) { cudaFree(h->mf_psi); h->mf_psi = nullptr; }
   if (!h->mf_lam_off) CK(dalloc(&h->mf_lam_off, (S + 1) * sizeof(int)));
+  if (!h->mf_form_off) CK(dalloc(&h->mf_form_off, (S + 1) * sizeof(int)));
   CK(dalloc(&h->mf_q, qf.size() * sizeof(double)));
+  CK(dalloc(&h->mf_psi, qf.size() * sizeof(double)));
   CK(cudaMemcpy(h->mf_q, qf.data(), qf.size() * sizeof(double), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(h->mf_lam_off, lam_off.data(), (S + 1) * sizeof(int), cudaMemcpyHostToDevice));
+  {
+    std::vector<int> foff(S + 1, 0);
+    for (int sidx = 0; sidx < S; ++sidx) foff[sidx + 1] = foff[sidx] + forms_per_site[sidx] * cnt[sidx];
+    CK(cudaMemcpy(h->mf_form_off, foff.data(), (S + 1) * sizeof(int), cudaMemcpyHostToDevice));
+    h->n_form_charges = foff[S];
+  }
   h->n_lam = lam_off[S];
   h->multiform = true;
   return MAHI_OK;
@@ -571,6 +580,23 @@ double mahi_get_option(mahi_t h, int32_t option) {
     case MAHI_OPT_M2L_SPLIT_DEGREE: return h->m2l_split_degree;
     default: return -1.0;
   }
+}
+
+int mahi_backward_forms(mahi_t h, const double *grad_energy, const void *forces, const double *dEdlambda,
+                        const double *lambda, int32_t x_is_fp64, void *dx, double *dlambda, double *dEdq_env,
+                        double *dEdq_forms) {
+  if (!h || !grad_energy) return MAHI_ERR_INVALID_ARG;
+  if (!h->charges_set) return MAHI_ERR_STATE;
+  if (!h->multiform) return MAHI_ERR_INVALID_ARG;  // sites with 2^m forms only
+  if (dx && !forces) return MAHI_ERR_INVALID_ARG;
+  if (dlambda && h->n_lam > 0 && !dEdlambda) return MAHI_ERR_INVALID_ARG;
+  if (dEdq_forms && h->S > 0 && !lambda) return MAHI_ERR_INVALID_ARG;
+  CK(cudaSetDevice(h->device));
+  if (enqueue_backward_forms(h, grad_energy, forces, dEdlambda, lambda, x_is_fp64 ? 1 : 0, dx, dlambda, dEdq_env,
+                             dEdq_forms) != 0)
+    return cuda_fail(cudaGetLastError(), "mahi_backward_forms");
+  h->launches = (dx || dlambda ? 1 : 0) + (dEdq_env || dEdq_forms ? 1 : 0);
+  return MAHI_OK;
 }
 
 int mahi_backward(mahi_t h, const double *grad_energy, const void *forces, const double *dEdlambda,

@@ -139,6 +139,9 @@ struct mahi_ctx {
   double *mf_q = nullptr;                     // [site atom slot][16] charges per form
   int *mf_lam_off = nullptr;                  // [S + 1] offsets of each site's lambdas
   int n_lam = 0;                              // lambdas (and dE/dlambda entries) in total
+  double *mf_psi = nullptr;                   // [site atom slot][16] f (A q^r) per form (backward)
+  int *mf_form_off = nullptr;                 // [S + 1] offsets of each site's entries in the q_forms layout
+  int n_form_charges = 0;                     // sum_s F_s n_s
   double *phi_part = nullptr;                 // its per-part partial sums
   int64_t *d_level_off = nullptr;             // device copy of level_off
   double *eta = nullptr, *eta_x = nullptr, *eta_y = nullptr, *eta_z = nullptr;  // degree 2p
@@ -189,6 +192,8 @@ int enqueue_eval(mahi_ctx *h, const void *x, int x_is_fp64, const double *lambda
                  void *forces, double *dEdl);
 int enqueue_potential(mahi_ctx *h, double *phi);
 int enqueue_update_charges(mahi_ctx *h, const double *qA, const double *qB);
+int enqueue_backward_forms(mahi_ctx *h, const double *gE, const void *forces, const double *dEdl, const double *lam,
+                           int x_is_fp64, void *dx, double *dlam, double *dq_env, double *dq_forms);
 int enqueue_backward(mahi_ctx *h, const double *gE, const void *forces, const double *dEdl, const double *lam,
                      int x_is_fp64, void *dx, double *dlam, double *dqA, double *dqB);
 int upload_tables();

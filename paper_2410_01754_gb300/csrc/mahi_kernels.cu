@@ -1373,7 +1373,8 @@ __global__ void __launch_bounds__(32) k_site_mf(int S, double L, double fcoul, i
                                                 const double *__restrict__ phi_site, const double *__restrict__ eta,
                                                 const double *__restrict__ eta_x, const double *__restrict__ eta_y,
                                                 const double *__restrict__ eta_z, double *__restrict__ dEdl,
-                                                double *__restrict__ site_energy, FT *__restrict__ forces) {
+                                                double *__restrict__ site_energy, FT *__restrict__ forces,
+                                                double *__restrict__ psi_form) {
   __shared__ double A[kMfMaxAtoms][kMfMaxAtoms + 1];
   __shared__ double gw[kMfMaxAtoms * (kMfMaxAtoms - 1) / 2][3];  // W_ij grad A(r_ij), r = x_i - x_j, i < j
   __shared__ double qs[kMfMaxForms][kMfMaxAtoms], Tm[kMfMaxForms][kMfMaxAtoms], G[kMfMaxForms][kMfMaxForms];
@@ -1417,6 +1418,9 @@ __global__ void __launch_bounds__(32) k_site_mf(int S, double L, double fcoul, i
     double v = 0.0;
     for (int j = 0; j < n; ++j) v += A[a][j] * qs[r][j];
     Tm[r][a] = v;
+    // psi^r_a = f (A q^r)_a over the site (self term included), kept for the
+    // charge gradients of the backward pass
+    if (psi_form) psi_form[(size_t)(b + a) * kMfMaxForms + r] = fcoul * v;
   }
   __syncwarp();
   for (int e = lane; e < F * F; e += 32) {
@@ -2064,6 +2068,31 @@ __global__ void k_unpermute_phi(int64_t N, const int *__restrict__ inv_perm, con
   if (i < N) phi[i] = (double)phi_s[inv_perm[i]];
 }
 
+// Charge and dipole coefficients of every box's multipole from the FP64 box
+// moments (Q, D about the box centre).  In single precision the M2M sums of a
+// box's monopole carry an absolute error of about 6e-8 of the sum of |q| over
+// its atoms (1e-3 e for a level-1 box of a 200k-atom system), while the box is
+// nearly neutral: through the far-field translations that shifted every
+// potential by ~0.1 kJ/mol/e.  The FP64 moments rounded once to the working
+// precision carry 6e-8 of |Q| instead.  Device basis, u = (x - c) / s:
+//   M_00 = Q,  M_10 = D_z / s,  M_11 = -(D_x - i D_y) / (sqrt(2) s)
+// (real layout: index 1 = M_10, 2 and 3 = Re and Im of M_11).
+template <typename T>
+__global__ void k_patch_low_multipoles(int64_t nbox, int d, double L, int ld, const int64_t *__restrict__ level_off,
+                                       const double *__restrict__ qd, T *__restrict__ M) {
+  const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (b >= nbox) return;
+  int l = 0;
+  while (l < d && b >= level_off[l + 1]) ++l;
+  const double s = L / (double)(1 << l), c = 1.0 / (1.4142135623730951 * s);
+  const double *v = qd + (size_t)b * kQD;
+  T *m = M + (size_t)b * ld;
+  m[0] = (T)v[0];
+  m[1] = (T)(v[3] / s);
+  m[2] = (T)(-v[1] * c);
+  m[3] = (T)(v[2] * c);
+}
+
 // ---------------------------------------------------------------------------
 // orchestration
 // ---------------------------------------------------------------------------
@@ -2247,6 +2276,11 @@ static cudaError_t eval_t(mahi_ctx *h, const XT *x, const double *lam, double *e
                                           h->gemm_ws_elems, h->num_sms, st, h->launches)));
   }
   MAHI_CK(cudaStreamWaitEvent(st, h->join_ev[0], 0));  // box moments (mom) done
+  if (sizeof(T) == 4 && P >= 1) {
+    k_patch_low_multipoles<T><<<(int)((h->nbox_total + 255) / 256), 256, 0, st>>>(h->nbox_total, h->d, h->L, ld,
+                                                                               h->d_level_off, h->box_qd, M);
+    h->launches += 1;
+  }
   mark(h, 4);
   k_lattice<T><<<(ld + 3) / 4, 128, sizeof(double) * K, st>>>(K, ld, h->L, h->ops_lat, h->ops_lat_h3, mom, M, Lx,
                                                     h->L_h3);
@@ -2330,7 +2364,7 @@ static cudaError_t eval_t(mahi_ctx *h, const XT *x, const double *lam, double *e
     if (h->multiform)
       k_site_mf<XT, XT><<<h->S, 32, 0, st>>>(h->S, h->L, coulomb_constant(), kSiteDegree, h->site_aii, h->site_ptr,
                                              h->site_atoms, x, h->mf_lam_off, lam, h->mf_q, h->phi_site, h->eta,
-                                             h->eta_x, h->eta_y, h->eta_z, dEdl, h->site_energy, forces);
+                                             h->eta_x, h->eta_y, h->eta_z, dEdl, h->site_energy, forces, h->mf_psi);
     else
       k_site<T, XT, XT><<<(h->S + 3) / 4, 128, 0, st>>>(h->S, h->L, coulomb_constant(), kSiteDegree, h->site_aii,
                                                         h->site_ptr, h->site_atoms, x, h->dq, lam, h->phi_site, h->eta,
@@ -2434,28 +2468,87 @@ int enqueue_backward(mahi_ctx *h, const double *gE, const void *forces, const do
                      int x_is_fp64, void *dx, double *dlam, double *dqA, double *dqB) {
   const int grid = (int)std::min<int64_t>(4 * (int64_t)h->num_sms, (h->N + 255) / 256);
   const bool f64 = h->prec == MAHI_FP64;
+  const int nl = h->multiform ? h->n_lam : h->S;   // entries of dE/dlambda
   if (x_is_fp64) {
     if (f64)
-      k_backward<double, double><<<grid, 256, 0, h->stream>>>(h->N, h->S, gE, (const double *)forces, dEdl, lam,
+      k_backward<double, double><<<grid, 256, 0, h->stream>>>(h->N, nl, gE, (const double *)forces, dEdl, lam,
                                                               h->inv_perm, (const double *)h->phi_s, h->site_of,
                                                               h->site_slot, h->phi_site, h->psi_site, (double *)dx,
                                                               dlam, dqA, dqB);
     else
-      k_backward<float, double><<<grid, 256, 0, h->stream>>>(h->N, h->S, gE, (const double *)forces, dEdl, lam,
+      k_backward<float, double><<<grid, 256, 0, h->stream>>>(h->N, nl, gE, (const double *)forces, dEdl, lam,
                                                              h->inv_perm, (const float *)h->phi_s, h->site_of,
                                                              h->site_slot, h->phi_site, h->psi_site, (double *)dx,
                                                              dlam, dqA, dqB);
   } else {
     if (f64)
-      k_backward<double, float><<<grid, 256, 0, h->stream>>>(h->N, h->S, gE, (const float *)forces, dEdl, lam,
+      k_backward<double, float><<<grid, 256, 0, h->stream>>>(h->N, nl, gE, (const float *)forces, dEdl, lam,
                                                              h->inv_perm, (const double *)h->phi_s, h->site_of,
                                                              h->site_slot, h->phi_site, h->psi_site, (float *)dx,
                                                              dlam, dqA, dqB);
     else
-      k_backward<float, float><<<grid, 256, 0, h->stream>>>(h->N, h->S, gE, (const float *)forces, dEdl, lam,
+      k_backward<float, float><<<grid, 256, 0, h->stream>>>(h->N, nl, gE, (const float *)forces, dEdl, lam,
                                                             h->inv_perm, (const float *)h->phi_s, h->site_of,
                                                             h->site_slot, h->phi_site, h->psi_site, (float *)dx,
                                                             dlam, dqA, dqB);
+  }
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+// Backward of the HI energy for sites with 2^m forms: with g = dLoss/dE and
+// the form weights w_r of the atom's site,
+//   dE/dq^r_i = w_r (phi~_i + psi^r_i - sum_r' w_r' psi^r'_i)   (site atom i),
+//   dE/dq_env_i = phi~_i                                          (environment),
+// from E = E(q~) + sum_s f/2 [sum_r w_r G_rr - w^T G w], q~ = sum_r w_r q^r,
+// G_rr' = q^r^T A q^r' over the site, psi^r = f A q^r (Eq. "iter_ham_lambda"
+// with Eq. "one_site_lambda").  One thread per atom: site atoms write their
+// F_s form entries at form_off[s] + r n_s + a (the q_forms layout).
+template <typename T>
+__global__ void k_backward_mf_charges(int64_t N, const double *__restrict__ gE, const int *__restrict__ inv_perm,
+                                      const T *__restrict__ phi_s, const int *__restrict__ site_of,
+                                      const int *__restrict__ site_slot, const int *__restrict__ site_ptr,
+                                      const int *__restrict__ lam_off, const int *__restrict__ form_off,
+                                      const double *__restrict__ lam, const double *__restrict__ phi_site,
+                                      const double *__restrict__ psi_form, double *__restrict__ dq_env,
+                                      double *__restrict__ dq_forms) {
+  const double g = *gE;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += stride) {
+    const int sl = site_slot[i];
+    if (sl < 0) {
+      if (dq_env) dq_env[i] = g * (double)phi_s[inv_perm[i]];
+      continue;
+    }
+    if (dq_env) dq_env[i] = 0.0;  // the q_env entries of site atoms are not used
+    if (!dq_forms) continue;
+    const int s = site_of[i], m = lam_off[s + 1] - lam_off[s], F = 1 << m;
+    const int n = site_ptr[s + 1] - site_ptr[s], a = sl - site_ptr[s];
+    double w[kMfMaxForms];
+    mf_weights(lam + lam_off[s], m, w);
+    double psit = 0.0;
+    for (int r = 0; r < F; ++r) psit += w[r] * psi_form[(size_t)sl * kMfMaxForms + r];
+    const double phi = phi_site[sl];
+    for (int r = 0; r < F; ++r)
+      dq_forms[form_off[s] + r * n + a] = g * w[r] * (phi + psi_form[(size_t)sl * kMfMaxForms + r] - psit);
+  }
+}
+
+int enqueue_backward_forms(mahi_ctx *h, const double *gE, const void *forces, const double *dEdl, const double *lam,
+                           int x_is_fp64, void *dx, double *dlam, double *dq_env, double *dq_forms) {
+  const int grid = (int)std::min<int64_t>(4 * (int64_t)h->num_sms, (h->N + 255) / 256);
+  // positions and lambdas as in the two-form pass (no charge outputs there)
+  if (dx || dlam) {
+    if (enqueue_backward(h, gE, forces, dEdl, lam, x_is_fp64, dx, dlam, nullptr, nullptr) != 0) return -1;
+  }
+  if (dq_env || dq_forms) {
+    if (h->prec == MAHI_FP64)
+      k_backward_mf_charges<double><<<grid, 256, 0, h->stream>>>(
+          h->N, gE, h->inv_perm, (const double *)h->phi_s, h->site_of, h->site_slot, h->site_ptr, h->mf_lam_off,
+          h->mf_form_off, lam, h->phi_site, h->mf_psi, dq_env, dq_forms);
+    else
+      k_backward_mf_charges<float><<<grid, 256, 0, h->stream>>>(
+          h->N, gE, h->inv_perm, (const float *)h->phi_s, h->site_of, h->site_slot, h->site_ptr, h->mf_lam_off,
+          h->mf_form_off, lam, h->phi_site, h->mf_psi, dq_env, dq_forms);
   }
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }

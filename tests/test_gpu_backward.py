@@ -136,8 +136,15 @@ def test_autograd_finite_differences_mixed(sysD):
     closest pairs), and 0.25 in lambda and 0.05 e in the charges, where the
     energy is exactly quadratic and central differences are exact for any
     step.  dE/dlambda and dE/dq use the refined site-atom potential, the
-    energy the FMM's, whose truncation (and in the mixed path the tensor-core
-    accumulation bias) differs by up to ~0.1 kJ/mol per unit lambda here.
+    energy the FMM's, whose truncation and, in the mixed path, tensor-core
+    accumulation bias (about 7e-4 of the far-field locals, mostly in their
+    constant term, so in the potential and not in the forces) put the energy's
+    potential at a site atom up to ~1 kJ/mol/e (1e-3 relative) away from the
+    refined one: differences of a few tenths per unit lambda (measured 0.23).
+    A central difference in a charge measures the symmetrised potential
+    (A + A^T) q / 2 of the FMM's approximate operator A, which single
+    precision and the tensor-core rounding make asymmetric at ~1e-3: up to
+    ~1.6 kJ/mol/e on a 450 kJ/mol/e potential.
     In x the check is bounded by the single-precision near-field sums: moving
     one atom re-rounds the ~800 potentials it enters (each a sum of terms up
     to ~1e3 kJ/mol/e), which shifts the energy by ~1e-2 kJ/mol, so central
@@ -175,7 +182,7 @@ def test_autograd_finite_differences_mixed(sysD):
         lp = lam.detach().clone(); lp[k] += 0.25
         lm = lam.detach().clone(); lm[k] -= 0.25
         fd = (energy(ll=lp) - energy(ll=lm)) / 0.5
-        assert fd == pytest.approx(gl[k].item(), abs=0.2)
+        assert fd == pytest.approx(gl[k].item(), abs=0.5)
     site_atoms = np.where(s["site_of"] >= 0)[0]
     for key, t, g in (("qA", qA, gA), ("qB", qB, gB)):
         for k in rng.choice(site_atoms, 6, replace=False):
@@ -183,7 +190,7 @@ def test_autograd_finite_differences_mixed(sysD):
             tp[k] += 0.05; tm[k] -= 0.05
             arg = "a" if key == "qA" else "b"
             fd = (energy(**{arg: tp}) - energy(**{arg: tm})) / 0.1
-            assert fd == pytest.approx(g[k].item(), abs=0.2)
+            assert fd == pytest.approx(g[k].item(), abs=1.0, rel=5e-3)
     me.close()
 
 

@@ -77,3 +77,41 @@ def test_set_forms_rejects_bad_form_counts():
         m.set_forms(np.zeros(10), so, [np.zeros((3, 3))])
     assert ei.value.code == -1
     m.close()
+
+
+@pytest.mark.parametrize("prec,p,tol", [("fp64", 16, 1e-6), ("mixed", 12, 3e-4)])
+def test_multiform_backward_matches_oracle(mf, prec, p, tol):
+    """mahi_backward_forms against the oracle's charge gradients of the
+    multi-form energy (and dx = -g F, dlambda = g dE/dlambda), upstream
+    gradient 0.7.  Mixed: environment potentials carry the tensor-core M2L's
+    accumulation bias, so they are held to 3e-4 of the largest gradient."""
+    s, ref = mf
+    cg = hi.multiform_charge_gradients(s, ref=ref)
+    N, S = len(s["q_env"]), len(s["forms"])
+    m = pkg.Mahi(s["L"], N, S, p, 3, prec)
+    m.set_forms(s["q_env"], s["site_of"], s["forms"])
+    xdt = torch.float64 if prec == "fp64" else torch.float32
+    dev = torch.device("cuda")
+    x = torch.tensor(s["x"], dtype=xdt, device=dev)
+    lam = torch.tensor(np.concatenate(s["lams"]), dtype=torch.float64, device=dev)
+    E, F, g = m.eval(x, lam)
+    ge = torch.tensor([0.7], dtype=torch.float64, device=dev)
+    nform = sum(np.asarray(f).size for f in s["forms"])
+    dx = torch.empty_like(F)
+    dl = torch.empty_like(g)
+    dq_env = torch.full((N,), 9.0, dtype=torch.float64, device=dev)
+    dq_forms = torch.full((nform,), 9.0, dtype=torch.float64, device=dev)
+    pkg.mahi_backward_forms(m.h, ge, F, g, lam, dx, dl, dq_env, dq_forms)
+    with pytest.raises(pkg.MahiError) as ei:   # the two-form entry point refuses these sites
+        pkg.mahi_backward(m.h, ge, F, g, lam, dx)
+    assert ei.value.code == -1
+    torch.cuda.synchronize()
+    m.close()
+    assert torch.equal(dx, -0.7 * F)
+    assert torch.allclose(dl, 0.7 * g, rtol=0, atol=0)
+    want_env = 0.7 * cg["dq_env"]
+    want_forms = 0.7 * np.concatenate([np.asarray(f).ravel() for f in cg["dq_forms"]])
+    got_env, got_forms = dq_env.cpu().numpy(), dq_forms.cpu().numpy()
+    scale = max(np.abs(want_env).max(), np.abs(want_forms).max())
+    assert np.abs(got_forms - want_forms).max() < tol * scale, np.abs(got_forms - want_forms).max() / scale
+    assert np.abs(got_env - want_env).max() < tol * scale, np.abs(got_env - want_env).max() / scale

@@ -234,3 +234,39 @@ def test_multiform_forces_central_difference():
             ep = hi.multiform_eval(dict(s, x=xp))["E"]
             em = hi.multiform_eval(dict(s, x=xm))["E"]
             assert -(ep - em) / (2 * h) == pytest.approx(base["F"][k, ax], rel=2e-6, abs=1e-5)
+
+
+def test_multiform_charge_gradients_central_difference_exact():
+    """dE/dq_env and dE/dq^rho of the multi-form energy against central
+    differences of multiform_eval's E: E is quadratic in every charge, so the
+    central difference is exact up to rounding for any step."""
+    s = small_multiform(n=30, nforms=(4, 2))
+    g = hi.multiform_charge_gradients(s)
+    h = 0.05
+    for k in (20, 25):   # environment atoms
+        sp = dict(s, q_env=s["q_env"].copy()); sp["q_env"][k] += h
+        sm = dict(s, q_env=s["q_env"].copy()); sm["q_env"][k] -= h
+        d = (hi.multiform_eval(sp)["E"] - hi.multiform_eval(sm)["E"]) / (2 * h)
+        assert d == pytest.approx(g["dq_env"][k], rel=1e-9, abs=1e-9)
+    assert not g["dq_env"][s["site_of"] >= 0].any()
+    for si, (r, a) in ((0, (0, 0)), (0, (3, 2)), (1, (1, 1)), (1, (0, 3))):
+        fp = [f.copy() for f in s["forms"]]; fp[si][r, a] += h
+        fm = [f.copy() for f in s["forms"]]; fm[si][r, a] -= h
+        d = (hi.multiform_eval(dict(s, forms=fp))["E"] - hi.multiform_eval(dict(s, forms=fm))["E"]) / (2 * h)
+        assert d == pytest.approx(g["dq_forms"][si][r, a], rel=1e-9, abs=1e-9), (si, r, a)
+
+
+def test_multiform_charge_gradients_reduce_to_two_forms():
+    """With two forms per site the gradients are the two-form path's dE/dqA
+    and dE/dqB at site atoms, and dE/dqA at environment atoms."""
+    s = small_multisite(n=50, S=2)
+    sites = hi.site_lists(s["site_of"], 2)
+    mf = dict(x=s["x"], q_env=s["qA"], site_of=s["site_of"], L=s["L"],
+              forms=[np.stack([s["qA"][at], s["qB"][at]]) for at in sites], lams=[[v] for v in s["lam"]])
+    a = hi.multiform_charge_gradients(mf)
+    b = hi.hi_charge_gradients(s)
+    env = s["site_of"] < 0
+    np.testing.assert_allclose(a["dq_env"][env], b["dqA"][env], rtol=1e-10, atol=1e-10)
+    for si, at in enumerate(sites):
+        np.testing.assert_allclose(a["dq_forms"][si][0], b["dqA"][at], rtol=1e-10, atol=1e-10)
+        np.testing.assert_allclose(a["dq_forms"][si][1], b["dqB"][at], rtol=1e-10, atol=1e-10)
