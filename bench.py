@@ -521,7 +521,8 @@ def run_replicas(args):
     tune = []
     for h, x, lam, out, N, S in reps:
         pkg.mahi_autotune(h, x, lam, 2)
-        tune.append(pkg.mahi_get_tuning(h))
+        tune.append(list(pkg.mahi_get_tuning(h)) + [int(pkg.mahi_get_option(h, "m2l_single_tile")),
+                                                     int(pkg.mahi_get_option(h, "m2l_b_stages"))])
     t_tuned = timed(eager)
     batch = pkg.MahiBatch([r[0] for r in reps], stream, [r[1] for r in reps], [r[2] for r in reps],
                           [r[3][0] for r in reps], [r[3][1] for r in reps], [r[3][2] for r in reps])
@@ -534,7 +535,7 @@ def run_replicas(args):
                       "precision": "mixed", "ms_per_step_eager": round(t_eager, 4),
                       "ms_per_step_tuned_eager": round(t_tuned, 4), "ms_per_step_graph": round(t_graph, 4),
                       "atoms_per_s_graph": round(n_atoms / (t_graph * 1e-3), 1),
-                      "tuning_p2p_threads_site_blocks": tune}), flush=True)
+                      "tuning_p2p_threads_site_blocks_m2l_single_m2l_stages": tune}), flush=True)
 
 
 def cpu_baseline(s, n_targets=8192, atom_frac=1 / 8):

@@ -214,13 +214,29 @@ int mahi_backward(mahi_t h, const double *grad_energy, const void *forces, const
  *       charge and dipole of the sources, which set the far-field energy of
  *       charged configurations: one product there gives 1.8e-4 relative energy
  *       error on the 3,000-charge random system, three give 1.6e-5.
+ * Launch shapes (results change only in the order of floating-point sums;
+ * mahi_autotune sets them):
+ *   MAHI_OPT_M2L_SINGLE_TILE  1: the tensor-core M2L uses single 128-row tiles
+ *       per unit even where two fit (more, smaller units: better balance on
+ *       small trees); 0: pairs where they fit (default).  Synchronises the
+ *       handle's stream when it changes.
+ *   MAHI_OPT_M2L_B_STAGES     operator stages of the tensor-core M2L: 2, 3 or 4
+ *       (at most what fits in shared memory); 0 = as many as fit (default).
+ *   MAHI_OPT_P2P_THREADS      threads per target leaf of the near field: 64,
+ *       128 or 256 (0 = 128, the default).
+ *   MAHI_OPT_SITE_BLOCKS      blocks per site of the site-atom traversal, 1 to
+ *       16 (0 = about 12 per SM over all sites, the default).
  * MAHI_ERR_INVALID_ARG for an unknown option or a value out of range. */
 enum {
   MAHI_OPT_SITE_THETA = 1,
   MAHI_OPT_SITE_LIST_CAP = 2,
   MAHI_OPT_WAIT_LIMIT_MS = 3,
   MAHI_OPT_WATCHDOG_SELFTEST = 4,
-  MAHI_OPT_M2L_SPLIT_DEGREE = 5
+  MAHI_OPT_M2L_SPLIT_DEGREE = 5,
+  MAHI_OPT_M2L_SINGLE_TILE = 6,
+  MAHI_OPT_M2L_B_STAGES = 7,
+  MAHI_OPT_P2P_THREADS = 8,
+  MAHI_OPT_SITE_BLOCKS = 9
 };
 int mahi_set_option(mahi_t h, int32_t option, double value);
 /* Current value of an option (the effective one for defaults). */
@@ -320,9 +336,10 @@ int mahi_site_terms_static(double box_L_nm, int64_t n_atoms, int32_t n_sites, co
  * Independent constant-pH replicas (each its own handle: box, atoms, sites,
  * lambdas) evaluated as ONE CUDA graph.  mahi_batch_create sets every handle's
  * stream to cuda_stream (which must not be the legacy NULL stream), runs one
- * ordinary evaluation per replica, then captures the n evaluations, in order,
- * into a graph with the given device buffers (arrays of n pointers, same
- * meaning as in mahi_eval).  mahi_batch_launch enqueues the graph on that
+ * ordinary evaluation per replica, then captures the n evaluations into a
+ * graph with the given device buffers (arrays of n pointers, same meaning as
+ * in mahi_eval), each replica on its own branch forked from and joined back
+ * into cuda_stream, so the replicas' kernels run side by side.  mahi_batch_launch enqueues the graph on that
  * stream (one host call for all replicas); results equal n mahi_eval calls.
  * The graph keeps the captured pointers: update positions and lambdas in place
  * between launches; changing charges or tuning needs a new batch.  The batch
@@ -336,12 +353,14 @@ int mahi_batch_launch(mahi_batch_t b);
 int mahi_batch_destroy(mahi_batch_t b);
 
 /* Launch-shape autotuner: times reps evaluations (outputs discarded) for each
- * candidate shape of the near-field kernel (64, 128 or 256 threads per target
- * leaf) and of the site-potential traversal (default blocks per site, half,
- * double) on the given input, keeps the fastest in the handle and returns;
- * synchronises the handle's stream.  Results change only in the order of
- * floating-point sums.  mahi_get_tuning reports the choice (site_blocks 0 =
- * the default count). */
+ * candidate shape on the given input and keeps the fastest in the handle:
+ * first the near-field kernel (64, 128 or 256 threads per target leaf) with
+ * the site-potential traversal (default blocks per site, half, double), then,
+ * for MAHI_MIXED, the tensor-core M2L's tiling (paired or single 128-row tiles)
+ * with its operator stage count (as many as fit, 3, 2).  Synchronises the
+ * handle's stream.  Results change only in the order of floating-point sums.
+ * mahi_get_tuning reports the first two choices (site_blocks 0 = the default
+ * count); mahi_get_option reports all of them (MAHI_OPT_M2L_SINGLE_TILE, ...). */
 int mahi_autotune(mahi_t h, const void *x, int32_t x_is_fp64, const double *lambda, int32_t reps);
 int mahi_get_tuning(mahi_t h, int32_t *p2p_threads, int32_t *site_blocks);
 

@@ -326,9 +326,14 @@ int mahi_create(double box_L_nm, int64_t n_atoms, int32_t n_sites, int32_t order
       if ((e = cudaMemcpy(h->tc_ops, img.data(), img.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
         return fail(e, "tc ops");
       std::vector<int> units;
+      // allocate the unit table for single tiles (the larger count), fill it for the default
+      h->tune_m2l_single = true;
       int r = tc_build_units(h, units);
+      h->tune_m2l_single = false;
       if (r != 0) { free_all(h); delete h; return MAHI_ERR_INVALID_ARG; }
       AL(h->tc_units, units.size() * sizeof(int));
+      r = tc_build_units(h, units);
+      if (r != 0) { free_all(h); delete h; return MAHI_ERR_INVALID_ARG; }
       if ((e = cudaMemcpy(h->tc_units, units.data(), units.size() * sizeof(int), cudaMemcpyHostToDevice)) !=
           cudaSuccess)
         return fail(e, "tc units");
@@ -566,6 +571,30 @@ int mahi_set_option(mahi_t h, int32_t option, double value) {
       if (value != std::floor(value) || value < -1.0 || value > h->p) return MAHI_ERR_INVALID_ARG;
       h->m2l_split_degree = (int)value;
       return MAHI_OK;
+    case MAHI_OPT_M2L_SINGLE_TILE: {
+      if (value != 0.0 && value != 1.0) return MAHI_ERR_INVALID_ARG;
+      const bool single = value != 0.0;
+      if (single == h->tune_m2l_single) return MAHI_OK;
+      h->tune_m2l_single = single;
+      if (h->tc_units) {
+        CK(cudaSetDevice(h->device));
+        CK(cudaStreamSynchronize(h->stream));   // the table may be in use by enqueued work
+        if (tc_upload_units(h) != 0) return cuda_fail(cudaGetLastError(), "M2L units");
+      }
+      return MAHI_OK;
+    }
+    case MAHI_OPT_M2L_B_STAGES:
+      if (value != 0.0 && value != 2.0 && value != 3.0 && value != 4.0) return MAHI_ERR_INVALID_ARG;
+      h->tune_m2l_nsb = (int)value;
+      return MAHI_OK;
+    case MAHI_OPT_P2P_THREADS:
+      if (value != 0.0 && value != 64.0 && value != 128.0 && value != 256.0) return MAHI_ERR_INVALID_ARG;
+      h->tune_p2p_threads = value == 0.0 ? 128 : (int)value;
+      return MAHI_OK;
+    case MAHI_OPT_SITE_BLOCKS:
+      if (value < 0.0 || value > kSiteChunksMax || value != std::floor(value)) return MAHI_ERR_INVALID_ARG;
+      h->tune_site_blocks = (int)value;
+      return MAHI_OK;
     default: return MAHI_ERR_INVALID_ARG;
   }
 }
@@ -578,6 +607,10 @@ double mahi_get_option(mahi_t h, int32_t option) {
     case MAHI_OPT_WAIT_LIMIT_MS: return (double)h->wait_limit_ns * 1e-6;
     case MAHI_OPT_WATCHDOG_SELFTEST: return h->watchdog_selftest;
     case MAHI_OPT_M2L_SPLIT_DEGREE: return h->m2l_split_degree;
+    case MAHI_OPT_M2L_SINGLE_TILE: return h->tune_m2l_single ? 1.0 : 0.0;
+    case MAHI_OPT_M2L_B_STAGES: return h->tune_m2l_nsb;
+    case MAHI_OPT_P2P_THREADS: return h->tune_p2p_threads;
+    case MAHI_OPT_SITE_BLOCKS: return h->tune_site_blocks;
     default: return -1.0;
   }
 }

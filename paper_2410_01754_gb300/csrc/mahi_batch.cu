@@ -4,9 +4,12 @@
 // own box, atoms, sites and lambdas).  mahi_batch_create records one MAHI
 // evaluation of every replica, back to back on one stream, into a CUDA graph;
 // mahi_batch_launch replays it with a single launch call, so the host cost of
-// the ~40 kernel launches per replica is paid once at capture.  The graph
-// keeps the pointers it was captured with: callers update positions and
-// lambdas in place between launches.
+// the ~40 kernel launches per replica is paid once at capture.  Each replica
+// is captured on its own branch stream, so the graph holds the replicas as
+// parallel branches and the GPU runs their kernels side by side (most of a
+// small replica's kernels fill a fraction of the SMs).  The graph keeps the
+// pointers it was captured with: callers update positions and lambdas in
+// place between launches.
 //
 // mahi_autotune times candidate launch shapes of the two kernels whose best
 // shape depends on the system (atoms per leaf, sites) on the caller's input
@@ -26,7 +29,21 @@ struct mahi_batch_ctx {
   cudaStream_t stream = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
+  std::vector<cudaStream_t> branch;     // one capture stream per replica: parallel graph branches
+  std::vector<cudaEvent_t> ev;          // fork event, then one join event per branch
 };
+
+namespace {
+void release(mahi_batch_ctx *b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  for (cudaStream_t s : b->branch)
+    if (s) cudaStreamDestroy(s);
+  for (cudaEvent_t e : b->ev)
+    if (e) cudaEventDestroy(e);
+  delete b;
+}
+}  // namespace
 
 namespace {
 int fail_cuda(cudaError_t e) { return e == cudaSuccess ? MAHI_OK : MAHI_ERR_CUDA; }
@@ -80,6 +97,41 @@ int mahi_autotune(mahi_t h, const void *x, int32_t x_is_fp64, const double *lamb
     }
   h->tune_p2p_threads = best_p;
   h->tune_site_blocks = best_g;
+  // then the tensor-core M2L's tiling with the shapes chosen above
+  if (rc == MAHI_OK && h->prec == MAHI_MIXED && h->d >= 1) {
+    const bool single0 = h->tune_m2l_single;
+    const int nsb0 = h->tune_m2l_nsb;
+    bool best_single = single0;
+    int best_nsb = nsb0;
+    float best_m = 1e30f;
+    const int nsbs[3] = {0, 3, 2};
+    for (int si = 0; si < 2 && rc == MAHI_OK; ++si) {
+      if (si == 1 && h->ld > 192) break;      // single tiles already (no pairs fit)
+      rc = mahi_set_option(h, MAHI_OPT_M2L_SINGLE_TILE, si);
+      for (int ni = 0; ni < 3 && rc == MAHI_OK; ++ni) {
+        h->tune_m2l_nsb = nsbs[ni];
+        rc = mahi_eval(h, x, x_is_fp64, lambda, nullptr, nullptr, nullptr);
+        if (rc != MAHI_OK) break;
+        if (cudaEventRecord(a, h->stream) != cudaSuccess) { rc = MAHI_ERR_CUDA; break; }
+        for (int r = 0; r < reps && rc == MAHI_OK; ++r) rc = mahi_eval(h, x, x_is_fp64, lambda, nullptr, nullptr, nullptr);
+        if (rc != MAHI_OK) break;
+        float ms = 0.f;
+        if (cudaEventRecord(b, h->stream) != cudaSuccess || cudaEventSynchronize(b) != cudaSuccess ||
+            cudaEventElapsedTime(&ms, a, b) != cudaSuccess) {
+          rc = MAHI_ERR_CUDA;
+          break;
+        }
+        if (ms < best_m) {
+          best_m = ms;
+          best_single = si == 1;
+          best_nsb = nsbs[ni];
+        }
+      }
+    }
+    const int rc2 = mahi_set_option(h, MAHI_OPT_M2L_SINGLE_TILE, best_single ? 1 : 0);
+    if (rc == MAHI_OK) rc = rc2;
+    h->tune_m2l_nsb = best_nsb;
+  }
   h->timing = timing;
   cudaEventDestroy(a);
   cudaEventDestroy(b);
@@ -111,6 +163,12 @@ int mahi_batch_create(const mahi_t *handles, int32_t n, void *cuda_stream, const
   b->h.assign(handles, handles + n);
   b->stream = st;
   int rc = MAHI_OK;
+  b->branch.assign(n, nullptr);
+  b->ev.assign(n + 1, nullptr);
+  for (int i = 0; i < n && rc == MAHI_OK; ++i)
+    rc = fail_cuda(cudaStreamCreateWithFlags(&b->branch[i], cudaStreamNonBlocking));
+  for (int i = 0; i <= n && rc == MAHI_OK; ++i)
+    rc = fail_cuda(cudaEventCreateWithFlags(&b->ev[i], cudaEventDisableTiming));
   // one eager evaluation per replica first: launch attributes are set outside capture
   for (int i = 0; i < n && rc == MAHI_OK; ++i) {
     handles[i]->stream = st;
@@ -119,8 +177,18 @@ int mahi_batch_create(const mahi_t *handles, int32_t n, void *cuda_stream, const
   if (rc == MAHI_OK) rc = fail_cuda(cudaStreamSynchronize(st));
   if (rc == MAHI_OK) rc = fail_cuda(cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
   if (rc == MAHI_OK) {
-    for (int i = 0; i < n && rc == MAHI_OK; ++i)
+    // the replicas are independent: each is captured on its own branch stream
+    // forked from (and joined back into) the batch stream, so the graph has n
+    // parallel branches and their small kernels run side by side
+    rc = fail_cuda(cudaEventRecord(b->ev[0], st));
+    for (int i = 0; i < n && rc == MAHI_OK; ++i) rc = fail_cuda(cudaStreamWaitEvent(b->branch[i], b->ev[0], 0));
+    for (int i = 0; i < n && rc == MAHI_OK; ++i) {
+      handles[i]->stream = b->branch[i];
       rc = mahi_eval(handles[i], x[i], x_is_fp64[i], lambda[i], energy[i], forces[i], dEdlambda[i]);
+      handles[i]->stream = st;
+      if (rc == MAHI_OK) rc = fail_cuda(cudaEventRecord(b->ev[i + 1], b->branch[i]));
+      if (rc == MAHI_OK) rc = fail_cuda(cudaStreamWaitEvent(st, b->ev[i + 1], 0));
+    }
     cudaGraph_t g = nullptr;
     const cudaError_t e = cudaStreamEndCapture(st, &g);
     if (rc == MAHI_OK && e != cudaSuccess) rc = MAHI_ERR_CUDA;
@@ -128,10 +196,9 @@ int mahi_batch_create(const mahi_t *handles, int32_t n, void *cuda_stream, const
   }
   if (rc == MAHI_OK) rc = fail_cuda(cudaGraphInstantiate(&b->exec, b->graph, 0));
   if (rc != MAHI_OK) {
-    if (b->exec) cudaGraphExecDestroy(b->exec);
-    if (b->graph) cudaGraphDestroy(b->graph);
+    for (int i = 0; i < n; ++i) handles[i]->stream = st;
     cudaGetLastError();
-    delete b;
+    release(b);
     return rc;
   }
   *out = b;
@@ -145,9 +212,7 @@ int mahi_batch_launch(mahi_batch_t b) {
 
 int mahi_batch_destroy(mahi_batch_t b) {
   if (!b) return MAHI_OK;
-  if (b->exec) cudaGraphExecDestroy(b->exec);
-  if (b->graph) cudaGraphDestroy(b->graph);
-  delete b;
+  release(b);
   return MAHI_OK;
 }
 

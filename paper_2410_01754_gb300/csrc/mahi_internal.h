@@ -157,6 +157,8 @@ struct mahi_ctx {
   int *status_dev = nullptr;                  // the same words as seen from the device
   int tune_p2p_threads = 128;                 // autotuned launch shapes (mahi_autotune)
   int tune_site_blocks = 0;                   // 0 = default count of blocks per site
+  bool tune_m2l_single = false;               // tensor-core M2L: single 128-row tiles where pairs would fit
+  int tune_m2l_nsb = 0;                       // tensor-core M2L operator stages (0 = as many as fit)
   int *m2l_list = nullptr;                    // [8][189] offset ids
   int *m2l_off = nullptr;                     // [316][3]
   int *site_ptr = nullptr, *site_atoms = nullptr;
@@ -204,5 +206,6 @@ int num_stages();
 size_t tc_ops_bytes(int p);
 void tc_pack_ops(int p, const std::vector<std::vector<double>> &m2l, void *host_image);
 int tc_build_units(mahi_ctx *h, std::vector<int> &units);
+int tc_upload_units(mahi_ctx *h);
 int tc_m2l(mahi_ctx *h);
 }  // namespace mahi

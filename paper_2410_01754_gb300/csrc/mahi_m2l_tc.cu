@@ -837,12 +837,13 @@ void tc_pack_ops(int p, const std::vector<std::vector<double>> &m2l, void *host_
     }
 }
 
-// two accumulators of Kp columns fit below the A stages only for Kp <= 192
-static inline bool tc_paired(int ld) { return ld <= (int)tc::kAcc1; }
+// two accumulators of Kp columns fit below the A stages only for Kp <= 192;
+// the launch-shape tuning may also choose single tiles there
+static inline bool tc_paired(const mahi_ctx *h) { return h->ld <= (int)tc::kAcc1 && !h->tune_m2l_single; }
 
 int tc_build_units(mahi_ctx *h, std::vector<int> &units) {
   if (h->ld > tc::kMaxN || h->ld % tc::kKC) return -1;
-  const int step = (tc_paired(h->ld) ? 2 : 1) * tc::kRows;
+  const int step = (tc_paired(h) ? 2 : 1) * tc::kRows;
   // targets of one child class over all levels 1..d, in the merged row order
   int rows = 0;
   for (int l = 1; l <= h->d; ++l) rows += 1 << (3 * (l - 1));
@@ -856,6 +857,16 @@ int tc_build_units(mahi_ctx *h, std::vector<int> &units) {
     }
   h->tc_nunits = (int)units.size() / 4;
   return 0;
+}
+
+// rebuild the unit table after a change of the tile choice (the device table
+// was allocated for the single-tile count, the larger one)
+int tc_upload_units(mahi_ctx *h) {
+  std::vector<int> units;
+  if (tc_build_units(h, units) != 0) return -1;
+  return cudaMemcpy(h->tc_units, units.data(), units.size() * sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess
+             ? 0
+             : -1;
 }
 
 // dynamic shared memory of k_m2l_tc with nsb operator stages
@@ -893,10 +904,11 @@ int tc_m2l(mahi_ctx *h) {
   prm.ngrp = (prm.nvc + tc::kKPI - 1) / tc::kKPI;
   prm.ngroups = h->ld / 8;
   prm.nunits = h->tc_nunits;
-  prm.paired = tc_paired(h->ld) ? 1 : 0;
-  // as many operator stages as fit (4 at p <= 12, 3 at p = 15)
+  prm.paired = tc_paired(h) ? 1 : 0;
+  // as many operator stages as fit (4 at p <= 12, 3 at p = 15), or the tuned count
   prm.nsb = tc::kStagesB;
   while (prm.nsb > 2 && tc_smem_bytes(prm.ngroups, prm.nsb) > 227 * 1024) --prm.nsb;
+  if (h->tune_m2l_nsb >= 2 && h->tune_m2l_nsb < prm.nsb) prm.nsb = h->tune_m2l_nsb;
   const size_t sm = tc_smem_bytes(prm.ngroups, prm.nsb);
   if (sm > 227 * 1024) return -1;
   if (cudaFuncSetAttribute(k_m2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess) return -1;

@@ -96,10 +96,15 @@ def test_autotune_keeps_results():
     pkg.mahi_autotune(m.h, x, lam, 2)
     p2p, blocks = pkg.mahi_get_tuning(m.h)
     assert p2p in (64, 128, 256) and blocks in range(0, 17)
+    assert m.get_option("p2p_threads") == p2p and m.get_option("site_blocks") == blocks
+    assert m.get_option("m2l_single_tile") in (0, 1) and m.get_option("m2l_b_stages") in (0, 2, 3)
     E1, F1, g1 = m.eval(x, lam)
     torch.cuda.synchronize()
     m.close()
     a, b = F0.double().cpu().numpy(), F1.double().cpu().numpy()
+    # the M2L's tile choice changes which rows share an accumulator's rounding
+    # history only through the order of the items (the same per unit), so the
+    # results move at the single-precision rounding level
     assert np.sqrt(((a - b) ** 2).sum() / (a ** 2).sum()) < 1e-6
-    assert abs(E0.item() - E1.item()) < 1e-9 * abs(E0.item())
+    assert abs(E0.item() - E1.item()) < 1e-8 * abs(E0.item())
     assert np.abs(g0.cpu().numpy() - g1.cpu().numpy()).max() < 1e-6

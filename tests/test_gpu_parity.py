@@ -125,6 +125,20 @@ def test_tensor_core_m2l_matches_fp64_path(sysB, p, split):
     assert np.abs(a["dEdl"] - b["dEdl"]).max() < 1e-3
 
 
+@pytest.mark.parametrize("single,nsb", [(1, 0), (0, 2), (1, 3)])
+def test_tensor_core_m2l_tilings(sysB, single, nsb):
+    """The autotuner's M2L shapes: single 128-row tiles where pairs would fit
+    (twice the units), and fewer operator stages in shared memory, against the
+    FP64 path (p = 12, depth 4)."""
+    s, _ = sysB
+    a = run_gpu(s, "fp64", p=12)
+    b = run_gpu(s, "mixed", p=12, options={"m2l_single_tile": single, "m2l_b_stages": nsb})
+    rel = np.sqrt(((a["F"] - b["F"]) ** 2).sum() / (a["F"] ** 2).sum())
+    assert rel < 2e-5, rel
+    assert abs(a["E"] - b["E"]) / abs(a["E"]) < 3e-6
+    assert np.abs(a["dEdl"] - b["dEdl"]).max() < 1e-3
+
+
 def test_tensor_core_m2l_full_units():
     """Depth 5: each child class holds 4,681 targets over levels 1-5, merged
     into 19 units of two 128-row tiles, so 152 units: one whole unit per SM."""
