@@ -62,10 +62,11 @@ enum {
 /* Device-side failures.  Two conditions are detected inside the kernels of an
  * evaluation and recorded in a status word of the handle (host-mapped memory,
  * written by the device only on failure):
- *   MAHI_ERR_TIMEOUT        a bounded wait of the tensor-core M2L gave up (the
- *                           kernel then drains its copies, frees its tensor
- *                           memory and returns; the local expansions of that
- *                           evaluation are incomplete);
+ *   MAHI_ERR_TIMEOUT        a bounded wait of the tensor-core M2L or of the
+ *                           site-atom potential gave up (the kernel then
+ *                           drains its copies, frees its tensor memory and
+ *                           returns; the local expansions or site potentials
+ *                           of that evaluation are incomplete);
  *   MAHI_ERR_SITE_OVERFLOW  the separation-controlled traversal of a site (the
  *                           refined site-atom potential) had more boxes at one
  *                           level than its list capacity (MAHI_OPT_SITE_LIST_CAP);
@@ -191,11 +192,12 @@ int mahi_backward(mahi_t h, const double *grad_energy, const void *forces, const
  *       theta(p) = 0.4^(13/(p+1)) clamped to [0.25, 0.4]: the truncation bound
  *       of p = 12 at theta = 0.4 held at orders 8 and up.  Range (0, 0.7].
  *   MAHI_OPT_SITE_LIST_CAP  boxes per level of one site's traversal (list
- *       capacity, 64 to 12288).  Default: 1536 at theta >= 0.4, else grown
+ *       capacity, 64 to 8192).  Default: 1536 at theta >= 0.4, else grown
  *       with the number of boxes a theta-ball holds.  A site that needs more
  *       fails with MAHI_ERR_SITE_OVERFLOW.
  *   MAHI_OPT_WAIT_LIMIT_MS  limit of every bounded device wait of the
- *       tensor-core M2L (default 2000 ms, range 1 to 60000).
+ *       tensor-core M2L and the site-atom potential (default 2000 ms, range 1
+ *       to 60000).
  *   MAHI_OPT_WATCHDOG_SELFTEST  1: every following evaluation's tensor-core
  *       M2L makes its first wait on a barrier that nothing completes, so that
  *       the wait runs out after the wait limit and the evaluation reports

@@ -67,7 +67,7 @@ static void free_all(mahi_ctx *h) {
                   h->m2l_list, h->m2l_off, h->site_ptr, h->site_atoms,
                   h->energy_part, h->site_energy, h->tc_ops, h->tc_partial, h->tc_msrc, h->tc_level_off, h->tc_units, h->d_x_stage,
                   h->d_lam_stage, h->d_E_stage, h->d_dEdl_stage, h->d_F_stage, h->ops_lat_h3, h->L_h3,
-                  h->box_qd, h->vtmp, h->relD, h->phi_site, h->psi_site, h->site_pairs, h->site_slot, h->mf_q, h->mf_lam_off, h->phi_part, h->d_level_off, h->mf_psi, h->mf_form_off};
+                  h->box_qd, h->box_qdf, h->vtmp, h->relD, h->phi_site, h->psi_site, h->site_pairs, h->site_slot, h->mf_q, h->mf_lam_off, h->phi_part, h->d_level_off, h->mf_psi, h->mf_form_off};
   for (void *b : bufs)
     if (b) cudaFree(b);
   if (h->status_host) cudaFreeHost(h->status_host);
@@ -291,6 +291,7 @@ int mahi_create(double box_L_nm, int64_t n_atoms, int32_t n_sites, int32_t order
     h->m2l_split_degree = default_m2l_split_degree(order_p);
     h->site_list_cap = default_site_list_cap(h->site_theta);
     AL(h->box_qd, sizeof(double) * 8 * h->nbox_total);
+    AL(h->box_qdf, sizeof(float) * 8 * h->nbox_total);
     AL(h->d_level_off, sizeof(int64_t) * (kMaxDepth + 2));
     if ((e = cudaMemcpy(h->d_level_off, h->level_off, sizeof(int64_t) * (kMaxDepth + 2), cudaMemcpyHostToDevice)) !=
         cudaSuccess)
@@ -506,7 +507,7 @@ int mahi_n_lambdas(mahi_t h) { return h ? (h->multiform ? h->n_lam : h->S) : MAH
 static int take_status(mahi_t h) {
   volatile int *st = h->status_host;
   int rc = MAHI_OK;
-  if (st[kStatusM2LTimeout]) rc = MAHI_ERR_TIMEOUT;
+  if (st[kStatusM2LTimeout] || st[kStatusSiteTimeout]) rc = MAHI_ERR_TIMEOUT;
   else if (st[kStatusSiteOverflow]) rc = MAHI_ERR_SITE_OVERFLOW;
   if (rc != MAHI_OK)
     for (int i = 0; i < kStatusWords; ++i) st[i] = 0;

@@ -35,13 +35,14 @@ int cuda_fail(cudaError_t e, const char *what);
 // Slots of the per-handle device status word (host-mapped, set by kernels on failure).
 constexpr int kStatusM2LTimeout = 0;   // a bounded wait of the tensor-core M2L gave up
 constexpr int kStatusSiteOverflow = 1; // a site traversal list outgrew its capacity
+constexpr int kStatusSiteTimeout = 2;  // a bounded wait of the site-atom potential gave up
 constexpr int kStatusWords = 4;
 // Default separation ratio of the site-atom traversal at order p (truncation
 // bound theta^(p+1) of p = 12, theta = 0.4 kept at every order, within [0.25, 0.4])
 float default_site_theta(int p);
 // Default list capacity of the site traversal for a separation ratio theta
 int default_site_list_cap(float theta);
-constexpr int kSiteListCapMax = 12288;
+constexpr int kSiteListCapMax = 8192;
 // Default input degree up to which the tensor-core M2L uses three TF32 products
 // (above it one product; -1: one product for every degree): 2, i.e. the first
 // two K chunks (coefficients 0..15)
@@ -130,6 +131,7 @@ struct mahi_ctx {
   double *ops_lat_h3 = nullptr;               // FP64 H_3 part alone (site-atom path)
   double *L_h3 = nullptr;                     // root local of H_3 (K doubles)
   double *box_qd = nullptr;                   // FP64 Q, D, T per box (8 doubles), all levels
+  float *box_qdf = nullptr;                   // Q, D per box as (hi, lo) float pairs (8 floats), all levels
   double *phi_site = nullptr;                 // refined potential at site atoms
   double *psi_site = nullptr;                 // f sum_j A_ij D_j at site atoms (charge gradients)
   double *site_pairs = nullptr;               // [S][kSiteSymPairs][4]: grad A, A of every site pair

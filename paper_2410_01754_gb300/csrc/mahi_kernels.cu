@@ -13,10 +13,12 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
 #include <cmath>
 #include <cstdio>
 
 #include "mahi_internal.h"
+#include "mahi_sync.h"
 
 namespace mahi {
 
@@ -168,6 +170,7 @@ __device__ __forceinline__ int ridx(int l, int m) { return m == 0 ? l * l : l * 
 // ---------------------------------------------------------------------------
 constexpr int kMaxSide = 1 << kMaxDepth;  // leaves along one edge
 constexpr int kQD = 8;                    // doubles per box in box_qd: Q, Dx, Dy, Dz, T, pad
+constexpr int kQDF = 8;                   // floats per box in box_qdf: Q, Dx, Dy, Dz as (hi, lo)
 
 // wrapped coordinate in [0, L); the in-box test is exact: Lf_up is the
 // smallest float >= L, so x < Lf_up <=> x < L for a float x
@@ -318,9 +321,20 @@ __global__ void k_leaf_sort(int nleaf, const int *__restrict__ leaf_start, const
 // kernel.  One thread per leaf: FP64 issues at a small fraction of the FP32
 // rate on GB300, and a warp-wide FP64 reduction per leaf would cost far more
 // instructions than the sums themselves.
+// Q and D as (hi, lo) float pairs beside the FP64 row: the site-atom
+// potential forms its charge/dipole terms in double-float
+__device__ __forceinline__ void qd_split(const double *v, float *f) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const float hi = (float)v[k];
+    f[2 * k] = hi;
+    f[2 * k + 1] = (float)(v[k] - (double)hi);
+  }
+}
+
 __global__ void k_leaf_moments(int nleaf, const int *__restrict__ leaf_start, const int *__restrict__ perm,
                                const double *__restrict__ qt, const double *__restrict__ relD,
-                               double *__restrict__ qd) {
+                               double *__restrict__ qd, float *__restrict__ qdf) {
   const int leaf = blockIdx.x * blockDim.x + threadIdx.x;
   if (leaf >= nleaf) return;
   const int b = leaf_start[leaf], e = leaf_start[leaf + 1];
@@ -337,6 +351,7 @@ __global__ void k_leaf_moments(int nleaf, const int *__restrict__ leaf_start, co
   }
 #pragma unroll
   for (int k = 0; k < 5; ++k) qd[(size_t)leaf * kQD + k] = v[k];
+  qd_split(v, qdf + (size_t)leaf * kQDF);
 }
 
 // ---------------------------------------------------------------------------
@@ -1480,7 +1495,8 @@ __global__ void __launch_bounds__(32) k_site_mf(int S, double L, double fcoul, i
 //    o_c = child centre - parent centre.  The root's values are the moments
 //    of the whole box about its centre used by the dipole / background term.
 // ---------------------------------------------------------------------------
-__global__ void k_qd_up(int nparent, double s_child, const double *__restrict__ child, double *__restrict__ parent) {
+__global__ void k_qd_up(int nparent, double s_child, const double *__restrict__ child, double *__restrict__ parent,
+                        float *__restrict__ parent_f) {
   int P = blockIdx.x * blockDim.x + threadIdx.x;
   if (P >= nparent) return;
   double v[5] = {0, 0, 0, 0, 0};
@@ -1494,6 +1510,7 @@ __global__ void k_qd_up(int nparent, double s_child, const double *__restrict__ 
     for (int k = 0; k < 3; ++k) v[1 + k] += ch[1 + k] + ch[0] * off[k];
   }
   for (int k = 0; k < 5; ++k) parent[(size_t)P * kQD + k] = v[k];
+  qd_split(v, parent_f + (size_t)P * kQDF);
 }
 
 // ---------------------------------------------------------------------------
@@ -1546,8 +1563,18 @@ __device__ __forceinline__ T m2p_high(int P, const T *__restrict__ M, T ux, T uy
 // The batches of separated boxes and leaves are dealt round-robin to G blocks
 // per site; each block repeats the (cheap) classification and writes its own
 // partial sum, so results are bitwise reproducible.
+//
+// Pipeline.  A block's batches form one stream over all levels; the multipole
+// rows and FP64 charge/dipole rows of the next batch are copied (cp.async)
+// into the second of two buffers while the current batch is evaluated, and a
+// level is classified when the stream first reaches it (its list goes to the
+// one of two list buffers that the level two above had used).  Without the
+// overlap, each batch waited a full memory round trip before any arithmetic.
 constexpr int kSiteThreads = 128;
 constexpr int kSiteBatchMax = 64;
+// dynamic shared memory of one block (lists + two batch buffers): with the
+// static arrays three blocks fit on an SM
+constexpr size_t kSiteSmemBudget = 64 * 1024;
 
 __device__ __forceinline__ int pack_entry(int box, int img) { return (box << 9) | img; }
 
@@ -1579,6 +1606,42 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
   s = a + b;
   const float bv = s - a;
   e = (a - (s - bv)) + (b - bv);
+}
+
+// double-float values h + l (|l| <= ulp(h) / 2 after normalisation), from
+// the error-free transforms: Dekker's product by one FMA, Knuth's sum
+struct DF {
+  float h, l;
+};
+__device__ __forceinline__ DF df_norm(float h, float l) {
+  const float s = h + l;
+  return DF{s, l - (s - h)};
+}
+__device__ __forceinline__ DF df_from(float a) { return DF{a, 0.f}; }
+__device__ __forceinline__ DF df_neg(DF a) { return DF{-a.h, -a.l}; }
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+  float s, e;
+  two_sum(a.h, b.h, s, e);
+  return df_norm(s, e + (a.l + b.l));
+}
+__device__ __forceinline__ DF df_mul(DF a, DF b) {
+  const float p = a.h * b.h;
+  return df_norm(p, fmaf(a.h, b.h, -p) + fmaf(a.h, b.l, a.l * b.h));
+}
+__device__ __forceinline__ DF df_sq(DF a) {
+  const float p = a.h * a.h;
+  return df_norm(p, fmaf(a.h, a.h, -p) + 2.f * a.h * a.l);
+}
+// 1 / sqrt(a) for a > 0: the hardware estimate y and one Newton-Raphson step
+// whose residual 1 - a y^2 is formed in double-float; the step's relative
+// error is about 1.5 e^2 for the estimate's e (2^-22): near 2^-44
+__device__ __forceinline__ DF df_rsqrt(DF a) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(a.h));
+  const float yy = y * y;
+  const DF t = df_mul(a, DF{yy, fmaf(y, y, -yy)});
+  const float r = (1.f - t.h) - t.l;  // 1 - t.h is exact (t.h within 2^-20 of 1)
+  return df_norm(y, 0.5f * y * r);
 }
 
 // running sum in double-float (single precision) or plain FP64
@@ -1617,8 +1680,8 @@ __device__ __forceinline__ void split_offset(float x, int g, float slh, float sl
   ml = (ml - oe) - gf * sll;
 }
 
-__device__ __forceinline__ SiteTarget<float> site_target(float x, float y, float z, int gx, int gy, int gz, double sl) {
-  const float slh = (float)sl, sll = (float)(sl - (double)slh);
+__device__ __forceinline__ SiteTarget<float> site_target(float x, float y, float z, int gx, int gy, int gz, float slh,
+                                                         float sll) {
   SiteTarget<float> t;
   split_offset(x, gx, slh, sll, t.hx, t.lx);
   split_offset(y, gy, slh, sll, t.hy, t.ly);
@@ -1725,26 +1788,48 @@ __global__ void __launch_bounds__(kSiteThreads, 3) k_site_phi(
     int S, int G, const int *__restrict__ site_ptr, const int *__restrict__ site_atoms, int d, int P, int ld,
     int lds, int nbmax, double L, const int64_t *__restrict__ level_off, const int *__restrict__ leaf_start,
     const int *__restrict__ inv_perm, const typename V4<T>::type *__restrict__ part, const T *__restrict__ M,
-    const double *__restrict__ qd, const double *__restrict__ mom, const double *__restrict__ Lh3,
-    double *__restrict__ phi_part, int *__restrict__ err, float theta, int fcap) {
+    const double *__restrict__ qd, const float *__restrict__ qdf, const double *__restrict__ mom,
+    const double *__restrict__ Lh3, double *__restrict__ phi_part, int *__restrict__ status, float theta, int fcap,
+    uint64_t wait_ns) {
   using V = typename V4<T>::type;
+  // charge/dipole rows as staged: (hi, lo) float pairs in single precision,
+  // FP64 otherwise; 32 bytes either way
+  constexpr bool kDF = std::is_same<T, float>::value;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   int *fa = reinterpret_cast<int *>(smem_raw);          // frontier (current)
   int *fb = fa + fcap;                                  // frontier (next)
-  int *sep = fb + fcap;                                 // separated boxes / direct leaves of this level
-  T *Ms = reinterpret_cast<T *>(sep + fcap);            // [nbmax][lds] staged multipole rows
+  int *sep0 = fb + fcap;                                // separated boxes / direct leaves, even levels
+  int *sep1 = sep0 + fcap;                              // the same, odd levels
+  T *Ms = reinterpret_cast<T *>(sep1 + fcap);           // [2][nbmax][lds] staged multipole rows
+  double *qds = reinterpret_cast<double *>(Ms + (size_t)2 * nbmax * lds);  // [2][nbmax][32 B] Q, Dx, Dy, Dz
+  // levels 0 and 1 (the root and its 8 children, which every site's first
+  // batches refer to over and over through their images) stay resident: rows
+  // [0] root, [1 + box] level 1
+  const int nres = (d >= 1) ? 9 : 1;
+  T *Mres = reinterpret_cast<T *>(qds + (size_t)2 * nbmax * 4);  // [nres][lds]
+  double *qres = reinterpret_cast<double *>(Mres + (size_t)nres * lds);  // [nres][32 B]
   __shared__ double pa[kMaxSiteAtoms][3], cen[4], base_s[kSiteBatchMax], res_s[kSiteThreads][2];
   __shared__ T pu[kMaxSiteAtoms][3], puu[kMaxSiteAtoms];
   __shared__ T rw[kSiteBatchMax][3], rp[kSiteBatchMax][3], rQ[kSiteBatchMax], rB[kSiteBatchMax],
       rBi[kSiteBatchMax], rpw[kSiteBatchMax];
   __shared__ V me[kMaxSiteAtoms];
-  __shared__ int sa_s[kMaxSiteAtoms], aI[kMaxSiteAtoms][3], brow_s[kSiteBatchMax], bimg[kSiteBatchMax], wsum[64];
+  __shared__ int sa_s[kMaxSiteAtoms], aI[kMaxSiteAtoms][3], ent_s[2][kSiteBatchMax], wsum[64];
+  __shared__ int64_t lvo[kMaxDepth + 2];  // level offsets (rows)
+  __shared__ uint64_t sbar[2];            // copies of batch buffer 0 / 1 complete
+  __shared__ int s_abort;
   const int site = blockIdx.x / G, g = blockIdx.x % G, tid = threadIdx.x;
   if (site >= S) return;
   const int b0 = site_ptr[site], n = site_ptr[site + 1] - b0;
   if (n <= 0 || n > kMaxSiteAtoms) return;  // rejected when the site map is set
   const int nb = 1 << d;
   const double sl = L / nb;
+  if (tid <= d + 1) lvo[tid] = level_off[tid];
+  if (tid == 0) {
+    mbar_init(&sbar[0], 1);
+    mbar_init(&sbar[1], 1);
+    s_abort = 0;
+    fence_mbar_init();
+  }
   for (int a = tid; a < n; a += blockDim.x) {
     const int i = site_atoms[b0 + a], sa = inv_perm[i];
     int lo = 0, hi = (1 << (3 * d)) - 1;  // leaf of sorted position sa
@@ -1773,6 +1858,23 @@ __global__ void __launch_bounds__(kSiteThreads, 3) k_site_phi(
     }
   }
   __syncthreads();
+  {
+    constexpr int EPV = 16 / sizeof(T);
+    const int per_row = ld / EPV;
+    for (int q = tid; q < nres * per_row; q += blockDim.x) {
+      const int r = q / per_row, c = q - r * per_row;
+      const int64_t row = (r == 0) ? level_off[0] : level_off[1] + (r - 1);
+      if (P >= 2) cpa16(Mres + (size_t)r * lds + c * EPV, M + (size_t)row * ld + c * EPV);
+    }
+    for (int q = tid; q < 2 * nres; q += blockDim.x) {
+      const int r = q >> 1;
+      const int64_t row = (r == 0) ? level_off[0] : level_off[1] + (r - 1);
+      if (kDF) cpa16(qres + (size_t)r * 4 + (q & 1) * 2, qdf + (size_t)row * kQDF + (q & 1) * 4);
+      else cpa16(qres + (size_t)r * 4 + (q & 1) * 2, qd + (size_t)row * kQD + (q & 1) * 2);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+  }
   // A compact site (radius at most two leaf edges, the usual case: the atoms
   // of one residue) shares one traversal between its atoms; a spread site (its
   // atoms scattered over the box) would have to open nearly every box near
@@ -1793,6 +1895,10 @@ __global__ void __launch_bounds__(kSiteThreads, 3) k_site_phi(
   __syncthreads();
   const bool spread = cen[3] > 2.0 * sl;
   const int ngroups = spread ? n : 1;
+  // phase parity of the next completion of sbar[0] / sbar[1] (the barriers
+  // run on over the groups)
+  uint32_t ph0 = 0, ph1 = 0;
+  bool timed_out = false;  // a wait ran out: the remaining groups are skipped
   for (int grp = 0; grp < ngroups; ++grp) {
   const int ga = spread ? grp : 0, gn = spread ? 1 : n;   // atoms ga .. ga + gn - 1 of the site
   __syncthreads();
@@ -1806,7 +1912,7 @@ __global__ void __launch_bounds__(kSiteThreads, 3) k_site_phi(
     puu[a] = (T)(ux * ux + uy * uy + uz * uz);
   }
   for (int t = tid; t < 343 && t < fcap; t += blockDim.x) fa[t] = pack_entry(0, t);  // root images
-  if (fcap < 343 && tid == 0) *(volatile int *)err = 1;  // capacity below the root images
+  if (fcap < 343 && tid == 0) *(volatile int *)(status + kStatusSiteOverflow) = 1;  // capacity below the root images
   __syncthreads();
   // thread -> (atom pair, slot), fixed for the whole traversal; a slot takes
   // the rows slot, slot + nslot, ... of every batch
@@ -1814,18 +1920,31 @@ __global__ void __launch_bounds__(kSiteThreads, 3) k_site_phi(
   const int my_p = (tid < nslot * npair) ? tid % npair : -1, my_s = tid / npair;
   const int a0 = ga + (my_p < 0 ? 0 : my_p), a1 = ga + ((my_p >= 0 && my_p + npair < gn) ? my_p + npair : (my_p < 0 ? 0 : my_p));
   const int nbatch = (nslot <= nbmax) ? nslot * (nbmax / nslot) : nbmax;
+  const int lane = tid & 31, warp = tid >> 5;
   SiteAcc<T> acc0, acc1;
-  double base = 0.0;  // FP64 charge + dipole values at c of the rows this thread stages
+  double base = 0.0;          // charge + dipole values at c of the rows this thread takes (FP64)
+  DF base_df = df_from(0.f);  // the same in double-float
+  // L and c as (hi, lo) float pairs for the double-float terms
+  const DF Lsp = df_norm((float)L, (float)(L - (double)(float)L));
+  const T iLt = (T)(1.0 / L);
+  const float slh = (float)sl, sll = (float)(sl - (double)slh);  // leaf edge, double-float
+  const DF csp[3] = {df_norm((float)cen[0], (float)(cen[0] - (double)(float)cen[0])),
+                     df_norm((float)cen[1], (float)(cen[1] - (double)(float)cen[1])),
+                     df_norm((float)cen[2], (float)(cen[2] - (double)(float)cen[2]))};
   int n0 = min(343, fcap), bc = 0, scan_par = 0;
+  int ns0 = 0, ns1 = 0;  // entries in the lists of the last even / odd level classified
+  int lcl = -1;          // deepest level classified
   const T Rf = (T)cen[3];
   // the separation test runs in single precision (its 1e-4 safety margin is far
   // above the rounding of box centres at |x| < 4L); every block of a site
   // evaluates it identically
   const float cfx = (float)cen[0], cfy = (float)cen[1], cfz = (float)cen[2], Lf = (float)L;
-  for (int l = 0; l <= d && n0 > 0; ++l) {
-    const double s = L / (double)(1 << l);
-    const T a_l = (T)(0.86602540378443865 * s), th = (T)theta, is = (T)(1.0 / s);
-    const float sf = (float)s;
+  // level l: the frontier fa[0, n0) becomes the list of separated boxes and
+  // direct leaves (sep0 / sep1 by the parity of l) and the children of the
+  // opened boxes, the next frontier
+  auto classify = [&](int l) {
+    int *sep = (l & 1) ? sep1 : sep0;
+    const float sf = ldexpf(Lf, -l), a_l = 0.86602540378443865f * sf, th = theta;
     int nsep = 0, n1 = 0;
     for (int t0 = 0; t0 < n0; t0 += blockDim.x) {
       const int t = t0 + tid;
@@ -1839,7 +1958,7 @@ __global__ void __launch_bounds__(kSiteThreads, 3) k_site_phi(
                     dy = cfy - (((float)d_compact(box >> 1) + 0.5f) * sf + (float)ny * Lf),
                     dz = cfz - (((float)d_compact(box >> 2) + 0.5f) * sf + (float)nz * Lf);
         const float D = sqrtf(dx * dx + dy * dy + dz * dz);
-        if ((float)a_l < (float)th * (D - (float)Rf) * 0.9999f) kind = 0;
+        if (a_l < th * (D - (float)Rf) * 0.9999f) kind = 0;
         else if (l == d) kind = 1;
         else kind = 2;
       }
@@ -1862,27 +1981,144 @@ __global__ void __launch_bounds__(kSiteThreads, 3) k_site_phi(
     if (nsep > fcap || n1 > fcap) {
       // list capacity exceeded: recorded in the handle's status word; the
       // traversal goes on with the entries that fit (all accesses stay in bounds)
-      if (tid == 0) *(volatile int *)err = 1;
+      if (tid == 0) *(volatile int *)(status + kStatusSiteOverflow) = 1;
       nsep = min(nsep, fcap);
       n1 = min(n1, fcap);
     }
     __syncthreads();
-    for (int b = 0; b < nsep; b += nbatch, ++bc) {
-      if (bc % G != g) continue;  // batch dealt to another block of this site
-      const int nbx = min(nbatch, nsep - b);
-      if (tid < nbx) {
-        const int e = sep[b + tid] & 0x7fffffff, box = e >> 9, img = e & 511;
+    for (int t = tid; t < n1; t += blockDim.x) fa[t] = fb[t];
+    n0 = (l < d) ? n1 : 0;
+    if (l & 1) ns1 = nsep; else ns0 = nsep;
+    lcl = l;
+    __syncthreads();
+  };
+  // the next batch of this block at or after (level gl, entry gb): level,
+  // first entry and size; classifies a level on first use; false once the
+  // traversal is exhausted (uniform over the block)
+  int gl = 0, gb = 0;
+  auto next_batch = [&](int &bl, int &bb, int &bn) -> bool {
+    for (;;) {
+      if (gl > d) return false;
+      if (gl > lcl) {
+        if (n0 <= 0) {
+          gl = d + 1;
+          return false;
+        }
+        classify(gl);
+      }
+      const int nl = (gl & 1) ? ns1 : ns0;
+      if (gb < nl) {
+        const bool mine = (bc % G) == g;
+        ++bc;
+        bb = gb;
+        gb += nbatch;
+        if (mine) {
+          bl = gl;
+          bn = min(nbatch, nl - bb);
+          return true;
+        }
+      } else {
+        ++gl;
+        gb = 0;
+      }
+    }
+  };
+  // copies of one batch into buffer `buf` by warp 0: its entries, and (one
+  // bulk copy per row, completing on sbar[buf]) the charge/dipole rows and
+  // multipole rows of its separated boxes; levels 0 and 1 are resident
+  const uint32_t qrow_bytes = 32, mrow_bytes = (P >= 2) ? (uint32_t)(ld * sizeof(T)) : 0u;
+  auto stage = [&](int buf, int bl, int bb, int bn) {
+    if (warp != 0) return;
+    const int *sp = ((bl & 1) ? sep1 : sep0) + bb;
+    const bool res = bl <= 1;
+    const int r0 = lane, r1 = lane + 32;
+    const int e0 = (r0 < bn) ? sp[r0] : -1, e1 = (r1 < bn) ? sp[r1] : -1;
+    if (r0 < bn) ent_s[buf][r0] = e0;
+    if (r1 < bn) ent_s[buf][r1] = e1;
+    const bool c0 = !res && e0 >= 0, c1 = !res && e1 >= 0;
+    const int ncp = __popc(__ballot_sync(0xffffffffu, c0)) + __popc(__ballot_sync(0xffffffffu, c1));
+    if (lane == 0) mbar_arrive_expect_tx(&sbar[buf], (uint32_t)ncp * (qrow_bytes + mrow_bytes));
+    __syncwarp();
+    // the buffer was last read by generic loads (ordered by the block barrier)
+    fence_proxy_async();
+    const int64_t lo = lvo[bl];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const bool c = h ? c1 : c0;
+      const int r = h ? r1 : r0, e = h ? e1 : e0;
+      if (!c) continue;
+      const int64_t row = lo + (e >> 9);
+      double *qdst = qds + ((size_t)buf * nbmax + r) * 4;
+      if (kDF) bulk_g2s(qdst, qdf + (size_t)row * kQDF, qrow_bytes, &sbar[buf]);
+      else bulk_g2s(qdst, qd + (size_t)row * kQD, qrow_bytes, &sbar[buf]);
+      if (P >= 2) bulk_g2s(Ms + ((size_t)buf * nbmax + r) * lds, M + (size_t)row * ld, mrow_bytes, &sbar[buf]);
+    }
+  };
+  int cl = 0, cb = 0, cn = 0, cur = 0;
+  bool have = next_batch(cl, cb, cn);
+  if (have) stage(0, cl, cb, cn);
+  while (have) {
+    int nl2 = 0, nb2 = 0, nn2 = 0;
+    const bool nxt = next_batch(nl2, nb2, nn2);
+    if (nxt) stage(cur ^ 1, nl2, nb2, nn2);
+    // the current batch's copies (bounded wait; on expiry the block records
+    // the failure, drains the copies in flight and leaves the traversal)
+    const uint32_t pc = cur ? ph1 : ph0;
+    const bool ok = mbar_wait(&sbar[cur], pc, &s_abort, wait_ns);
+    if (cur) ph1 ^= 1u; else ph0 ^= 1u;
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) *(volatile int *)(status + kStatusSiteTimeout) = 1;
+      mbar_wait_for(&sbar[cur], pc, wait_ns);
+      if (nxt) mbar_wait_for(&sbar[cur ^ 1], cur ? ph0 : ph1, wait_ns);
+      __syncthreads();
+      timed_out = true;
+      break;
+    }
+    const T is = iLt * (T)(1 << cl);  // 1 / s, exact scaling of 1 / L
+    const int *ent = ent_s[cur];
+    const T *Mb = Ms + (size_t)cur * nbmax * lds;
+    if (tid < cn) {
+      const int e = ent[tid];
+      if (e >= 0) {
+        const int box = e >> 9, img = e & 511;
         const int nx = img / 49 - 3, ny = (img / 7) % 7 - 3, nz = img % 7 - 3;
-        if (sep[b + tid] < 0) {
-          brow_s[tid] = -1 - box;
+        const double *q = (cl <= 1) ? qres + (size_t)((cl == 0) ? 0 : 1 + box) * 4
+                                    : qds + ((size_t)cur * nbmax + tid) * 4;
+        if constexpr (kDF) {
+          // double-float: w = m h - c with the odd integer m = 2 i + 1 + 2^(l+1) n
+          // (exact in single precision) and h = L / 2^(l+1) = hh + hl; then
+          // B^2, 1/B, p.w and Q/B - (p.w)/B^3 to about 2^-44 relative
+          const float hh = ldexpf(Lsp.h, -(cl + 1)), hl = ldexpf(Lsp.l, -(cl + 1));
+          const int ms = 2 << cl;
+          const int mi[3] = {2 * (int)d_compact(box) + 1 + ms * nx, 2 * (int)d_compact(box >> 1) + 1 + ms * ny,
+                             2 * (int)d_compact(box >> 2) + 1 + ms * nz};
+          DF w[3];
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            const float mf = (float)mi[k], ph = mf * hh, pe = fmaf(mf, hh, -ph);
+            float sh, se;
+            two_sum(ph, -csp[k].h, sh, se);
+            w[k] = df_norm(sh, se + (fmaf(mf, hl, pe) - csp[k].l));
+          }
+          const float *qf = reinterpret_cast<const float *>(q);
+          const DF Q{qf[0], qf[1]}, px{qf[2], qf[3]}, py{qf[4], qf[5]}, pz{qf[6], qf[7]};
+          const DF B2 = df_add(df_add(df_sq(w[0]), df_sq(w[1])), df_sq(w[2]));
+          const DF Bi = df_rsqrt(B2), Bi3 = df_mul(df_sq(Bi), Bi);
+          const DF pw = df_add(df_add(df_mul(px, w[0]), df_mul(py, w[1])), df_mul(pz, w[2]));
+          base_df = df_add(base_df, df_add(df_mul(Q, Bi), df_neg(df_mul(pw, Bi3))));  // at c the box centre is at -w
+          rw[tid][0] = w[0].h; rw[tid][1] = w[1].h; rw[tid][2] = w[2].h;
+          rp[tid][0] = px.h; rp[tid][1] = py.h; rp[tid][2] = pz.h;
+          rQ[tid] = Q.h;
+          rB[tid] = B2.h * Bi.h;
+          rBi[tid] = Bi.h;
+          rpw[tid] = pw.h;
         } else {
-          const int64_t row = level_off[l] + box;
-          brow_s[tid] = (int)row;
+          const double s = ldexp(L, -cl);
           const double wx = (((int)d_compact(box) + 0.5) * s + nx * L) - cen[0];
           const double wy = (((int)d_compact(box >> 1) + 0.5) * s + ny * L) - cen[1];
           const double wz = (((int)d_compact(box >> 2) + 0.5) * s + nz * L) - cen[2];
           const double B2 = wx * wx + wy * wy + wz * wz, Bi = rinv_dd(B2);
-          const double Q = qd[row * kQD], px = qd[row * kQD + 1], py = qd[row * kQD + 2], pz = qd[row * kQD + 3];
+          const double Q = q[0], px = q[1], py = q[2], pz = q[3];
           const double pw = px * wx + py * wy + pz * wz;
           base += Q * Bi - pw * (Bi * Bi * Bi);  // at c the box centre is at -w
           rw[tid][0] = (T)wx; rw[tid][1] = (T)wy; rw[tid][2] = (T)wz;
@@ -1892,93 +2128,92 @@ __global__ void __launch_bounds__(kSiteThreads, 3) k_site_phi(
           rBi[tid] = (T)Bi;
           rpw[tid] = (T)pw;
         }
-        bimg[tid] = img;
       }
-      // the multipole rows of the batch (row index straight from the list, so
-      // this needs no barrier after the per-row values above)
-      if (P >= 2) {
-        constexpr int EPV = 16 / sizeof(T);
-        const int per_row = ld / EPV;
-        for (int q = tid; q < nbx * per_row; q += blockDim.x) {
-          const int r = q / per_row, e2 = q % per_row;
-          const int er = sep[b + r];
-          if (er >= 0)
-            cpa16(Ms + (size_t)r * lds + (size_t)e2 * EPV, M + (size_t)(level_off[l] + (er >> 9)) * ld + (size_t)e2 * EPV);
-        }
-        asm volatile("cp.async.wait_all;" ::: "memory");
-      }
-      __syncthreads();
-      if (my_p >= 0) {
-        for (int r = my_s; r < nbx; r += nslot) {
-          if (brow_s[r] >= 0) {
-            // charge + dipole: change from the value at c,
-            //   Q (1/A - 1/B) + p.u / A^3 - (p.w) (1/A^3 - 1/B^3),
-            // A = |u - w|, B = |w|, A^2 - B^2 = u.u - 2 u.w, A - B = (A^2 - B^2) / (A + B)
-            const T wx = rw[r][0], wy = rw[r][1], wz = rw[r][2];
-            const T Q = rQ[r], px = rp[r][0], py = rp[r][1], pz = rp[r][2];
-            const T B = rB[r], Bi = rBi[r], pw = rpw[r], Bi3 = Bi * Bi * Bi;
-            T ux[2], uy[2], uz[2], dev[2];
+    }
+    __syncthreads();
+    if (my_p >= 0) {
+      for (int r = my_s; r < cn; r += nslot) {
+        const int e = ent[r];
+        if (e >= 0) {
+          // charge + dipole: change from the value at c,
+          //   Q (1/A - 1/B) + p.u / A^3 - (p.w) (1/A^3 - 1/B^3),
+          // A = |u - w|, B = |w|, A^2 - B^2 = u.u - 2 u.w, A - B = (A^2 - B^2) / (A + B)
+          const T wx = rw[r][0], wy = rw[r][1], wz = rw[r][2];
+          const T Q = rQ[r], px = rp[r][0], py = rp[r][1], pz = rp[r][2];
+          const T B = rB[r], Bi = rBi[r], pw = rpw[r], Bi3 = Bi * Bi * Bi;
+          T ux[2], uy[2], uz[2], dev[2];
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-              const int a = h ? a1 : a0;
-              ux[h] = pu[a][0] - wx; uy[h] = pu[a][1] - wy; uz[h] = pu[a][2] - wz;
-              const T A2 = ux[h] * ux[h] + uy[h] * uy[h] + uz[h] * uz[h];
-              const T Ai = rinv(A2), A = A2 * Ai, Ai3 = Ai * Ai * Ai;
-              const T d2 = puu[a] - T(2) * (pu[a][0] * wx + pu[a][1] * wy + pu[a][2] * wz);
-              const T f1 = site_div(d2, A + B);
-              const T pu_ = px * pu[a][0] + py * pu[a][1] + pz * pu[a][2];
-              dev[h] = -Q * f1 * Ai * Bi + pu_ * Ai3 + pw * f1 * (A2 + A * B + B * B) * Ai3 * Bi3;
+          for (int h = 0; h < 2; ++h) {
+            const int a = h ? a1 : a0;
+            ux[h] = pu[a][0] - wx; uy[h] = pu[a][1] - wy; uz[h] = pu[a][2] - wz;
+            const T A2 = ux[h] * ux[h] + uy[h] * uy[h] + uz[h] * uz[h];
+            const T Ai = rinv(A2), A = A2 * Ai, Ai3 = Ai * Ai * Ai;
+            const T d2 = puu[a] - T(2) * (pu[a][0] * wx + pu[a][1] * wy + pu[a][2] * wz);
+            const T f1 = site_div(d2, A + B);
+            const T pu_ = px * pu[a][0] + py * pu[a][1] + pz * pu[a][2];
+            dev[h] = -Q * f1 * Ai * Bi + pu_ * Ai3 + pw * f1 * (A2 + A * B + B * B) * Ai3 * Bi3;
+          }
+          if (P >= 2) {
+            const T *Mr = (cl <= 1) ? Mres + (size_t)((cl == 0) ? 0 : 1 + (e >> 9)) * lds : Mb + (size_t)r * lds;
+            T v0, v1;
+            if constexpr (PP > 0) {
+              m2p_high2<T, PP>(Mr, ux[0] * is, uy[0] * is, uz[0] * is, ux[1] * is, uy[1] * is, uz[1] * is, v0, v1);
+            } else {
+              v0 = m2p_high<T>(P, Mr, ux[0] * is, uy[0] * is, uz[0] * is);
+              v1 = m2p_high<T>(P, Mr, ux[1] * is, uy[1] * is, uz[1] * is);
             }
-            if (P >= 2) {
-              const T *Mr = Ms + (size_t)r * lds;
-              T v0, v1;
-              if constexpr (PP > 0) {
-                m2p_high2<T, PP>(Mr, ux[0] * is, uy[0] * is, uz[0] * is, ux[1] * is, uy[1] * is, uz[1] * is, v0, v1);
-              } else {
-                v0 = m2p_high<T>(P, Mr, ux[0] * is, uy[0] * is, uz[0] * is);
-                v1 = m2p_high<T>(P, Mr, ux[1] * is, uy[1] * is, uz[1] * is);
-              }
-              dev[0] += v0 * is;
-              dev[1] += v1 * is;
-            }
-            acc0.add(dev[0]);
-            acc1.add(dev[1]);
+            dev[0] += v0 * is;
+            dev[1] += v1 * is;
+          }
+          acc0.add(dev[0]);
+          acc1.add(dev[1]);
+        } else {
+          // unseparated leaf: direct sum over its atoms
+          const int box = (e & 0x7fffffff) >> 9, img = e & 511;
+          const int nx = img / 49 - 3, ny = (img / 7) % 7 - 3, nz = img % 7 - 3;
+          const int bx = (int)d_compact(box) + nx * nb, by = (int)d_compact(box >> 1) + ny * nb,
+                    bz = (int)d_compact(box >> 2) + nz * nb;
+          const int gx0 = bx - aI[a0][0], gy0 = by - aI[a0][1], gz0 = bz - aI[a0][2];
+          const int gx1 = bx - aI[a1][0], gy1 = by - aI[a1][1], gz1 = bz - aI[a1][2];
+          const int self0 = (gx0 == 0 && gy0 == 0 && gz0 == 0) ? sa_s[a0] : -1;
+          const int self1 = (gx1 == 0 && gy1 == 0 && gz1 == 0) ? sa_s[a1] : -1;
+          const V m0 = me[a0], m1 = me[a1];
+          SiteTarget<T> t0, t1;
+          if constexpr (kDF) {
+            t0 = site_target(m0.x, m0.y, m0.z, gx0, gy0, gz0, slh, sll);
+            t1 = site_target(m1.x, m1.y, m1.z, gx1, gy1, gz1, slh, sll);
           } else {
-            // unseparated leaf: direct sum over its atoms
-            const int box = -1 - brow_s[r], img = bimg[r];
-            const int nx = img / 49 - 3, ny = (img / 7) % 7 - 3, nz = img % 7 - 3;
-            const int bx = (int)d_compact(box) + nx * nb, by = (int)d_compact(box >> 1) + ny * nb,
-                      bz = (int)d_compact(box >> 2) + nz * nb;
-            const int gx0 = bx - aI[a0][0], gy0 = by - aI[a0][1], gz0 = bz - aI[a0][2];
-            const int gx1 = bx - aI[a1][0], gy1 = by - aI[a1][1], gz1 = bz - aI[a1][2];
-            const int self0 = (gx0 == 0 && gy0 == 0 && gz0 == 0) ? sa_s[a0] : -1;
-            const int self1 = (gx1 == 0 && gy1 == 0 && gz1 == 0) ? sa_s[a1] : -1;
-            const V m0 = me[a0], m1 = me[a1];
-            const SiteTarget<T> t0 = site_target(m0.x, m0.y, m0.z, gx0, gy0, gz0, sl);
-            const SiteTarget<T> t1 = site_target(m1.x, m1.y, m1.z, gx1, gy1, gz1, sl);
-            for (int q2 = leaf_start[box]; q2 < leaf_start[box + 1]; ++q2) {
-              const V src = part[q2];
-              T vh, vl;
-              if (q2 != self0) {
-                pair_pot(t0, src.x, src.y, src.z, src.w, vh, vl);
-                acc0.add2(vh, vl);
-              }
-              if (q2 != self1) {
-                pair_pot(t1, src.x, src.y, src.z, src.w, vh, vl);
-                acc1.add2(vh, vl);
-              }
+            t0 = site_target(m0.x, m0.y, m0.z, gx0, gy0, gz0, sl);
+            t1 = site_target(m1.x, m1.y, m1.z, gx1, gy1, gz1, sl);
+          }
+          for (int q2 = leaf_start[box]; q2 < leaf_start[box + 1]; ++q2) {
+            const V src = part[q2];
+            T vh, vl;
+            if (q2 != self0) {
+              pair_pot(t0, src.x, src.y, src.z, src.w, vh, vl);
+              acc0.add2(vh, vl);
+            }
+            if (q2 != self1) {
+              pair_pot(t1, src.x, src.y, src.z, src.w, vh, vl);
+              acc1.add2(vh, vl);
             }
           }
         }
       }
-      __syncthreads();
     }
-    for (int t = tid; t < n1; t += blockDim.x) fa[t] = fb[t];
-    n0 = (l < d) ? n1 : 0;
+    // the next iteration copies into this batch's buffer
     __syncthreads();
+    cur ^= 1;
+    cl = nl2; cb = nb2; cn = nn2;
+    have = nxt;
   }
+  // the far-image lattice coefficients in working precision, over the batch
+  // buffers (free now: the loop ended with a barrier and no copy in flight)
+  T *Lh3s = Ms;
+  if (g == 0)
+    for (int k = tid; k < (P + 1) * (P + 1); k += blockDim.x) Lh3s[k] = (T)Lh3[k];
   // fixed-order reductions: the staged FP64 values, then per atom over its slots
-  if (tid < kSiteBatchMax) base_s[tid] = base;
+  if (tid < kSiteBatchMax) base_s[tid] = base + ((double)base_df.h + (double)base_df.l);
   res_s[tid][0] = acc0.value();
   res_s[tid][1] = acc1.value();
   __syncthreads();
@@ -1995,21 +2230,27 @@ __global__ void __launch_bounds__(kSiteThreads, 3) k_site_phi(
     double acc = common;
     for (int k = 0; k < nslot; ++k) acc += res_s[pp + k * npair][hh];
     if (g == 0) {
-      // far-image lattice part and dipole / background term
+      // far-image lattice part: degrees 0 and 1 (the offset and the field,
+      // which carry most of it) in FP64, the rest in working precision (each
+      // degree is smaller by about |x| / 3.5 L, and FP64 issues at a small
+      // fraction of the FP32 rate here); then the dipole / background term
       const double px = pa[a][0], py = pa[a][1], pz = pa[a][2];
-      double hsum = 0.0;
-      rt_columns<double>(P, (px - 0.5 * L) / L, (py - 0.5 * L) / L, (pz - 0.5 * L) / L,
-                         [&](int l, int m, double re, double im) {
-                           const int k = ridx(l, m);
-                           hsum += (m == 0) ? Lh3[k] * re : 2.0 * (Lh3[k] * re + Lh3[k + 1] * im);
-                         });
+      const double ax = px - 0.5 * L, ay = py - 0.5 * L, az = pz - 0.5 * L, iL = 1.0 / L;
+      const double ux = ax * iL, uy = ay * iL, uz = az * iL, r11 = -tab_diag<double>(1);
+      double hlow = Lh3[0];
+      if (P >= 1) hlow += Lh3[1] * (tab_a<double>(1) * uz) + 2.0 * (Lh3[2] * (r11 * ux) + Lh3[3] * (r11 * uy));
+      T hsum = T(0);
+      rt_columns<T>(P, (T)ux, (T)uy, (T)uz, [&](int l, int m, T re, T im) {
+        const int k = ridx(l, m);
+        if (l >= 2) hsum += (m == 0) ? Lh3s[k] * re : T(2) * (Lh3s[k] * re + Lh3s[k + 1] * im);
+      });
       const double V3 = L * L * L, c2 = 2.0 * kPi / (3.0 * V3);
-      const double ax = px - 0.5 * L, ay = py - 0.5 * L, az = pz - 0.5 * L;
-      acc += hsum / L + c2 * (mom[0] * (ax * ax + ay * ay + az * az) -
-                              2.0 * (ax * mom[1] + ay * mom[2] + az * mom[3]) + mom[4]);
+      acc += (hlow + (double)hsum) * iL + c2 * (mom[0] * (ax * ax + ay * ay + az * az) -
+                                                2.0 * (ax * mom[1] + ay * mom[2] + az * mom[3]) + mom[4]);
     }
     phi_part[(size_t)(b0 + a) * G + g] = acc;
   }
+  if (timed_out) break;
   }  // groups
 }
 
@@ -2240,11 +2481,13 @@ static cudaError_t eval_t(mahi_ctx *h, const XT *x, const double *lam, double *e
   MAHI_CK(cudaEventRecord(h->fork_ev[0], st));
   MAHI_CK(cudaStreamWaitEvent(h->side, h->fork_ev[0], 0));
   k_leaf_moments<<<(nleaf + 127) / 128, 128, 0, h->side>>>(nleaf, h->leaf_start, h->perm, h->qt, h->relD,
-                                                            h->box_qd + h->level_off[h->d] * kQD);
+                                                            h->box_qd + h->level_off[h->d] * kQD,
+                                                            h->box_qdf + h->level_off[h->d] * kQDF);
   for (int l = h->d - 1; l >= 0; --l) {
     const int np = 1 << (3 * l);
     k_qd_up<<<(np + 127) / 128, 128, 0, h->side>>>(np, h->L / (1 << (l + 1)), h->box_qd + h->level_off[l + 1] * kQD,
-                                                   h->box_qd + h->level_off[l] * kQD);
+                                                   h->box_qd + h->level_off[l] * kQD,
+                                                   h->box_qdf + h->level_off[l] * kQDF);
   }
   MAHI_CK(cudaEventRecord(h->join_ev[0], h->side));
   h->launches += 4 + h->d;
@@ -2307,20 +2550,24 @@ static cudaError_t eval_t(mahi_ctx *h, const XT *x, const double *lam, double *e
     MAHI_CK(cudaEventRecord(h->fork_ev[1], st));
     MAHI_CK(cudaStreamWaitEvent(h->side, h->fork_ev[1], 0));
     mark_side(h, 1, 0);
-    // rows of staged multipoles: as many as keep three blocks per SM
+    // rows per batch: as many as two buffers of staged multipole and
+    // charge/dipole rows hold beside the four lists and the resident rows of
+    // levels 0 and 1 at three blocks per SM
     const int lds = ld + 16 / (int)sizeof(T);
-    const size_t fixed = sizeof(int) * 3 * (size_t)h->site_list_cap;
-    const size_t budget = std::max<size_t>(72 * 1024, fixed + 8 * sizeof(T) * lds);
-    const int nbmax = (int)std::max<size_t>(8, std::min<size_t>(kSiteBatchMax, (budget - fixed) / (sizeof(T) * lds)));
-    const size_t smp = fixed + sizeof(T) * nbmax * lds;
+    const size_t per_row = 2 * (sizeof(T) * lds + 4 * sizeof(double));
+    const size_t fixed = sizeof(int) * 4 * (size_t)h->site_list_cap +
+                         (h->d >= 1 ? 9 : 1) * (sizeof(T) * lds + 4 * sizeof(double));  // lists, resident rows
+    const size_t budget = std::max<size_t>(kSiteSmemBudget, fixed + 8 * per_row);
+    const int nbmax = (int)std::max<size_t>(8, std::min<size_t>(kSiteBatchMax, (budget - fixed) / per_row));
+    const size_t smp = fixed + per_row * nbmax;
     // blocks per site: about 4 x 3 per SM over all sites, unless the autotuner picked a count
     const int G = h->tune_site_blocks > 0
                       ? std::min(kSiteChunksMax, h->tune_site_blocks)
                       : std::max(1, std::min(kSiteChunksMax, (4 * 3 * h->num_sms + h->S - 1) / std::max(1, h->S)));
     MAHI_CK(launch_site_phi<T>(P, G, smp, h->side, h->S, G, h->site_ptr, h->site_atoms, h->d, P, ld, lds, nbmax, h->L,
                                h->d_level_off, h->leaf_start, h->inv_perm, (const V *)h->part, M, h->box_qd,
-                               mom, h->L_h3, h->phi_part, h->status_dev + kStatusSiteOverflow, h->site_theta,
-                               h->site_list_cap));
+                               h->box_qdf, mom, h->L_h3, h->phi_part, h->status_dev, h->site_theta,
+                               h->site_list_cap, h->wait_limit_ns));
     k_site_phi_sum<<<(h->n_site_atoms + 127) / 128, 128, 0, h->side>>>(h->n_site_atoms, G, coulomb_constant(),
                                                                         h->phi_part, h->phi_site);
     mark_side(h, 1, 1);

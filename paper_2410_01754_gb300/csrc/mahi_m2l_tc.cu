@@ -33,6 +33,7 @@
 #include <vector>
 
 #include "mahi_internal.h"
+#include "mahi_sync.h"
 
 namespace mahi {
 
@@ -45,7 +46,6 @@ constexpr int kStagesS = 3;      // A staging slots in shared memory per produce
 constexpr int kStagesB = 4;      // B stages in shared memory (at most; Params::nsb is the count used)
 constexpr int kDone = 8;         // done ring: one entry per item pair
 constexpr int kThreads = 480;     // 15 warps: MMA (tile 0), B producer, 2 x 4 A producers, 4 epilogue, MMA (tile 1)
-constexpr uint32_t kSpinLimit = 1u << 26;
 constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s: drains of work in flight (they end in microseconds)
 constexpr int kMaxN = 256;       // MMA N limit: Kp <= 256, order <= 15
 constexpr int kSlotBytes = kKPI * 2 * 2 * kRows * 16;   // A staging slot: [chunk][tile][granule][row] 16 B
@@ -91,67 +91,6 @@ struct Params {
 // ---------------------------------------------------------------------------
 // PTX wrappers
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ void mbar_init(uint64_t *b, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t *b) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *b, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *b, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_u32(b)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// bounded wait; returns false (and raises the abort flag) on expiry
-__device__ __forceinline__ bool mbar_test(uint64_t *b, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_u32(b)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ uint64_t global_ns() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-// bounded wait: gives up after lim ns (or when another role of the CTA gave
-// up), raising the abort flag; returns false then
-__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity, volatile int *abort_flag, uint64_t lim) {
-  if (mbar_test(b, parity)) return true;  // non-blocking test first: most waits find the phase complete
-  const uint64_t t0 = global_ns();
-  for (uint32_t it = 0; it < tc::kSpinLimit; ++it) {
-    if (mbar_try_wait(b, parity)) return true;
-    if (*abort_flag) return false;
-    if ((it & 255) == 255 && global_ns() - t0 > lim) break;
-  }
-  *abort_flag = 1;
-  return false;
-}
-// two bounded waits whose first (non-blocking) tests are issued together, so
-// that their shared-memory latencies overlap when both phases are complete
-__device__ __forceinline__ bool mbar_wait2(uint64_t *a, uint32_t pa, uint64_t *b, uint32_t pb, volatile int *abort_flag,
-                                           uint64_t lim) {
-  const bool ra = mbar_test(a, pa), rb = mbar_test(b, pb);
-  if (ra && rb) return true;
-  return (ra || mbar_wait(a, pa, abort_flag, lim)) && (rb || mbar_wait(b, pb, abort_flag, lim));
-}
 // 16-byte copy; with src_bytes = 0 the destination is zero-filled and nothing is read
 __device__ __forceinline__ void cp_async16_zfill(void *smem, const void *gmem, uint32_t src_bytes) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(smem)), "l"(gmem), "r"(src_bytes)
@@ -165,15 +104,6 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N> __device__ __forceinline__ void cp_async_wait_group() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
-__device__ __forceinline__ void fence_proxy_async() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-__device__ __forceinline__ void bulk_g2s(void *smem, const void *gmem, uint32_t bytes, uint64_t *bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(smem)),
-      "l"(gmem), "r"(bytes), "r"(smem_u32(bar))
-      : "memory");
 }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
