@@ -228,6 +228,12 @@ int mahi_backward(mahi_t h, const double *grad_energy, const void *forces, const
  *       128 or 256 (0 = 128, the default).
  *   MAHI_OPT_SITE_BLOCKS      blocks per site of the site-atom traversal, 1 to
  *       16 (0 = about 12 per SM over all sites, the default).
+ *   MAHI_OPT_P2P_TARGETS      near-field scheme of the single-precision paths:
+ *       4 or 8 = every unordered pair of neighbouring atoms evaluated once
+ *       (Newton's third law over the forward half shell of 13 neighbour
+ *       leaves), with that many targets held per thread; -1 = every directed
+ *       pair over all 27 neighbour leaves (block size MAHI_OPT_P2P_THREADS).
+ *       0 = 8, the default.  The FP64 path always takes every directed pair.
  * MAHI_ERR_INVALID_ARG for an unknown option or a value out of range. */
 enum {
   MAHI_OPT_SITE_THETA = 1,
@@ -238,7 +244,8 @@ enum {
   MAHI_OPT_M2L_SINGLE_TILE = 6,
   MAHI_OPT_M2L_B_STAGES = 7,
   MAHI_OPT_P2P_THREADS = 8,
-  MAHI_OPT_SITE_BLOCKS = 9
+  MAHI_OPT_SITE_BLOCKS = 9,
+  MAHI_OPT_P2P_TARGETS = 10
 };
 int mahi_set_option(mahi_t h, int32_t option, double value);
 /* Current value of an option (the effective one for defaults). */
@@ -269,7 +276,11 @@ int mahi_get_potential(mahi_t h, double *phi_device);
  * mahi_stage_times fills up to n floats (ms) of the last evaluation in the
  * order of mahi_stage_name(i) and returns the stage count.  The first ten are
  * consecutive intervals on the handle's stream (bin, sort, p2m, m2m, lattice,
- * m2l, l2l, l2p, p2p, site); the last two are the internal side stream's work,
+ * m2l, l2l, near_pairs, far_near_out, site): near_pairs is the half-shell
+ * near-field pair kernel and far_near_out the far field (L2P) fused with the
+ * near-field sums and the outputs; in the directed near-field scheme
+ * (MAHI_OPT_P2P_TARGETS = -1, and the FP64 path) they are L2P and the 27-leaf
+ * near field with the outputs.  The last two are the internal side stream's work,
  * which overlaps them: side_site_pairs (the sites' FP64 pair terms, from the
  * start of the evaluation) and side_site_potential (the refined site-atom
  * potential, after the M2L), 0 when there are no sites.  It synchronises the

@@ -19,7 +19,8 @@ LIB_PATH = os.path.join(_HERE, "libmahi.so")
 MAHI_FP64, MAHI_MIXED, MAHI_MIXED_SIMT = 0, 1, 2
 MAHI_ERR_TIMEOUT, MAHI_ERR_SITE_OVERFLOW = -5, -8
 OPTIONS = {"site_theta": 1, "site_list_cap": 2, "wait_limit_ms": 3, "watchdog_selftest": 4,
-           "m2l_split_degree": 5, "m2l_single_tile": 6, "m2l_b_stages": 7, "p2p_threads": 8, "site_blocks": 9}
+           "m2l_split_degree": 5, "m2l_single_tile": 6, "m2l_b_stages": 7, "p2p_threads": 8, "site_blocks": 9,
+           "p2p_targets": 10}
 PRECISIONS = {"fp64": MAHI_FP64, "mixed": MAHI_MIXED, "mixed_simt": MAHI_MIXED_SIMT}
 
 _lib = None

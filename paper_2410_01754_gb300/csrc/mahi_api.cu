@@ -44,6 +44,32 @@ int default_site_list_cap(float theta) {
   cap = (cap + 255) / 256 * 256;
   return std::max(1536, std::min(kSiteListCapMax, cap));
 }
+
+// the half-shell near field's slots (13 float4 per atom), allocated when
+// that scheme is first selected
+int alloc_near_slots(mahi_ctx *h) {
+  if (h->nf_slots) return 0;
+  return cudaMalloc(&h->nf_slots, (size_t)13 * h->N * sizeof(float4)) == cudaSuccess ? 0 : -1;
+}
+
+// traversal-list buffers of the sites for the current list capacity; keeps
+// buffers that are large enough (work enqueued earlier may still read them:
+// the handle's streams are synchronised before any buffer is replaced)
+int alloc_site_lists(mahi_ctx *h) {
+  if (h->S <= 0) return 0;
+  if (h->site_lists && h->site_lists_cap >= h->site_list_cap) return 0;
+  if (h->site_lists) {
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess || cudaStreamSynchronize(h->side) != cudaSuccess) return -1;
+    cudaFree(h->site_lists); cudaFree(h->site_list_n); cudaFree(h->site_cen);
+    h->site_lists = nullptr; h->site_list_n = nullptr; h->site_cen = nullptr; h->site_lists_cap = 0;
+  }
+  const size_t nl = (size_t)h->S * (h->d + 1) * h->site_list_cap;
+  if (cudaMalloc(&h->site_lists, nl * sizeof(int)) != cudaSuccess) return -1;
+  if (cudaMalloc(&h->site_list_n, (size_t)h->S * (h->d + 2) * sizeof(int)) != cudaSuccess) return -1;
+  if (cudaMalloc(&h->site_cen, (size_t)h->S * 4 * sizeof(double)) != cudaSuccess) return -1;
+  h->site_lists_cap = h->site_list_cap;
+  return 0;
+}
 }  // namespace mahi
 
 #define CK(call)                                      \
@@ -67,7 +93,7 @@ static void free_all(mahi_ctx *h) {
                   h->m2l_list, h->m2l_off, h->site_ptr, h->site_atoms,
                   h->energy_part, h->site_energy, h->tc_ops, h->tc_partial, h->tc_msrc, h->tc_level_off, h->tc_units, h->d_x_stage,
                   h->d_lam_stage, h->d_E_stage, h->d_dEdl_stage, h->d_F_stage, h->ops_lat_h3, h->L_h3,
-                  h->box_qd, h->box_qdf, h->vtmp, h->relD, h->phi_site, h->psi_site, h->site_pairs, h->site_slot, h->mf_q, h->mf_lam_off, h->phi_part, h->d_level_off, h->mf_psi, h->mf_form_off};
+                  h->box_qd, h->box_qdf, h->vtmp, h->relD, h->phi_site, h->psi_site, h->site_pairs, h->site_slot, h->mf_q, h->mf_lam_off, h->phi_part, h->d_level_off, h->mf_psi, h->mf_form_off, h->nf_slots, h->site_lists, h->site_list_n, h->site_cen};
   for (void *b : bufs)
     if (b) cudaFree(b);
   if (h->status_host) cudaFreeHost(h->status_host);
@@ -436,6 +462,7 @@ int mahi_set_charges(mahi_t h, const double *qA_in, const double *qB_in, const i
   CK(cudaMemcpy(h->site_ptr, ptr.data(), (S + 1) * sizeof(int), cudaMemcpyHostToDevice));
   if (!atoms.empty()) CK(cudaMemcpy(h->site_atoms, atoms.data(), atoms.size() * sizeof(int), cudaMemcpyHostToDevice));
   h->n_site_atoms = (int)atoms.size();
+  if (alloc_site_lists(h) != 0) return cuda_fail(cudaGetLastError(), "site lists");
   h->charges_set = true;
   h->multiform = false;  // mahi_set_forms sets it after calling this
   return MAHI_OK;
@@ -553,12 +580,14 @@ int mahi_set_option(mahi_t h, int32_t option, double value) {
       h->site_theta_set = value > 0.0;
       h->site_theta = h->site_theta_set ? (float)value : default_site_theta(h->p);
       if (!h->site_list_cap_set) h->site_list_cap = default_site_list_cap(h->site_theta);
+      if (h->charges_set && alloc_site_lists(h) != 0) return cuda_fail(cudaGetLastError(), "site lists");
       return MAHI_OK;
     case MAHI_OPT_SITE_LIST_CAP:
       if (value != 0.0 && (value < 64 || value > kSiteListCapMax || value != std::floor(value)))
         return MAHI_ERR_INVALID_ARG;
       h->site_list_cap_set = value > 0.0;
       h->site_list_cap = h->site_list_cap_set ? (int)value : default_site_list_cap(h->site_theta);
+      if (h->charges_set && alloc_site_lists(h) != 0) return cuda_fail(cudaGetLastError(), "site lists");
       return MAHI_OK;
     case MAHI_OPT_WAIT_LIMIT_MS:
       if (value < 0.0 || (value > 0.0 && value < 1.0) || value > 60000.0) return MAHI_ERR_INVALID_ARG;
@@ -596,6 +625,12 @@ int mahi_set_option(mahi_t h, int32_t option, double value) {
       if (value < 0.0 || value > kSiteChunksMax || value != std::floor(value)) return MAHI_ERR_INVALID_ARG;
       h->tune_site_blocks = (int)value;
       return MAHI_OK;
+    case MAHI_OPT_P2P_TARGETS:
+      if (value != 0.0 && value != -1.0 && value != 4.0 && value != 8.0) return MAHI_ERR_INVALID_ARG;
+      h->tune_p2p_targets = value == 0.0 ? -1 : (int)value;
+      if (h->tune_p2p_targets > 0 && h->prec != MAHI_FP64 && alloc_near_slots(h) != 0)
+        return cuda_fail(cudaGetLastError(), "near-field slots");
+      return MAHI_OK;
     default: return MAHI_ERR_INVALID_ARG;
   }
 }
@@ -612,6 +647,7 @@ double mahi_get_option(mahi_t h, int32_t option) {
     case MAHI_OPT_M2L_B_STAGES: return h->tune_m2l_nsb;
     case MAHI_OPT_P2P_THREADS: return h->tune_p2p_threads;
     case MAHI_OPT_SITE_BLOCKS: return h->tune_site_blocks;
+    case MAHI_OPT_P2P_TARGETS: return h->tune_p2p_targets;
     default: return -1.0;
   }
 }

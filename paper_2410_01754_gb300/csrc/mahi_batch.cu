@@ -63,7 +63,11 @@ int mahi_autotune(mahi_t h, const void *x, int32_t x_is_fp64, const double *lamb
   }
   const bool timing = h->timing;
   h->timing = false;
-  const int p2p[3] = {64, 128, 256};
+  // near-field shapes: half shell with 8 or 4 targets per thread (single
+  // precision), or all directed pairs with 64 / 128 / 256 threads per leaf
+  const bool sp = h->prec != MAHI_FP64;
+  const int p2p_t[5] = {8, 4, -1, -1, -1}, p2p[5] = {128, 128, 64, 128, 256};
+  const int np = sp ? 5 : 3, p0 = sp ? 0 : 2;
   const int g0 = std::max(1, std::min(16, (4 * 3 * h->num_sms + h->S - 1) / std::max(1, h->S)));
   std::vector<int> gs = {0};
   if (h->S > 0) {
@@ -71,11 +75,13 @@ int mahi_autotune(mahi_t h, const void *x, int32_t x_is_fp64, const double *lamb
     if (g0 * 2 <= 16) gs.push_back(g0 * 2);
   }
   float best = 1e30f;
-  int best_p = h->tune_p2p_threads, best_g = h->tune_site_blocks;
+  int best_p = h->tune_p2p_threads, best_t = h->tune_p2p_targets, best_g = h->tune_site_blocks;
   int rc = MAHI_OK;
-  for (int pi = 0; pi < 3 && rc == MAHI_OK; ++pi)
+  for (int pi = p0; pi < p0 + np && rc == MAHI_OK; ++pi)
     for (size_t gi = 0; gi < gs.size() && rc == MAHI_OK; ++gi) {
       h->tune_p2p_threads = p2p[pi];
+      rc = mahi_set_option(h, MAHI_OPT_P2P_TARGETS, sp ? p2p_t[pi] : -1);  // allocates the slots on first use
+      if (rc != MAHI_OK) break;
       h->tune_site_blocks = gs[gi];
       // one untimed evaluation (launch attributes, caches), then reps timed
       rc = mahi_eval(h, x, x_is_fp64, lambda, nullptr, nullptr, nullptr);
@@ -92,10 +98,12 @@ int mahi_autotune(mahi_t h, const void *x, int32_t x_is_fp64, const double *lamb
       if (ms < best) {
         best = ms;
         best_p = p2p[pi];
+        best_t = sp ? p2p_t[pi] : -1;
         best_g = gs[gi];
       }
     }
   h->tune_p2p_threads = best_p;
+  h->tune_p2p_targets = best_t;
   h->tune_site_blocks = best_g;
   // then the tensor-core M2L's tiling with the shapes chosen above
   if (rc == MAHI_OK && h->prec == MAHI_MIXED && h->d >= 1) {

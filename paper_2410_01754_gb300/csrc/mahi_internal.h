@@ -124,6 +124,7 @@ struct mahi_ctx {
   double *relD = nullptr;                     // N x 3 offsets from the leaf centre (FP64)
   void *Mexp = nullptr, *Lexp = nullptr;      // expansions, all levels
   void *phi_s = nullptr, *grad_s = nullptr;   // sorted potential / gradient
+  void *nf_slots = nullptr;                   // [13][N] float4: half-shell near-field sums (single precision)
   void *ops_m2m = nullptr, *ops_l2l = nullptr, *ops_m2l = nullptr;
   void *gemm_ws = nullptr;                    // K-split partials of the M2M / L2L GEMMs
   size_t gemm_ws_elems = 0;
@@ -151,6 +152,10 @@ struct mahi_ctx {
   float site_theta = 0.40f;                   // separation ratio of the site-potential traversal
   bool site_theta_set = false;                // set by mahi_set_option (else the default rule)
   int site_list_cap = 1536;                   // boxes per level of one site's traversal
+  int *site_lists = nullptr;                  // [S][d + 1][cap] traversal lists of compact sites (k_site_lists)
+  int *site_list_n = nullptr;                 // [S][d + 2] their lengths (-1: spread site)
+  double *site_cen = nullptr;                 // [S][4] site centre and radius
+  int site_lists_cap = 0;                     // list capacity the buffers were sized for
   bool site_list_cap_set = false;
   uint64_t wait_limit_ns = 2000000000ull;     // bounded device waits of the tensor-core M2L
   int watchdog_selftest = 0;                  // 1: the M2L's first wait is on a barrier nothing completes
@@ -158,6 +163,7 @@ struct mahi_ctx {
   int *status_host = nullptr;                 // kStatusWords ints, host-mapped pinned memory
   int *status_dev = nullptr;                  // the same words as seen from the device
   int tune_p2p_threads = 128;                 // autotuned launch shapes (mahi_autotune)
+  int tune_p2p_targets = -1;                  // near field: 4 / 8 targets per lane (half shell), -1 all directed pairs
   int tune_site_blocks = 0;                   // 0 = default count of blocks per site
   bool tune_m2l_single = false;               // tensor-core M2L: single 128-row tiles where pairs would fit
   int tune_m2l_nsb = 0;                       // tensor-core M2L operator stages (0 = as many as fit)
@@ -201,6 +207,8 @@ int enqueue_backward_forms(mahi_ctx *h, const double *gE, const void *forces, co
 int enqueue_backward(mahi_ctx *h, const double *gE, const void *forces, const double *dEdl, const double *lam,
                      int x_is_fp64, void *dx, double *dlam, double *dqA, double *dqB);
 int upload_tables();
+int alloc_site_lists(mahi_ctx *h);
+int alloc_near_slots(mahi_ctx *h);
 size_t gemm_workspace_elems(int d, int ld, int num_sms);
 const char *stage_name(int i);
 int num_stages();

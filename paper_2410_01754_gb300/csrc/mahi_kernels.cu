@@ -879,8 +879,44 @@ __device__ __forceinline__ void gradient_row_coeffs(int P, const T *c, T *cx, T 
 // The leaf's local coefficients and the three gradient rows are kept
 // interleaved per coefficient, so one vector load of shared memory serves the
 // potential and the gradient of a term; PP > 0 makes the order a compile-time
-// constant (the harmonic recursion is then unrolled; six blocks of four warps
-// per SM measured fastest, with a few registers spilled).
+// constant (the harmonic recursion is then unrolled).
+template <typename T>
+__device__ __forceinline__ void l2p_stage_leaf(int P, int K, const T *__restrict__ Lv, T *cf, int lane) {
+  for (int k = lane; k < K; k += 32) cf[4 * k] = Lv[k];
+  __syncwarp();
+  gradient_row_coeffs<T>(P, cf, cf + 1, cf + 2, cf + 3, lane, 32, 4);
+  __syncwarp();
+}
+
+// far-field potential f and gradient g at u = (x - leaf centre) / s from the
+// staged rows cc, in the leaf's units (multiply f by 1/s and g by 1/s^2)
+template <typename T, int PP>
+__device__ __forceinline__ void l2p_point(int P, const typename V4<T>::type *__restrict__ cc, T ux, T uy, T uz, T &f,
+                                          T &gx, T &gy, T &gz) {
+  using V = typename V4<T>::type;
+  const int Q = PP > 0 ? PP : P;
+  f = 0; gx = 0; gy = 0; gz = 0;
+  // sum over m of X_lm conj(R_lm) = X_l0 R_l0 + 2 sum_{m>0} (Xr Rr + Xi Ri)
+  rt_columns<T>(Q, ux, uy, uz, [&](int l, int m, T re, T im) {
+    const int k = ridx(l, m);
+    const V c0 = cc[k];
+    if (m == 0) {
+      f += c0.x * re;
+      if (l < Q) { gx += c0.y * re; gy += c0.z * re; gz += c0.w * re; }
+    } else {
+      const V c1 = cc[k + 1];
+      f += T(2) * (c0.x * re + c1.x * im);
+      if (l < Q) {
+        gx += T(2) * (c0.y * re + c1.y * im);
+        gy += T(2) * (c0.z * re + c1.z * im);
+        gz += T(2) * (c0.w * re + c1.w * im);
+      }
+    }
+  });
+}
+
+// One warp per leaf (six blocks of four warps per SM measured fastest, with a
+// few registers spilled).
 template <typename T, int PP>
 __global__ void __launch_bounds__(128, 6) k_l2p(int nleaf, int Pr, int ld, T s, const int *__restrict__ leaf_start,
                       const typename V4<T>::type *__restrict__ part, const T *__restrict__ Lleaf,
@@ -891,36 +927,15 @@ __global__ void __launch_bounds__(128, 6) k_l2p(int nleaf, int Pr, int ld, T s, 
   const int K = (P + 1) * (P + 1);
   const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
   V *cc = reinterpret_cast<V *>(smem_raw) + (size_t)wib * K;  // {c, cx, cy, cz} per coefficient
-  T *cf = reinterpret_cast<T *>(cc);
   int warp = blockIdx.x * (blockDim.x >> 5) + wib;
   if (warp >= nleaf) return;
-  const T *Lv = Lleaf + (size_t)warp * ld;
-  for (int k = lane; k < K; k += 32) cf[4 * k] = Lv[k];
-  __syncwarp();
-  gradient_row_coeffs<T>(P, cf, cf + 1, cf + 2, cf + 3, lane, 32, 4);
-  __syncwarp();
+  l2p_stage_leaf<T>(P, K, Lleaf + (size_t)warp * ld, reinterpret_cast<T *>(cc), lane);
   int b = leaf_start[warp], e = leaf_start[warp + 1];
   T inv_s = T(1) / s;
   for (int a = b + lane; a < e; a += 32) {
     V pt = part[a];
-    T f = 0, gx = 0, gy = 0, gz = 0;
-    // sum over m of X_lm conj(R_lm) = X_l0 R_l0 + 2 sum_{m>0} (Xr Rr + Xi Ri)
-    rt_columns<T>(P, pt.x * inv_s, pt.y * inv_s, pt.z * inv_s, [&](int l, int m, T re, T im) {
-      const int k = ridx(l, m);
-      const V c0 = cc[k];
-      if (m == 0) {
-        f += c0.x * re;
-        if (l < P) { gx += c0.y * re; gy += c0.z * re; gz += c0.w * re; }
-      } else {
-        const V c1 = cc[k + 1];
-        f += T(2) * (c0.x * re + c1.x * im);
-        if (l < P) {
-          gx += T(2) * (c0.y * re + c1.y * im);
-          gy += T(2) * (c0.z * re + c1.z * im);
-          gz += T(2) * (c0.w * re + c1.w * im);
-        }
-      }
-    });
+    T f, gx, gy, gz;
+    l2p_point<T, PP>(P, cc, pt.x * inv_s, pt.y * inv_s, pt.z * inv_s, f, gx, gy, gz);
     phi[a] = f * inv_s;
     grad[3 * (size_t)a + 0] = gx * inv_s * inv_s;
     grad[3 * (size_t)a + 1] = gy * inv_s * inv_s;
@@ -1148,6 +1163,295 @@ __global__ void __launch_bounds__(NT) k_p2p(int nb, T c2, T half_L, T s_leaf, T 
     for (int w = 0; w < NT / 32; ++w) v += ered[w];
     energy_part[leaf] = v;
   }
+}
+
+// ---------------------------------------------------------------------------
+// 6b. Near field by Newton's third law (single precision).  Every unordered
+//     pair of atoms in neighbouring leaves is evaluated once.  The block of
+//     target leaf A takes the atoms of the 13 neighbours B = A + o of the
+//     forward half shell (o > 0 in (z, y, x) lexicographic order; neighbour
+//     k = 14 ... 26 of the 3 x 3 x 3 stencil, periodic images included) and,
+//     target side only, the ordered pairs inside A.  A's sums end in phi_s /
+//     grad_s; the sums of B's atoms go to slot k - 14 of those atoms
+//     (slots[k - 14][N], one float4 {phi, grad} per atom), each slot written
+//     by exactly one block.  k_l2p_near adds own sums, the 13 slots, the far
+//     field and the dipole / background term in a fixed order, so results are
+//     bitwise reproducible.
+//
+//     Work split: the block stages up to kN3Src sources (shifted to A's frame)
+//     and up to kN3Tgt targets.  The staged list is cut into chunks of 32
+//     sources (the half shell's, then A's own), dealt round-robin to the
+//     warps; a warp takes every target block of TB atoms (in registers)
+//     against each of its chunks, so the sum of a staged source over all
+//     targets stays in one lane (accumulated in target-block order), and the
+//     TB x 4 target sums are reduce-scattered over the lanes once per target
+//     block and warp, then summed over the warps in warp order.  One barrier
+//     per pass: no warp waits for another between target blocks.
+// ---------------------------------------------------------------------------
+constexpr int kN3Src = 512;  // staged sources per pass
+constexpr int kN3Tgt = 64;   // targets per chunk
+constexpr int kN3Slots = 13;
+
+template <int NW>
+constexpr size_t n3_smem_bytes() {
+  // src, ssum [kN3Src] float4; tgt [kN3Tgt] float4; tpart [NW][4 kN3Tgt]
+  // floats; tsum [kN3Tgt] float4; sidx, sk [kN3Src] ints
+  return sizeof(float4) * (2 * (size_t)kN3Src + 2 * kN3Tgt) + sizeof(float) * 4 * kN3Tgt * NW +
+         2 * sizeof(int) * kN3Src;
+}
+
+// V (a power of two, 4 <= V <= 32) values per lane summed over the warp; lane
+// l returns the total of value l / (32 / V) (pairwise halving: at offset o a
+// lane keeps the upper half of its values if bit o of its lane is set and
+// sends the other half to lane l ^ o)
+template <int V>
+__device__ __forceinline__ float warp_reduce_scatter(float (&v)[V], int lane) {
+#pragma unroll
+  for (int h = V / 2, o = 16; h >= 1; h >>= 1, o >>= 1) {
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < h; ++i) {
+      const float send = up ? v[i] : v[i + h];
+      const float keep = up ? v[i + h] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffff, send, o);
+    }
+  }
+  float x = v[0];
+#pragma unroll
+  for (int o = 16 / V; o >= 1; o >>= 1) x += __shfl_xor_sync(0xffffffff, x, o);
+  return x;
+}
+
+template <int TB, int NT>
+__global__ void __launch_bounds__(NT, (TB == 4) ? 5 : 4) k_p2p_n3(int nb, float s_leaf, int64_t N,
+                                                                const int *__restrict__ leaf_start,
+                                                                const float4 *__restrict__ part,
+                                                                float *__restrict__ own_phi,
+                                                                float *__restrict__ own_grad,
+                                                                float4 *__restrict__ slots) {
+  constexpr int NW = NT / 32;
+  constexpr int V = 4 * TB;  // per-lane target sums: {phi, gx, gy, gz} x TB
+  static_assert(V == 16 || V == 32, "TB must be 4 or 8");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float4 *src = reinterpret_cast<float4 *>(smem_raw);
+  float4 *ssum = src + kN3Src;         // [kN3Src] a staged source's sum over the chunk's targets
+  float4 *tgt = ssum + kN3Src;         // [kN3Tgt] the chunk's targets
+  float4 *tsum = tgt + kN3Tgt;         // [kN3Tgt] target sums over the passes
+  float *tpart = reinterpret_cast<float *>(tsum + kN3Tgt);  // [NW][4 kN3Tgt] per-warp target sums
+  int *sidx = reinterpret_cast<int *>(tpart + 4 * kN3Tgt * NW);  // sorted index of each staged source
+  int *sk = sidx + kN3Src;                                       // its slot
+  __shared__ int nb_start[14], nb_pre[15];                       // 13 forward neighbours, then A
+  const int leaf = blockIdx.x, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const float s = s_leaf;
+  const int ix = (int)d_compact(leaf), iy = (int)d_compact(leaf >> 1), iz = (int)d_compact(leaf >> 2);
+  if (tid < 14) {
+    int n = leaf;
+    if (tid < 13) {
+      const int k = 14 + tid;
+      n = (int)d_morton(wrapi(ix + k % 3 - 1, nb), wrapi(iy + (k / 3) % 3 - 1, nb), wrapi(iz + k / 9 - 1, nb));
+    }
+    nb_start[tid] = leaf_start[n];
+    nb_pre[tid + 1] = leaf_start[n + 1] - leaf_start[n];
+  }
+  __syncthreads();
+  if (tid == 0) {
+    nb_pre[0] = 0;
+    for (int k = 0; k < 14; ++k) nb_pre[k + 1] += nb_pre[k];
+  }
+  __syncthreads();
+  const int a0 = nb_start[13], nt = nb_pre[14] - nb_pre[13];
+  const int n_fwd = nb_pre[13], n_all = nb_pre[14];
+  if (nt == 0) {
+    // no targets: the forward neighbours' slots from this leaf are zero
+    for (int k = warp; k < kN3Slots; k += NW)
+      for (int i = lane; i < nb_pre[k + 1] - nb_pre[k]; i += 32)
+        slots[(size_t)k * N + nb_start[k] + i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    return;
+  }
+  for (int c0 = 0; c0 < nt; c0 += kN3Tgt) {
+    const int nct = min(kN3Tgt, nt - c0);
+    const int ntb = (nct + TB - 1) / TB;
+    for (int s0 = 0; s0 < n_all; s0 += kN3Src) {
+      const int ns = min(kN3Src, n_all - s0);
+      const int ns3 = max(0, min(ns, n_fwd - s0));  // staged sources of the half shell
+      __syncthreads();  // the previous pass is done with every buffer
+      // the chunk's targets, padding far away and without charge; then the
+      // sources: staged index d = nb_pre[k] + i - s0, one thread per source
+      for (int i = tid; i < ntb * TB; i += NT)
+        tgt[i] = i < nct ? part[a0 + c0 + i] : make_float4(1e3f, 1e3f, 1e3f, 0.f);
+      for (int d = tid; d < ns; d += NT) {
+        const int g = s0 + d;
+        int k = 0;
+        while (g >= nb_pre[k + 1]) ++k;
+        const int kk = k < 13 ? 14 + k : 13;
+        float4 v = part[nb_start[k] + g - nb_pre[k]];
+        v.x += (float)(kk % 3 - 1) * s;
+        v.y += (float)((kk / 3) % 3 - 1) * s;
+        v.z += (float)(kk / 9 - 1) * s;
+        src[d] = v;
+        sidx[d] = nb_start[k] + g - nb_pre[k];
+        sk[d] = k;
+      }
+      __syncthreads();
+      const int nc3 = (ns3 + 31) >> 5, nch = nc3 + ((ns - ns3 + 31) >> 5);
+      for (int tb = 0; tb < ntb; ++tb) {
+        float4 t[TB];
+        float acc[V];
+#pragma unroll
+        for (int u = 0; u < TB; ++u) t[u] = tgt[tb * TB + u];
+#pragma unroll
+        for (int i = 0; i < V; ++i) acc[i] = 0.f;
+        for (int c = warp; c < nch; c += NW) {
+          if (c < nc3) {
+            // half shell: both sides of every pair
+            const int j = 32 * c + lane;
+            if (j < ns3) {
+              const float4 v = src[j];
+              float sf = 0.f, sx = 0.f, sy = 0.f, sz = 0.f;
+#pragma unroll
+              for (int u = 0; u < TB; ++u) {
+                const float dx = t[u].x - v.x, dy = t[u].y - v.y, dz = t[u].z - v.z;
+                const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+                const float ri = rsqrt_ftz(r2);
+                const float ri3 = ri * ri * ri;
+                const float b = v.w * ri3, e = t[u].w * ri3;
+                acc[4 * u + 0] = fmaf(v.w, ri, acc[4 * u + 0]);
+                acc[4 * u + 1] = fmaf(-b, dx, acc[4 * u + 1]);
+                acc[4 * u + 2] = fmaf(-b, dy, acc[4 * u + 2]);
+                acc[4 * u + 3] = fmaf(-b, dz, acc[4 * u + 3]);
+                sf = fmaf(t[u].w, ri, sf);
+                sx = fmaf(e, dx, sx);
+                sy = fmaf(e, dy, sy);
+                sz = fmaf(e, dz, sz);
+              }
+              // this lane owns source j in every target block: in-place sum
+              if (tb == 0) {
+                ssum[j] = make_float4(sf, sx, sy, sz);
+              } else {
+                float4 o = ssum[j];
+                o.x += sf; o.y += sx; o.z += sy; o.w += sz;
+                ssum[j] = o;
+              }
+            }
+          } else {
+            // pairs inside A: every ordered pair but the atom itself, target side
+            const int j = ns3 + 32 * (c - nc3) + lane;
+            if (j < ns) {
+              const float4 v = src[j];
+              const int ja = s0 + j - n_fwd;  // index of the source in A
+#pragma unroll
+              for (int u = 0; u < TB; ++u) {
+                const float dx = t[u].x - v.x, dy = t[u].y - v.y, dz = t[u].z - v.z;
+                const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+                const float ri = (c0 + tb * TB + u == ja) ? 0.f : rsqrt_ftz(r2);
+                const float b = v.w * ri * ri * ri;
+                acc[4 * u + 0] = fmaf(v.w, ri, acc[4 * u + 0]);
+                acc[4 * u + 1] = fmaf(-b, dx, acc[4 * u + 1]);
+                acc[4 * u + 2] = fmaf(-b, dy, acc[4 * u + 2]);
+                acc[4 * u + 3] = fmaf(-b, dz, acc[4 * u + 3]);
+              }
+            }
+          }
+        }
+        const float tot = warp_reduce_scatter<V>(acc, lane);
+        // lane l holds value l / (32 / V): target tb TB + value / 4, component value % 4
+        if ((lane & (32 / V - 1)) == 0) tpart[warp * 4 * kN3Tgt + tb * V + lane / (32 / V)] = tot;
+      }
+      __syncthreads();
+      // the targets' sums over the warps (warp order), after earlier passes
+      for (int i = tid; i < 4 * nct; i += NT) {
+        float v = tpart[i];
+        for (int w = 1; w < NW; ++w) v += tpart[w * 4 * kN3Tgt + i];
+        float *o = reinterpret_cast<float *>(tsum) + i;
+        *o = (s0 == 0) ? v : *o + v;
+      }
+      // slots: the first target chunk writes them, later chunks add
+      for (int j = tid; j < ns3; j += NT) {
+        float4 *p = slots + (size_t)sk[j] * N + sidx[j];
+        float4 a = ssum[j];
+        if (c0 > 0) {
+          const float4 o = *p;
+          a.x = o.x + a.x; a.y = o.y + a.y; a.z = o.z + a.z; a.w = o.w + a.w;
+        }
+        *p = a;
+      }
+    }
+    __syncthreads();
+    for (int i = tid; i < nct; i += NT) {
+      const int a = a0 + c0 + i;
+      const float4 v = tsum[i];
+      own_phi[a] = v.x;
+      own_grad[3 * (size_t)a + 0] = v.y;
+      own_grad[3 * (size_t)a + 1] = v.z;
+      own_grad[3 * (size_t)a + 2] = v.w;
+    }
+  }
+}
+
+// Far field (L2P) fused with the end of the near field: per atom, its own
+// near sums (phi_s, grad_s from k_p2p_n3) + the 13 slots in order + the far
+// field + the dipole / background term, times the Coulomb constant; writes the
+// total potential to phi_s, the force (original order) and the leaf's energy
+// partial.  One warp per leaf.
+template <int PP, typename FT>
+__global__ void __launch_bounds__(128, 6) k_l2p_near(int nleaf, int Pr, int ld, float s, int64_t N, float c2,
+                                                     float half_L, float fc, const int *__restrict__ leaf_start,
+                                                     const float4 *__restrict__ part, const float *__restrict__ Lleaf,
+                                                     const int *__restrict__ perm, const double *__restrict__ mom,
+                                                     const float4 *__restrict__ slots, float *__restrict__ phi_s,
+                                                     const float *__restrict__ grad_s, FT *__restrict__ forces,
+                                                     double *__restrict__ energy_part) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int P = PP > 0 ? PP : Pr;
+  const int K = (P + 1) * (P + 1);
+  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float4 *cc = reinterpret_cast<float4 *>(smem_raw) + (size_t)wib * K;
+  const int leaf = blockIdx.x * (blockDim.x >> 5) + wib;
+  if (leaf >= nleaf) return;
+  l2p_stage_leaf<float>(P, K, Lleaf + (size_t)leaf * ld, reinterpret_cast<float *>(cc), lane);
+  // dipole / background term as in k_p2p: K0 + K1.m + K2 |m|^2 about the leaf centre
+  const int ix = (int)d_compact(leaf), iy = (int)d_compact(leaf >> 1), iz = (int)d_compact(leaf >> 2);
+  const float A = c2 * (float)mom[0], C = c2 * (float)mom[4];
+  const float Bx = 2.f * c2 * (float)mom[1], By = 2.f * c2 * (float)mom[2], Bz = 2.f * c2 * (float)mom[3];
+  const float lcx = ((float)ix + 0.5f) * s - half_L, lcy = ((float)iy + 0.5f) * s - half_L,
+              lcz = ((float)iz + 0.5f) * s - half_L;
+  const float k0 = A * (lcx * lcx + lcy * lcy + lcz * lcz) - (Bx * lcx + By * lcy + Bz * lcz) + C;
+  const float k1 = 2.f * A * lcx - Bx, k2 = 2.f * A * lcy - By, k3 = 2.f * A * lcz - Bz, k4 = A;
+  const int b = leaf_start[leaf], e = leaf_start[leaf + 1];
+  const float inv_s = 1.f / s;
+  SiteAccE<float> e_acc;
+  for (int a = b + lane; a < e; a += 32) {
+    const float4 me = part[a];
+    float ff = phi_s[a], g0 = grad_s[3 * (size_t)a], g1 = grad_s[3 * (size_t)a + 1], g2 = grad_s[3 * (size_t)a + 2];
+#pragma unroll
+    for (int k = 0; k < kN3Slots; ++k) {
+      const float4 v = slots[(size_t)k * N + a];
+      ff += v.x; g0 += v.y; g1 += v.z; g2 += v.w;
+    }
+    float f, gx, gy, gz;
+    l2p_point<float, PP>(P, cc, me.x * inv_s, me.y * inv_s, me.z * inv_s, f, gx, gy, gz);
+    ff += f * inv_s;
+    g0 += gx * inv_s * inv_s;
+    g1 += gy * inv_s * inv_s;
+    g2 += gz * inv_s * inv_s;
+    const float mx = me.x, my = me.y, mz = me.z;
+    ff += k0 + k1 * mx + k2 * my + k3 * mz + k4 * (mx * mx + my * my + mz * mz);
+    g0 += k1 + 2.f * k4 * mx;
+    g1 += k2 + 2.f * k4 * my;
+    g2 += k3 + 2.f * k4 * mz;
+    ff *= fc; g0 *= fc; g1 *= fc; g2 *= fc;
+    const float q = me.w;
+    phi_s[a] = ff;
+    e_acc.add(0.5f * q * ff);
+    if (forces) {
+      const int io = perm[a];
+      forces[3 * (size_t)io + 0] = (FT)(-q * g0);
+      forces[3 * (size_t)io + 1] = (FT)(-q * g1);
+      forces[3 * (size_t)io + 2] = (FT)(-q * g2);
+    }
+  }
+  e_acc.warp_reduce();
+  if (lane == 0) energy_part[leaf] = e_acc.value();
 }
 
 // ---------------------------------------------------------------------------
@@ -1783,6 +2087,162 @@ __device__ __forceinline__ void m2p_high2(const T *__restrict__ M, T x0, T y0, T
   v1 = acc1;
 }
 
+// The atoms of a site (block-wide): sorted index, leaf, stored particle and
+// FP64 position, the latter as the minimum images around the first atom (a
+// site may straddle the box faces; the periodic decomposition holds at any
+// position, and the leaf index used by the direct sums moves with the image).
+template <typename V>
+__device__ __forceinline__ void site_load_atoms(int n, const int *__restrict__ atoms, int d, double L,
+                                                const int *__restrict__ inv_perm, const int *__restrict__ leaf_start,
+                                                const V *__restrict__ part, double (*pa)[3], int (*aI)[3], V *me,
+                                                int *sa_s) {
+  const int nb = 1 << d;
+  const double sl = L / nb;
+  for (int a = threadIdx.x; a < n; a += blockDim.x) {
+    const int i = atoms[a], sa = inv_perm[i];
+    int lo = 0, hi = (1 << (3 * d)) - 1;  // leaf of sorted position sa
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (leaf_start[mid] <= sa) lo = mid; else hi = mid - 1;
+    }
+    const V v = part[sa];
+    if (me) me[a] = v;
+    if (sa_s) sa_s[a] = sa;
+    aI[a][0] = (int)d_compact(lo); aI[a][1] = (int)d_compact(lo >> 1); aI[a][2] = (int)d_compact(lo >> 2);
+    pa[a][0] = (aI[a][0] + 0.5) * sl + (double)v.x;
+    pa[a][1] = (aI[a][1] + 0.5) * sl + (double)v.y;
+    pa[a][2] = (aI[a][2] + 0.5) * sl + (double)v.z;
+  }
+  __syncthreads();
+  for (int a = threadIdx.x; a < n; a += blockDim.x) {
+    if (a == 0) continue;
+    for (int k = 0; k < 3; ++k) {
+      const double dk = rint((pa[a][k] - pa[0][k]) / L);
+      pa[a][k] -= dk * L;
+      aI[a][k] -= (int)dk * nb;
+    }
+  }
+  __syncthreads();
+}
+
+// centroid c and radius R of the site's atoms (thread 0; the caller syncs)
+__device__ __forceinline__ void site_centre(int n, const double (*pa)[3], double *cen) {
+  double c[3] = {0, 0, 0};
+  for (int a = 0; a < n; ++a)
+    for (int k = 0; k < 3; ++k) c[k] += pa[a][k];
+  for (int k = 0; k < 3; ++k) c[k] /= n;
+  double R = 0.0;
+  for (int a = 0; a < n; ++a) {
+    const double dx = pa[a][0] - c[0], dy = pa[a][1] - c[1], dz = pa[a][2] - c[2];
+    R = fmax(R, sqrt(dx * dx + dy * dy + dz * dz));
+  }
+  cen[0] = c[0]; cen[1] = c[1]; cen[2] = c[2]; cen[3] = R;
+}
+
+// One level l of the separation-controlled traversal (block-wide): the
+// frontier fa[0, n0) becomes the list `sep` of separated boxes and direct
+// leaves (bit 31 set) and the children of the opened boxes, the next frontier
+// (back in fa; n0 becomes its size, 0 below the leaves).  A box of circumradius
+// a at distance D from the centre c is separated if a < theta (D - R).  Returns
+// the list length.  Capacity overflows are recorded in the status word and
+// the traversal goes on with the entries that fit (all accesses stay in bounds).
+__device__ int site_classify_level(int l, int d, int *fa, int *fb, int *sep, int &n0, int *wsum, int &scan_par,
+                                   float cfx, float cfy, float cfz, float Rf, float Lf, float theta, int fcap,
+                                   int *status) {
+  const int tid = threadIdx.x;
+  const float sf = ldexpf(Lf, -l), a_l = 0.86602540378443865f * sf, th = theta;
+  int nsep = 0, n1 = 0;
+  for (int t0 = 0; t0 < n0; t0 += blockDim.x) {
+    const int t = t0 + tid;
+    int kind = -1;  // 0 separated, 1 direct leaf, 2 open
+    int e = 0;
+    if (t < n0) {
+      e = fa[t];
+      const int box = e >> 9, img = e & 511;
+      const int nx = img / 49 - 3, ny = (img / 7) % 7 - 3, nz = img % 7 - 3;
+      const float dx = cfx - (((float)d_compact(box) + 0.5f) * sf + (float)nx * Lf),
+                  dy = cfy - (((float)d_compact(box >> 1) + 0.5f) * sf + (float)ny * Lf),
+                  dz = cfz - (((float)d_compact(box >> 2) + 0.5f) * sf + (float)nz * Lf);
+      const float D = sqrtf(dx * dx + dy * dy + dz * dz);
+      if (a_l < th * (D - Rf) * 0.9999f) kind = 0;
+      else if (l == d) kind = 1;
+      else kind = 2;
+    }
+    // one scan for both lists: separated / direct entries in the low 16
+    // bits, the 8 children of an opened box in the high 16 (a chunk of at
+    // most 1024 threads adds at most 8192 children)
+    int tot;
+    const int off = block_scan((kind == 0 || kind == 1) ? 1 : (kind == 2 ? (8 << 16) : 0), wsum, scan_par, &tot);
+    scan_par ^= 1;
+    const int osep = off & 0xffff, oopen = off >> 16;
+    if ((kind == 0 || kind == 1) && nsep + osep < fcap) sep[nsep + osep] = (kind == 1) ? (e | (1 << 31)) : e;
+    nsep += tot & 0xffff;
+    if (kind == 2) {
+      const int box = e >> 9, img = e & 511;
+      for (int c = 0; c < 8; ++c)
+        if (n1 + oopen + c < fcap) fb[n1 + oopen + c] = pack_entry(8 * box + c, img);
+    }
+    n1 += tot >> 16;
+  }
+  if (nsep > fcap || n1 > fcap) {
+    if (tid == 0) *(volatile int *)(status + kStatusSiteOverflow) = 1;
+    nsep = min(nsep, fcap);
+    n1 = min(n1, fcap);
+  }
+  __syncthreads();
+  for (int t = tid; t < n1; t += blockDim.x) fa[t] = fb[t];
+  n0 = (l < d) ? n1 : 0;
+  __syncthreads();
+  return nsep;
+}
+
+// The traversal lists of every compact site (radius at most two leaf edges),
+// computed once per evaluation from the geometry alone: the site's centre and
+// radius and the box centres, so they are built on the side stream right after
+// the sort, while the main stream runs P2M and M2M.  One block per site.
+// lists[(site (d + 1) + l) fcap + i]: level l's separated boxes and direct
+// leaves; counts[site (d + 2) + l]: their numbers (counts[site (d + 2)] = -1
+// marks a spread site, which k_site_phi traverses atom by atom itself);
+// cen_out[4 site ...]: the centre and radius.
+template <typename T>
+__global__ void __launch_bounds__(kSiteThreads) k_site_lists(
+    int S, const int *__restrict__ site_ptr, const int *__restrict__ site_atoms, int d, double L,
+    const int *__restrict__ leaf_start, const int *__restrict__ inv_perm, const typename V4<T>::type *__restrict__ part,
+    float theta, int fcap, int *__restrict__ lists, int *__restrict__ counts, double *__restrict__ cen_out,
+    int *__restrict__ status) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  int *fa = reinterpret_cast<int *>(smem_raw), *fb = fa + fcap;
+  __shared__ double pa[kMaxSiteAtoms][3], cen[4];
+  __shared__ int aI[kMaxSiteAtoms][3], wsum[64];
+  const int site = blockIdx.x, tid = threadIdx.x;
+  if (site >= S) return;
+  const int b0 = site_ptr[site], n = site_ptr[site + 1] - b0;
+  if (n <= 0 || n > kMaxSiteAtoms) return;  // rejected when the site map is set
+  site_load_atoms(n, site_atoms + b0, d, L, inv_perm, leaf_start, part, pa, aI,
+                  (typename V4<T>::type *)nullptr, (int *)nullptr);
+  if (tid == 0) site_centre(n, pa, cen);
+  __syncthreads();
+  int *cnt = counts + (size_t)site * (d + 2);
+  if (tid < 4) cen_out[4 * (size_t)site + tid] = cen[tid];
+  const double sl = L / (1 << d);
+  if (cen[3] > 2.0 * sl) {  // spread site
+    if (tid == 0) cnt[0] = -1;
+    return;
+  }
+  for (int t = tid; t < 343 && t < fcap; t += blockDim.x) fa[t] = pack_entry(0, t);  // root images
+  if (fcap < 343 && tid == 0) *(volatile int *)(status + kStatusSiteOverflow) = 1;
+  __syncthreads();
+  int n0 = min(343, fcap), scan_par = 0;
+  const float cfx = (float)cen[0], cfy = (float)cen[1], cfz = (float)cen[2], Lf = (float)L, Rf = (float)cen[3];
+  for (int l = 0; l <= d; ++l) {
+    int ns = 0;
+    if (n0 > 0)
+      ns = site_classify_level(l, d, fa, fb, lists + ((size_t)site * (d + 1) + l) * fcap, n0, wsum, scan_par, cfx,
+                               cfy, cfz, Rf, Lf, theta, fcap, status);
+    if (tid == 0) cnt[l] = ns;
+  }
+}
+
 template <typename T, int PP>
 __global__ void __launch_bounds__(kSiteThreads, 3) k_site_phi(
     int S, int G, const int *__restrict__ site_ptr, const int *__restrict__ site_atoms, int d, int P, int ld,
@@ -1790,7 +2250,8 @@ __global__ void __launch_bounds__(kSiteThreads, 3) k_site_phi(
     const int *__restrict__ inv_perm, const typename V4<T>::type *__restrict__ part, const T *__restrict__ M,
     const double *__restrict__ qd, const float *__restrict__ qdf, const double *__restrict__ mom,
     const double *__restrict__ Lh3, double *__restrict__ phi_part, int *__restrict__ status, float theta, int fcap,
-    uint64_t wait_ns) {
+    uint64_t wait_ns, const int *__restrict__ pre_lists, const int *__restrict__ pre_counts,
+    const double *__restrict__ pre_cen) {
   using V = typename V4<T>::type;
   // charge/dipole rows as staged: (hi, lo) float pairs in single precision,
   // FP64 otherwise; 32 bytes either way
@@ -1830,34 +2291,7 @@ __global__ void __launch_bounds__(kSiteThreads, 3) k_site_phi(
     s_abort = 0;
     fence_mbar_init();
   }
-  for (int a = tid; a < n; a += blockDim.x) {
-    const int i = site_atoms[b0 + a], sa = inv_perm[i];
-    int lo = 0, hi = (1 << (3 * d)) - 1;  // leaf of sorted position sa
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (leaf_start[mid] <= sa) lo = mid; else hi = mid - 1;
-    }
-    const V v = part[sa];
-    me[a] = v;
-    sa_s[a] = sa;
-    aI[a][0] = (int)d_compact(lo); aI[a][1] = (int)d_compact(lo >> 1); aI[a][2] = (int)d_compact(lo >> 2);
-    pa[a][0] = (aI[a][0] + 0.5) * sl + (double)v.x;
-    pa[a][1] = (aI[a][1] + 0.5) * sl + (double)v.y;
-    pa[a][2] = (aI[a][2] + 0.5) * sl + (double)v.z;
-  }
-  __syncthreads();
-  // represent the site by its minimum images around its first atom (a site may
-  // straddle the box faces); the periodic decomposition holds at any position,
-  // and the leaf index used by the direct sums moves with the image
-  for (int a = tid; a < n; a += blockDim.x) {
-    if (a == 0) continue;
-    for (int k = 0; k < 3; ++k) {
-      const double dk = rint((pa[a][k] - pa[0][k]) / L);
-      pa[a][k] -= dk * L;
-      aI[a][k] -= (int)dk * nb;
-    }
-  }
-  __syncthreads();
+  site_load_atoms(n, site_atoms + b0, d, L, inv_perm, leaf_start, part, pa, aI, me, sa_s);
   {
     constexpr int EPV = 16 / sizeof(T);
     const int per_row = ld / EPV;
@@ -1880,20 +2314,18 @@ __global__ void __launch_bounds__(kSiteThreads, 3) k_site_phi(
   // atoms scattered over the box) would have to open nearly every box near
   // any of them, so each of its atoms then takes its own traversal (a group
   // of one atom about itself).  All blocks of a site take the same decision.
+  // A compact site's lists may have been built by k_site_lists (pre).
+  const int *pcnt = pre_counts ? pre_counts + (size_t)site * (d + 2) : nullptr;
+  const bool pre = pcnt && pcnt[0] >= 0;
   if (tid == 0) {
-    double c[3] = {0, 0, 0};
-    for (int a = 0; a < n; ++a)
-      for (int k = 0; k < 3; ++k) c[k] += pa[a][k];
-    for (int k = 0; k < 3; ++k) c[k] /= n;
-    double R = 0.0;
-    for (int a = 0; a < n; ++a) {
-      const double dx = pa[a][0] - c[0], dy = pa[a][1] - c[1], dz = pa[a][2] - c[2];
-      R = fmax(R, sqrt(dx * dx + dy * dy + dz * dz));
+    if (pre) {
+      for (int k = 0; k < 4; ++k) cen[k] = pre_cen[4 * (size_t)site + k];
+    } else {
+      site_centre(n, pa, cen);
     }
-    cen[0] = c[0]; cen[1] = c[1]; cen[2] = c[2]; cen[3] = R;
   }
   __syncthreads();
-  const bool spread = cen[3] > 2.0 * sl;
+  const bool spread = !pre && cen[3] > 2.0 * sl;
   const int ngroups = spread ? n : 1;
   // phase parity of the next completion of sbar[0] / sbar[1] (the barriers
   // run on over the groups)
@@ -1911,8 +2343,10 @@ __global__ void __launch_bounds__(kSiteThreads, 3) k_site_phi(
     pu[a][0] = (T)ux; pu[a][1] = (T)uy; pu[a][2] = (T)uz;
     puu[a] = (T)(ux * ux + uy * uy + uz * uz);
   }
-  for (int t = tid; t < 343 && t < fcap; t += blockDim.x) fa[t] = pack_entry(0, t);  // root images
-  if (fcap < 343 && tid == 0) *(volatile int *)(status + kStatusSiteOverflow) = 1;  // capacity below the root images
+  if (!pre) {
+    for (int t = tid; t < 343 && t < fcap; t += blockDim.x) fa[t] = pack_entry(0, t);  // root images
+    if (fcap < 343 && tid == 0) *(volatile int *)(status + kStatusSiteOverflow) = 1;  // capacity below the root images
+  }
   __syncthreads();
   // thread -> (atom pair, slot), fixed for the whole traversal; a slot takes
   // the rows slot, slot + nslot, ... of every batch
@@ -1943,54 +2377,15 @@ __global__ void __launch_bounds__(kSiteThreads, 3) k_site_phi(
   // direct leaves (sep0 / sep1 by the parity of l) and the children of the
   // opened boxes, the next frontier
   auto classify = [&](int l) {
-    int *sep = (l & 1) ? sep1 : sep0;
-    const float sf = ldexpf(Lf, -l), a_l = 0.86602540378443865f * sf, th = theta;
-    int nsep = 0, n1 = 0;
-    for (int t0 = 0; t0 < n0; t0 += blockDim.x) {
-      const int t = t0 + tid;
-      int kind = -1;  // 0 separated, 1 direct leaf, 2 open
-      int e = 0;
-      if (t < n0) {
-        e = fa[t];
-        const int box = e >> 9, img = e & 511;
-        const int nx = img / 49 - 3, ny = (img / 7) % 7 - 3, nz = img % 7 - 3;
-        const float dx = cfx - (((float)d_compact(box) + 0.5f) * sf + (float)nx * Lf),
-                    dy = cfy - (((float)d_compact(box >> 1) + 0.5f) * sf + (float)ny * Lf),
-                    dz = cfz - (((float)d_compact(box >> 2) + 0.5f) * sf + (float)nz * Lf);
-        const float D = sqrtf(dx * dx + dy * dy + dz * dz);
-        if (a_l < th * (D - (float)Rf) * 0.9999f) kind = 0;
-        else if (l == d) kind = 1;
-        else kind = 2;
-      }
-      // one scan for both lists: separated / direct entries in the low 16
-      // bits, the 8 children of an opened box in the high 16 (a chunk of at
-      // most 1024 threads adds at most 8192 children)
-      int tot;
-      const int off = block_scan((kind == 0 || kind == 1) ? 1 : (kind == 2 ? (8 << 16) : 0), wsum, scan_par, &tot);
-      scan_par ^= 1;
-      const int osep = off & 0xffff, oopen = off >> 16;
-      if ((kind == 0 || kind == 1) && nsep + osep < fcap) sep[nsep + osep] = (kind == 1) ? (e | (1 << 31)) : e;
-      nsep += tot & 0xffff;
-      if (kind == 2) {
-        const int box = e >> 9, img = e & 511;
-        for (int c = 0; c < 8; ++c)
-          if (n1 + oopen + c < fcap) fb[n1 + oopen + c] = pack_entry(8 * box + c, img);
-      }
-      n1 += tot >> 16;
+    int ns = 0;
+    if (pre) {
+      ns = pcnt[l];
+    } else {
+      ns = site_classify_level(l, d, fa, fb, (l & 1) ? sep1 : sep0, n0, wsum, scan_par, cfx, cfy, cfz, (float)Rf, Lf,
+                               theta, fcap, status);
     }
-    if (nsep > fcap || n1 > fcap) {
-      // list capacity exceeded: recorded in the handle's status word; the
-      // traversal goes on with the entries that fit (all accesses stay in bounds)
-      if (tid == 0) *(volatile int *)(status + kStatusSiteOverflow) = 1;
-      nsep = min(nsep, fcap);
-      n1 = min(n1, fcap);
-    }
-    __syncthreads();
-    for (int t = tid; t < n1; t += blockDim.x) fa[t] = fb[t];
-    n0 = (l < d) ? n1 : 0;
-    if (l & 1) ns1 = nsep; else ns0 = nsep;
+    if (l & 1) ns1 = ns; else ns0 = ns;
     lcl = l;
-    __syncthreads();
   };
   // the next batch of this block at or after (level gl, entry gb): level,
   // first entry and size; classifies a level on first use; false once the
@@ -2000,7 +2395,7 @@ __global__ void __launch_bounds__(kSiteThreads, 3) k_site_phi(
     for (;;) {
       if (gl > d) return false;
       if (gl > lcl) {
-        if (n0 <= 0) {
+        if (!pre && n0 <= 0) {
           gl = d + 1;
           return false;
         }
@@ -2029,7 +2424,7 @@ __global__ void __launch_bounds__(kSiteThreads, 3) k_site_phi(
   const uint32_t qrow_bytes = 32, mrow_bytes = (P >= 2) ? (uint32_t)(ld * sizeof(T)) : 0u;
   auto stage = [&](int buf, int bl, int bb, int bn) {
     if (warp != 0) return;
-    const int *sp = ((bl & 1) ? sep1 : sep0) + bb;
+    const int *sp = (pre ? pre_lists + ((size_t)site * (d + 1) + bl) * fcap : ((bl & 1) ? sep1 : sep0)) + bb;
     const bool res = bl <= 1;
     const int r0 = lane, r1 = lane + 32;
     const int e0 = (r0 < bn) ? sp[r0] : -1, e1 = (r1 < bn) ? sp[r1] : -1;
@@ -2340,7 +2735,7 @@ __global__ void k_patch_low_multipoles(int64_t nbox, int d, double L, int ld, co
 // main-stream intervals, then the two side-stream intervals (overlapping the
 // main stream: the sites' FP64 pair terms during binning/P2M/M2M, the refined
 // site-atom potential during L2L/L2P/P2P)
-static const char *kStageNames[] = {"bin", "sort", "p2m", "m2m", "lattice", "m2l", "l2l", "l2p", "p2p", "site",
+static const char *kStageNames[] = {"bin", "sort", "p2m", "m2m", "lattice", "m2l", "l2l", "near_pairs", "far_near_out", "site",
                                     "side_site_pairs", "side_site_potential"};
 const char *stage_name(int i) { return (i >= 0 && i < 12) ? kStageNames[i] : "?"; }
 int num_stages() { return 10; }
@@ -2431,6 +2826,48 @@ static cudaError_t launch_p2p(mahi_ctx *h, int nleaf, int nb, const double *mom,
   return cudaGetLastError();
 }
 
+static cudaError_t launch_p2p_n3(mahi_ctx *h, int nleaf, int nb, cudaStream_t st) {
+  constexpr int NT = 128;
+  constexpr size_t sm = n3_smem_bytes<NT / 32>();
+  static_assert(sm <= 227 * 1024, "near-field staging exceeds shared memory");
+  const float s_leaf = (float)(h->L / nb);
+  float *phi = (float *)h->phi_s, *grad = (float *)h->grad_s;
+  float4 *slots = (float4 *)h->nf_slots;
+  const float4 *part = (const float4 *)h->part;
+  cudaError_t e;
+  if (h->tune_p2p_targets == 4) {
+    e = cudaFuncSetAttribute(k_p2p_n3<4, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    k_p2p_n3<4, NT><<<nleaf, NT, sm, st>>>(nb, s_leaf, h->N, h->leaf_start, part, phi, grad, slots);
+  } else {
+    e = cudaFuncSetAttribute(k_p2p_n3<8, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    k_p2p_n3<8, NT><<<nleaf, NT, sm, st>>>(nb, s_leaf, h->N, h->leaf_start, part, phi, grad, slots);
+  }
+  return cudaGetLastError();
+}
+
+template <typename XT>
+static cudaError_t launch_l2p_near(mahi_ctx *h, int nleaf, int nb, const float *Lleaf, const double *mom, XT *forces,
+                                   cudaStream_t st) {
+  const int K = h->K, P = h->p, ld = h->ld;
+  const size_t per_warp = sizeof(float4) * (size_t)K;
+  const int wpb = (int)std::max<size_t>(1, std::min<size_t>(4, (40 * 1024) / per_warp));
+  const dim3 gl((nleaf + wpb - 1) / wpb), bl(32 * wpb);
+  const float s = (float)(h->L / nb), c2 = (float)(2.0 * kPi / (3.0 * h->L * h->L * h->L));
+  const float half_L = (float)(0.5 * h->L), fc = (float)coulomb_constant();
+  const float4 *part = (const float4 *)h->part, *slots = (const float4 *)h->nf_slots;
+  if (P == 12)
+    k_l2p_near<12, XT><<<gl, bl, per_warp * wpb, st>>>(nleaf, P, ld, s, h->N, c2, half_L, fc, h->leaf_start, part, Lleaf,
+                                                       h->perm, mom, slots, (float *)h->phi_s,
+                                                       (const float *)h->grad_s, forces, h->energy_part);
+  else
+    k_l2p_near<0, XT><<<gl, bl, per_warp * wpb, st>>>(nleaf, P, ld, s, h->N, c2, half_L, fc, h->leaf_start, part, Lleaf,
+                                                      h->perm, mom, slots, (float *)h->phi_s,
+                                                      (const float *)h->grad_s, forces, h->energy_part);
+  return cudaGetLastError();
+}
+
 template <typename T, typename XT>
 static cudaError_t eval_t(mahi_ctx *h, const XT *x, const double *lam, double *energy, XT *forces, double *dEdl) {
   using V = typename V4<T>::type;
@@ -2491,6 +2928,19 @@ static cudaError_t eval_t(mahi_ctx *h, const XT *x, const double *lam, double *e
   }
   MAHI_CK(cudaEventRecord(h->join_ev[0], h->side));
   h->launches += 4 + h->d;
+  // the compact sites' traversal lists (geometry only), on the side stream
+  // behind the box moments; the site-atom potential follows on that stream
+  const bool site_pre = h->S > 0 && h->site_lists && h->site_lists_cap >= h->site_list_cap;
+  if (site_pre) {
+    const size_t sml = 2 * sizeof(int) * (size_t)h->site_list_cap;
+    if (sml > 48 * 1024)
+      MAHI_CK(cudaFuncSetAttribute(k_site_lists<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sml));
+    k_site_lists<T><<<h->S, kSiteThreads, sml, h->side>>>(h->S, h->site_ptr, h->site_atoms, h->d, h->L, h->leaf_start,
+                                                          h->inv_perm, (const V *)h->part, h->site_theta,
+                                                          h->site_list_cap, h->site_lists, h->site_list_n,
+                                                          h->site_cen, h->status_dev);
+    h->launches += 1;
+  }
   MAHI_CK(cudaGetLastError());
   mark(h, 2);
   const double s_leaf = h->L / nb;
@@ -2567,7 +3017,8 @@ static cudaError_t eval_t(mahi_ctx *h, const XT *x, const double *lam, double *e
     MAHI_CK(launch_site_phi<T>(P, G, smp, h->side, h->S, G, h->site_ptr, h->site_atoms, h->d, P, ld, lds, nbmax, h->L,
                                h->d_level_off, h->leaf_start, h->inv_perm, (const V *)h->part, M, h->box_qd,
                                h->box_qdf, mom, h->L_h3, h->phi_part, h->status_dev, h->site_theta,
-                               h->site_list_cap, h->wait_limit_ns));
+                               h->site_list_cap, h->wait_limit_ns, site_pre ? h->site_lists : nullptr,
+                               site_pre ? h->site_list_n : nullptr, site_pre ? h->site_cen : nullptr));
     k_site_phi_sum<<<(h->n_site_atoms + 127) / 128, 128, 0, h->side>>>(h->n_site_atoms, G, coulomb_constant(),
                                                                         h->phi_part, h->phi_site);
     mark_side(h, 1, 1);
@@ -2579,32 +3030,36 @@ static cudaError_t eval_t(mahi_ctx *h, const XT *x, const double *lam, double *e
                                          (T *)h->gemm_ws, h->gemm_ws_elems, h->num_sms, st, h->launches)));
   }
   mark(h, 7);
-  {
+  const T *Lleaf = Lx + h->level_off[h->d] * ld;
+  if (std::is_same<T, float>::value && h->tune_p2p_targets > 0 && h->nf_slots) {
+    // near field over the half shell (both sides of every pair), then the far
+    // field fused with the near-field sums and the outputs
+    MAHI_CK((launch_p2p_n3(h, nleaf, nb, st)));
+    mark(h, 8);
+    MAHI_CK((launch_l2p_near<XT>(h, nleaf, nb, (const float *)Lleaf, mom, (XT *)forces, st)));
+    h->launches += 2;
+  } else {
     size_t per_warp = sizeof(T) * 4 * (size_t)K;
     int wpb = (int)std::max<size_t>(1, std::min<size_t>(4, (40 * 1024) / per_warp));
     const dim3 gl((nleaf + wpb - 1) / wpb), bl(32 * wpb);
     const T sl = (T)s_leaf;
-    const T *Ll = Lx + h->level_off[h->d] * ld;
     if (P == 12)
-      k_l2p<T, 12><<<gl, bl, per_warp * wpb, st>>>(nleaf, P, ld, sl, h->leaf_start, (const V *)h->part, Ll,
+      k_l2p<T, 12><<<gl, bl, per_warp * wpb, st>>>(nleaf, P, ld, sl, h->leaf_start, (const V *)h->part, Lleaf,
                                                     (T *)h->phi_s, (T *)h->grad_s);
     else
-      k_l2p<T, 0><<<gl, bl, per_warp * wpb, st>>>(nleaf, P, ld, sl, h->leaf_start, (const V *)h->part, Ll,
+      k_l2p<T, 0><<<gl, bl, per_warp * wpb, st>>>(nleaf, P, ld, sl, h->leaf_start, (const V *)h->part, Lleaf,
                                                    (T *)h->phi_s, (T *)h->grad_s);
-    h->launches += 1;
     MAHI_CK(cudaGetLastError());
-  }
-  mark(h, 8);
-  {
+    mark(h, 8);
     // threads per target leaf: 128 unless the autotuner picked another
     switch (h->tune_p2p_threads) {
       case 64: MAHI_CK((launch_p2p<T, XT, 64>(h, nleaf, nb, mom, forces, st))); break;
       case 256: MAHI_CK((launch_p2p<T, XT, 256>(h, nleaf, nb, mom, forces, st))); break;
       default: MAHI_CK((launch_p2p<T, XT, 128>(h, nleaf, nb, mom, forces, st))); break;
     }
-    h->launches += 1;
-    MAHI_CK(cudaGetLastError());
+    h->launches += 2;
   }
+  MAHI_CK(cudaGetLastError());
   mark(h, 9);
   if (h->S > 0) {
     MAHI_CK(cudaStreamWaitEvent(st, h->join_ev[1], 0));  // site-atom potential done

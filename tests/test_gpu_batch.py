@@ -97,6 +97,7 @@ def test_autotune_keeps_results():
     p2p, blocks = pkg.mahi_get_tuning(m.h)
     assert p2p in (64, 128, 256) and blocks in range(0, 17)
     assert m.get_option("p2p_threads") == p2p and m.get_option("site_blocks") == blocks
+    assert m.get_option("p2p_targets") in (8, 4, -1)
     assert m.get_option("m2l_single_tile") in (0, 1) and m.get_option("m2l_b_stages") in (0, 2, 3)
     E1, F1, g1 = m.eval(x, lam)
     torch.cuda.synchronize()

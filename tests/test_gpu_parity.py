@@ -231,3 +231,33 @@ def test_error_codes():
         m.set_charges(qA, qA, empty)
     assert ei.value.code == -2
     m.close()
+
+
+@pytest.mark.parametrize("case", ["water_d4", "dense_d1", "sparse_d3", "one_leaf_d0"])
+def test_near_field_schemes_agree(case, sysB):
+    """The half-shell near field (each unordered pair once, 8 or 4 targets per
+    thread) against every directed pair over the 27 neighbour leaves and the
+    oracle: the schemes differ only in the order of single-precision sums.
+    Cases: the 96,000-atom water box (~23 atoms per leaf); 3,000 charges in 8
+    leaves (~375 atoms each: several target chunks of 64 and source passes of
+    512, slots summed over the chunks); 30 charges in 512 leaves (empty leaves
+    and empty neighbours); one leaf (depth 0: the pairs with the 26 images of
+    the box itself)."""
+    if case == "water_d4":
+        s, ref = sysB
+    else:
+        n, L, d, dmin = {"dense_d1": (3000, 3.2, 1, 0.1), "sparse_d3": (30, 3.0, 3, 0.2),
+                         "one_leaf_d0": (400, 2.2, 0, 0.1)}[case]
+        s = synth.make_charges(n=n, L=L, n_sites=2, atoms_per_site=3, seed=21, depth=d, order=10, dmin=dmin)
+        ref = hi.hi_eval(s)
+    r = {t: run_gpu(s, "mixed", options={"p2p_targets": t}) for t in (-1, 8, 4)}
+    e = {t: errors(v, ref) for t, v in r.items()}
+    for t in (8, 4):
+        a, b = r[t]["F"], r[-1]["F"]
+        assert np.sqrt(((a - b) ** 2).sum() / (b ** 2).sum()) < 1e-5, (t, e)
+        # energies: the same terms summed in another order; at depth 0 each
+        # potential sums 10,800 single-precision terms
+        assert abs(r[t]["E"] - r[-1]["E"]) < 3e-6 * abs(r[-1]["E"]), (t, e)
+        assert e[t]["Erel"] < e[-1]["Erel"] + 3e-6, (t, e)
+        assert e[t]["Frel"] < 1.1 * e[-1]["Frel"] + 1e-6 and e[t]["Fmax"] < 1.1 * e[-1]["Fmax"] + 1e-5, (t, e)
+        assert np.abs(r[t]["dEdl"] - r[-1]["dEdl"]).max() < 1e-6, (t, e)

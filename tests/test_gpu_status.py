@@ -125,7 +125,7 @@ def test_option_defaults_and_range():
                              ("site_list_cap", 20000), ("wait_limit_ms", 0.5), ("watchdog_selftest", 2),
                              ("m2l_split_degree", -2), ("m2l_split_degree", p + 1), ("m2l_split_degree", 1.5),
                              ("m2l_single_tile", 2), ("m2l_b_stages", 1), ("m2l_b_stages", 5), ("p2p_threads", 100),
-                             ("site_blocks", 17), (99, 1)]:
+                             ("site_blocks", 17), ("p2p_targets", 3), ("p2p_targets", 16), (99, 1)]:
                 with pytest.raises(pkg.MahiError) as ei:
                     m.set_option(opt, bad)
                 assert ei.value.code == -1
