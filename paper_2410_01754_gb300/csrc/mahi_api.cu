@@ -104,6 +104,9 @@ static void free_all(mahi_ctx *h) {
   for (int i = 0; i < 2; ++i)
     if (h->join_ev[i]) cudaEventDestroy(h->join_ev[i]);
   if (h->side) cudaStreamDestroy(h->side);
+  for (int i = 0; i < 2; ++i)
+    if (h->hp_ev[i]) cudaEventDestroy(h->hp_ev[i]);
+  if (h->hp) cudaStreamDestroy(h->hp);
 }
 
 // SIMT operator layout: transposed and zero padded, opT[term][k][n], k, n < ld.
@@ -380,6 +383,10 @@ int mahi_create(double box_L_nm, int64_t n_atoms, int32_t n_sites, int32_t order
     cudaError_t e = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking);
     for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&h->fork_ev[i], cudaEventDisableTiming);
     for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&h->join_ev[i], cudaEventDisableTiming);
+    int prio_lo = 0, prio_hi = 0;
+    if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&h->hp, cudaStreamNonBlocking, prio_hi);
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&h->hp_ev[i], cudaEventDisableTiming);
     if (e != cudaSuccess) return fail(e, "side stream");
   }
 #undef AL

@@ -194,6 +194,11 @@ struct mahi_ctx {
   // joined with events inside every evaluation
   cudaStream_t side = nullptr;
   cudaEvent_t fork_ev[3] = {}, join_ev[2] = {};
+  // stream of the greatest priority for the main chain after the M2L (L2L,
+  // L2P, P2P), forked from and joined back into the handle's stream: its
+  // blocks are dispatched before the side stream's as SMs free up
+  cudaStream_t hp = nullptr;
+  cudaEvent_t hp_ev[2] = {};
 };
 
 namespace mahi {

@@ -2243,7 +2243,11 @@ __global__ void __launch_bounds__(kSiteThreads) k_site_lists(
   }
 }
 
-template <typename T, int PP>
+// kCompact: only the compact sites, whose lists k_site_lists built (no list
+// storage in shared memory, so the batches hold more rows); otherwise only the
+// other sites (spread sites, or all of them when no lists were built), with
+// the in-kernel traversal.  Each site is evaluated by exactly one of the two.
+template <typename T, int PP, bool kCompact>
 __global__ void __launch_bounds__(kSiteThreads, 3) k_site_phi(
     int S, int G, const int *__restrict__ site_ptr, const int *__restrict__ site_atoms, int d, int P, int ld,
     int lds, int nbmax, double L, const int64_t *__restrict__ level_off, const int *__restrict__ leaf_start,
@@ -2257,11 +2261,12 @@ __global__ void __launch_bounds__(kSiteThreads, 3) k_site_phi(
   // FP64 otherwise; 32 bytes either way
   constexpr bool kDF = std::is_same<T, float>::value;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lcap = kCompact ? 0 : fcap;                 // in-kernel traversal lists
   int *fa = reinterpret_cast<int *>(smem_raw);          // frontier (current)
-  int *fb = fa + fcap;                                  // frontier (next)
-  int *sep0 = fb + fcap;                                // separated boxes / direct leaves, even levels
-  int *sep1 = sep0 + fcap;                              // the same, odd levels
-  T *Ms = reinterpret_cast<T *>(sep1 + fcap);           // [2][nbmax][lds] staged multipole rows
+  int *fb = fa + lcap;                                  // frontier (next)
+  int *sep0 = fb + lcap;                                // separated boxes / direct leaves, even levels
+  int *sep1 = sep0 + lcap;                              // the same, odd levels
+  T *Ms = reinterpret_cast<T *>(sep1 + lcap);           // [2][nbmax][lds] staged multipole rows
   double *qds = reinterpret_cast<double *>(Ms + (size_t)2 * nbmax * lds);  // [2][nbmax][32 B] Q, Dx, Dy, Dz
   // levels 0 and 1 (the root and its 8 children, which every site's first
   // batches refer to over and over through their images) stay resident: rows
@@ -2282,6 +2287,10 @@ __global__ void __launch_bounds__(kSiteThreads, 3) k_site_phi(
   if (site >= S) return;
   const int b0 = site_ptr[site], n = site_ptr[site + 1] - b0;
   if (n <= 0 || n > kMaxSiteAtoms) return;  // rejected when the site map is set
+  // a compact site's lists may have been built by k_site_lists (pre)
+  const int *pcnt = pre_counts ? pre_counts + (size_t)site * (d + 2) : nullptr;
+  const bool pre = pcnt && pcnt[0] >= 0;
+  if (pre != kCompact) return;  // the other instantiation takes this site
   const int nb = 1 << d;
   const double sl = L / nb;
   if (tid <= d + 1) lvo[tid] = level_off[tid];
@@ -2314,9 +2323,6 @@ __global__ void __launch_bounds__(kSiteThreads, 3) k_site_phi(
   // atoms scattered over the box) would have to open nearly every box near
   // any of them, so each of its atoms then takes its own traversal (a group
   // of one atom about itself).  All blocks of a site take the same decision.
-  // A compact site's lists may have been built by k_site_lists (pre).
-  const int *pcnt = pre_counts ? pre_counts + (size_t)site * (d + 2) : nullptr;
-  const bool pre = pcnt && pcnt[0] >= 0;
   if (tid == 0) {
     if (pre) {
       for (int k = 0; k < 4; ++k) cen[k] = pre_cen[4 * (size_t)site + k];
@@ -2746,23 +2752,24 @@ int num_stages() { return 10; }
     if (e_ != cudaSuccess) return e_;                   \
   } while (0)
 
-// k_site_phi with the M2P order a compile-time constant where one is built
-template <typename T, int PP, typename... A>
+// k_site_phi with the M2P order a compile-time constant where one is built;
+// `nbmax` is the argument after the row stride
+template <typename T, int PP, bool C, typename... A>
 static cudaError_t launch_site_phi_pp(int G, size_t smp, cudaStream_t st, int S, A... args) {
-  cudaError_t e = cudaFuncSetAttribute(k_site_phi<T, PP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smp);
+  cudaError_t e = cudaFuncSetAttribute(k_site_phi<T, PP, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smp);
   if (e != cudaSuccess) return e;
-  k_site_phi<T, PP><<<S * G, kSiteThreads, smp, st>>>(S, args...);
+  k_site_phi<T, PP, C><<<S * G, kSiteThreads, smp, st>>>(S, args...);
   return cudaGetLastError();
 }
-template <typename T, typename... A>
+template <typename T, bool C, typename... A>
 static cudaError_t launch_site_phi(int P, int G, size_t smp, cudaStream_t st, int S, A... args) {
   switch (P) {
-    case 8: return launch_site_phi_pp<T, 8>(G, smp, st, S, args...);
-    case 10: return launch_site_phi_pp<T, 10>(G, smp, st, S, args...);
-    case 12: return launch_site_phi_pp<T, 12>(G, smp, st, S, args...);
-    case 14: return launch_site_phi_pp<T, 14>(G, smp, st, S, args...);
-    case 16: return launch_site_phi_pp<T, 16>(G, smp, st, S, args...);
-    default: return launch_site_phi_pp<T, 0>(G, smp, st, S, args...);
+    case 8: return launch_site_phi_pp<T, 8, C>(G, smp, st, S, args...);
+    case 10: return launch_site_phi_pp<T, 10, C>(G, smp, st, S, args...);
+    case 12: return launch_site_phi_pp<T, 12, C>(G, smp, st, S, args...);
+    case 14: return launch_site_phi_pp<T, 14, C>(G, smp, st, S, args...);
+    case 16: return launch_site_phi_pp<T, 16, C>(G, smp, st, S, args...);
+    default: return launch_site_phi_pp<T, 0, C>(G, smp, st, S, args...);
   }
 }
 
@@ -2797,9 +2804,9 @@ static cudaError_t launch_gemm(const GemmMap &mp, int K, int ld, const T *in, T 
   return launch_gemm_nc<T, 20>(mp, grid, K, ld, in, out, ops, st);
 }
 
-static inline void mark(mahi_ctx *h, int stage) {
+static inline void mark(mahi_ctx *h, int stage, cudaStream_t on = nullptr) {
   if (h->timing && stage < 20) {
-    cudaEventRecord(h->ev[stage], h->stream);
+    cudaEventRecord(h->ev[stage], on ? on : h->stream);
     h->n_ev = stage + 1;
   }
 }
@@ -3001,41 +3008,65 @@ static cudaError_t eval_t(mahi_ctx *h, const XT *x, const double *lam, double *e
     MAHI_CK(cudaStreamWaitEvent(h->side, h->fork_ev[1], 0));
     mark_side(h, 1, 0);
     // rows per batch: as many as two buffers of staged multipole and
-    // charge/dipole rows hold beside the four lists and the resident rows of
-    // levels 0 and 1 at three blocks per SM
+    // charge/dipole rows hold beside the resident rows of levels 0 and 1 (and,
+    // for the in-kernel traversal, its four lists) at three blocks per SM
     const int lds = ld + 16 / (int)sizeof(T);
     const size_t per_row = 2 * (sizeof(T) * lds + 4 * sizeof(double));
-    const size_t fixed = sizeof(int) * 4 * (size_t)h->site_list_cap +
-                         (h->d >= 1 ? 9 : 1) * (sizeof(T) * lds + 4 * sizeof(double));  // lists, resident rows
-    const size_t budget = std::max<size_t>(kSiteSmemBudget, fixed + 8 * per_row);
-    const int nbmax = (int)std::max<size_t>(8, std::min<size_t>(kSiteBatchMax, (budget - fixed) / per_row));
-    const size_t smp = fixed + per_row * nbmax;
-    // blocks per site: about 4 x 3 per SM over all sites, unless the autotuner picked a count
+    const size_t resident = (h->d >= 1 ? 9 : 1) * (sizeof(T) * lds + 4 * sizeof(double));
+    auto batch_rows = [&](size_t fixed, size_t &smp) {
+      const size_t budget = std::max<size_t>(kSiteSmemBudget, fixed + 8 * per_row);
+      const int nbm = (int)std::max<size_t>(8, std::min<size_t>(kSiteBatchMax, (budget - fixed) / per_row));
+      smp = fixed + per_row * nbm;
+      return nbm;
+    };
+    size_t smp = 0, smp_c = 0;
+    const int nbmax = batch_rows(sizeof(int) * 4 * (size_t)h->site_list_cap + resident, smp);
+    const int nbmax_c = batch_rows(resident, smp_c);
+    // blocks per site: about 3 x 3 per SM over all sites (three resident per
+    // SM), unless the autotuner picked a count
     const int G = h->tune_site_blocks > 0
                       ? std::min(kSiteChunksMax, h->tune_site_blocks)
-                      : std::max(1, std::min(kSiteChunksMax, (4 * 3 * h->num_sms + h->S - 1) / std::max(1, h->S)));
-    MAHI_CK(launch_site_phi<T>(P, G, smp, h->side, h->S, G, h->site_ptr, h->site_atoms, h->d, P, ld, lds, nbmax, h->L,
-                               h->d_level_off, h->leaf_start, h->inv_perm, (const V *)h->part, M, h->box_qd,
-                               h->box_qdf, mom, h->L_h3, h->phi_part, h->status_dev, h->site_theta,
-                               h->site_list_cap, h->wait_limit_ns, site_pre ? h->site_lists : nullptr,
-                               site_pre ? h->site_list_n : nullptr, site_pre ? h->site_cen : nullptr));
+                      : std::max(1, std::min(kSiteChunksMax, (3 * 3 * h->num_sms + h->S - 1) / std::max(1, h->S)));
+    if (site_pre)
+      MAHI_CK((launch_site_phi<T, true>(P, G, smp_c, h->side, h->S, G, h->site_ptr, h->site_atoms, h->d, P, ld, lds,
+                                         nbmax_c, h->L, h->d_level_off, h->leaf_start, h->inv_perm, (const V *)h->part,
+                                         M, h->box_qd, h->box_qdf, mom, h->L_h3, h->phi_part, h->status_dev,
+                                         h->site_theta, h->site_list_cap, h->wait_limit_ns, h->site_lists,
+                                         h->site_list_n, h->site_cen)));
+    // the other sites (spread ones; all of them without lists): the blocks of
+    // compact sites leave at once
+    MAHI_CK((launch_site_phi<T, false>(P, G, smp, h->side, h->S, G, h->site_ptr, h->site_atoms, h->d, P, ld, lds,
+                                        nbmax, h->L, h->d_level_off, h->leaf_start, h->inv_perm, (const V *)h->part, M,
+                                        h->box_qd, h->box_qdf, mom, h->L_h3, h->phi_part, h->status_dev,
+                                        h->site_theta, h->site_list_cap, h->wait_limit_ns,
+                                        site_pre ? h->site_lists : nullptr, site_pre ? h->site_list_n : nullptr,
+                                        site_pre ? h->site_cen : nullptr)));
+    h->launches += site_pre ? 1 : 0;
     k_site_phi_sum<<<(h->n_site_atoms + 127) / 128, 128, 0, h->side>>>(h->n_site_atoms, G, coulomb_constant(),
                                                                         h->phi_part, h->phi_site);
     mark_side(h, 1, 1);
     MAHI_CK(cudaEventRecord(h->join_ev[1], h->side));
   }
+  // the main chain after the M2L runs on the handle's stream of the greatest
+  // priority (forked here, joined after the near field): as blocks of the
+  // site-atom potential retire, the scheduler dispatches these first instead
+  // of leaving the short L2L levels and the near field behind the side stream
+  const cudaStream_t st_main = st;
+  MAHI_CK(cudaEventRecord(h->hp_ev[0], st_main));
+  MAHI_CK(cudaStreamWaitEvent(h->hp, h->hp_ev[0], 0));
+  st = h->hp;
   for (int l = 1; l <= h->d; ++l) {
     MAHI_CK((launch_dense_gemm<T, true>(1 << (3 * (l - 1)), 8 * ld, ld, Lx + h->level_off[l - 1] * ld, ld,
                                          (const T *)h->ops_l2l, 8 * ld, Lx + h->level_off[l] * ld, 8 * ld,
                                          (T *)h->gemm_ws, h->gemm_ws_elems, h->num_sms, st, h->launches)));
   }
-  mark(h, 7);
+  mark(h, 7, st);
   const T *Lleaf = Lx + h->level_off[h->d] * ld;
   if (std::is_same<T, float>::value && h->tune_p2p_targets > 0 && h->nf_slots) {
     // near field over the half shell (both sides of every pair), then the far
     // field fused with the near-field sums and the outputs
     MAHI_CK((launch_p2p_n3(h, nleaf, nb, st)));
-    mark(h, 8);
+    mark(h, 8, st);
     MAHI_CK((launch_l2p_near<XT>(h, nleaf, nb, (const float *)Lleaf, mom, (XT *)forces, st)));
     h->launches += 2;
   } else {
@@ -3050,7 +3081,7 @@ static cudaError_t eval_t(mahi_ctx *h, const XT *x, const double *lam, double *e
       k_l2p<T, 0><<<gl, bl, per_warp * wpb, st>>>(nleaf, P, ld, sl, h->leaf_start, (const V *)h->part, Lleaf,
                                                    (T *)h->phi_s, (T *)h->grad_s);
     MAHI_CK(cudaGetLastError());
-    mark(h, 8);
+    mark(h, 8, st);
     // threads per target leaf: 128 unless the autotuner picked another
     switch (h->tune_p2p_threads) {
       case 64: MAHI_CK((launch_p2p<T, XT, 64>(h, nleaf, nb, mom, forces, st))); break;
@@ -3060,7 +3091,10 @@ static cudaError_t eval_t(mahi_ctx *h, const XT *x, const double *lam, double *e
     h->launches += 2;
   }
   MAHI_CK(cudaGetLastError());
-  mark(h, 9);
+  mark(h, 9, st);
+  MAHI_CK(cudaEventRecord(h->hp_ev[1], st));
+  st = st_main;
+  MAHI_CK(cudaStreamWaitEvent(st, h->hp_ev[1], 0));
   if (h->S > 0) {
     MAHI_CK(cudaStreamWaitEvent(st, h->join_ev[1], 0));  // site-atom potential done
     if (h->multiform)
