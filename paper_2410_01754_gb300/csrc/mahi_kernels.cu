@@ -2093,18 +2093,14 @@ __device__ __forceinline__ void m2p_high2(const T *__restrict__ M, T x0, T y0, T
 // position, and the leaf index used by the direct sums moves with the image).
 template <typename V>
 __device__ __forceinline__ void site_load_atoms(int n, const int *__restrict__ atoms, int d, double L,
-                                                const int *__restrict__ inv_perm, const int *__restrict__ leaf_start,
+                                                const int *__restrict__ inv_perm, const int *__restrict__ leaf_of,
                                                 const V *__restrict__ part, double (*pa)[3], int (*aI)[3], V *me,
                                                 int *sa_s) {
   const int nb = 1 << d;
   const double sl = L / nb;
   for (int a = threadIdx.x; a < n; a += blockDim.x) {
     const int i = atoms[a], sa = inv_perm[i];
-    int lo = 0, hi = (1 << (3 * d)) - 1;  // leaf of sorted position sa
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (leaf_start[mid] <= sa) lo = mid; else hi = mid - 1;
-    }
+    const int lo = leaf_of[i];  // the leaf binning put atom i in
     const V v = part[sa];
     if (me) me[a] = v;
     if (sa_s) sa_s[a] = sa;
@@ -2207,7 +2203,7 @@ __device__ int site_classify_level(int l, int d, int *fa, int *fb, int *sep, int
 template <typename T>
 __global__ void __launch_bounds__(kSiteThreads) k_site_lists(
     int S, const int *__restrict__ site_ptr, const int *__restrict__ site_atoms, int d, double L,
-    const int *__restrict__ leaf_start, const int *__restrict__ inv_perm, const typename V4<T>::type *__restrict__ part,
+    const int *__restrict__ leaf_of, const int *__restrict__ inv_perm, const typename V4<T>::type *__restrict__ part,
     float theta, int fcap, int *__restrict__ lists, int *__restrict__ counts, double *__restrict__ cen_out,
     int *__restrict__ status) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -2218,7 +2214,7 @@ __global__ void __launch_bounds__(kSiteThreads) k_site_lists(
   if (site >= S) return;
   const int b0 = site_ptr[site], n = site_ptr[site + 1] - b0;
   if (n <= 0 || n > kMaxSiteAtoms) return;  // rejected when the site map is set
-  site_load_atoms(n, site_atoms + b0, d, L, inv_perm, leaf_start, part, pa, aI,
+  site_load_atoms(n, site_atoms + b0, d, L, inv_perm, leaf_of, part, pa, aI,
                   (typename V4<T>::type *)nullptr, (int *)nullptr);
   if (tid == 0) site_centre(n, pa, cen);
   __syncthreads();
@@ -2251,7 +2247,8 @@ template <typename T, int PP, bool kCompact>
 __global__ void __launch_bounds__(kSiteThreads, 3) k_site_phi(
     int S, int G, const int *__restrict__ site_ptr, const int *__restrict__ site_atoms, int d, int P, int ld,
     int lds, int nbmax, double L, const int64_t *__restrict__ level_off, const int *__restrict__ leaf_start,
-    const int *__restrict__ inv_perm, const typename V4<T>::type *__restrict__ part, const T *__restrict__ M,
+    const int *__restrict__ leaf_of, const int *__restrict__ inv_perm, const typename V4<T>::type *__restrict__ part,
+    const T *__restrict__ M,
     const double *__restrict__ qd, const float *__restrict__ qdf, const double *__restrict__ mom,
     const double *__restrict__ Lh3, double *__restrict__ phi_part, int *__restrict__ status, float theta, int fcap,
     uint64_t wait_ns, const int *__restrict__ pre_lists, const int *__restrict__ pre_counts,
@@ -2300,7 +2297,7 @@ __global__ void __launch_bounds__(kSiteThreads, 3) k_site_phi(
     s_abort = 0;
     fence_mbar_init();
   }
-  site_load_atoms(n, site_atoms + b0, d, L, inv_perm, leaf_start, part, pa, aI, me, sa_s);
+  site_load_atoms(n, site_atoms + b0, d, L, inv_perm, leaf_of, part, pa, aI, me, sa_s);
   {
     constexpr int EPV = 16 / sizeof(T);
     const int per_row = ld / EPV;
@@ -2942,7 +2939,7 @@ static cudaError_t eval_t(mahi_ctx *h, const XT *x, const double *lam, double *e
     const size_t sml = 2 * sizeof(int) * (size_t)h->site_list_cap;
     if (sml > 48 * 1024)
       MAHI_CK(cudaFuncSetAttribute(k_site_lists<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sml));
-    k_site_lists<T><<<h->S, kSiteThreads, sml, h->side>>>(h->S, h->site_ptr, h->site_atoms, h->d, h->L, h->leaf_start,
+    k_site_lists<T><<<h->S, kSiteThreads, sml, h->side>>>(h->S, h->site_ptr, h->site_atoms, h->d, h->L, h->leaf_of,
                                                           h->inv_perm, (const V *)h->part, h->site_theta,
                                                           h->site_list_cap, h->site_lists, h->site_list_n,
                                                           h->site_cen, h->status_dev);
@@ -3029,14 +3026,14 @@ static cudaError_t eval_t(mahi_ctx *h, const XT *x, const double *lam, double *e
                       : std::max(1, std::min(kSiteChunksMax, (3 * 3 * h->num_sms + h->S - 1) / std::max(1, h->S)));
     if (site_pre)
       MAHI_CK((launch_site_phi<T, true>(P, G, smp_c, h->side, h->S, G, h->site_ptr, h->site_atoms, h->d, P, ld, lds,
-                                         nbmax_c, h->L, h->d_level_off, h->leaf_start, h->inv_perm, (const V *)h->part,
+                                         nbmax_c, h->L, h->d_level_off, h->leaf_start, h->leaf_of, h->inv_perm, (const V *)h->part,
                                          M, h->box_qd, h->box_qdf, mom, h->L_h3, h->phi_part, h->status_dev,
                                          h->site_theta, h->site_list_cap, h->wait_limit_ns, h->site_lists,
                                          h->site_list_n, h->site_cen)));
     // the other sites (spread ones; all of them without lists): the blocks of
     // compact sites leave at once
     MAHI_CK((launch_site_phi<T, false>(P, G, smp, h->side, h->S, G, h->site_ptr, h->site_atoms, h->d, P, ld, lds,
-                                        nbmax, h->L, h->d_level_off, h->leaf_start, h->inv_perm, (const V *)h->part, M,
+                                        nbmax, h->L, h->d_level_off, h->leaf_start, h->leaf_of, h->inv_perm, (const V *)h->part, M,
                                         h->box_qd, h->box_qdf, mom, h->L_h3, h->phi_part, h->status_dev,
                                         h->site_theta, h->site_list_cap, h->wait_limit_ns,
                                         site_pre ? h->site_lists : nullptr, site_pre ? h->site_list_n : nullptr,
