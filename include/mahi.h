@@ -142,10 +142,11 @@ int mahi_set_forms(mahi_t h, const double *q_env, const int32_t *site_of_atom, c
 int mahi_n_lambdas(mahi_t h);
 
 /* One MAHI evaluation, enqueued on the handle's stream; returns after enqueueing.
- * Independent parts of it run on internal streams of the handle (the sites'
- * pair terms, the box moments, the site-atom potential); they are forked from
- * and joined back to the handle's stream with events inside the call, so the
- * outputs are complete in the handle's stream order, work queued on that
+ * Its chain of kernels runs on an internal stream of the greatest priority and
+ * its independent parts (the sites' pair terms, the box moments, the traversal
+ * lists, the site-atom potential) on a second internal stream; both are forked
+ * from and joined back to the handle's stream with events inside the call, so
+ * the outputs are complete in the handle's stream order, work queued on that
  * stream before the call is seen, and the call can be captured in a CUDA graph.
  *   x          device, n_atoms x 3 row-major positions in nm (float64 if
  *              x_is_fp64 else float32); any real values (wrapped into the box).
@@ -275,7 +276,7 @@ int mahi_get_potential(mahi_t h, double *phi_device);
 /* Stage timing (CUDA events).  mahi_set_timing(h, 1) turns recording on;
  * mahi_stage_times fills up to n floats (ms) of the last evaluation in the
  * order of mahi_stage_name(i) and returns the stage count.  The first ten are
- * consecutive intervals on the handle's stream (bin, sort, p2m, m2m, lattice,
+ * consecutive intervals of the evaluation's chain (bin, sort, p2m, m2m, lattice,
  * m2l, l2l, near_pairs, far_near_out, site): near_pairs is the half-shell
  * near-field pair kernel and far_near_out the far field (L2P) fused with the
  * near-field sums and the outputs; in the directed near-field scheme

@@ -194,9 +194,9 @@ struct mahi_ctx {
   // joined with events inside every evaluation
   cudaStream_t side = nullptr;
   cudaEvent_t fork_ev[3] = {}, join_ev[2] = {};
-  // stream of the greatest priority for the main chain after the M2L (L2L,
-  // L2P, P2P), forked from and joined back into the handle's stream: its
-  // blocks are dispatched before the side stream's as SMs free up
+  // stream of the greatest priority for the main chain of an evaluation,
+  // forked from and joined back into the handle's stream: its blocks are
+  // dispatched before the side stream's as SMs free up
   cudaStream_t hp = nullptr;
   cudaEvent_t hp_ev[2] = {};
 };
@@ -222,5 +222,5 @@ size_t tc_ops_bytes(int p);
 void tc_pack_ops(int p, const std::vector<std::vector<double>> &m2l, void *host_image);
 int tc_build_units(mahi_ctx *h, std::vector<int> &units);
 int tc_upload_units(mahi_ctx *h);
-int tc_m2l(mahi_ctx *h);
+int tc_m2l(mahi_ctx *h, cudaStream_t st);
 }  // namespace mahi

@@ -2875,7 +2875,15 @@ static cudaError_t launch_l2p_near(mahi_ctx *h, int nleaf, int nb, const float *
 template <typename T, typename XT>
 static cudaError_t eval_t(mahi_ctx *h, const XT *x, const double *lam, double *energy, XT *forces, double *dEdl) {
   using V = typename V4<T>::type;
-  cudaStream_t st = h->stream;
+  // The whole chain runs on the handle's stream of the greatest priority,
+  // forked from the caller's stream here and joined back at the end: the side
+  // stream's work (site pair terms, box moments, traversal lists, the
+  // site-atom potential) then fills the SMs the chain leaves free instead of
+  // delaying it.
+  const cudaStream_t st_user = h->stream;
+  MAHI_CK(cudaEventRecord(h->hp_ev[0], st_user));
+  MAHI_CK(cudaStreamWaitEvent(h->hp, h->hp_ev[0], 0));
+  const cudaStream_t st = h->hp;
   const int nb = 1 << h->d;
   const int nleaf = h->nleaf;
   const int64_t N = h->N;
@@ -2884,7 +2892,7 @@ static cudaError_t eval_t(mahi_ctx *h, const XT *x, const double *lam, double *e
   const double *mom = h->box_qd;  // root box row: Q, D, T of the system about the box centre
   h->launches = 0;
   h->side_timed = 0;
-  mark(h, 0);
+  mark(h, 0, st);
   if (h->S > 0 && !h->multiform) {
     // the sites' FP64 pair terms need only the positions: side stream, from
     // the start (the FP64 pipe is idle during binning, P2M and M2M)
@@ -2910,7 +2918,7 @@ static cudaError_t eval_t(mahi_ctx *h, const XT *x, const double *lam, double *e
                                                                     h->mf_lam_off, lam, h->mf_q, h->qt, (V *)h->vtmp);
     h->launches += 1;
   }
-  mark(h, 1);
+  mark(h, 1, st);
   k_scan<<<1, 1024, 0, st>>>(h->leaf_count, nleaf, h->leaf_start);
   int gb = (int)((N + 255) / 256);
   k_scatter<T><<<gb, 256, 0, st>>>(N, h->leaf_of, h->slot, h->leaf_start, (const V *)h->vtmp, (V *)h->part_tmp,
@@ -2946,7 +2954,7 @@ static cudaError_t eval_t(mahi_ctx *h, const XT *x, const double *lam, double *e
     h->launches += 1;
   }
   MAHI_CK(cudaGetLastError());
-  mark(h, 2);
+  mark(h, 2, st);
   const double s_leaf = h->L / nb;
   {
     const int Ks = K | 1;
@@ -2966,7 +2974,7 @@ static cudaError_t eval_t(mahi_ctx *h, const XT *x, const double *lam, double *e
   }
   h->launches += 1;
   MAHI_CK(cudaGetLastError());
-  mark(h, 3);
+  mark(h, 3, st);
   for (int l = h->d - 1; l >= 0; --l) {
     MAHI_CK((launch_dense_gemm<T, false>(1 << (3 * l), ld, 8 * ld, M + h->level_off[l + 1] * ld, 8 * ld,
                                           (const T *)h->ops_m2m, ld, M + h->level_off[l] * ld, ld, (T *)h->gemm_ws,
@@ -2978,14 +2986,14 @@ static cudaError_t eval_t(mahi_ctx *h, const XT *x, const double *lam, double *e
                                                                                h->d_level_off, h->box_qd, M);
     h->launches += 1;
   }
-  mark(h, 4);
+  mark(h, 4, st);
   k_lattice<T><<<(ld + 3) / 4, 128, sizeof(double) * K, st>>>(K, ld, h->L, h->ops_lat, h->ops_lat_h3, mom, M, Lx,
                                                     h->L_h3);
   h->launches += 1;
   MAHI_CK(cudaGetLastError());
-  mark(h, 5);
+  mark(h, 5, st);
   if (h->prec == MAHI_MIXED && h->d >= 1) {
-    int rc = tc_m2l(h);
+    int rc = tc_m2l(h, st);
     if (rc != 0) return cudaErrorUnknown;
   } else {
     for (int l = 1; l <= h->d; ++l) {
@@ -2995,7 +3003,7 @@ static cudaError_t eval_t(mahi_ctx *h, const XT *x, const double *lam, double *e
       h->launches += 1;
     }
   }
-  mark(h, 6);
+  mark(h, 6, st);
   if (h->S > 0) {
     // The site-atom potential needs only the multipoles, the box moments and
     // the lattice part, so it runs on the side stream alongside L2L, L2P and
@@ -3044,14 +3052,6 @@ static cudaError_t eval_t(mahi_ctx *h, const XT *x, const double *lam, double *e
     mark_side(h, 1, 1);
     MAHI_CK(cudaEventRecord(h->join_ev[1], h->side));
   }
-  // the main chain after the M2L runs on the handle's stream of the greatest
-  // priority (forked here, joined after the near field): as blocks of the
-  // site-atom potential retire, the scheduler dispatches these first instead
-  // of leaving the short L2L levels and the near field behind the side stream
-  const cudaStream_t st_main = st;
-  MAHI_CK(cudaEventRecord(h->hp_ev[0], st_main));
-  MAHI_CK(cudaStreamWaitEvent(h->hp, h->hp_ev[0], 0));
-  st = h->hp;
   for (int l = 1; l <= h->d; ++l) {
     MAHI_CK((launch_dense_gemm<T, true>(1 << (3 * (l - 1)), 8 * ld, ld, Lx + h->level_off[l - 1] * ld, ld,
                                          (const T *)h->ops_l2l, 8 * ld, Lx + h->level_off[l] * ld, 8 * ld,
@@ -3089,9 +3089,6 @@ static cudaError_t eval_t(mahi_ctx *h, const XT *x, const double *lam, double *e
   }
   MAHI_CK(cudaGetLastError());
   mark(h, 9, st);
-  MAHI_CK(cudaEventRecord(h->hp_ev[1], st));
-  st = st_main;
-  MAHI_CK(cudaStreamWaitEvent(st, h->hp_ev[1], 0));
   if (h->S > 0) {
     MAHI_CK(cudaStreamWaitEvent(st, h->join_ev[1], 0));  // site-atom potential done
     if (h->multiform)
@@ -3112,7 +3109,9 @@ static cudaError_t eval_t(mahi_ctx *h, const XT *x, const double *lam, double *e
     h->launches += 1;
   }
   MAHI_CK(cudaGetLastError());
-  mark(h, 10);
+  mark(h, 10, st);
+  MAHI_CK(cudaEventRecord(h->hp_ev[1], st));
+  MAHI_CK(cudaStreamWaitEvent(st_user, h->hp_ev[1], 0));
   return cudaSuccess;
 }
 

@@ -807,9 +807,9 @@ static size_t tc_smem_bytes(int ng, int nsb) {
   return nsb * tc::kKPI * 2 * b + stage + tables + (tc::kStagesA + tc::kStagesB + tc::kDone + 6) * 8 + 16;
 }
 
-int tc_m2l(mahi_ctx *h) {
+int tc_m2l(mahi_ctx *h, cudaStream_t st) {
   // rewrite the multipoles of levels 1..d for coalesced gathers
-  k_m2l_src_layout<<<4 * h->num_sms, 256, 0, h->stream>>>((const float *)h->Mexp, (float *)h->tc_msrc, h->tc_level_off,
+  k_m2l_src_layout<<<4 * h->num_sms, 256, 0, st>>>((const float *)h->Mexp, (float *)h->tc_msrc, h->tc_level_off,
                                                          h->ld, h->d);
   h->launches += 1;
   tc::Params prm;
@@ -848,9 +848,9 @@ int tc_m2l(mahi_ctx *h) {
   prm.nrem = h->tc_nunits - prm.nfull;
   prm.q = prm.nrem > 0 ? G / prm.nrem : 1;
   prm.partial = (float *)h->tc_partial;
-  k_m2l_tc<<<G, tc::kThreads, sm, h->stream>>>(prm);
+  k_m2l_tc<<<G, tc::kThreads, sm, st>>>(prm);
   if (prm.nrem > 0) {
-    k_m2l_tc_reduce<<<2 * G, 256, 0, h->stream>>>(prm);
+    k_m2l_tc_reduce<<<2 * G, 256, 0, st>>>(prm);
     h->launches += 1;
   }
   h->launches += 1;
