@@ -1520,31 +1520,30 @@ __device__ __forceinline__ void site_pair_r(const XT *__restrict__ x, int i, int
 }
 
 // The FP64 pair terms (grad A, A) of every unordered pair of every site of
-// up to kSiteSymMax atoms, one pair per thread and one block per site.  They
-// depend only on the positions, so they are computed at the start of an
-// evaluation on the side stream, where the FP64 pipe is otherwise idle, and
-// k_site reads them back; pairs[site][p] with p the pair index of k_site.
+// up to kSiteSymMax atoms, one pair per thread over all sites (the pair list
+// {site, i, j, slot} is built when the site map is set): on GB300 the FP64 pipe
+// is charged per warp instruction whatever the number of active lanes, so full
+// warps (32 pairs) matter more than keeping a site in one block.  They depend
+// only on the positions, so they are computed at the start of an evaluation
+// on the side stream, where the FP64 pipe is otherwise idle, and k_site reads
+// them back; pairs[site][p] with p the pair index of k_site.
 template <typename XT>
-__global__ void __launch_bounds__(64) k_site_pairs(double L, int Pmax, const int *__restrict__ site_ptr,
+__global__ void __launch_bounds__(64) k_site_pairs(int npairs, const int4 *__restrict__ plist, double L, int Pmax,
+                                                   const int *__restrict__ site_ptr,
                                                    const int *__restrict__ site_atoms, const XT *__restrict__ x,
                                                    const double *__restrict__ eta, const double *__restrict__ eta_x,
                                                    const double *__restrict__ eta_y, const double *__restrict__ eta_z,
                                                    double *__restrict__ pairs) {
-  const int site = blockIdx.x;
-  const int b = site_ptr[site], n = site_ptr[site + 1] - b;
-  if (n > kSiteSymMax) return;  // larger sites evaluate their ordered pairs in k_site
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= npairs) return;
+  const int4 e = plist[t];  // site, i, j (atom indices within the site), pair index
   const double V = L * L * L, c2 = 2.0 * kPi / (3.0 * V);
-  const int np = n * (n - 1) / 2;
-  for (int p = threadIdx.x; p < np; p += blockDim.x) {
-    int ia = 0, rem = p;
-    while (rem >= n - 1 - ia) { rem -= n - 1 - ia; ++ia; }
-    const int ja = ia + 1 + rem;
-    double r[3], A, g[3];
-    site_pair_r(x, site_atoms[b + ia], site_atoms[b + ja], L, r);
-    site_pair_kernel(r, L, c2, Pmax, eta, eta_x, eta_y, eta_z, A, g);
-    double *o = pairs + ((size_t)site * kSiteSymPairs + p) * 4;
-    o[0] = g[0]; o[1] = g[1]; o[2] = g[2]; o[3] = A;
-  }
+  const int b = site_ptr[e.x];
+  double r[3], A, g[3];
+  site_pair_r(x, site_atoms[b + e.y], site_atoms[b + e.z], L, r);
+  site_pair_kernel(r, L, c2, Pmax, eta, eta_x, eta_y, eta_z, A, g);
+  double *o = pairs + ((size_t)e.x * kSiteSymPairs + e.w) * 4;
+  o[0] = g[0]; o[1] = g[1]; o[2] = g[2]; o[3] = A;
 }
 
 // pairs: the terms of k_site_pairs, or null to evaluate them here
@@ -2899,8 +2898,11 @@ static cudaError_t eval_t(mahi_ctx *h, const XT *x, const double *lam, double *e
     MAHI_CK(cudaEventRecord(h->fork_ev[2], st));
     MAHI_CK(cudaStreamWaitEvent(h->side, h->fork_ev[2], 0));
     mark_side(h, 0, 0);
-    k_site_pairs<XT><<<h->S, 64, 0, h->side>>>(h->L, kSiteDegree, h->site_ptr, h->site_atoms, x, h->eta, h->eta_x,
-                                               h->eta_y, h->eta_z, h->site_pairs);
+    if (h->n_site_pairs > 0)
+      k_site_pairs<XT><<<(h->n_site_pairs + 63) / 64, 64, 0, h->side>>>(h->n_site_pairs, h->site_pair_list, h->L,
+                                                                       kSiteDegree, h->site_ptr, h->site_atoms, x,
+                                                                       h->eta, h->eta_x, h->eta_y, h->eta_z,
+                                                                       h->site_pairs);
     mark_side(h, 0, 1);
     h->launches += 1;
   }
