@@ -2041,7 +2041,9 @@ __device__ __forceinline__ void m2p_high2(const T *__restrict__ M, T x0, T y0, T
   const T i0 = rinv(x0 * x0 + y0 * y0 + z0 * z0), i1 = rinv(x1 * x1 + y1 * y1 + z1 * z1);
   const T q0 = i0 * i0, q1 = i1 * i1, zq0 = z0 * q0, zq1 = z1 * q1;
   T dr0 = i0, di0 = T(0), dr1 = i1, di1 = T(0);
-  T acc0 = T(0), acc1 = T(0);
+  // m = 0 terms and m > 0 terms in separate sums, the factor 2 of the latter
+  // applied once at the end (exact): each m > 0 term is then two FMAs per point
+  T az0 = T(0), az1 = T(0), ap0 = T(0), ap1 = T(0);
 #pragma unroll
   for (int m = 0; m <= PP; ++m) {
     if (m > 0) {
@@ -2055,9 +2057,9 @@ __device__ __forceinline__ void m2p_high2(const T *__restrict__ M, T x0, T y0, T
     T pr1 = T(0), pi1 = T(0), cr1 = dr1, ci1 = di1;
     if (m >= 2) {
       const int k = ridx(m, m);
-      const T mr = T(2) * M[k], mi = T(-2) * M[k + 1];
-      acc0 += mr * cr0 + mi * ci0;
-      acc1 += mr * cr1 + mi * ci1;
+      const T mr = M[k], mi = M[k + 1];
+      ap0 = fma(mr, cr0, ap0); ap0 = fma(-mi, ci0, ap0);
+      ap1 = fma(mr, cr1, ap1); ap1 = fma(-mi, ci1, ap1);
     }
 #pragma unroll
     for (int l = m + 1; l <= PP; ++l) {
@@ -2072,18 +2074,18 @@ __device__ __forceinline__ void m2p_high2(const T *__restrict__ M, T x0, T y0, T
         const int kk = ridx(l, m);
         if (m == 0) {
           const T mr = M[kk];
-          acc0 += mr * cr0;
-          acc1 += mr * cr1;
+          az0 = fma(mr, cr0, az0);
+          az1 = fma(mr, cr1, az1);
         } else {
-          const T mr = T(2) * M[kk], mi = T(-2) * M[kk + 1];
-          acc0 += mr * cr0 + mi * ci0;
-          acc1 += mr * cr1 + mi * ci1;
+          const T mr = M[kk], mi = M[kk + 1];
+          ap0 = fma(mr, cr0, ap0); ap0 = fma(-mi, ci0, ap0);
+          ap1 = fma(mr, cr1, ap1); ap1 = fma(-mi, ci1, ap1);
         }
       }
     }
   }
-  v0 = acc0;
-  v1 = acc1;
+  v0 = az0 + T(2) * ap0;
+  v1 = az1 + T(2) * ap1;
 }
 
 // The atoms of a site (block-wide): sorted index, leaf, stored particle and
