@@ -2272,10 +2272,9 @@ __global__ void __launch_bounds__(kSiteThreads, 3) k_site_phi(
   const int nres = (d >= 1) ? 9 : 1;
   T *Mres = reinterpret_cast<T *>(qds + (size_t)2 * nbmax * 4);  // [nres][lds]
   double *qres = reinterpret_cast<double *>(Mres + (size_t)nres * lds);  // [nres][32 B]
-  __shared__ double pa[kMaxSiteAtoms][3], cen[4], base_s[kSiteBatchMax], res_s[kSiteThreads][2];
+  __shared__ double pa[kMaxSiteAtoms][3], cen[4], base_s[kSiteThreads], res_s[kSiteThreads][2];
+  static_assert(kSiteThreads == 128, "the charge/dipole sums at c are reduced over 128 threads");
   __shared__ T pu[kMaxSiteAtoms][3], puu[kMaxSiteAtoms];
-  __shared__ T rw[kSiteBatchMax][3], rp[kSiteBatchMax][3], rQ[kSiteBatchMax], rB[kSiteBatchMax],
-      rBi[kSiteBatchMax], rpw[kSiteBatchMax];
   __shared__ V me[kMaxSiteAtoms];
   __shared__ int sa_s[kMaxSiteAtoms], aI[kMaxSiteAtoms][3], ent_s[2][kSiteBatchMax], wsum[64];
   __shared__ int64_t lvo[kMaxDepth + 2];  // level offsets (rows)
@@ -2476,60 +2475,64 @@ __global__ void __launch_bounds__(kSiteThreads, 3) k_site_phi(
     const T is = iLt * (T)(1 << cl);  // 1 / s, exact scaling of 1 / L
     const int *ent = ent_s[cur];
     const T *Mb = Ms + (size_t)cur * nbmax * lds;
-    if (tid < cn) {
-      const int e = ent[tid];
-      if (e >= 0) {
-        const int box = e >> 9, img = e & 511;
-        const int nx = img / 49 - 3, ny = (img / 7) % 7 - 3, nz = img % 7 - 3;
-        const double *q = (cl <= 1) ? qres + (size_t)((cl == 0) ? 0 : 1 + box) * 4
-                                    : qds + ((size_t)cur * nbmax + tid) * 4;
-        if constexpr (kDF) {
-          // double-float: w = m h - c with the odd integer m = 2 i + 1 + 2^(l+1) n
-          // (exact in single precision) and h = L / 2^(l+1) = hh + hl; then
-          // B^2, 1/B, p.w and Q/B - (p.w)/B^3 to about 2^-44 relative
-          const float hh = ldexpf(Lsp.h, -(cl + 1)), hl = ldexpf(Lsp.l, -(cl + 1));
-          const int ms = 2 << cl;
-          const int mi[3] = {2 * (int)d_compact(box) + 1 + ms * nx, 2 * (int)d_compact(box >> 1) + 1 + ms * ny,
-                             2 * (int)d_compact(box >> 2) + 1 + ms * nz};
-          DF w[3];
+    // Per row: the box centre relative to c, w, and its charge/dipole values,
+    // computed by every thread that takes the row (no setup phase and no
+    // barrier before the rows); the FP64 / double-float value at c,
+    // Q/B - (p.w)/B^3, is added by the row's thread of pair 0 only.
+    auto row_values = [&](int r, int e, bool add_base, T &wx, T &wy, T &wz, T &Q, T &px, T &py, T &pz, T &B,
+                          T &Bi, T &pw) {
+      const int box = e >> 9, img = e & 511;
+      const int nx = img / 49 - 3, ny = (img / 7) % 7 - 3, nz = img % 7 - 3;
+      const double *q = (cl <= 1) ? qres + (size_t)((cl == 0) ? 0 : 1 + box) * 4
+                                  : qds + ((size_t)cur * nbmax + r) * 4;
+      if constexpr (kDF) {
+        // double-float: w = m h - c with the odd integer m = 2 i + 1 + 2^(l+1) n
+        // (exact in single precision) and h = L / 2^(l+1) = hh + hl; then
+        // B^2, 1/B, p.w and Q/B - (p.w)/B^3 to about 2^-44 relative
+        const float hh = ldexpf(Lsp.h, -(cl + 1)), hl = ldexpf(Lsp.l, -(cl + 1));
+        const int ms = 2 << cl;
+        const int mi[3] = {2 * (int)d_compact(box) + 1 + ms * nx, 2 * (int)d_compact(box >> 1) + 1 + ms * ny,
+                           2 * (int)d_compact(box >> 2) + 1 + ms * nz};
+        DF w[3];
 #pragma unroll
-          for (int k = 0; k < 3; ++k) {
-            const float mf = (float)mi[k], ph = mf * hh, pe = fmaf(mf, hh, -ph);
-            float sh, se;
-            two_sum(ph, -csp[k].h, sh, se);
-            w[k] = df_norm(sh, se + (fmaf(mf, hl, pe) - csp[k].l));
-          }
-          const float *qf = reinterpret_cast<const float *>(q);
-          const DF Q{qf[0], qf[1]}, px{qf[2], qf[3]}, py{qf[4], qf[5]}, pz{qf[6], qf[7]};
-          const DF B2 = df_add(df_add(df_sq(w[0]), df_sq(w[1])), df_sq(w[2]));
-          const DF Bi = df_rsqrt(B2), Bi3 = df_mul(df_sq(Bi), Bi);
-          const DF pw = df_add(df_add(df_mul(px, w[0]), df_mul(py, w[1])), df_mul(pz, w[2]));
-          base_df = df_add(base_df, df_add(df_mul(Q, Bi), df_neg(df_mul(pw, Bi3))));  // at c the box centre is at -w
-          rw[tid][0] = w[0].h; rw[tid][1] = w[1].h; rw[tid][2] = w[2].h;
-          rp[tid][0] = px.h; rp[tid][1] = py.h; rp[tid][2] = pz.h;
-          rQ[tid] = Q.h;
-          rB[tid] = B2.h * Bi.h;
-          rBi[tid] = Bi.h;
-          rpw[tid] = pw.h;
-        } else {
-          const double s = ldexp(L, -cl);
-          const double wx = (((int)d_compact(box) + 0.5) * s + nx * L) - cen[0];
-          const double wy = (((int)d_compact(box >> 1) + 0.5) * s + ny * L) - cen[1];
-          const double wz = (((int)d_compact(box >> 2) + 0.5) * s + nz * L) - cen[2];
-          const double B2 = wx * wx + wy * wy + wz * wz, Bi = rinv_dd(B2);
-          const double Q = q[0], px = q[1], py = q[2], pz = q[3];
-          const double pw = px * wx + py * wy + pz * wz;
-          base += Q * Bi - pw * (Bi * Bi * Bi);  // at c the box centre is at -w
-          rw[tid][0] = (T)wx; rw[tid][1] = (T)wy; rw[tid][2] = (T)wz;
-          rp[tid][0] = (T)px; rp[tid][1] = (T)py; rp[tid][2] = (T)pz;
-          rQ[tid] = (T)Q;
-          rB[tid] = (T)(B2 * Bi);
-          rBi[tid] = (T)Bi;
-          rpw[tid] = (T)pw;
+        for (int k = 0; k < 3; ++k) {
+          const float mf = (float)mi[k], ph = mf * hh, pe = fmaf(mf, hh, -ph);
+          float sh, se;
+          two_sum(ph, -csp[k].h, sh, se);
+          w[k] = df_norm(sh, se + (fmaf(mf, hl, pe) - csp[k].l));
         }
+        const float *qf = reinterpret_cast<const float *>(q);
+        const DF Qd{qf[0], qf[1]}, pxd{qf[2], qf[3]}, pyd{qf[4], qf[5]}, pzd{qf[6], qf[7]};
+        const DF B2 = df_add(df_add(df_sq(w[0]), df_sq(w[1])), df_sq(w[2]));
+        const DF Bid = df_rsqrt(B2);
+        const DF pwd = df_add(df_add(df_mul(pxd, w[0]), df_mul(pyd, w[1])), df_mul(pzd, w[2]));
+        if (add_base) {
+          const DF Bi3 = df_mul(df_sq(Bid), Bid);
+          base_df = df_add(base_df, df_add(df_mul(Qd, Bid), df_neg(df_mul(pwd, Bi3))));  // at c the box centre is at -w
+        }
+        wx = w[0].h; wy = w[1].h; wz = w[2].h;
+        px = pxd.h; py = pyd.h; pz = pzd.h;
+        Q = Qd.h;
+        B = B2.h * Bid.h;
+        Bi = Bid.h;
+        pw = pwd.h;
+      } else {
+        const double s = ldexp(L, -cl);
+        const double dwx = (((int)d_compact(box) + 0.5) * s + nx * L) - cen[0];
+        const double dwy = (((int)d_compact(box >> 1) + 0.5) * s + ny * L) - cen[1];
+        const double dwz = (((int)d_compact(box >> 2) + 0.5) * s + nz * L) - cen[2];
+        const double B2 = dwx * dwx + dwy * dwy + dwz * dwz, dBi = rinv_dd(B2);
+        const double dQ = q[0], dpx = q[1], dpy = q[2], dpz = q[3];
+        const double dpw = dpx * dwx + dpy * dwy + dpz * dwz;
+        if (add_base) base += dQ * dBi - dpw * (dBi * dBi * dBi);  // at c the box centre is at -w
+        wx = (T)dwx; wy = (T)dwy; wz = (T)dwz;
+        px = (T)dpx; py = (T)dpy; pz = (T)dpz;
+        Q = (T)dQ;
+        B = (T)(B2 * dBi);
+        Bi = (T)dBi;
+        pw = (T)dpw;
       }
-    }
-    __syncthreads();
+    };
     if (my_p >= 0) {
       for (int r = my_s; r < cn; r += nslot) {
         const int e = ent[r];
@@ -2537,9 +2540,9 @@ __global__ void __launch_bounds__(kSiteThreads, 3) k_site_phi(
           // charge + dipole: change from the value at c,
           //   Q (1/A - 1/B) + p.u / A^3 - (p.w) (1/A^3 - 1/B^3),
           // A = |u - w|, B = |w|, A^2 - B^2 = u.u - 2 u.w, A - B = (A^2 - B^2) / (A + B)
-          const T wx = rw[r][0], wy = rw[r][1], wz = rw[r][2];
-          const T Q = rQ[r], px = rp[r][0], py = rp[r][1], pz = rp[r][2];
-          const T B = rB[r], Bi = rBi[r], pw = rpw[r], Bi3 = Bi * Bi * Bi;
+          T wx, wy, wz, Q, px, py, pz, B, Bi, pw;
+          row_values(r, e, my_p == 0, wx, wy, wz, Q, px, py, pz, B, Bi, pw);
+          const T Bi3 = Bi * Bi * Bi;
           T ux[2], uy[2], uz[2], dev[2];
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
@@ -2553,7 +2556,7 @@ __global__ void __launch_bounds__(kSiteThreads, 3) k_site_phi(
             dev[h] = -Q * f1 * Ai * Bi + pu_ * Ai3 + pw * f1 * (A2 + A * B + B * B) * Ai3 * Bi3;
           }
           if (P >= 2) {
-            const T *Mr = (cl <= 1) ? Mres + (size_t)((cl == 0) ? 0 : 1 + (e >> 9)) * lds : Mb + (size_t)r * lds;
+          const T *Mr = (cl <= 1) ? Mres + (size_t)((cl == 0) ? 0 : 1 + (e >> 9)) * lds : Mb + (size_t)r * lds;
             T v0, v1;
             if constexpr (PP > 0) {
               m2p_high2<T, PP>(Mr, ux[0] * is, uy[0] * is, uz[0] * is, ux[1] * is, uy[1] * is, uz[1] * is, v0, v1);
@@ -2585,7 +2588,9 @@ __global__ void __launch_bounds__(kSiteThreads, 3) k_site_phi(
             t0 = site_target(m0.x, m0.y, m0.z, gx0, gy0, gz0, sl);
             t1 = site_target(m1.x, m1.y, m1.z, gx1, gy1, gz1, sl);
           }
-          for (int q2 = leaf_start[box]; q2 < leaf_start[box + 1]; ++q2) {
+          const int q2e = leaf_start[box + 1];
+#pragma unroll 4
+          for (int q2 = leaf_start[box]; q2 < q2e; ++q2) {
             const V src = part[q2];
             T vh, vl;
             if (q2 != self0) {
@@ -2612,12 +2617,12 @@ __global__ void __launch_bounds__(kSiteThreads, 3) k_site_phi(
   if (g == 0)
     for (int k = tid; k < (P + 1) * (P + 1); k += blockDim.x) Lh3s[k] = (T)Lh3[k];
   // fixed-order reductions: the staged FP64 values, then per atom over its slots
-  if (tid < kSiteBatchMax) base_s[tid] = base + ((double)base_df.h + (double)base_df.l);
+  base_s[tid] = base + ((double)base_df.h + (double)base_df.l);
   res_s[tid][0] = acc0.value();
   res_s[tid][1] = acc1.value();
   __syncthreads();
   if (tid < 32) {
-    double v = base_s[tid] + base_s[tid + 32];
+    double v = (base_s[tid] + base_s[tid + 32]) + (base_s[tid + 64] + base_s[tid + 96]);
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffff, v, o);
     if (tid == 0) cen[3] = v;  // R is no longer needed
   }
