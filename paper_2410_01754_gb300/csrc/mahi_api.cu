@@ -93,7 +93,7 @@ static void free_all(mahi_ctx *h) {
                   h->m2l_list, h->m2l_off, h->site_ptr, h->site_atoms,
                   h->energy_part, h->site_energy, h->tc_ops, h->tc_partial, h->tc_msrc, h->tc_level_off, h->tc_units, h->d_x_stage,
                   h->d_lam_stage, h->d_E_stage, h->d_dEdl_stage, h->d_F_stage, h->ops_lat_h3, h->L_h3,
-                  h->box_qd, h->box_qdf, h->vtmp, h->relD, h->phi_site, h->psi_site, h->site_pairs, h->site_slot, h->mf_q, h->mf_lam_off, h->phi_part, h->d_level_off, h->mf_psi, h->mf_form_off, h->nf_slots, h->site_lists, h->site_list_n, h->site_cen, h->site_pair_list};
+                  h->box_qd, h->box_qdf, h->vtmp, h->relD, h->phi_site, h->psi_site, h->site_pairs, h->site_slot, h->mf_q, h->mf_lam_off, h->phi_part, h->d_level_off, h->mf_psi, h->mf_form_off, h->nf_slots, h->site_lists, h->site_list_n, h->site_cen, h->site_pair_list, h->site_order};
   for (void *b : bufs)
     if (b) cudaFree(b);
   if (h->status_host) cudaFreeHost(h->status_host);
@@ -454,6 +454,7 @@ int mahi_set_charges(mahi_t h, const double *qA_in, const double *qB_in, const i
   if (h->psi_site) { cudaFree(h->psi_site); h->psi_site = nullptr; }
   if (h->site_pairs) { cudaFree(h->site_pairs); h->site_pairs = nullptr; }
   if (h->site_pair_list) { cudaFree(h->site_pair_list); h->site_pair_list = nullptr; }
+  if (h->site_order) { cudaFree(h->site_order); h->site_order = nullptr; }
   if (h->phi_part) { cudaFree(h->phi_part); h->phi_part = nullptr; }
   CK(dalloc(&h->phi_site, std::max<size_t>(1, atoms.size()) * sizeof(double)));
   CK(dalloc(&h->psi_site, std::max<size_t>(1, atoms.size()) * sizeof(double)));
@@ -469,6 +470,12 @@ int mahi_set_charges(mahi_t h, const double *qA_in, const double *qB_in, const i
         for (int j = i + 1; j < n; ++j) pl.push_back(make_int4(s, i, j, p++));
     }
     h->n_site_pairs = (int)pl.size();
+    std::vector<int> order(S);
+    for (int s2 = 0; s2 < S; ++s2) order[s2] = s2;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int b) { return ptr[a + 1] - ptr[a] > ptr[b + 1] - ptr[b]; });
+    CK(dalloc(&h->site_order, std::max<size_t>(1, (size_t)S) * sizeof(int)));
+    if (S > 0) CK(cudaMemcpy(h->site_order, order.data(), (size_t)S * sizeof(int), cudaMemcpyHostToDevice));
     CK(dalloc(&h->site_pair_list, std::max<size_t>(1, pl.size()) * sizeof(int4)));
     if (!pl.empty()) CK(cudaMemcpy(h->site_pair_list, pl.data(), pl.size() * sizeof(int4), cudaMemcpyHostToDevice));
   }

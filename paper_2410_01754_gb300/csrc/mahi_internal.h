@@ -138,6 +138,7 @@ struct mahi_ctx {
   double *site_pairs = nullptr;               // [S][kSiteSymPairs][4]: grad A, A of every site pair
   int4 *site_pair_list = nullptr;             // [n_site_pairs] {site, i, j, pair index} of sites up to kSiteSymMax atoms
   int n_site_pairs = 0;
+  int *site_order = nullptr;                  // [S] sites by descending atom count (site-potential blocks)
   int *site_slot = nullptr;                   // N: position in site_atoms, -1 for environment atoms
   // sites with 2^m forms (mahi_set_forms)
   bool multiform = false;

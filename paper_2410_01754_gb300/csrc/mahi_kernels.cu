@@ -2253,7 +2253,7 @@ __global__ void __launch_bounds__(kSiteThreads, 3) k_site_phi(
     const double *__restrict__ qd, const float *__restrict__ qdf, const double *__restrict__ mom,
     const double *__restrict__ Lh3, double *__restrict__ phi_part, int *__restrict__ status, float theta, int fcap,
     uint64_t wait_ns, const int *__restrict__ pre_lists, const int *__restrict__ pre_counts,
-    const double *__restrict__ pre_cen) {
+    const double *__restrict__ pre_cen, const int *__restrict__ site_order) {
   using V = typename V4<T>::type;
   // charge/dipole rows as staged: (hi, lo) float pairs in single precision,
   // FP64 otherwise; 32 bytes either way
@@ -2280,8 +2280,11 @@ __global__ void __launch_bounds__(kSiteThreads, 3) k_site_phi(
   __shared__ int64_t lvo[kMaxDepth + 2];  // level offsets (rows)
   __shared__ uint64_t sbar[2];            // copies of batch buffer 0 / 1 complete
   __shared__ int s_abort;
-  const int site = blockIdx.x / G, g = blockIdx.x % G, tid = threadIdx.x;
-  if (site >= S) return;
+  // blocks take the sites largest first (site_order), so the longest blocks
+  // start early and the last wave is short; results do not depend on it
+  if ((int)(blockIdx.x / G) >= S) return;
+  const int site = site_order ? site_order[blockIdx.x / G] : (int)(blockIdx.x / G);
+  const int g = blockIdx.x % G, tid = threadIdx.x;
   const int b0 = site_ptr[site], n = site_ptr[site + 1] - b0;
   if (n <= 0 || n > kMaxSiteAtoms) return;  // rejected when the site map is set
   // a compact site's lists may have been built by k_site_lists (pre)
@@ -3046,7 +3049,7 @@ static cudaError_t eval_t(mahi_ctx *h, const XT *x, const double *lam, double *e
                                          nbmax_c, h->L, h->d_level_off, h->leaf_start, h->leaf_of, h->inv_perm, (const V *)h->part,
                                          M, h->box_qd, h->box_qdf, mom, h->L_h3, h->phi_part, h->status_dev,
                                          h->site_theta, h->site_list_cap, h->wait_limit_ns, h->site_lists,
-                                         h->site_list_n, h->site_cen)));
+                                         h->site_list_n, h->site_cen, h->site_order)));
     // the other sites (spread ones; all of them without lists): the blocks of
     // compact sites leave at once
     MAHI_CK((launch_site_phi<T, false>(P, G, smp, h->side, h->S, G, h->site_ptr, h->site_atoms, h->d, P, ld, lds,
@@ -3054,7 +3057,7 @@ static cudaError_t eval_t(mahi_ctx *h, const XT *x, const double *lam, double *e
                                         h->box_qd, h->box_qdf, mom, h->L_h3, h->phi_part, h->status_dev,
                                         h->site_theta, h->site_list_cap, h->wait_limit_ns,
                                         site_pre ? h->site_lists : nullptr, site_pre ? h->site_list_n : nullptr,
-                                        site_pre ? h->site_cen : nullptr)));
+                                        site_pre ? h->site_cen : nullptr, h->site_order)));
     h->launches += site_pre ? 1 : 0;
     k_site_phi_sum<<<(h->n_site_atoms + 127) / 128, 128, 0, h->side>>>(h->n_site_atoms, G, coulomb_constant(),
                                                                         h->phi_part, h->phi_site);
