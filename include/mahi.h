@@ -228,7 +228,7 @@ int mahi_backward(mahi_t h, const double *grad_energy, const void *forces, const
  *   MAHI_OPT_P2P_THREADS      threads per target leaf of the near field: 64,
  *       128 or 256 (0 = 128, the default).
  *   MAHI_OPT_SITE_BLOCKS      blocks per site of the site-atom traversal, 1 to
- *       16 (0 = about 6 per SM over all sites, the default).
+ *       16 (0 = about 3 per SM over all sites, one wave: the default).
  *   MAHI_OPT_P2P_TARGETS      near-field scheme of the single-precision paths:
  *       4 or 8 = every unordered pair of neighbouring atoms evaluated once
  *       (Newton's third law over the forward half shell of 13 neighbour

@@ -68,7 +68,7 @@ int mahi_autotune(mahi_t h, const void *x, int32_t x_is_fp64, const double *lamb
   const bool sp = h->prec != MAHI_FP64;
   const int p2p_t[5] = {8, 4, -1, -1, -1}, p2p[5] = {128, 128, 64, 128, 256};
   const int np = sp ? 5 : 3, p0 = sp ? 0 : 2;
-  const int g0 = std::max(1, std::min(16, (2 * 3 * h->num_sms + h->S - 1) / std::max(1, h->S)));
+  const int g0 = std::max(1, std::min(16, (3 * h->num_sms + h->S - 1) / std::max(1, h->S)));
   std::vector<int> gs = {0};
   if (h->S > 0) {
     if (g0 / 2 >= 1) gs.push_back(g0 / 2);

@@ -3039,11 +3039,11 @@ static cudaError_t eval_t(mahi_ctx *h, const XT *x, const double *lam, double *e
     size_t smp = 0, smp_c = 0;
     const int nbmax = batch_rows(sizeof(int) * 4 * (size_t)h->site_list_cap + resident, smp);
     const int nbmax_c = batch_rows(resident, smp_c);
-    // blocks per site: about 2 x 3 per SM over all sites (three resident per
-    // SM), unless the autotuner picked a count
+    // blocks per site: about one wave over all sites (three resident per SM),
+    // unless the autotuner picked a count
     const int G = h->tune_site_blocks > 0
                       ? std::min(kSiteChunksMax, h->tune_site_blocks)
-                      : std::max(1, std::min(kSiteChunksMax, (2 * 3 * h->num_sms + h->S - 1) / std::max(1, h->S)));
+                      : std::max(1, std::min(kSiteChunksMax, (3 * h->num_sms + h->S - 1) / std::max(1, h->S)));
     if (site_pre)
       MAHI_CK((launch_site_phi<T, true>(P, G, smp_c, h->side, h->S, G, h->site_ptr, h->site_atoms, h->d, P, ld, lds,
                                          nbmax_c, h->L, h->d_level_off, h->leaf_start, h->leaf_of, h->inv_perm, (const V *)h->part,
