@@ -1855,28 +1855,30 @@ __device__ __forceinline__ T m2p_high(int P, const T *__restrict__ M, T ux, T uy
 // potential at the site to about 1e-8 relative, which single precision per term
 // does not reach over thousands of terms.  FP64 is slow on this part, so it is
 // kept to dense per-site work:
-//  * charge + dipole of a separated box: the FP64 value at c (one per box and
-//    site, packed across the lanes that stage the batch) plus, per atom, the
-//    change from c to the atom in working precision by a cancellation-free
+//  * charge + dipole of a separated box: the double-float value at c (one per
+//    box and site, added by the row's thread of atom pair 0) plus, per atom,
+//    the change from c to the atom in working precision by a cancellation-free
 //    difference formula, whose error is smaller by |x - c| / D;
 //  * orders l >= 2: working precision (their rounding is far below the bar);
 //  * direct leaves: double-float pair sums from error-free transforms (relative
 //    error near 2^-44 per pair);
 //  * per-thread sums in double-float, reduced in FP64 in a fixed order.
 // The batches of separated boxes and leaves are dealt round-robin to G blocks
-// per site; each block repeats the (cheap) classification and writes its own
-// partial sum, so results are bitwise reproducible.
+// per site; each block writes its own partial sum, so results are bitwise
+// reproducible.  A compact site's lists come from k_site_lists; otherwise each
+// block classifies the levels itself (the same lists in every block).
 //
 // Pipeline.  A block's batches form one stream over all levels; the multipole
-// rows and FP64 charge/dipole rows of the next batch are copied (cp.async)
-// into the second of two buffers while the current batch is evaluated, and a
-// level is classified when the stream first reaches it (its list goes to the
-// one of two list buffers that the level two above had used).  Without the
-// overlap, each batch waited a full memory round trip before any arithmetic.
+// rows and charge/dipole rows of the next batch are copied (bulk copies on an
+// mbarrier) into the second of two buffers while the current batch is
+// evaluated, and, in the in-kernel traversal, a level is classified when the
+// stream first reaches it (its list goes to the one of two list buffers that
+// the level two above had used).  Without the overlap, each batch waited a
+// full memory round trip before any arithmetic.
 constexpr int kSiteThreads = 128;
 constexpr int kSiteBatchMax = 64;
-// dynamic shared memory of one block (lists + two batch buffers): with the
-// static arrays three blocks fit on an SM
+// dynamic shared memory of one block (lists, if any, + two batch buffers):
+// with the static arrays three blocks fit on an SM
 constexpr size_t kSiteSmemBudget = 64 * 1024;
 
 __device__ __forceinline__ int pack_entry(int box, int img) { return (box << 9) | img; }
