@@ -195,7 +195,10 @@ int mahi_backward(mahi_t h, const double *grad_energy, const void *forces, const
  *   MAHI_OPT_SITE_LIST_CAP  boxes per level of one site's traversal (list
  *       capacity, 64 to 8192).  Default: 1536 at theta >= 0.4, else grown
  *       with the number of boxes a theta-ball holds.  A site that needs more
- *       fails with MAHI_ERR_SITE_OVERFLOW.
+ *       fails with MAHI_ERR_SITE_OVERFLOW.  The traversal lists of compact
+ *       sites are built once per evaluation in device buffers sized for this
+ *       capacity: raising it after mahi_set_charges (directly, or by a smaller
+ *       theta) reallocates them and synchronises the handle's streams.
  *   MAHI_OPT_WAIT_LIMIT_MS  limit of every bounded device wait of the
  *       tensor-core M2L and the site-atom potential (default 2000 ms, range 1
  *       to 60000).
