@@ -93,3 +93,22 @@ def test_lattice_function_matches_oracle_kernel(shell, p, tol, span):
         near = sum(1 / np.linalg.norm(ri + np.array(n) * L) for n in shells)
         ref.append(A - near - 2 * np.pi / (3 * L ** 3) * ri @ ri)
     assert np.abs(H - np.array(ref)).max() * L < tol
+
+
+def test_binding_option_names_match_the_header():
+    """Every MAHI_OPT_* value of include/mahi.h is in the binding's OPTIONS
+    under its lower-case name with the same number, and nothing else is."""
+    txt = open(os.path.join(ROOT, "include", "mahi.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    header = {m.group(1).lower(): int(m.group(2)) for m in re.finditer(r"\bMAHI_OPT_([A-Z0-9_]+)\s*=\s*(\d+)", txt)}
+    assert header, "no MAHI_OPT_* enum found"
+    assert pkg.OPTIONS == header
+
+
+def test_stage_names():
+    """Ten intervals of the evaluation's chain, then the two side-stream intervals."""
+    lib = pkg.lib()
+    names = [lib.mahi_stage_name(i).decode() for i in range(12)]
+    assert names == ["bin", "sort", "p2m", "m2m", "lattice", "m2l", "l2l", "near_pairs", "far_near_out", "site",
+                     "side_site_pairs", "side_site_potential"]
+    assert lib.mahi_stage_name(12).decode() == "?"
